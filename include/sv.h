@@ -1,0 +1,238 @@
+/*
+ * sv.h -- C ABI of the batched state-vector gradient library (libsv.so).
+ *
+ * The library simulates, as one batch on one GPU, the many slightly different
+ * circuits a gradient needs: parameter-shift copies of a parametrised circuit,
+ * taken over several reference states (multi-contracted VQE, paper Sec. 4.1)
+ * or over many training inputs (data-driven circuit learning, Sec. 4.2), each
+ * ending in the expectation value of a Pauli sum (Sec. 4.1, the paragraph
+ * casting Eq. 2 as generic terms P_i weighed by c_i).  The paper spreads these
+ * independent circuits over virtual QPUs (Sec. 3); here the same partition
+ * runs over thread blocks of one GPU.
+ *
+ * Conventions (the paper fixes none of them):
+ *   - qubit q is bit q of a basis index;
+ *   - RX/RY/RZ(a) = exp(-i a P / 2);
+ *   - CNOT(control -> target) flips the target bit when the control bit is 1;
+ *   - amplitudes are interleaved (re, im); SV_C64 = 2 x float, SV_C128 = 2 x double;
+ *   - a state batch is row-major [batch][2^n] amplitudes.
+ *
+ * Memory: pointers documented as "device" must be device memory of the
+ * current CUDA device (e.g. from torch); pointers documented as "host" are
+ * read during the call only and may be freed when it returns.  The library
+ * never frees caller memory.  It owns only its plan cache and its per-stream
+ * scratch buffers, released by sv_shutdown().
+ *
+ * Asynchrony: every call that takes a stream only enqueues work on it
+ * (except where noted) and returns; outputs are valid once the stream has
+ * reached that point.  Argument errors are reported synchronously; errors
+ * of the CUDA runtime as SV_ERR_CUDA.  First use of a new circuit
+ * structure builds and uploads its plan (synchronous, not capturable), so
+ * make that first call before any CUDA graph capture.
+ *
+ * Errors: functions return sv_status; sv_last_error() gives a thread-local
+ * text of the last failure.  Arguments are never silently clamped.
+ *
+ * Limits: n_qubits <= 30 (SV_C64) or <= 29 (SV_C128).
+ */
+#ifndef SV_H
+#define SV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *sv_stream_t;
+
+typedef enum {
+    SV_OK = 0,
+    SV_ERR_ARG = 1,         /* invalid argument: null pointer, size, gate, qubit index */
+    SV_ERR_OOM = 2,         /* device memory for state or scratch could not be allocated */
+    SV_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    SV_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    SV_ERR_UNSUPPORTED = 5  /* well-formed request outside this build's limits */
+} sv_status;
+
+typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
+
+/* Gate set.  ENC_* are the circuit-learning data encodings
+ * Ry(arcsin x) and Rz(arccos x^2) with x read from the instance's input row. */
+typedef enum {
+    SV_GATE_RX = 0,
+    SV_GATE_RY = 1,
+    SV_GATE_RZ = 2,
+    SV_GATE_CNOT = 3,
+    SV_GATE_X = 4,
+    SV_GATE_H = 5,
+    SV_GATE_CZ = 6,
+    SV_GATE_ENC_RY_ASIN = 7,
+    SV_GATE_ENC_RZ_ACOS_SQ = 8
+} sv_gate_op;
+
+typedef struct {
+    int32_t op;       /* sv_gate_op */
+    int32_t target;   /* qubit the gate acts on (CZ: second qubit) */
+    int32_t control;  /* CNOT / CZ control qubit; -1 otherwise */
+    int32_t param;    /* RX/RY/RZ: index into theta, or -1 to use `angle`;
+                         ENC_*: column of the instance's input row */
+    double angle;     /* fixed rotation angle when param < 0 */
+} sv_gate;
+
+/* A circuit: gates in time order (host array). */
+typedef struct {
+    int32_t n_qubits;
+    int32_t n_gates;
+    int32_t n_params;    /* length of a theta row */
+    int32_t input_dim;   /* length of an input row (0 if no ENC_* gates) */
+    const sv_gate *gates;
+} sv_circuit;
+
+/* Pauli sum H = sum_t coeff[t] P_t (host arrays).  P_t has X on the qubits set
+ * only in x_mask, Z on those set only in z_mask, Y on those set in both. */
+typedef struct {
+    int32_t n_qubits;
+    int32_t n_terms;
+    const uint64_t *x_mask;
+    const uint64_t *z_mask;
+    const double *coeff;
+} sv_pauli_sum;
+
+/* Planning knobs; all-zero (or a NULL pointer) selects the defaults. */
+typedef struct {
+    int32_t reg_bits;        /* amplitudes held per thread = 2^reg_bits (1..5); 0 = default */
+    int32_t threads_per_block; /* 0 = default */
+    int32_t no_fusion;       /* 1 = apply every gate on its own (no 1-qubit gate fusion) */
+    int32_t reserved;
+} sv_plan_opts;
+
+/* ---------------------------------------------------------------- states */
+
+typedef struct sv_state_s *sv_state;
+
+/* Create a batch of `batch` states of n_qubits.  If dev_buf is non-NULL it
+ * must hold dev_bytes >= batch * 2^n * sizeof(amplitude) bytes of device
+ * memory, 256-byte aligned; it stays owned by the caller.  Otherwise the
+ * library allocates (and sv_free releases) the buffer.  Contents are
+ * undefined until written. */
+sv_status sv_alloc(sv_state *out, int32_t n_qubits, int32_t batch, sv_dtype dtype,
+                   void *dev_buf, size_t dev_bytes, sv_stream_t stream);
+sv_status sv_free(sv_state state);
+/* Device pointer, sizes and dtype of a state batch (any out-pointer may be NULL). */
+sv_status sv_state_info(sv_state state, void **dev_ptr, int32_t *n_qubits, int32_t *batch,
+                        sv_dtype *dtype);
+
+/* --------------------------------------------------- forward simulation */
+
+/* One row of a batch: which circuit, parameters, shift, inputs and reference. */
+typedef struct {
+    int32_t circuit;      /* index into the circuits array */
+    int32_t theta_row;    /* row of theta used by the slot */
+    int32_t shift_param;  /* parameter to shift, or -1 */
+    int32_t input_row;    /* row of inputs used by ENC_* gates, or -1 */
+    int64_t ref;          /* initial basis state |ref> */
+    double shift;         /* added to theta[theta_row][shift_param] */
+} sv_slot;
+
+/* State-vector simulation (paper Sec. 4; Eq. 1's U(theta)|ref>) of n_slots
+ * circuits into rows 0..n_slots-1 of `state`: row s = U_{circuit(s)}(theta
+ * row + shift) |ref_s>.  circuits/slots: host.  theta: device
+ * [rows][theta_stride] doubles; inputs: device [rows][input_stride] doubles
+ * (NULL if no ENC_* gates).  Every circuit must have the state's n_qubits. */
+sv_status sv_apply_circuit_batch(sv_state state, const sv_circuit *circuits, int32_t n_circuits,
+                                 const sv_slot *slots, int32_t n_slots, const double *theta,
+                                 int32_t theta_stride, const double *inputs,
+                                 int32_t input_stride, const sv_plan_opts *opts,
+                                 sv_stream_t stream);
+
+/* Direct expectation values (Sec. 4.1: a simulator evaluates
+ * <psi|P_i|psi> exactly): out[s] = sum_t c_t <psi_s|P_t|psi_s> for the first
+ * n_rows rows of the batch.  out: device [n_rows] doubles.  Products are
+ * taken in the state's precision, sums in FP64. */
+sv_status sv_expect_pauli_sum(sv_state state, const sv_pauli_sum *h, int32_t n_rows,
+                              double *out, sv_stream_t stream);
+
+/* ------------------------------------------------------------ gradients */
+
+typedef enum {
+    SV_COST_LINEAR = 0,  /* L = sum_i w_i E_i  (state averaging, Sec. 4.1: w_i = 1/R) */
+    SV_COST_MSE = 1      /* L = (1/I) sum_i (E_i - y_i)^2  (circuit learning) */
+} sv_cost;
+
+/* A gradient problem: one circuit, one observable, n_instances instances.
+ * Instance i starts from |refs[i]> and reads input row i. */
+typedef struct {
+    sv_dtype dtype;
+    const sv_circuit *circuit;       /* host */
+    const sv_pauli_sum *observable;  /* host */
+    int32_t n_instances;
+    const int64_t *refs;             /* host [n_instances] */
+    const double *inputs;            /* device [n_instances][input_stride], or NULL */
+    int32_t input_stride;
+    sv_cost cost;
+    const double *weights;           /* device [n_instances] (SV_COST_LINEAR) */
+    const double *targets;           /* device [n_instances] (SV_COST_MSE) */
+    const sv_plan_opts *opts;        /* may be NULL */
+} sv_problem;
+
+/* Energies of every instance, E_i = <ref_i| U^dag H U |ref_i> (Eq. 1 per
+ * instance), and the cost, in one batched launch.  energy_out: device
+ * [n_instances]; loss_out: device [1] or NULL.  Uses library scratch of
+ * I doubles when loss_out is set. */
+sv_status sv_energies(const sv_problem *problem, const double *theta, double *energy_out,
+                      double *loss_out, sv_stream_t stream);
+
+/* Every circuit of the parameter-shift batch, one expectation value each
+ * (the per-circuit results the paper's execute() returns, Sec. 4.1): slot b
+ * < I is instance b unshifted; slot I + 2kI + i is instance i with
+ * theta_k + pi/2, slot I + (2k+1)I + i with theta_k - pi/2.  out: device
+ * [(2P + 1) I] doubles.  One kernel launch. */
+sv_status sv_param_shift_energies(const sv_problem *problem, const double *theta, double *out,
+                                  sv_stream_t stream);
+
+/* Parameter-shift gradient (Sec. 4.1: O(2 N_H N_theta) shifted circuits per
+ * update; here the whole <H> per circuit, so (2P + 1) circuits per instance,
+ * all in one batched launch): dE_i/dtheta_k = 1/2 [E_i(theta + pi/2 e_k)
+ * - E_i(theta - pi/2 e_k)], chained through the cost.  theta: device [P].
+ * energy_out: device [n_instances] or NULL; loss_out: device [1] or NULL;
+ * grad_out: device [P].  Uses library scratch of (2P+1) I doubles. */
+sv_status sv_grad_param_shift(const sv_problem *problem, const double *theta,
+                              double *energy_out, double *loss_out, double *grad_out,
+                              sv_stream_t stream);
+
+/* Adjoint (reverse-sweep) gradient, same result as sv_grad_param_shift:
+ * lambda = H psi, then for each gate in reverse order the derivative
+ * Im <lambda| G psi> of its generator G, psi <- U^dag psi, lambda <- U^dag lambda.
+ * weights: device [n_instances] dL/dE_i; NULL derives them from the
+ * problem's cost.  checkpoint_every: gates between stored forward states
+ * for states that do not fit on chip (0 = library choice).  Uses library
+ * scratch of I * P doubles. */
+sv_status sv_grad_adjoint(const sv_problem *problem, const double *theta, const double *weights,
+                          double *energy_out, double *loss_out, double *grad_out,
+                          int32_t checkpoint_every, sv_stream_t stream);
+
+/* The plain form, for comparison only: one circuit at a time, one kernel
+ * launch per gate and per Pauli term, complex128 state in device memory,
+ * parameter shift as above.  Host-synchronous per circuit batch. */
+sv_status sv_grad_param_shift_plain(const sv_problem *problem, const double *theta,
+                                    double *energy_out, double *loss_out, double *grad_out,
+                                    sv_stream_t stream);
+
+/* ----------------------------------------------------------------- misc */
+
+const char *sv_status_string(sv_status status);
+/* Thread-local description of the last failed call (empty if none). */
+const char *sv_last_error(void);
+/* Synchronize `stream` and report any pending CUDA error as a status. */
+sv_status sv_sync_status(sv_stream_t stream);
+/* Release plan caches and scratch on every device. */
+sv_status sv_shutdown(void);
+int32_t sv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SV_H */

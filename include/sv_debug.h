@@ -1,0 +1,30 @@
+/*
+ * sv_debug.h -- test hooks of libsv.so (not part of the computational API).
+ *
+ * sv_debug_plan compiles a circuit exactly as the GPU entry points do and
+ * copies the resulting stage program to host buffers, so that the planner's
+ * fusion, staging, index permutations and shared-memory address vectors can
+ * be checked on a machine without a GPU.  Call it once with NULL buffers to
+ * read the four counts (stages, ops, groups, members), then again with
+ * buffers of counts[i] * sizes[i] bytes (sizes from sv_debug_sizes).
+ */
+#ifndef SV_DEBUG_H
+#define SV_DEBUG_H
+
+#include "sv.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* sizes[0..5] = sizeof of Stage, Op, Group, Member, TermGroup, Term. */
+void sv_debug_sizes(int32_t *sizes);
+
+sv_status sv_debug_plan(const sv_circuit *circuit, int32_t reg_bits, int32_t fuse,
+                        int32_t swz_bits, int32_t *counts, void *stages, void *ops,
+                        void *groups, void *members);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,383 @@
+"""Batched state-vector gradients on one GB300 GPU: Python binding of libsv.so.
+
+A thin ctypes layer over the C ABI in ``include/sv.h``.  It only marshals
+arguments: gate lists become ``sv_gate`` arrays, Pauli rows become X/Z bit
+masks, torch tensors become device pointers and streams.  Every step of the
+computation (state preparation, gate application, expectation values,
+parameter-shift and adjoint gradients) runs in the library's CUDA kernels.
+PyTorch provides device memory and streams.
+
+There is no CPU fallback: importing this package fails if ``libsv.so`` has
+not been built (``python paper_2406_03466_gb300/build.py``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsv.so")
+
+SV_OK, SV_ERR_ARG, SV_ERR_OOM, SV_ERR_CUDA, SV_ERR_TIMEOUT, SV_ERR_UNSUPPORTED = range(6)
+SV_C64, SV_C128 = 0, 1
+SV_COST_LINEAR, SV_COST_MSE = 0, 1
+GATE_CODES = {"RX": 0, "RY": 1, "RZ": 2, "CNOT": 3, "X": 4, "H": 5, "CZ": 6,
+              "ENC_RY_ASIN": 7, "ENC_RZ_ACOS_SQ": 8}
+
+
+class SvError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        detail = _lib.sv_last_error().decode() if _lib is not None else ""
+        msg = _lib.sv_status_string(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{where}: {msg} ({detail})")
+
+
+# ------------------------------------------------------------------ ABI types
+
+class sv_gate(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("target", ctypes.c_int32), ("control", ctypes.c_int32),
+                ("param", ctypes.c_int32), ("angle", ctypes.c_double)]
+
+
+class sv_circuit(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("n_gates", ctypes.c_int32),
+                ("n_params", ctypes.c_int32), ("input_dim", ctypes.c_int32),
+                ("gates", ctypes.POINTER(sv_gate))]
+
+
+class sv_pauli_sum(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("n_terms", ctypes.c_int32),
+                ("x_mask", ctypes.POINTER(ctypes.c_uint64)),
+                ("z_mask", ctypes.POINTER(ctypes.c_uint64)),
+                ("coeff", ctypes.POINTER(ctypes.c_double))]
+
+
+class sv_plan_opts(ctypes.Structure):
+    _fields_ = [("reg_bits", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
+                ("no_fusion", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class sv_slot(ctypes.Structure):
+    _fields_ = [("circuit", ctypes.c_int32), ("theta_row", ctypes.c_int32),
+                ("shift_param", ctypes.c_int32), ("input_row", ctypes.c_int32),
+                ("ref", ctypes.c_int64), ("shift", ctypes.c_double)]
+
+
+class sv_problem(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("circuit", ctypes.POINTER(sv_circuit)),
+                ("observable", ctypes.POINTER(sv_pauli_sum)), ("n_instances", ctypes.c_int32),
+                ("refs", ctypes.POINTER(ctypes.c_int64)), ("inputs", ctypes.c_void_p),
+                ("input_stride", ctypes.c_int32), ("cost", ctypes.c_int32),
+                ("weights", ctypes.c_void_p), ("targets", ctypes.c_void_p),
+                ("opts", ctypes.POINTER(sv_plan_opts))]
+
+
+EXPORTED = ("sv_alloc", "sv_free", "sv_state_info", "sv_apply_circuit_batch",
+            "sv_expect_pauli_sum", "sv_energies", "sv_param_shift_energies", "sv_grad_param_shift", "sv_grad_adjoint",
+            "sv_grad_param_shift_plain", "sv_status_string", "sv_last_error",
+            "sv_sync_status", "sv_shutdown", "sv_version")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run `python paper_2406_03466_gb300/build.py` "
+                          "(requires nvcc). There is no CPU fallback.")
+    lib = ctypes.CDLL(LIB_PATH)
+    V, I32, P = ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER
+    lib.sv_alloc.argtypes = [P(V), I32, I32, I32, V, ctypes.c_size_t, V]
+    lib.sv_free.argtypes = [V]
+    lib.sv_state_info.argtypes = [V, P(V), P(I32), P(I32), P(I32)]
+    lib.sv_apply_circuit_batch.argtypes = [V, P(sv_circuit), I32, P(sv_slot), I32, V, I32, V, I32,
+                                           P(sv_plan_opts), V]
+    lib.sv_expect_pauli_sum.argtypes = [V, P(sv_pauli_sum), I32, V, V]
+    lib.sv_energies.argtypes = [P(sv_problem), V, V, V, V]
+    lib.sv_param_shift_energies.argtypes = [P(sv_problem), V, V, V]
+    lib.sv_grad_param_shift.argtypes = [P(sv_problem), V, V, V, V, V]
+    lib.sv_grad_adjoint.argtypes = [P(sv_problem), V, V, V, V, V, I32, V]
+    lib.sv_grad_param_shift_plain.argtypes = [P(sv_problem), V, V, V, V, V]
+    lib.sv_status_string.argtypes = [I32]
+    lib.sv_status_string.restype = ctypes.c_char_p
+    lib.sv_last_error.restype = ctypes.c_char_p
+    lib.sv_sync_status.argtypes = [V]
+    lib.sv_version.restype = I32
+    for name in EXPORTED:
+        if name not in ("sv_status_string", "sv_last_error", "sv_version"):
+            getattr(lib, name).restype = I32
+    return lib
+
+
+_lib = None
+_lib = _load()
+
+
+def _check(status, where):
+    if status != SV_OK:
+        raise SvError(status, where)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dtype_code(dtype) -> int:
+    if dtype in (SV_C64, "c64", "complex64"):
+        return SV_C64
+    if dtype in (SV_C128, "c128", "complex128"):
+        return SV_C128
+    raise ValueError(f"dtype {dtype!r}")
+
+
+# ---------------------------------------------------------------- marshalling
+
+class Circuit:
+    """A gate list marshalled into an ``sv_circuit``.
+
+    ``gates`` holds objects with ``op`` (name or code), ``target``, ``control``,
+    ``param`` and ``angle`` attributes, or 5-tuples in that order.
+    """
+
+    def __init__(self, n_qubits: int, gates: Sequence, n_params: int, input_dim: int = 0):
+        arr = (sv_gate * max(1, len(gates)))()
+        for i, g in enumerate(gates):
+            if isinstance(g, tuple):
+                op, target, control, param, angle = g
+            else:
+                op, target, control, param, angle = g.op, g.target, g.control, g.param, g.angle
+            arr[i] = sv_gate(GATE_CODES[op] if isinstance(op, str) else int(op), int(target),
+                             int(control), int(param), float(angle))
+        self._arr = arr
+        self.n_qubits, self.n_params, self.input_dim = n_qubits, n_params, input_dim
+        self.struct = sv_circuit(n_qubits, len(gates), n_params, input_dim,
+                                 ctypes.cast(arr, ctypes.POINTER(sv_gate)))
+
+
+class PauliSum:
+    """Pauli rows (0=I, 1=X, 2=Y, 3=Z per qubit) and coefficients as X/Z masks."""
+
+    def __init__(self, n_qubits: int, letters, coeffs):
+        letters = np.asarray(letters, dtype=np.int64).reshape(-1, n_qubits)
+        bits = np.uint64(1) << np.arange(n_qubits, dtype=np.uint64)
+        xm = (((letters == 1) | (letters == 2)) * bits).sum(axis=1).astype(np.uint64)
+        zm = (((letters == 3) | (letters == 2)) * bits).sum(axis=1).astype(np.uint64)
+        self._x = np.ascontiguousarray(xm, dtype=np.uint64)
+        self._z = np.ascontiguousarray(zm, dtype=np.uint64)
+        self._c = np.ascontiguousarray(coeffs, dtype=np.float64)
+        U64 = ctypes.POINTER(ctypes.c_uint64)
+        self.n_qubits = n_qubits
+        self.struct = sv_pauli_sum(n_qubits, len(self._c),
+                                   self._x.ctypes.data_as(U64), self._z.ctypes.data_as(U64),
+                                   self._c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+
+
+def plan_opts(reg_bits=0, threads_per_block=0, no_fusion=False) -> sv_plan_opts:
+    return sv_plan_opts(int(reg_bits), int(threads_per_block), int(bool(no_fusion)), 0)
+
+
+class Problem:
+    """An ``sv_problem``: circuit, observable, instances and cost.
+
+    ``inputs``/``weights``/``targets`` are float64 CUDA tensors (or None).
+    """
+
+    def __init__(self, circuit: Circuit, observable: PauliSum, refs, dtype="c64",
+                 inputs=None, cost="linear", weights=None, targets=None,
+                 opts: Optional[sv_plan_opts] = None):
+        self.circuit, self.observable, self.opts = circuit, observable, opts
+        self._refs = np.ascontiguousarray(refs, dtype=np.int64)
+        self.inputs, self.weights, self.targets = inputs, weights, targets
+        self.n_instances = len(self._refs)
+        self.dtype = _dtype_code(dtype)
+        self.cost = SV_COST_MSE if cost == "mse" else SV_COST_LINEAR
+        self.struct = sv_problem(
+            self.dtype, ctypes.pointer(circuit.struct), ctypes.pointer(observable.struct),
+            self.n_instances, self._refs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+            _ptr(inputs), 0 if inputs is None else int(inputs.shape[1]), self.cost,
+            _ptr(weights), _ptr(targets), None if opts is None else ctypes.pointer(opts))
+
+    @property
+    def n_params(self) -> int:
+        return self.circuit.n_params
+
+    @classmethod
+    def from_spec(cls, spec, dtype="c64", device="cuda", opts=None):
+        """Marshal any object with the workload attributes (n_qubits, gates,
+        n_params, pauli_letters, pauli_coeffs, refs, inputs, weights, targets, cost)."""
+        import torch
+        d = 0 if spec.inputs is None else int(np.asarray(spec.inputs).shape[1])
+        circ = Circuit(spec.n_qubits, spec.gates, spec.n_params, d)
+        obs = PauliSum(spec.n_qubits, spec.pauli_letters, spec.pauli_coeffs)
+
+        def dev(a):
+            return None if a is None else torch.as_tensor(np.asarray(a, dtype=np.float64),
+                                                          device=device).contiguous()
+        return cls(circ, obs, spec.refs, dtype, inputs=dev(spec.inputs), cost=spec.cost,
+                   weights=dev(spec.weights), targets=dev(spec.targets), opts=opts)
+
+
+# ------------------------------------------------------------------- states
+
+class StateBatch:
+    """``sv_state`` over a torch-owned buffer of shape (batch, 2^n), complex."""
+
+    def __init__(self, n_qubits: int, batch: int, dtype="c64", device="cuda", stream=None):
+        import torch
+        code = _dtype_code(dtype)
+        tdt = torch.complex64 if code == SV_C64 else torch.complex128
+        self.tensor = torch.empty((batch, 1 << n_qubits), dtype=tdt, device=device)
+        h = ctypes.c_void_p()
+        nbytes = self.tensor.numel() * self.tensor.element_size()
+        _check(_lib.sv_alloc(ctypes.byref(h), n_qubits, batch, code, _ptr(self.tensor), nbytes,
+                             _stream(stream)), "sv_alloc")
+        self.handle = h
+        self.n_qubits, self.batch, self.dtype = n_qubits, batch, code
+
+    def free(self):
+        if self.handle:
+            _lib.sv_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sv_alloc(n_qubits: int, batch: int, dtype="c64", device="cuda", stream=None) -> StateBatch:
+    return StateBatch(n_qubits, batch, dtype, device, stream)
+
+
+def sv_free(state: StateBatch) -> None:
+    state.free()
+
+
+def make_slots(rows) -> ctypes.Array:
+    """rows: iterables (circuit, theta_row, shift_param, input_row, ref, shift)."""
+    rows = list(rows)
+    arr = (sv_slot * max(1, len(rows)))()
+    for i, (c, tr, sp, ir, ref, sh) in enumerate(rows):
+        arr[i] = sv_slot(int(c), int(tr), int(sp), int(ir), int(ref), float(sh))
+    return arr, len(rows)
+
+
+def sv_apply_circuit_batch(state: StateBatch, circuits: Sequence[Circuit], slots, theta,
+                           inputs=None, opts: Optional[sv_plan_opts] = None, stream=None):
+    """slots: the (array, count) pair of ``make_slots``; theta: float64 CUDA
+    tensor (rows, P); inputs: float64 CUDA tensor (rows, D) or None."""
+    arr, count = slots
+    circ_arr = (sv_circuit * len(circuits))(*[c.struct for c in circuits])
+    th_stride = int(theta.shape[-1]) if theta is not None and theta.dim() > 1 else (
+        0 if theta is None else int(theta.numel()))
+    in_stride = 0 if inputs is None else int(inputs.shape[-1])
+    _check(_lib.sv_apply_circuit_batch(state.handle, circ_arr, len(circuits), arr, count,
+                                       _ptr(theta), th_stride, _ptr(inputs), in_stride,
+                                       None if opts is None else ctypes.byref(opts),
+                                       _stream(stream)), "sv_apply_circuit_batch")
+
+
+def sv_expect_pauli_sum(state: StateBatch, h: PauliSum, n_rows: Optional[int] = None, out=None,
+                        stream=None):
+    import torch
+    rows = state.batch if n_rows is None else n_rows
+    if out is None:
+        out = torch.empty(rows, dtype=torch.float64, device=state.tensor.device)
+    _check(_lib.sv_expect_pauli_sum(state.handle, ctypes.byref(h.struct), rows, _ptr(out),
+                                    _stream(stream)), "sv_expect_pauli_sum")
+    return out
+
+
+def _outputs(problem: Problem, device, energy_out, loss_out, grad_out):
+    import torch
+    f = dict(dtype=torch.float64, device=device)
+    if energy_out is None:
+        energy_out = torch.empty(problem.n_instances, **f)
+    if loss_out is None:
+        loss_out = torch.empty(1, **f)
+    if grad_out is None:
+        grad_out = torch.empty(max(1, problem.n_params), **f)
+    return energy_out, loss_out, grad_out
+
+
+def sv_energies(problem: Problem, theta, energy_out=None, loss_out=None, stream=None):
+    """(loss[1], energies[I]) of every instance in one batched launch."""
+    e, l, _ = _outputs(problem, theta.device, energy_out, loss_out, None)
+    _check(_lib.sv_energies(ctypes.byref(problem.struct), _ptr(theta), _ptr(e), _ptr(l),
+                            _stream(stream)), "sv_energies")
+    return l, e
+
+
+def sv_param_shift_energies(problem: Problem, theta, out=None, stream=None):
+    """Energies of the whole parameter-shift batch, [(2P + 1) I], one launch."""
+    import torch
+    if out is None:
+        out = torch.empty((2 * problem.n_params + 1) * problem.n_instances, dtype=torch.float64,
+                          device=theta.device)
+    _check(_lib.sv_param_shift_energies(ctypes.byref(problem.struct), _ptr(theta), _ptr(out),
+                                        _stream(stream)), "sv_param_shift_energies")
+    return out
+
+
+def sv_grad_param_shift(problem: Problem, theta, energy_out=None, loss_out=None, grad_out=None,
+                        stream=None):
+    """(loss[1], energies[I], grad[P]) by the batched parameter-shift rule."""
+    e, l, g = _outputs(problem, theta.device, energy_out, loss_out, grad_out)
+    _check(_lib.sv_grad_param_shift(ctypes.byref(problem.struct), _ptr(theta), _ptr(e), _ptr(l),
+                                    _ptr(g), _stream(stream)), "sv_grad_param_shift")
+    return l, e, g
+
+
+def sv_grad_adjoint(problem: Problem, theta, weights=None, energy_out=None, loss_out=None,
+                    grad_out=None, checkpoint_every: int = 0, stream=None):
+    """(loss[1], energies[I], grad[P]) by the adjoint reverse sweep.  ``weights``
+    (float64 CUDA tensor [I]) replaces dL/dE_i of the problem's cost."""
+    e, l, g = _outputs(problem, theta.device, energy_out, loss_out, grad_out)
+    _check(_lib.sv_grad_adjoint(ctypes.byref(problem.struct), _ptr(theta), _ptr(weights),
+                                _ptr(e), _ptr(l), _ptr(g), int(checkpoint_every),
+                                _stream(stream)), "sv_grad_adjoint")
+    return l, e, g
+
+
+def sv_grad_param_shift_plain(problem: Problem, theta, energy_out=None, loss_out=None,
+                              grad_out=None, stream=None):
+    """The plain one-circuit-at-a-time complex128 form (comparison only)."""
+    e, l, g = _outputs(problem, theta.device, energy_out, loss_out, grad_out)
+    _check(_lib.sv_grad_param_shift_plain(ctypes.byref(problem.struct), _ptr(theta), _ptr(e),
+                                          _ptr(l), _ptr(g), _stream(stream)),
+           "sv_grad_param_shift_plain")
+    return l, e, g
+
+
+def sv_status_string(status: int) -> str:
+    return _lib.sv_status_string(int(status)).decode()
+
+
+def sv_last_error() -> str:
+    return _lib.sv_last_error().decode()
+
+
+def sv_sync_status(stream=None) -> None:
+    _check(_lib.sv_sync_status(_stream(stream)), "sv_sync_status")
+
+
+def sv_shutdown() -> None:
+    _check(_lib.sv_shutdown(), "sv_shutdown")
+
+
+def sv_version() -> int:
+    return int(_lib.sv_version())
+
+
+def library():
+    """The loaded ctypes library (for symbol checks)."""
+    return _lib

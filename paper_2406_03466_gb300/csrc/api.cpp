@@ -1,0 +1,787 @@
+// C ABI of libsv: argument checking, plan and observable caches, per-stream
+// scratch, and the launch sequences of every entry point in sv.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "kernels.h"
+#include "planner.h"
+#include "sv.h"
+
+using namespace svk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sv_status fail(sv_status s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+
+sv_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(e == cudaErrorMemoryAllocation ? SV_ERR_OOM : SV_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SV_CUDA(call)                                  \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+struct DeviceBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    DeviceBuf() = default;
+    DeviceBuf(const DeviceBuf &) = delete;
+    DeviceBuf &operator=(const DeviceBuf &) = delete;
+    ~DeviceBuf() {
+        if (ptr) cudaFree(ptr);
+    }
+};
+
+// Packs host arrays into one device allocation at 256-byte aligned offsets.
+struct Packer {
+    std::vector<unsigned char> bytes;
+    size_t add(const void *src, size_t n) {
+        size_t off = (bytes.size() + 255) & ~size_t(255);
+        bytes.resize(off + n);
+        if (n) std::memcpy(bytes.data() + off, src, n);
+        return off;
+    }
+};
+
+struct PlanEntry {
+    std::vector<sv_gate> gates;  // exact key check against hash collisions
+    int n = 0, n_params = 0, input_dim = 0;
+    HostProgram host;
+    DeviceBuf buf;
+    Program dev{};
+};
+
+struct ObsEntry {
+    std::vector<uint64_t> xm, zm;
+    std::vector<double> c;
+    HostObservable host;
+    DeviceBuf buf;
+    Observable dev{};
+};
+
+struct ArrayEntry {
+    std::vector<unsigned char> bytes;
+    DeviceBuf buf;
+};
+
+struct DeviceCtx {
+    std::mutex mu;
+    std::unordered_map<uint64_t, std::unique_ptr<PlanEntry>> plans;
+    std::unordered_map<uint64_t, std::unique_ptr<ObsEntry>> obs;
+    std::unordered_map<uint64_t, std::unique_ptr<ArrayEntry>> arrays;
+    std::unordered_map<cudaStream_t, std::unique_ptr<DeviceBuf>> scratch;
+};
+
+std::mutex g_mu;
+std::unordered_map<int, std::unique_ptr<DeviceCtx>> g_ctx;
+
+DeviceCtx *context(int *dev_out = nullptr) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    if (dev_out) *dev_out = dev;
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto &p = g_ctx[dev];
+    if (!p) p.reset(new DeviceCtx());
+    return p.get();
+}
+
+uint64_t mix64(uint64_t h, uint64_t v) {
+    h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    return h * 0xff51afd7ed558ccdull;
+}
+
+uint64_t hash_bytes(const void *p, size_t n) {
+    const unsigned char *b = (const unsigned char *)p;
+    uint64_t h = 0xcbf29ce484222325ull ^ n;
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 0x100000001b3ull;
+    return h;
+}
+
+int swz_bits(sv_dtype d) { return d == SV_C128 ? 3 : 4; }
+
+// Compiled program of a circuit for (reg_bits, fusion, dtype), cached.
+sv_status get_plan(DeviceCtx *ctx, const sv_circuit &c, int R, bool fuse, sv_dtype dt,
+                   PlanEntry **out) {
+    uint64_t key = hash_circuit(c);
+    key = mix64(key, (uint64_t)R);
+    key = mix64(key, fuse ? 1 : 0);
+    key = mix64(key, (uint64_t)swz_bits(dt));
+    auto it = ctx->plans.find(key);
+    if (it != ctx->plans.end()) {
+        PlanEntry *e = it->second.get();
+        if (e->n == c.n_qubits && e->n_params == c.n_params && e->input_dim == c.input_dim &&
+            e->gates.size() == (size_t)c.n_gates &&
+            (c.n_gates == 0 || std::memcmp(e->gates.data(), c.gates, sizeof(sv_gate) * c.n_gates) == 0)) {
+            *out = e;
+            return SV_OK;
+        }
+    }
+    std::unique_ptr<PlanEntry> e(new PlanEntry());
+    std::string err = plan_circuit(c, R, fuse, swz_bits(dt), &e->host);
+    if (!err.empty()) return fail(SV_ERR_ARG, "circuit: " + err);
+    e->gates.assign(c.gates, c.gates + c.n_gates);
+    e->n = c.n_qubits;
+    e->n_params = c.n_params;
+    e->input_dim = c.input_dim;
+    const HostProgram &h = e->host;
+    Packer pk;
+    size_t o_st = pk.add(h.stages.data(), h.stages.size() * sizeof(Stage));
+    size_t o_op = pk.add(h.ops.data(), h.ops.size() * sizeof(Op));
+    size_t o_gr = pk.add(h.groups.data(), h.groups.size() * sizeof(Group));
+    size_t o_me = pk.add(h.members.data(), h.members.size() * sizeof(Member));
+    e->buf.bytes = pk.bytes.size() ? pk.bytes.size() : 256;
+    SV_CUDA(cudaMalloc(&e->buf.ptr, e->buf.bytes));
+    if (!pk.bytes.empty())
+        SV_CUDA(cudaMemcpy(e->buf.ptr, pk.bytes.data(), pk.bytes.size(), cudaMemcpyHostToDevice));
+    unsigned char *base = (unsigned char *)e->buf.ptr;
+    Program &p = e->dev;
+    p.n = h.n;
+    p.R = h.R;
+    p.n_stages = (int)h.stages.size();
+    p.n_groups = (int)h.groups.size();
+    p.n_params = h.n_params;
+    p.input_dim = h.input_dim;
+    p.swz_bits = h.swz_bits;
+    p.stages = (const Stage *)(base + o_st);
+    p.ops = (const Op *)(base + o_op);
+    p.groups = (const Group *)(base + o_gr);
+    p.members = (const Member *)(base + o_me);
+    *out = e.get();
+    ctx->plans[key] = std::move(e);
+    return SV_OK;
+}
+
+sv_status get_obs(DeviceCtx *ctx, const sv_pauli_sum &h, int n, sv_dtype dt, ObsEntry **out) {
+    if (h.n_terms < 0 || (h.n_terms > 0 && (!h.x_mask || !h.z_mask || !h.coeff)))
+        return fail(SV_ERR_ARG, "observable: missing arrays");
+    uint64_t key = mix64(hash_observable(h), (uint64_t)swz_bits(dt));
+    key = mix64(key, (uint64_t)n);
+    auto it = ctx->obs.find(key);
+    if (it != ctx->obs.end()) {
+        ObsEntry *e = it->second.get();
+        if (e->xm.size() == (size_t)h.n_terms &&
+            std::memcmp(e->xm.data(), h.x_mask, 8 * h.n_terms) == 0 &&
+            std::memcmp(e->zm.data(), h.z_mask, 8 * h.n_terms) == 0 &&
+            std::memcmp(e->c.data(), h.coeff, 8 * h.n_terms) == 0 && e->host.n == n) {
+            *out = e;
+            return SV_OK;
+        }
+    }
+    std::unique_ptr<ObsEntry> e(new ObsEntry());
+    std::string err = plan_observable(h, n, swz_bits(dt), &e->host);
+    if (!err.empty()) return fail(SV_ERR_ARG, "observable: " + err);
+    e->xm.assign(h.x_mask, h.x_mask + h.n_terms);
+    e->zm.assign(h.z_mask, h.z_mask + h.n_terms);
+    e->c.assign(h.coeff, h.coeff + h.n_terms);
+    Packer pk;
+    size_t o_g = pk.add(e->host.tgroups.data(), e->host.tgroups.size() * sizeof(TermGroup));
+    size_t o_t = pk.add(e->host.terms.data(), e->host.terms.size() * sizeof(Term));
+    e->buf.bytes = pk.bytes.size() ? pk.bytes.size() : 256;
+    SV_CUDA(cudaMalloc(&e->buf.ptr, e->buf.bytes));
+    if (!pk.bytes.empty())
+        SV_CUDA(cudaMemcpy(e->buf.ptr, pk.bytes.data(), pk.bytes.size(), cudaMemcpyHostToDevice));
+    unsigned char *base = (unsigned char *)e->buf.ptr;
+    e->dev.n_tgroups = (int)e->host.tgroups.size();
+    e->dev.n_terms = (int)e->host.terms.size();
+    e->dev.tgroups = (const TermGroup *)(base + o_g);
+    e->dev.terms = (const Term *)(base + o_t);
+    *out = e.get();
+    ctx->obs[key] = std::move(e);
+    return SV_OK;
+}
+
+// Small host arrays (references, slot lists) uploaded once and cached by content.
+sv_status get_array(DeviceCtx *ctx, const void *host, size_t bytes, const void **dev) {
+    const uint64_t key = hash_bytes(host, bytes);
+    auto it = ctx->arrays.find(key);
+    if (it != ctx->arrays.end() && it->second->bytes.size() == bytes &&
+        std::memcmp(it->second->bytes.data(), host, bytes) == 0) {
+        *dev = it->second->buf.ptr;
+        return SV_OK;
+    }
+    std::unique_ptr<ArrayEntry> e(new ArrayEntry());
+    e->bytes.assign((const unsigned char *)host, (const unsigned char *)host + bytes);
+    e->buf.bytes = bytes ? bytes : 16;
+    SV_CUDA(cudaMalloc(&e->buf.ptr, e->buf.bytes));
+    if (bytes) SV_CUDA(cudaMemcpy(e->buf.ptr, host, bytes, cudaMemcpyHostToDevice));
+    *dev = e->buf.ptr;
+    ctx->arrays[key] = std::move(e);
+    return SV_OK;
+}
+
+// Library scratch for one stream, grown on demand (growth synchronizes the stream).
+sv_status get_scratch(DeviceCtx *ctx, cudaStream_t st, size_t bytes, void **out) {
+    auto &s = ctx->scratch[st];
+    if (!s) s.reset(new DeviceBuf());
+    if (s->bytes < bytes) {
+        if (s->ptr) {
+            SV_CUDA(cudaStreamSynchronize(st));
+            cudaFree(s->ptr);
+            s->ptr = nullptr;
+            s->bytes = 0;
+        }
+        size_t want = bytes < 4096 ? 4096 : bytes;
+        SV_CUDA(cudaMalloc(&s->ptr, want));
+        s->bytes = want;
+    }
+    *out = s->ptr;
+    return SV_OK;
+}
+
+sv_status check_circuit(const sv_circuit *c, int n_limit) {
+    if (!c) return fail(SV_ERR_ARG, "circuit is NULL");
+    if (c->n_qubits < 1 || c->n_qubits > n_limit)
+        return fail(SV_ERR_ARG, "circuit n_qubits out of range");
+    if (c->n_gates < 0 || (c->n_gates > 0 && !c->gates))
+        return fail(SV_ERR_ARG, "circuit gates missing");
+    if (c->n_params < 0 || c->input_dim < 0) return fail(SV_ERR_ARG, "negative sizes");
+    return SV_OK;
+}
+
+int default_regbits(const sv_plan_opts *o) { return (o && o->reg_bits > 0) ? o->reg_bits : 0; }
+int default_tpb(const sv_plan_opts *o) { return (o && o->threads_per_block > 0) ? o->threads_per_block : 0; }
+bool use_fusion(const sv_plan_opts *o) { return !(o && o->no_fusion); }
+
+// Planner register bits for a kernel kind: the launch shape decides R first.
+sv_status shape_for(int kind, const sv_circuit &c, int n_groups_hint, sv_dtype dt, int n_slots,
+                    const sv_plan_opts *opts, OnchipShape *sh) {
+    const char *err = onchip_shape(kind, c.n_qubits, n_groups_hint, c.n_params, dt == SV_C128,
+                                   n_slots, default_regbits(opts), default_tpb(opts), sh);
+    if (err) return fail(SV_ERR_UNSUPPORTED, err);
+    return SV_OK;
+}
+
+// Plan + final launch shape (the shape needs the group count of the plan).
+sv_status plan_and_shape(DeviceCtx *ctx, int kind, const sv_circuit &c, sv_dtype dt, int n_slots,
+                         const sv_plan_opts *opts, PlanEntry **plan, OnchipShape *sh) {
+    OnchipShape pre{};
+    sv_status s = shape_for(kind, c, 0, dt, n_slots, opts, &pre);
+    if (s != SV_OK) return s;
+    s = get_plan(ctx, c, pre.R, use_fusion(opts), dt, plan);
+    if (s != SV_OK) return s;
+    return shape_for(kind, c, (*plan)->dev.n_groups, dt, n_slots, opts, sh);
+}
+
+sv_status check_problem(const sv_problem *p, bool need_cost_arrays) {
+    if (!p) return fail(SV_ERR_ARG, "problem is NULL");
+    if (p->dtype != SV_C64 && p->dtype != SV_C128) return fail(SV_ERR_ARG, "bad dtype");
+    sv_status s = check_circuit(p->circuit, p->dtype == SV_C128 ? 29 : 30);
+    if (s != SV_OK) return s;
+    if (!p->observable) return fail(SV_ERR_ARG, "observable is NULL");
+    if (p->observable->n_qubits != p->circuit->n_qubits)
+        return fail(SV_ERR_ARG, "observable and circuit qubit counts differ");
+    if (p->n_instances < 1) return fail(SV_ERR_ARG, "n_instances must be >= 1");
+    if (!p->refs) return fail(SV_ERR_ARG, "refs is NULL");
+    const int64_t dim = int64_t(1) << p->circuit->n_qubits;
+    for (int i = 0; i < p->n_instances; ++i)
+        if (p->refs[i] < 0 || p->refs[i] >= dim) return fail(SV_ERR_ARG, "reference out of range");
+    if (p->circuit->input_dim > 0 && (!p->inputs || p->input_stride < p->circuit->input_dim))
+        return fail(SV_ERR_ARG, "circuit reads inputs but inputs/input_stride are missing");
+    if (need_cost_arrays) {
+        if (p->cost == SV_COST_LINEAR && !p->weights) return fail(SV_ERR_ARG, "weights are NULL");
+        if (p->cost == SV_COST_MSE && !p->targets) return fail(SV_ERR_ARG, "targets are NULL");
+    }
+    if (p->cost != SV_COST_LINEAR && p->cost != SV_COST_MSE) return fail(SV_ERR_ARG, "bad cost");
+    return SV_OK;
+}
+
+CostSource cost_of(const sv_problem *p, const double *ext) {
+    CostSource c{};
+    c.cost = p->cost;
+    c.n_instances = p->n_instances;
+    c.ext_weights = ext;
+    c.weights = p->weights;
+    c.targets = p->targets;
+    return c;
+}
+
+}  // namespace
+
+struct sv_state_s {
+    int n = 0, batch = 0;
+    sv_dtype dtype = SV_C64;
+    void *ptr = nullptr;
+    bool owned = false;
+    int device = 0;
+};
+
+extern "C" {
+
+const char *sv_status_string(sv_status s) {
+    switch (s) {
+    case SV_OK: return "ok";
+    case SV_ERR_ARG: return "invalid argument";
+    case SV_ERR_OOM: return "out of device memory";
+    case SV_ERR_CUDA: return "CUDA error";
+    case SV_ERR_TIMEOUT: return "device-side wait timed out";
+    case SV_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *sv_last_error(void) { return g_last_error.c_str(); }
+
+int32_t sv_version(void) { return 1; }
+
+sv_status sv_alloc(sv_state *out, int32_t n, int32_t batch, sv_dtype dtype, void *dev_buf,
+                   size_t dev_bytes, sv_stream_t) {
+    if (!out) return fail(SV_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (dtype != SV_C64 && dtype != SV_C128) return fail(SV_ERR_ARG, "bad dtype");
+    const int lim = dtype == SV_C128 ? 29 : 30;
+    if (n < 1 || n > lim) return fail(SV_ERR_ARG, "n_qubits out of range");
+    if (batch < 1) return fail(SV_ERR_ARG, "batch must be >= 1");
+    const size_t bytes = (size_t)batch * (size_t(1) << n) * (dtype == SV_C128 ? 16 : 8);
+    std::unique_ptr<sv_state_s> s(new sv_state_s());
+    s->n = n;
+    s->batch = batch;
+    s->dtype = dtype;
+    cudaGetDevice(&s->device);
+    if (dev_buf) {
+        if (dev_bytes < bytes) return fail(SV_ERR_ARG, "dev_bytes smaller than the batch");
+        if (((uintptr_t)dev_buf & 255) != 0) return fail(SV_ERR_ARG, "dev_buf not 256-byte aligned");
+        s->ptr = dev_buf;
+    } else {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && bytes > fr)
+            return fail(SV_ERR_OOM, "state batch larger than free device memory");
+        cudaError_t e = cudaMalloc(&s->ptr, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(state)");
+        s->owned = true;
+    }
+    *out = s.release();
+    return SV_OK;
+}
+
+sv_status sv_free(sv_state s) {
+    if (!s) return SV_OK;
+    if (s->owned && s->ptr) cudaFree(s->ptr);
+    delete s;
+    return SV_OK;
+}
+
+sv_status sv_state_info(sv_state s, void **ptr, int32_t *n, int32_t *batch, sv_dtype *dt) {
+    if (!s) return fail(SV_ERR_ARG, "state is NULL");
+    if (ptr) *ptr = s->ptr;
+    if (n) *n = s->n;
+    if (batch) *batch = s->batch;
+    if (dt) *dt = s->dtype;
+    return SV_OK;
+}
+
+sv_status sv_apply_circuit_batch(sv_state state, const sv_circuit *circuits, int32_t n_circuits,
+                                 const sv_slot *slots, int32_t n_slots, const double *theta,
+                                 int32_t theta_stride, const double *inputs,
+                                 int32_t input_stride, const sv_plan_opts *opts,
+                                 sv_stream_t stream) {
+    if (!state) return fail(SV_ERR_ARG, "state is NULL");
+    if (!circuits || n_circuits < 1) return fail(SV_ERR_ARG, "no circuits");
+    if (n_slots < 0 || n_slots > state->batch) return fail(SV_ERR_ARG, "n_slots out of range");
+    if (n_slots > 0 && !slots) return fail(SV_ERR_ARG, "slots is NULL");
+    const int64_t dim = int64_t(1) << state->n;
+    for (int c = 0; c < n_circuits; ++c) {
+        sv_status s = check_circuit(&circuits[c], state->dtype == SV_C128 ? 29 : 30);
+        if (s != SV_OK) return s;
+        if (circuits[c].n_qubits != state->n)
+            return fail(SV_ERR_UNSUPPORTED, "every circuit must have the state's n_qubits");
+        if (circuits[c].n_params > 0 && (!theta || theta_stride < circuits[c].n_params))
+            return fail(SV_ERR_ARG, "theta/theta_stride too small for a circuit");
+        if (circuits[c].input_dim > 0 && (!inputs || input_stride < circuits[c].input_dim))
+            return fail(SV_ERR_ARG, "inputs/input_stride too small for a circuit");
+    }
+    for (int b = 0; b < n_slots; ++b) {
+        const sv_slot &sl = slots[b];
+        if (sl.circuit < 0 || sl.circuit >= n_circuits) return fail(SV_ERR_ARG, "slot circuit index");
+        if (sl.ref < 0 || sl.ref >= dim) return fail(SV_ERR_ARG, "slot reference out of range");
+        if (sl.theta_row < 0) return fail(SV_ERR_ARG, "slot theta_row negative");
+        if (sl.shift_param >= circuits[sl.circuit].n_params)
+            return fail(SV_ERR_ARG, "slot shift_param out of range");
+        if (circuits[sl.circuit].input_dim > 0 && sl.input_row < 0)
+            return fail(SV_ERR_ARG, "slot needs an input row");
+    }
+    if (n_slots == 0) return SV_OK;
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int c = 0; c < n_circuits; ++c) {
+        // compact the slots of circuit c, keeping their output rows
+        std::vector<sv_slot> sub;
+        std::vector<int32_t> rows;
+        for (int b = 0; b < n_slots; ++b)
+            if (slots[b].circuit == c) {
+                sub.push_back(slots[b]);
+                rows.push_back(b);
+            }
+        if (sub.empty()) continue;
+        PlanEntry *plan = nullptr;
+        OnchipShape sh{};
+        sv_status s = plan_and_shape(ctx, ONCHIP_STORE, circuits[c], state->dtype,
+                                     (int)sub.size(), opts, &plan, &sh);
+        if (s != SV_OK) return s;
+        const void *dslots = nullptr, *drows = nullptr;
+        s = get_array(ctx, sub.data(), sub.size() * sizeof(sv_slot), &dslots);
+        if (s != SV_OK) return s;
+        s = get_array(ctx, rows.data(), rows.size() * sizeof(int32_t), &drows);
+        if (s != SV_OK) return s;
+        SlotSource src{};
+        src.mode = SLOTS_EXPLICIT;
+        src.n_slots = (int)sub.size();
+        src.theta = theta;
+        src.theta_stride = theta_stride;
+        src.inputs = inputs;
+        src.input_stride = input_stride;
+        src.slots = (const sv_slot *)dslots;
+        src.rows = (const int32_t *)drows;
+        cudaError_t e = launch_onchip_store(state->dtype == SV_C128, sh, plan->dev, src,
+                                            state->ptr, st);
+        if (e != cudaSuccess) return cuda_fail(e, "apply_circuit_batch launch");
+    }
+    return SV_OK;
+}
+
+sv_status sv_expect_pauli_sum(sv_state state, const sv_pauli_sum *h, int32_t n_rows, double *out,
+                              sv_stream_t stream) {
+    if (!state || !h || !out) return fail(SV_ERR_ARG, "NULL argument");
+    if (n_rows < 0 || n_rows > state->batch) return fail(SV_ERR_ARG, "n_rows out of range");
+    if (h->n_qubits != state->n) return fail(SV_ERR_ARG, "observable qubit count differs");
+    if (n_rows == 0) return SV_OK;
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ObsEntry *obs = nullptr;
+    sv_status s = get_obs(ctx, *h, state->n, state->dtype, &obs);
+    if (s != SV_OK) return s;
+    OnchipShape sh{};
+    const char *err = onchip_shape(ONCHIP_EXPECT, state->n, 0, 0, state->dtype == SV_C128, n_rows,
+                                   0, 0, &sh);
+    if (err) return fail(SV_ERR_UNSUPPORTED, err);
+    cudaError_t e = launch_onchip_expect(state->dtype == SV_C128, sh, state->n,
+                                         swz_bits(state->dtype), obs->dev, state->ptr, n_rows,
+                                         out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "expect launch");
+    return SV_OK;
+}
+
+namespace {
+
+// Launches the batched energies of every parameter-shift slot into E[B].
+sv_status ps_energies_locked(DeviceCtx *ctx, const sv_problem *p, const double *theta, double *E,
+                             int B, cudaStream_t st) {
+    const int I = p->n_instances;
+    PlanEntry *plan = nullptr;
+    OnchipShape sh{};
+    sv_status s = plan_and_shape(ctx, ONCHIP_ENERGY, *p->circuit, p->dtype, B, p->opts, &plan, &sh);
+    if (s != SV_OK) return s;
+    ObsEntry *obs = nullptr;
+    s = get_obs(ctx, *p->observable, p->circuit->n_qubits, p->dtype, &obs);
+    if (s != SV_OK) return s;
+    const void *drefs = nullptr;
+    s = get_array(ctx, p->refs, sizeof(int64_t) * I, &drefs);
+    if (s != SV_OK) return s;
+    SlotSource src{};
+    src.mode = SLOTS_PARAM_SHIFT;
+    src.n_slots = B;
+    src.n_instances = I;
+    src.refs = (const int64_t *)drefs;
+    src.theta = theta;
+    src.inputs = p->inputs;
+    src.input_stride = p->input_stride;
+    cudaError_t e = launch_onchip_energy(p->dtype == SV_C128, sh, plan->dev, obs->dev, src, E, st);
+    if (e != cudaSuccess) return cuda_fail(e, "param-shift energy launch");
+    return SV_OK;
+}
+
+sv_status ps_batch_size(const sv_problem *p, int *B) {
+    const int64_t B64 = (int64_t)(2 * (int64_t)p->circuit->n_params + 1) * p->n_instances;
+    if (B64 > (int64_t)1 << 30) return fail(SV_ERR_UNSUPPORTED, "too many shifted circuits");
+    *B = (int)B64;
+    return SV_OK;
+}
+
+}  // namespace
+
+sv_status sv_param_shift_energies(const sv_problem *p, const double *theta, double *out,
+                                  sv_stream_t stream) {
+    sv_status s = check_problem(p, false);
+    if (s != SV_OK) return s;
+    if (!out) return fail(SV_ERR_ARG, "out is NULL");
+    if (p->circuit->n_params > 0 && !theta) return fail(SV_ERR_ARG, "theta is NULL");
+    int B = 0;
+    s = ps_batch_size(p, &B);
+    if (s != SV_OK) return s;
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return ps_energies_locked(ctx, p, theta, out, B, (cudaStream_t)stream);
+}
+
+sv_status sv_grad_param_shift(const sv_problem *p, const double *theta, double *energy_out,
+                              double *loss_out, double *grad_out, sv_stream_t stream) {
+    sv_status s = check_problem(p, true);
+    if (s != SV_OK) return s;
+    const int P = p->circuit->n_params, I = p->n_instances;
+    if (P > 0 && (!theta || !grad_out)) return fail(SV_ERR_ARG, "theta/grad_out is NULL");
+    int B = 0;
+    s = ps_batch_size(p, &B);
+    if (s != SV_OK) return s;
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    void *scr = nullptr;
+    s = get_scratch(ctx, st, sizeof(double) * ((size_t)B + I), &scr);
+    if (s != SV_OK) return s;
+    double *E = (double *)scr, *lp = E + B;
+    s = ps_energies_locked(ctx, p, theta, E, B, st);
+    if (s != SV_OK) return s;
+    cudaError_t e = launch_ps_combine(E, I, P, cost_of(p, nullptr), lp, energy_out, loss_out,
+                                      grad_out, st);
+    if (e != cudaSuccess) return cuda_fail(e, "param-shift combine launch");
+    return SV_OK;
+}
+
+sv_status sv_energies(const sv_problem *p, const double *theta, double *energy_out,
+                      double *loss_out, sv_stream_t stream) {
+    sv_status s = check_problem(p, loss_out != nullptr);
+    if (s != SV_OK) return s;
+    const int P = p->circuit->n_params, I = p->n_instances;
+    if (!energy_out) return fail(SV_ERR_ARG, "energy_out is NULL");
+    if (P > 0 && !theta) return fail(SV_ERR_ARG, "theta is NULL");
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    PlanEntry *plan = nullptr;
+    OnchipShape sh{};
+    s = plan_and_shape(ctx, ONCHIP_ENERGY, *p->circuit, p->dtype, I, p->opts, &plan, &sh);
+    if (s != SV_OK) return s;
+    ObsEntry *obs = nullptr;
+    s = get_obs(ctx, *p->observable, p->circuit->n_qubits, p->dtype, &obs);
+    if (s != SV_OK) return s;
+    const void *drefs = nullptr;
+    s = get_array(ctx, p->refs, sizeof(int64_t) * I, &drefs);
+    if (s != SV_OK) return s;
+    SlotSource src{};
+    src.mode = SLOTS_INSTANCES;
+    src.n_slots = I;
+    src.n_instances = I;
+    src.refs = (const int64_t *)drefs;
+    src.theta = theta;
+    src.inputs = p->inputs;
+    src.input_stride = p->input_stride;
+    cudaError_t e = launch_onchip_energy(p->dtype == SV_C128, sh, plan->dev, obs->dev, src,
+                                         energy_out, st);
+    if (e != cudaSuccess) return cuda_fail(e, "energy launch");
+    if (loss_out) {
+        void *scr = nullptr;
+        s = get_scratch(ctx, st, sizeof(double) * I, &scr);
+        if (s != SV_OK) return s;
+        e = launch_ps_combine(energy_out, I, 0, cost_of(p, nullptr), (double *)scr, nullptr,
+                              loss_out, nullptr, st);
+        if (e != cudaSuccess) return cuda_fail(e, "loss launch");
+    }
+    return SV_OK;
+}
+
+sv_status sv_grad_adjoint(const sv_problem *p, const double *theta, const double *weights,
+                          double *energy_out, double *loss_out, double *grad_out,
+                          int32_t checkpoint_every, sv_stream_t stream) {
+    sv_status s = check_problem(p, weights == nullptr);
+    if (s != SV_OK) return s;
+    if (checkpoint_every < 0) return fail(SV_ERR_ARG, "checkpoint_every must be >= 0");
+    const int P = p->circuit->n_params, I = p->n_instances;
+    if (P > 0 && (!theta || !grad_out)) return fail(SV_ERR_ARG, "theta/grad_out is NULL");
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    PlanEntry *plan = nullptr;
+    OnchipShape sh{};
+    s = plan_and_shape(ctx, ONCHIP_ADJOINT, *p->circuit, p->dtype, I, p->opts, &plan, &sh);
+    if (s != SV_OK) return s;
+    ObsEntry *obs = nullptr;
+    s = get_obs(ctx, *p->observable, p->circuit->n_qubits, p->dtype, &obs);
+    if (s != SV_OK) return s;
+    const void *drefs = nullptr;
+    s = get_array(ctx, p->refs, sizeof(int64_t) * I, &drefs);
+    if (s != SV_OK) return s;
+    void *scr = nullptr;
+    s = get_scratch(ctx, st, sizeof(double) * ((size_t)I * (P > 0 ? P : 1) + I), &scr);
+    if (s != SV_OK) return s;
+    double *G = (double *)scr, *E = G + (size_t)I * (P > 0 ? P : 1);
+    SlotSource src{};
+    src.mode = SLOTS_INSTANCES;
+    src.n_slots = I;
+    src.n_instances = I;
+    src.refs = (const int64_t *)drefs;
+    src.theta = theta;
+    src.inputs = p->inputs;
+    src.input_stride = p->input_stride;
+    const CostSource cs = cost_of(p, weights);
+    cudaError_t e = launch_onchip_adjoint(p->dtype == SV_C128, sh, plan->dev, obs->dev, src, cs,
+                                          G, E, st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+    e = launch_adjoint_combine(G, E, I, P, cs, energy_out, loss_out, grad_out, st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint combine launch");
+    return SV_OK;
+}
+
+// -------------------------------------------------------------- plain form
+
+namespace {
+
+void host_rotation(int axis, double a, double2 m[4]) {
+    const double c = std::cos(0.5 * a), s = std::sin(0.5 * a);
+    if (axis == 0) {
+        m[0] = make_double2(c, 0); m[1] = make_double2(0, -s); m[2] = make_double2(0, -s); m[3] = make_double2(c, 0);
+    } else if (axis == 1) {
+        m[0] = make_double2(c, 0); m[1] = make_double2(-s, 0); m[2] = make_double2(s, 0); m[3] = make_double2(c, 0);
+    } else {
+        m[0] = make_double2(c, -s); m[1] = make_double2(0, 0); m[2] = make_double2(0, 0); m[3] = make_double2(c, s);
+    }
+}
+
+}  // namespace
+
+sv_status sv_grad_param_shift_plain(const sv_problem *p, const double *theta, double *energy_out,
+                                    double *loss_out, double *grad_out, sv_stream_t stream) {
+    sv_status s = check_problem(p, true);
+    if (s != SV_OK) return s;
+    const sv_circuit &c = *p->circuit;
+    const int n = c.n_qubits, P = c.n_params, I = p->n_instances;
+    if (n > 29) return fail(SV_ERR_UNSUPPORTED, "plain form limited to 29 qubits");
+    if (P > 0 && (!theta || !grad_out)) return fail(SV_ERR_ARG, "theta/grad_out is NULL");
+    for (int g = 0; g < c.n_gates; ++g) {
+        const sv_gate &G = c.gates[g];
+        if (G.target < 0 || G.target >= n || G.op < 0 || G.op > SV_GATE_ENC_RZ_ACOS_SQ)
+            return fail(SV_ERR_ARG, "bad gate");
+        if ((G.op == SV_GATE_CNOT || G.op == SV_GATE_CZ) &&
+            (G.control < 0 || G.control >= n || G.control == G.target))
+            return fail(SV_ERR_ARG, "bad control");
+        if (G.op <= SV_GATE_RZ && G.param >= P) return fail(SV_ERR_ARG, "param out of range");
+        if (G.op >= SV_GATE_ENC_RY_ASIN && (G.param < 0 || G.param >= c.input_dim))
+            return fail(SV_ERR_ARG, "input column out of range");
+    }
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    // The plain form is driven from the host: parameters come back first.
+    std::vector<double> th(P), xs;
+    if (P) SV_CUDA(cudaMemcpyAsync(th.data(), theta, sizeof(double) * P, cudaMemcpyDeviceToHost, st));
+    if (c.input_dim > 0) {
+        xs.resize((size_t)I * p->input_stride);
+        SV_CUDA(cudaMemcpyAsync(xs.data(), p->inputs, sizeof(double) * xs.size(),
+                                cudaMemcpyDeviceToHost, st));
+    }
+    SV_CUDA(cudaStreamSynchronize(st));
+    const int B = (2 * P + 1) * I;
+    const size_t dim = size_t(1) << n;
+    void *scr = nullptr;
+    s = get_scratch(ctx, st, sizeof(double) * ((size_t)B + I) + 16 * dim + 256, &scr);
+    if (s != SV_OK) return s;
+    double *E = (double *)scr, *lp = E + B;
+    double2 *psi = (double2 *)(((uintptr_t)(lp + I) + 255) & ~uintptr_t(255));
+    SV_CUDA(cudaMemsetAsync(E, 0, sizeof(double) * B, st));
+    std::vector<std::vector<uint32_t>> xz;
+    const sv_pauli_sum &h = *p->observable;
+    for (int b = 0; b < B; ++b) {
+        int inst = b, sp = -1;
+        double shift = 0.0;
+        if (b >= I) {
+            const int bb = b - I, k = bb / (2 * I), r = bb % (2 * I);
+            inst = r % I;
+            sp = k;
+            shift = r < I ? 1.5707963267948966 : -1.5707963267948966;
+        }
+        cudaError_t e = launch_plain_init(psi, n, p->refs[inst], st);
+        if (e != cudaSuccess) return cuda_fail(e, "plain init");
+        for (int g = 0; g < c.n_gates; ++g) {
+            const sv_gate &G = c.gates[g];
+            double2 m[4];
+            if (G.op == SV_GATE_CNOT || G.op == SV_GATE_CZ) {
+                e = G.op == SV_GATE_CNOT ? launch_plain_cx(psi, n, G.control, G.target, st)
+                                         : launch_plain_cz(psi, n, G.control, G.target, st);
+                if (e != cudaSuccess) return cuda_fail(e, "plain gate");
+                continue;
+            }
+            switch (G.op) {
+            case SV_GATE_RX:
+            case SV_GATE_RY:
+            case SV_GATE_RZ: {
+                double a = G.angle;
+                if (G.param >= 0) a = th[G.param] + (G.param == sp ? shift : 0.0);
+                host_rotation(G.op - SV_GATE_RX, a, m);
+                break;
+            }
+            case SV_GATE_X:
+                m[0] = make_double2(0, 0); m[1] = make_double2(1, 0); m[2] = make_double2(1, 0); m[3] = make_double2(0, 0);
+                break;
+            case SV_GATE_H: {
+                const double r2 = 0.70710678118654752440;
+                m[0] = make_double2(r2, 0); m[1] = make_double2(r2, 0); m[2] = make_double2(r2, 0); m[3] = make_double2(-r2, 0);
+                break;
+            }
+            case SV_GATE_ENC_RY_ASIN:
+                host_rotation(1, std::asin(xs[(size_t)inst * p->input_stride + G.param]), m);
+                break;
+            default: {
+                const double x = xs[(size_t)inst * p->input_stride + G.param];
+                host_rotation(2, std::acos(x * x), m);
+                break;
+            }
+            }
+            e = launch_plain_u1(psi, n, G.target, m, st);
+            if (e != cudaSuccess) return cuda_fail(e, "plain gate");
+        }
+        for (int t = 0; t < h.n_terms; ++t) {
+            const uint32_t x = (uint32_t)h.x_mask[t], z = (uint32_t)h.z_mask[t];
+            e = launch_plain_term(psi, n, x, z, __builtin_popcount(x & z) & 3, h.coeff[t], E + b, st);
+            if (e != cudaSuccess) return cuda_fail(e, "plain term");
+        }
+    }
+    cudaError_t e = launch_ps_combine(E, I, P, cost_of(p, nullptr), lp, energy_out, loss_out,
+                                      grad_out, st);
+    if (e != cudaSuccess) return cuda_fail(e, "plain combine");
+    return SV_OK;
+}
+
+sv_status sv_sync_status(sv_stream_t stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pending error");
+    return SV_OK;
+}
+
+sv_status sv_shutdown(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto &kv : g_ctx) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(kv.first);
+        cudaDeviceSynchronize();
+        kv.second.reset();
+        cudaSetDevice(cur);
+    }
+    g_ctx.clear();
+    return SV_OK;
+}
+
+}  // extern "C"

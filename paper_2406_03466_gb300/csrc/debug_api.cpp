@@ -1,0 +1,39 @@
+// Test hooks declared in sv_debug.h: host-side planner output, no GPU needed.
+#include <cstring>
+#include <string>
+
+#include "planner.h"
+#include "sv_debug.h"
+
+using namespace svk;
+
+extern "C" {
+
+void sv_debug_sizes(int32_t *sizes) {
+    if (!sizes) return;
+    sizes[0] = (int32_t)sizeof(Stage);
+    sizes[1] = (int32_t)sizeof(Op);
+    sizes[2] = (int32_t)sizeof(Group);
+    sizes[3] = (int32_t)sizeof(Member);
+    sizes[4] = (int32_t)sizeof(TermGroup);
+    sizes[5] = (int32_t)sizeof(Term);
+}
+
+sv_status sv_debug_plan(const sv_circuit *c, int32_t reg_bits, int32_t fuse, int32_t swz_bits,
+                        int32_t *counts, void *stages, void *ops, void *groups, void *members) {
+    if (!c || !counts) return SV_ERR_ARG;
+    HostProgram h;
+    std::string err = plan_circuit(*c, reg_bits, fuse != 0, swz_bits, &h);
+    if (!err.empty()) return SV_ERR_ARG;
+    counts[0] = (int32_t)h.stages.size();
+    counts[1] = (int32_t)h.ops.size();
+    counts[2] = (int32_t)h.groups.size();
+    counts[3] = (int32_t)h.members.size();
+    if (stages) std::memcpy(stages, h.stages.data(), h.stages.size() * sizeof(Stage));
+    if (ops) std::memcpy(ops, h.ops.data(), h.ops.size() * sizeof(Op));
+    if (groups) std::memcpy(groups, h.groups.data(), h.groups.size() * sizeof(Group));
+    if (members) std::memcpy(members, h.members.data(), h.members.size() * sizeof(Member));
+    return SV_OK;
+}
+
+}  // extern "C"

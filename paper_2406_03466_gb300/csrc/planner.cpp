@@ -1,0 +1,273 @@
+// Host planner for the on-chip engine.  See svk_types.h for the program model.
+#include "planner.h"
+
+#include <algorithm>
+#include <cstring>
+#include <unordered_map>
+
+namespace svk {
+namespace {
+
+int find_pos(const std::vector<int> &v, int x) {
+    for (size_t i = 0; i < v.size(); ++i)
+        if (v[i] == x) return (int)i;
+    return -1;
+}
+
+uint32_t cx_apply(uint32_t v, int c, int t) { return v ^ (((v >> c) & 1u) << t); }
+
+// Logical op stream after single-qubit fusion.
+struct LOp {
+    int kind;  // 0 = U1 on qubit a, 1 = CNOT a -> b, 2 = CZ(a, b)
+    int a, b, group;
+};
+
+inline uint64_t mix(uint64_t h, uint64_t v) {
+    h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    return h * 0xff51afd7ed558ccdull;
+}
+
+}  // namespace
+
+std::string plan_circuit(const sv_circuit &c, int reg_bits, bool fuse, int swz_bits,
+                         HostProgram *P) {
+    const int n = c.n_qubits;
+    if (n < 1 || n > kNMax) return "n_qubits must be in [1, 30]";
+    if (c.n_gates < 0 || (c.n_gates > 0 && !c.gates)) return "circuit has no gate array";
+    if (c.n_params < 0 || c.input_dim < 0) return "negative n_params or input_dim";
+    if (reg_bits < 1 || reg_bits > kRMax) return "reg_bits must be in [1, 5]";
+    const int R = std::min(reg_bits, n);
+    *P = HostProgram();
+    P->n = n;
+    P->R = R;
+    P->n_params = c.n_params;
+    P->input_dim = c.input_dim;
+    P->swz_bits = swz_bits;
+
+    // ---- 1. fuse consecutive single-qubit gates per qubit into groups
+    std::vector<std::vector<Member>> gm;  // members per group
+    std::vector<int> gq;                  // qubit per group
+    std::vector<LOp> lops;
+    std::vector<int> open(n, -1);
+    auto close = [&](int q) {
+        if (open[q] >= 0) {
+            lops.push_back({0, q, -1, open[q]});
+            open[q] = -1;
+        }
+    };
+    for (int g = 0; g < c.n_gates; ++g) {
+        const sv_gate &G = c.gates[g];
+        const int t = G.target;
+        if (t < 0 || t >= n) return "gate " + std::to_string(g) + ": target out of range";
+        Member m{};
+        m.param = -1;
+        m.angle = 0.0;
+        bool single = true;
+        switch (G.op) {
+        case SV_GATE_RX: m.kind = M_RX; break;
+        case SV_GATE_RY: m.kind = M_RY; break;
+        case SV_GATE_RZ: m.kind = M_RZ; break;
+        case SV_GATE_X: m.kind = M_X; break;
+        case SV_GATE_H: m.kind = M_H; break;
+        case SV_GATE_ENC_RY_ASIN: m.kind = M_ENC_RY_ASIN; break;
+        case SV_GATE_ENC_RZ_ACOS_SQ: m.kind = M_ENC_RZ_ACOS_SQ; break;
+        case SV_GATE_CNOT:
+        case SV_GATE_CZ: single = false; break;
+        default: return "gate " + std::to_string(g) + ": unknown op";
+        }
+        if (single) {
+            if (m.kind <= M_RZ) {
+                if (G.param >= c.n_params)
+                    return "gate " + std::to_string(g) + ": param index out of range";
+                m.param = G.param < 0 ? -1 : G.param;
+                m.angle = G.angle;
+            } else if (m.kind == M_ENC_RY_ASIN || m.kind == M_ENC_RZ_ACOS_SQ) {
+                if (G.param < 0 || G.param >= c.input_dim)
+                    return "gate " + std::to_string(g) + ": input column out of range";
+                m.param = G.param;
+            }
+            if (!fuse || open[t] < 0) {
+                gm.emplace_back();
+                gq.push_back(t);
+                open[t] = (int)gm.size() - 1;
+            }
+            gm[open[t]].push_back(m);
+            if (!fuse) close(t);
+        } else {
+            const int ctl = G.control;
+            if (ctl < 0 || ctl >= n || ctl == t)
+                return "gate " + std::to_string(g) + ": bad control qubit";
+            close(ctl);
+            close(t);
+            lops.push_back({G.op == SV_GATE_CNOT ? 1 : 2, ctl, t, -1});
+        }
+    }
+    for (int q = 0; q < n; ++q) close(q);
+
+    for (size_t g = 0; g < gm.size(); ++g) {
+        Group grp{};
+        grp.m_begin = (int)P->members.size();
+        grp.qubit = gq[g];
+        for (const Member &m : gm[g]) {
+            P->members.push_back(m);
+            if (m.kind <= M_RZ && m.param >= 0) grp.has_param = 1;
+        }
+        grp.m_end = (int)P->members.size();
+        P->groups.push_back(grp);
+    }
+
+    // ---- 2. cut the op stream into register stages
+    std::vector<int> Q;
+    std::vector<Op> sops;
+    std::vector<uint32_t> col(n);
+    uint32_t dirty = 0;
+    int n_u1 = 0;
+    bool any = false;
+    auto reset = [&]() {
+        Q.clear();
+        sops.clear();
+        for (int b = 0; b < n; ++b) col[b] = 1u << b;
+        dirty = 0;
+        n_u1 = 0;
+        any = false;
+    };
+    const int w = swz_bits;
+    auto close_stage = [&]() {
+        for (int p = 0; (int)Q.size() < R && p < n; ++p)
+            if (find_pos(Q, p) < 0) Q.push_back(p);
+        Stage st{};
+        st.op_begin = (int)P->ops.size();
+        for (const Op &o : sops) P->ops.push_back(o);
+        st.op_end = (int)P->ops.size();
+        st.n_thr = n - R;
+        st.n_u1 = n_u1;
+        // Thread bit order: first one qubit of every residue mod w (so the
+        // lanes of a wavefront land in distinct banks), then the rest.
+        std::vector<int> rest, order;
+        for (int p = 0; p < n; ++p)
+            if (find_pos(Q, p) < 0) rest.push_back(p);
+        for (int r = 0; r < w; ++r)
+            for (int p : rest)
+                if (p % w == r && find_pos(order, p) < 0) {
+                    order.push_back(p);
+                    break;
+                }
+        for (int p : rest)
+            if (find_pos(order, p) < 0) order.push_back(p);
+        for (int i = 0; i < kRMax; ++i) {
+            st.q[i] = i < R ? Q[i] : -1;
+            st.ldq[i] = i < R ? swizzle(1u << Q[i], w) : 0u;
+            st.stq[i] = i < R ? swizzle(col[Q[i]], w) : 0u;
+        }
+        for (int k = 0; k < kNMax; ++k) {
+            const bool on = k < n - R;
+            st.tpos[k] = on ? order[k] : -1;
+            st.ldt[k] = on ? swizzle(1u << order[k], w) : 0u;
+            st.stt[k] = on ? swizzle(col[order[k]], w) : 0u;
+        }
+        P->stages.push_back(st);
+        P->perm_cols.push_back(col);
+        reset();
+    };
+    reset();
+    for (const LOp &o : lops) {
+        if (o.kind == 0) {
+            const int q = o.a;
+            if (((dirty >> q) & 1u) || n_u1 >= kMaxGroupOpsPerStage) close_stage();
+            int idx = find_pos(Q, q);
+            if (idx < 0) {
+                if ((int)Q.size() >= R) close_stage();
+                Q.push_back(q);
+                idx = (int)Q.size() - 1;
+            }
+            sops.push_back({OP_U1, idx, -1, o.group});
+            ++n_u1;
+            any = true;
+        } else if (o.kind == 1) {
+            for (int b = 0; b < n; ++b) col[b] = cx_apply(col[b], o.a, o.b);
+            dirty |= (1u << o.a) | (1u << o.b);
+            any = true;
+        } else {
+            if (dirty & ((1u << o.a) | (1u << o.b))) close_stage();
+            sops.push_back({OP_CZ, o.a, o.b, -1});
+            any = true;
+        }
+    }
+    if (any || P->stages.empty()) close_stage();
+    return "";
+}
+
+std::string plan_observable(const sv_pauli_sum &h, int n, int swz_bits, HostObservable *out) {
+    if (h.n_terms < 0) return "negative n_terms";
+    if (h.n_terms > 0 && (!h.x_mask || !h.z_mask || !h.coeff)) return "observable arrays missing";
+    if (h.n_qubits != n) return "observable qubit count differs from the state's";
+    const uint64_t lim = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+    *out = HostObservable();
+    out->n = n;
+    std::vector<uint32_t> xs;
+    std::vector<std::vector<Term>> per;
+    std::unordered_map<uint32_t, int> idx;
+    for (int t = 0; t < h.n_terms; ++t) {
+        if ((h.x_mask[t] & ~lim) || (h.z_mask[t] & ~lim))
+            return "term " + std::to_string(t) + ": mask has bits beyond n_qubits";
+        const uint32_t x = (uint32_t)h.x_mask[t], z = (uint32_t)h.z_mask[t];
+        auto it = idx.find(x);
+        int gi;
+        if (it == idx.end()) {
+            gi = (int)xs.size();
+            idx[x] = gi;
+            xs.push_back(x);
+            per.emplace_back();
+        } else {
+            gi = it->second;
+        }
+        Term tm{};
+        tm.z = z;
+        tm.phase = __builtin_popcount(x & z) & 3;
+        tm.coeff = h.coeff[t];
+        per[gi].push_back(tm);
+    }
+    for (size_t g = 0; g < xs.size(); ++g) {
+        TermGroup tg{};
+        tg.x = xs[g];
+        tg.sx = swizzle(xs[g], swz_bits);
+        tg.t_begin = (int)out->terms.size();
+        for (const Term &tm : per[g]) out->terms.push_back(tm);
+        tg.t_end = (int)out->terms.size();
+        out->tgroups.push_back(tg);
+    }
+    return "";
+}
+
+uint64_t hash_circuit(const sv_circuit &c) {
+    uint64_t h = 0x12345678abcdefull;
+    h = mix(h, (uint64_t)c.n_qubits);
+    h = mix(h, (uint64_t)c.n_gates);
+    h = mix(h, (uint64_t)c.n_params);
+    h = mix(h, (uint64_t)c.input_dim);
+    for (int g = 0; g < c.n_gates; ++g) {
+        const sv_gate &G = c.gates[g];
+        uint64_t a;
+        std::memcpy(&a, &G.angle, sizeof a);
+        h = mix(h, (uint64_t)(uint32_t)G.op | ((uint64_t)(uint32_t)G.target << 32));
+        h = mix(h, (uint64_t)(uint32_t)G.control | ((uint64_t)(uint32_t)G.param << 32));
+        h = mix(h, a);
+    }
+    return h;
+}
+
+uint64_t hash_observable(const sv_pauli_sum &o) {
+    uint64_t h = 0x2545F4914F6CDD1Dull;
+    h = mix(h, (uint64_t)o.n_qubits);
+    h = mix(h, (uint64_t)o.n_terms);
+    for (int t = 0; t < o.n_terms; ++t) {
+        uint64_t a;
+        std::memcpy(&a, &o.coeff[t], sizeof a);
+        h = mix(h, o.x_mask[t]);
+        h = mix(h, o.z_mask[t]);
+        h = mix(h, a);
+    }
+    return h;
+}
+
+}  // namespace svk

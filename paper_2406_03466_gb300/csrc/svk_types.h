@@ -1,0 +1,105 @@
+// Plain-old-data structures shared by the host planner and the CUDA kernels.
+//
+// A circuit is compiled into a *program* for the on-chip engine:
+//  * consecutive single-qubit gates on one qubit are fused into a *group*
+//    whose 2x2 matrix is built per circuit slot (shifted parameters and
+//    per-instance encoding inputs differ between slots);
+//  * the op stream is cut into *stages*.  In a stage every thread holds
+//    2^R amplitudes in registers; the R qubits in registers are the stage's
+//    register bits, the other index bits come from the thread index.  A
+//    stage applies its fused 2x2 groups in registers, then writes the
+//    amplitudes back to shared memory through the stage's GF(2)-linear
+//    index permutation (the CNOTs deferred to the end of the stage);
+//  * shared-memory addresses are XOR-swizzled so that the lanes of a warp
+//    hit distinct banks; the swizzle is GF(2)-linear, so every address is
+//    an XOR of per-bit address vectors, precomputed here for each stage.
+#pragma once
+#include <cstdint>
+
+namespace svk {
+
+constexpr int kRMax = 5;    // largest register-bit count
+constexpr int kNMax = 30;   // largest qubit count
+constexpr int kMaxGroupOpsPerStage = 8;
+
+// Members of a fused single-qubit group.
+enum MemberKind : int32_t {
+    M_RX = 0, M_RY = 1, M_RZ = 2, M_X = 3, M_H = 4, M_ENC_RY_ASIN = 5, M_ENC_RZ_ACOS_SQ = 6
+};
+
+struct Member {
+    int32_t kind;
+    int32_t param;   // theta index (rotations), input column (encodings), -1 otherwise
+    double angle;    // fixed angle of a rotation with param < 0
+};
+
+struct Group {
+    int32_t m_begin, m_end;  // members [m_begin, m_end) in time order
+    int32_t qubit;
+    int32_t has_param;       // 1 if some member reads theta (needs a gradient)
+};
+
+enum OpKind : int32_t { OP_U1 = 0, OP_CZ = 1 };
+
+struct Op {
+    int32_t kind;
+    int32_t a;      // OP_U1: register index; OP_CZ: first qubit position
+    int32_t b;      // OP_CZ: second qubit position
+    int32_t group;  // OP_U1: group index
+};
+
+struct Stage {
+    int32_t op_begin, op_end;
+    int32_t n_thr;              // thread bits = n - R
+    int32_t n_u1;               // OP_U1 ops in this stage (<= kMaxGroupOpsPerStage)
+    int32_t q[kRMax];           // register bit i -> qubit
+    int32_t tpos[kNMax];        // thread bit k -> qubit
+    uint32_t ldq[kRMax];        // swizzled address vector of register bit i, load layout
+    uint32_t stq[kRMax];        // swizzled address vector of register bit i, store layout
+    uint32_t ldt[kNMax];        // same for thread bit k
+    uint32_t stt[kNMax];
+};
+
+// Pauli terms grouped by X-mask: <psi|P|psi> = Re(i^phase sum_j (-1)^{|j & z|}
+// conj(psi_{j^x}) psi_j) with phase = (#Y) mod 4.
+struct TermGroup {
+    uint32_t x;
+    uint32_t sx;        // swizzled x (address vector of the partner offset)
+    int32_t t_begin, t_end;
+};
+
+struct Term {
+    uint32_t z;
+    int32_t phase;
+    double coeff;
+};
+
+// Device view of a compiled circuit (all pointers are device memory).
+struct Program {
+    int32_t n, R, n_stages, n_groups, n_params, input_dim, swz_bits;
+    int32_t pad;
+    const Stage *stages;
+    const Op *ops;
+    const Group *groups;
+    const Member *members;
+};
+
+struct Observable {
+    int32_t n_tgroups, n_terms;
+    const TermGroup *tgroups;
+    const Term *terms;
+};
+
+// GF(2)-linear swizzle of a shared-memory amplitude index: the low `w` bits
+// are XORed with the fold of all higher w-bit chunks.  w = 4 for 8-byte
+// amplitudes (16 per 128-byte wavefront), 3 for 16-byte amplitudes.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline uint32_t swizzle(uint32_t a, int w) {
+    uint32_t f = 0;
+    for (uint32_t h = a >> w; h; h >>= w) f ^= h;
+    return a ^ (f & ((1u << w) - 1u));
+}
+
+}  // namespace svk
