@@ -645,12 +645,14 @@ __global__ void __launch_bounds__(512) k_adjoint(Program p, Observable o, SlotSo
             lam[ad] = al[r];
         }
         __syncthreads();
-        if (tid < sg->n_u1) {
+        // Fold the per-warp partials of every group op of this stage (a slot
+        // may have fewer threads than the stage has group ops).
+        for (int uu = tid; uu < sg->n_u1; uu += Ts) {
             int cnt = 0, gi = -1;
             for (int oi = sg->op_begin; oi < sg->op_end; ++oi) {
                 const Op op = p.ops[oi];
                 if (op.kind != OP_U1) continue;
-                if (cnt == tid) {
+                if (cnt == uu) {
                     gi = op.group;
                     break;
                 }
@@ -660,7 +662,7 @@ __global__ void __launch_bounds__(512) k_adjoint(Program p, Observable o, SlotSo
 #pragma unroll
                 for (int v = 0; v < 8; ++v) {
                     double acc = 0.0;
-                    for (int wi = 0; wi < wps; ++wi) acc += (double)rw[(tid * wps + wi) * 8 + v];
+                    for (int wi = 0; wi < wps; ++wi) acc += (double)rw[(uu * wps + wi) * 8 + v];
                     rho[gi * 8 + v] = acc;
                 }
             }

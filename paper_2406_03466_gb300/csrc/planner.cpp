@@ -16,42 +16,29 @@ int find_pos(const std::vector<int> &v, int x) {
 
 uint32_t cx_apply(uint32_t v, int c, int t) { return v ^ (((v >> c) & 1u) << t); }
 
-// Logical op stream after single-qubit fusion.
-struct LOp {
-    int kind;  // 0 = U1 on qubit a, 1 = CNOT a -> b, 2 = CZ(a, b)
-    int a, b, group;
-};
-
 inline uint64_t mix(uint64_t h, uint64_t v) {
     h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
     return h * 0xff51afd7ed558ccdull;
 }
 
+uint32_t lop_qubits(const LOp &o) {
+    return o.kind == 0 ? (1u << o.a) : ((1u << o.a) | (1u << o.b));
+}
+
 }  // namespace
 
-std::string plan_circuit(const sv_circuit &c, int reg_bits, bool fuse, int swz_bits,
-                         HostProgram *P) {
+std::string fuse_circuit(const sv_circuit &c, bool fuse, FusedCircuit *F) {
     const int n = c.n_qubits;
     if (n < 1 || n > kNMax) return "n_qubits must be in [1, 30]";
     if (c.n_gates < 0 || (c.n_gates > 0 && !c.gates)) return "circuit has no gate array";
     if (c.n_params < 0 || c.input_dim < 0) return "negative n_params or input_dim";
-    if (reg_bits < 1 || reg_bits > kRMax) return "reg_bits must be in [1, 5]";
-    const int R = std::min(reg_bits, n);
-    *P = HostProgram();
-    P->n = n;
-    P->R = R;
-    P->n_params = c.n_params;
-    P->input_dim = c.input_dim;
-    P->swz_bits = swz_bits;
-
-    // ---- 1. fuse consecutive single-qubit gates per qubit into groups
+    *F = FusedCircuit();
     std::vector<std::vector<Member>> gm;  // members per group
     std::vector<int> gq;                  // qubit per group
-    std::vector<LOp> lops;
     std::vector<int> open(n, -1);
     auto close = [&](int q) {
         if (open[q] >= 0) {
-            lops.push_back({0, q, -1, open[q]});
+            F->lops.push_back({0, q, -1, open[q]});
             open[q] = -1;
         }
     };
@@ -99,52 +86,55 @@ std::string plan_circuit(const sv_circuit &c, int reg_bits, bool fuse, int swz_b
                 return "gate " + std::to_string(g) + ": bad control qubit";
             close(ctl);
             close(t);
-            lops.push_back({G.op == SV_GATE_CNOT ? 1 : 2, ctl, t, -1});
+            F->lops.push_back({G.op == SV_GATE_CNOT ? 1 : 2, ctl, t, -1});
         }
     }
     for (int q = 0; q < n; ++q) close(q);
-
     for (size_t g = 0; g < gm.size(); ++g) {
         Group grp{};
-        grp.m_begin = (int)P->members.size();
+        grp.m_begin = (int)F->members.size();
         grp.qubit = gq[g];
         for (const Member &m : gm[g]) {
-            P->members.push_back(m);
+            F->members.push_back(m);
             if (m.kind <= M_RZ && m.param >= 0) grp.has_param = 1;
         }
-        grp.m_end = (int)P->members.size();
-        P->groups.push_back(grp);
+        grp.m_end = (int)F->members.size();
+        F->groups.push_back(grp);
     }
+    return "";
+}
 
-    // ---- 2. cut the op stream into register stages
+void stage_lops(const std::vector<LOp> &lops, const std::vector<int> &pos, int t, int R, int w,
+                HostProgram *P) {
+    // lops act on positions pos[qubit] in [0, t); R <= t register bits.
     std::vector<int> Q;
     std::vector<Op> sops;
-    std::vector<uint32_t> col(n);
+    std::vector<uint32_t> col(t);
     uint32_t dirty = 0;
     int n_u1 = 0;
     bool any = false;
+    const int first_stage = (int)P->stages.size();
     auto reset = [&]() {
         Q.clear();
         sops.clear();
-        for (int b = 0; b < n; ++b) col[b] = 1u << b;
+        for (int b = 0; b < t; ++b) col[b] = 1u << b;
         dirty = 0;
         n_u1 = 0;
         any = false;
     };
-    const int w = swz_bits;
     auto close_stage = [&]() {
-        for (int p = 0; (int)Q.size() < R && p < n; ++p)
+        for (int p = 0; (int)Q.size() < R && p < t; ++p)
             if (find_pos(Q, p) < 0) Q.push_back(p);
         Stage st{};
         st.op_begin = (int)P->ops.size();
         for (const Op &o : sops) P->ops.push_back(o);
         st.op_end = (int)P->ops.size();
-        st.n_thr = n - R;
+        st.n_thr = t - R;
         st.n_u1 = n_u1;
-        // Thread bit order: first one qubit of every residue mod w (so the
+        // Thread bit order: first one position of every residue mod w (so the
         // lanes of a wavefront land in distinct banks), then the rest.
         std::vector<int> rest, order;
-        for (int p = 0; p < n; ++p)
+        for (int p = 0; p < t; ++p)
             if (find_pos(Q, p) < 0) rest.push_back(p);
         for (int r = 0; r < w; ++r)
             for (int p : rest)
@@ -160,7 +150,7 @@ std::string plan_circuit(const sv_circuit &c, int reg_bits, bool fuse, int swz_b
             st.stq[i] = i < R ? swizzle(col[Q[i]], w) : 0u;
         }
         for (int k = 0; k < kNMax; ++k) {
-            const bool on = k < n - R;
+            const bool on = k < t - R;
             st.tpos[k] = on ? order[k] : -1;
             st.ldt[k] = on ? swizzle(1u << order[k], w) : 0u;
             st.stt[k] = on ? swizzle(col[order[k]], w) : 0u;
@@ -172,7 +162,7 @@ std::string plan_circuit(const sv_circuit &c, int reg_bits, bool fuse, int swz_b
     reset();
     for (const LOp &o : lops) {
         if (o.kind == 0) {
-            const int q = o.a;
+            const int q = pos[o.a];
             if (((dirty >> q) & 1u) || n_u1 >= kMaxGroupOpsPerStage) close_stage();
             int idx = find_pos(Q, q);
             if (idx < 0) {
@@ -184,16 +174,107 @@ std::string plan_circuit(const sv_circuit &c, int reg_bits, bool fuse, int swz_b
             ++n_u1;
             any = true;
         } else if (o.kind == 1) {
-            for (int b = 0; b < n; ++b) col[b] = cx_apply(col[b], o.a, o.b);
-            dirty |= (1u << o.a) | (1u << o.b);
+            const int a = pos[o.a], b = pos[o.b];
+            for (int k = 0; k < t; ++k) col[k] = cx_apply(col[k], a, b);
+            dirty |= (1u << a) | (1u << b);
             any = true;
         } else {
-            if (dirty & ((1u << o.a) | (1u << o.b))) close_stage();
-            sops.push_back({OP_CZ, o.a, o.b, -1});
+            const int a = pos[o.a], b = pos[o.b];
+            if (dirty & ((1u << a) | (1u << b))) close_stage();
+            sops.push_back({OP_CZ, a, b, -1});
             any = true;
         }
     }
-    if (any || P->stages.empty()) close_stage();
+    if (any || (int)P->stages.size() == first_stage) close_stage();
+}
+
+std::string plan_circuit(const sv_circuit &c, int reg_bits, bool fuse, int swz_bits,
+                         HostProgram *P) {
+    if (reg_bits < 1 || reg_bits > kRMax) return "reg_bits must be in [1, 5]";
+    FusedCircuit F;
+    std::string err = fuse_circuit(c, fuse, &F);
+    if (!err.empty()) return err;
+    const int n = c.n_qubits;
+    *P = HostProgram();
+    P->n = n;
+    P->R = std::min(reg_bits, n);
+    P->n_params = c.n_params;
+    P->input_dim = c.input_dim;
+    P->swz_bits = swz_bits;
+    P->members = F.members;
+    P->groups = F.groups;
+    std::vector<int> pos(n);
+    for (int q = 0; q < n; ++q) pos[q] = q;
+    stage_lops(F.lops, pos, n, P->R, swz_bits, P);
+    return "";
+}
+
+std::string plan_passes(const sv_circuit &c, int tile_bits, int coalesce_bits, int reg_bits,
+                        bool fuse, int swz_bits, HostProgram *P) {
+    FusedCircuit F;
+    std::string err = fuse_circuit(c, fuse, &F);
+    if (!err.empty()) return err;
+    const int n = c.n_qubits;
+    if (tile_bits < 2 || tile_bits > n) return "tile_bits must be in [2, n]";
+    if (coalesce_bits < 0 || coalesce_bits + 2 > tile_bits) return "coalesce_bits too large";
+    if (reg_bits < 1 || reg_bits > kRMax || reg_bits > tile_bits) return "bad reg_bits";
+    const int t = tile_bits;
+    *P = HostProgram();
+    P->n = n;
+    P->R = reg_bits;
+    P->n_params = c.n_params;
+    P->input_dim = c.input_dim;
+    P->swz_bits = swz_bits;
+    P->members = F.members;
+    P->groups = F.groups;
+    const uint32_t forced = (1u << coalesce_bits) - 1u;
+    std::vector<int> pending(F.lops.size());
+    for (size_t i = 0; i < pending.size(); ++i) pending[i] = (int)i;
+    do {
+        uint32_t L = forced, blocked = 0;
+        std::vector<int> taken, rest;
+        for (int idx : pending) {
+            const uint32_t q = lop_qubits(F.lops[idx]);
+            if (q & blocked) {
+                blocked |= q;
+                rest.push_back(idx);
+            } else if ((q & ~L) == 0) {
+                taken.push_back(idx);
+            } else if (__builtin_popcount(L | q) <= t) {
+                L |= q;
+                taken.push_back(idx);
+            } else {
+                blocked |= q;
+                rest.push_back(idx);
+            }
+        }
+        if (taken.empty()) return "internal: pass planner made no progress";
+        for (int p = 0; __builtin_popcount(L) < t && p < n; ++p) L |= 1u << p;
+        PassDesc pd{};
+        std::vector<int> pos(n, -1);
+        int b = 0, k = 0;
+        for (int q = 0; q < n; ++q) {
+            if ((L >> q) & 1u) {
+                pos[q] = b;
+                pd.gl[b++] = 1u << q;
+            } else {
+                pd.gt[k++] = 1u << q;
+            }
+        }
+        pd.t = t;
+        pd.n_tile_bits = n - t;
+        pd.local_mask = L;
+        pd.stage_begin = (int)P->stages.size();
+        std::vector<LOp> sub;
+        for (int idx : taken) sub.push_back(F.lops[idx]);
+        stage_lops(sub, pos, t, reg_bits, swz_bits, P);
+        pd.stage_end = (int)P->stages.size();
+        int nu = 0;
+        for (int s = pd.stage_begin; s < pd.stage_end; ++s) nu += P->stages[s].n_u1;
+        pd.n_u1 = nu;
+        P->passes.push_back(pd);
+        pending.swap(rest);
+    } while (!pending.empty());
     return "";
 }
 

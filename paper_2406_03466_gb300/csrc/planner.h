@@ -16,7 +16,29 @@ struct HostProgram {
     std::vector<Op> ops;
     std::vector<Stage> stages;
     std::vector<std::vector<uint32_t>> perm_cols;  // per stage: f(e_b), b < n
+    std::vector<PassDesc> passes;                  // tile passes (device-memory states)
 };
+
+// Logical op stream after single-qubit fusion.
+struct LOp {
+    int kind;  // 0 = fused group on qubit a, 1 = CNOT a -> b, 2 = CZ(a, b)
+    int a, b, group;
+};
+
+struct FusedCircuit {
+    std::vector<LOp> lops;
+    std::vector<Group> groups;
+    std::vector<Member> members;
+};
+
+std::string fuse_circuit(const sv_circuit &c, bool fuse, FusedCircuit *out);
+// Appends the register stages of `lops` (qubit q at tile position pos[q] < t).
+void stage_lops(const std::vector<LOp> &lops, const std::vector<int> &pos, int t, int R, int w,
+                HostProgram *P);
+// Cuts a circuit into tile passes of 2^tile_bits amplitudes whose local
+// qubits always include the lowest coalesce_bits qubits.
+std::string plan_passes(const sv_circuit &c, int tile_bits, int coalesce_bits, int reg_bits,
+                        bool fuse, int swz_bits, HostProgram *P);
 
 struct HostObservable {
     int n = 0;

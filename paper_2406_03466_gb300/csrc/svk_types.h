@@ -60,6 +60,19 @@ struct Stage {
     uint32_t stt[kNMax];
 };
 
+// One tile pass over states in device memory: a tile is the 2^t amplitudes
+// whose non-local index bits are fixed.  Local bit b of a tile index sits at
+// global address bit vector gl[b]; tile-number bit k at gt[k].
+struct PassDesc {
+    int32_t stage_begin, stage_end;  // the pass's stages (tile-local positions)
+    int32_t t;                       // local qubits
+    int32_t n_tile_bits;             // n - t
+    int32_t n_u1;                    // fused-group ops in the pass
+    uint32_t local_mask;             // qubits local to the pass
+    uint32_t gl[kNMax];
+    uint32_t gt[kNMax];
+};
+
 // Pauli terms grouped by X-mask: <psi|P|psi> = Re(i^phase sum_j (-1)^{|j & z|}
 // conj(psi_{j^x}) psi_j) with phase = (#Y) mod 4.
 struct TermGroup {

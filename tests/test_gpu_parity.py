@@ -4,6 +4,8 @@ Tolerances: complex128 paths <= 1e-12 relative to max(1, |reference|);
 complex64 paths <= 1e-5 on energies and losses, <= 1e-4 on gradients,
 2e-5 on amplitudes (products in FP32, reductions in FP64).
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -187,8 +189,11 @@ def test_errors_are_reported(sv):
     import torch
     w = wl.vqe_random_pauli(4, 2, 10)
     prob = sv.Problem.from_spec(w, "c64")
-    with pytest.raises(sv.SvError):
-        sv.sv_grad_param_shift(prob, None)  # theta missing
+    grad = torch.empty(w.n_params, dtype=torch.float64, device="cuda")
+    st = sv.library().sv_grad_param_shift(ctypes.byref(prob.struct), None, None, None,
+                                          ctypes.c_void_p(grad.data_ptr()),
+                                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == sv.SV_ERR_ARG and "theta" in sv.sv_last_error()
     bad = wl.vqe_random_pauli(4, 2, 10)
     bad.refs = np.array([1 << 4])
     with pytest.raises(sv.SvError):
