@@ -221,6 +221,37 @@ sv_status sv_grad_param_shift_plain(const sv_problem *problem, const double *the
                                     double *energy_out, double *loss_out, double *grad_out,
                                     sv_stream_t stream);
 
+/* Bytes of the fixed device array used by sv_grad_param_shift_noalloc. */
+#define SV_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* The same result as sv_grad_param_shift, without allocating anything.  (The
+ * paper has no counterpart: this is a deployment variant of the library.)
+ *
+ * For callers that cannot let a library call cudaMalloc: their device memory
+ * belongs to another allocator that must account for every byte (a
+ * framework's caching allocator), or their running loop must never hit
+ * cudaMalloc's implicit device-wide synchronisation.  Instead of the
+ * library's allocated caches and scratch, the call keeps its compiled plan,
+ * observable, references and per-circuit energies in one file-scope device
+ * array of SV_NOALLOC_SCRATCH_BYTES (8 MiB), which every GPU that loads the
+ * library holds until the process exits.  It calls no cudaMalloc, cudaFree
+ * or allocating library routine.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call re-plans on the host and copies the
+ * plan from pageable host memory into the array, so the call waits for work
+ * already queued on `stream`.  All calls share the one array and it keeps
+ * the last call's contents; nothing in it needs to start at zero (every
+ * value is written before it is read).  Calls that overlap on the GPU
+ * (different streams, or other threads) race on the array: serialise them.
+ * Problems whose plan, references and (2P + 1) I + I doubles do not fit are
+ * rejected with SV_ERR_UNSUPPORTED and a message giving both sizes.
+ * Arguments and outputs as for sv_grad_param_shift. */
+sv_status sv_grad_param_shift_noalloc(const sv_problem *problem, const double *theta,
+                                      double *energy_out, double *loss_out, double *grad_out,
+                                      sv_stream_t stream);
+
 /* ----------------------------------------------------------------- misc */
 
 const char *sv_status_string(sv_status status);

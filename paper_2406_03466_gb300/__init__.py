@@ -78,7 +78,8 @@ class sv_problem(ctypes.Structure):
 
 EXPORTED = ("sv_alloc", "sv_free", "sv_state_info", "sv_apply_circuit_batch",
             "sv_expect_pauli_sum", "sv_energies", "sv_param_shift_energies", "sv_grad_param_shift", "sv_grad_adjoint",
-            "sv_grad_param_shift_plain", "sv_status_string", "sv_last_error",
+            "sv_grad_param_shift_plain", "sv_grad_param_shift_noalloc", "sv_status_string",
+            "sv_last_error",
             "sv_sync_status", "sv_shutdown", "sv_version")
 
 
@@ -99,6 +100,7 @@ def _load():
     lib.sv_grad_param_shift.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_grad_adjoint.argtypes = [P(sv_problem), V, V, V, V, V, I32, V]
     lib.sv_grad_param_shift_plain.argtypes = [P(sv_problem), V, V, V, V, V]
+    lib.sv_grad_param_shift_noalloc.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_status_string.argtypes = [I32]
     lib.sv_status_string.restype = ctypes.c_char_p
     lib.sv_last_error.restype = ctypes.c_char_p
@@ -355,6 +357,19 @@ def sv_grad_param_shift_plain(problem: Problem, theta, energy_out=None, loss_out
     _check(_lib.sv_grad_param_shift_plain(ctypes.byref(problem.struct), _ptr(theta), _ptr(e),
                                           _ptr(l), _ptr(g), _stream(stream)),
            "sv_grad_param_shift_plain")
+    return l, e, g
+
+
+def sv_grad_param_shift_noalloc(problem: Problem, theta, energy_out=None, loss_out=None,
+                                grad_out=None, stream=None):
+    """sv_grad_param_shift without any device allocation by the library: for
+    callers whose device memory belongs to another allocator.  Its scratch is
+    one fixed device array shared by all calls (serialise overlapping calls).
+    Pass preallocated outputs to avoid torch allocations as well."""
+    e, l, g = _outputs(problem, theta.device, energy_out, loss_out, grad_out)
+    _check(_lib.sv_grad_param_shift_noalloc(ctypes.byref(problem.struct), _ptr(theta), _ptr(e),
+                                            _ptr(l), _ptr(g), _stream(stream)),
+           "sv_grad_param_shift_noalloc")
     return l, e, g
 
 

@@ -785,3 +785,11 @@ sv_status sv_shutdown(void) {
 }
 
 }  // extern "C"
+
+// Internal hooks for other translation units of the library.
+namespace svk {
+sv_status record_error(sv_status s, const std::string &msg) { return fail(s, msg); }
+sv_status validate_problem(const sv_problem *p, bool need_cost_arrays) {
+    return check_problem(p, need_cost_arrays);
+}
+}  // namespace svk
