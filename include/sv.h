@@ -106,7 +106,8 @@ typedef struct {
     int32_t reg_bits;        /* amplitudes held per thread = 2^reg_bits (1..5); 0 = default */
     int32_t threads_per_block; /* 0 = default */
     int32_t no_fusion;       /* 1 = apply every gate on its own (no 1-qubit gate fusion) */
-    int32_t reserved;
+    int32_t epilogue;        /* <H> epilogue: 0 = default, 1 = per Pauli term, 2 = per-X-group
+                                diagonal tables (states of at most 13 qubits) */
 } sv_plan_opts;
 
 /* ---------------------------------------------------------------- states */
@@ -251,6 +252,20 @@ sv_status sv_grad_param_shift_plain(const sv_problem *problem, const double *the
 sv_status sv_grad_param_shift_noalloc(const sv_problem *problem, const double *theta,
                                       double *energy_out, double *loss_out, double *grad_out,
                                       sv_stream_t stream);
+
+/* ------------------------------------------------------------- autotune */
+
+/* Times the launch shapes (register bits 1..4, 32..512 threads per block) of
+ * the batched parameter-shift energy kernel (kinds bit 1) and of the adjoint
+ * kernel (kinds bit 2) on this problem and remembers the fastest per problem
+ * structure; later calls whose opts leave reg_bits and threads_per_block at
+ * zero use it.  Host-synchronous: launches and times kernels on `stream`,
+ * so do not call it during stream capture.  theta: device [P]. */
+sv_status sv_autotune(const sv_problem *problem, const double *theta, int32_t kinds,
+                      sv_stream_t stream);
+/* The remembered shape for kind 1 (parameter-shift energies) or 2 (adjoint). */
+sv_status sv_tuned_shape(const sv_problem *problem, int32_t kind, int32_t *reg_bits,
+                         int32_t *threads_per_block, float *microseconds);
 
 /* ----------------------------------------------------------------- misc */
 

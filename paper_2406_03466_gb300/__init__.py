@@ -58,7 +58,7 @@ class sv_pauli_sum(ctypes.Structure):
 
 class sv_plan_opts(ctypes.Structure):
     _fields_ = [("reg_bits", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
-                ("no_fusion", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("no_fusion", ctypes.c_int32), ("epilogue", ctypes.c_int32)]
 
 
 class sv_slot(ctypes.Structure):
@@ -78,7 +78,8 @@ class sv_problem(ctypes.Structure):
 
 EXPORTED = ("sv_alloc", "sv_free", "sv_state_info", "sv_apply_circuit_batch",
             "sv_expect_pauli_sum", "sv_energies", "sv_param_shift_energies", "sv_grad_param_shift", "sv_grad_adjoint",
-            "sv_grad_param_shift_plain", "sv_grad_param_shift_noalloc", "sv_status_string",
+            "sv_grad_param_shift_plain", "sv_grad_param_shift_noalloc", "sv_autotune",
+            "sv_tuned_shape", "sv_status_string",
             "sv_last_error",
             "sv_sync_status", "sv_shutdown", "sv_version")
 
@@ -101,6 +102,8 @@ def _load():
     lib.sv_grad_adjoint.argtypes = [P(sv_problem), V, V, V, V, V, I32, V]
     lib.sv_grad_param_shift_plain.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_grad_param_shift_noalloc.argtypes = [P(sv_problem), V, V, V, V, V]
+    lib.sv_autotune.argtypes = [P(sv_problem), V, I32, V]
+    lib.sv_tuned_shape.argtypes = [P(sv_problem), I32, P(I32), P(I32), P(ctypes.c_float)]
     lib.sv_status_string.argtypes = [I32]
     lib.sv_status_string.restype = ctypes.c_char_p
     lib.sv_last_error.restype = ctypes.c_char_p
@@ -182,8 +185,8 @@ class PauliSum:
                                    self._c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
 
 
-def plan_opts(reg_bits=0, threads_per_block=0, no_fusion=False) -> sv_plan_opts:
-    return sv_plan_opts(int(reg_bits), int(threads_per_block), int(bool(no_fusion)), 0)
+def plan_opts(reg_bits=0, threads_per_block=0, no_fusion=False, epilogue=0) -> sv_plan_opts:
+    return sv_plan_opts(int(reg_bits), int(threads_per_block), int(bool(no_fusion)), int(epilogue))
 
 
 class Problem:
@@ -371,6 +374,21 @@ def sv_grad_param_shift_noalloc(problem: Problem, theta, energy_out=None, loss_o
                                             _ptr(l), _ptr(g), _stream(stream)),
            "sv_grad_param_shift_noalloc")
     return l, e, g
+
+
+def sv_autotune(problem: Problem, theta, kinds: int = 3, stream=None) -> None:
+    """Time launch shapes for the parameter-shift energies (kinds & 1) and the
+    adjoint (kinds & 2) of this problem; later calls use the fastest."""
+    _check(_lib.sv_autotune(ctypes.byref(problem.struct), _ptr(theta), int(kinds),
+                            _stream(stream)), "sv_autotune")
+
+
+def sv_tuned_shape(problem: Problem, kind: int):
+    """(reg_bits, threads_per_block, microseconds) chosen by sv_autotune."""
+    r, t, us = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(_lib.sv_tuned_shape(ctypes.byref(problem.struct), int(kind), ctypes.byref(r),
+                               ctypes.byref(t), ctypes.byref(us)), "sv_tuned_shape")
+    return r.value, t.value, us.value
 
 
 def sv_status_string(status: int) -> str:

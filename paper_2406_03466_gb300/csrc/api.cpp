@@ -72,6 +72,7 @@ struct ObsEntry {
     HostObservable host;
     DeviceBuf buf;
     Observable dev{};
+    DeviceBuf dtab;  // diagonal tables D_g(j) for on-chip sizes, or empty
 };
 
 struct ArrayEntry {
@@ -79,8 +80,17 @@ struct ArrayEntry {
     DeviceBuf buf;
 };
 
+// Launch shape chosen by sv_autotune for one problem structure and kernel.
+struct Tuned {
+    int R = 0, tpb = 0, epi = 0;
+    float us = 0.f;
+};
+
 struct DeviceCtx {
     std::mutex mu;
+    int sms = 152;
+    std::unordered_map<uint64_t, Tuned> tuned;
+    std::unordered_map<cudaStream_t, std::unique_ptr<DeviceBuf>> counters;
     std::unordered_map<uint64_t, std::unique_ptr<PlanEntry>> plans;
     std::unordered_map<uint64_t, std::unique_ptr<ObsEntry>> obs;
     std::unordered_map<uint64_t, std::unique_ptr<ArrayEntry>> arrays;
@@ -96,7 +106,12 @@ DeviceCtx *context(int *dev_out = nullptr) {
     if (dev_out) *dev_out = dev;
     std::lock_guard<std::mutex> lk(g_mu);
     auto &p = g_ctx[dev];
-    if (!p) p.reset(new DeviceCtx());
+    if (!p) {
+        p.reset(new DeviceCtx());
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            p->sms = sms;
+    }
     return p.get();
 }
 
@@ -144,6 +159,8 @@ sv_status get_plan(DeviceCtx *ctx, const sv_circuit &c, int R, bool fuse, sv_dty
     size_t o_op = pk.add(h.ops.data(), h.ops.size() * sizeof(Op));
     size_t o_gr = pk.add(h.groups.data(), h.groups.size() * sizeof(Group));
     size_t o_me = pk.add(h.members.data(), h.members.size() * sizeof(Member));
+    size_t o_tb = pk.add(h.tbase.data(), h.tbase.size() * sizeof(ThreadBase));
+    pk.bytes.resize((pk.bytes.size() + 255) & ~size_t(255));  // whole 16-byte units for staging
     e->buf.bytes = pk.bytes.size() ? pk.bytes.size() : 256;
     SV_CUDA(cudaMalloc(&e->buf.ptr, e->buf.bytes));
     if (!pk.bytes.empty())
@@ -161,12 +178,19 @@ sv_status get_plan(DeviceCtx *ctx, const sv_circuit &c, int R, bool fuse, sv_dty
     p.ops = (const Op *)(base + o_op);
     p.groups = (const Group *)(base + o_gr);
     p.members = (const Member *)(base + o_me);
+    p.tbase = h.tbase.empty() ? nullptr : (const ThreadBase *)(base + o_tb);
     *out = e.get();
     ctx->plans[key] = std::move(e);
     return SV_OK;
 }
 
-sv_status get_obs(DeviceCtx *ctx, const sv_pauli_sum &h, int n, sv_dtype dt, ObsEntry **out) {
+// Tables of the diagonals D_g(j) are built for states that fit on chip and
+// tables of at most 2^20 entries.
+constexpr int kDtabMaxQubits = 13;
+constexpr int64_t kDtabMaxEntries = int64_t(1) << 20;
+
+sv_status get_obs(DeviceCtx *ctx, const sv_pauli_sum &h, int n, sv_dtype dt, ObsEntry **out,
+                  cudaStream_t st) {
     if (h.n_terms < 0 || (h.n_terms > 0 && (!h.x_mask || !h.z_mask || !h.coeff)))
         return fail(SV_ERR_ARG, "observable: missing arrays");
     uint64_t key = mix64(hash_observable(h), (uint64_t)swz_bits(dt));
@@ -191,6 +215,7 @@ sv_status get_obs(DeviceCtx *ctx, const sv_pauli_sum &h, int n, sv_dtype dt, Obs
     Packer pk;
     size_t o_g = pk.add(e->host.tgroups.data(), e->host.tgroups.size() * sizeof(TermGroup));
     size_t o_t = pk.add(e->host.terms.data(), e->host.terms.size() * sizeof(Term));
+    pk.bytes.resize((pk.bytes.size() + 255) & ~size_t(255));
     e->buf.bytes = pk.bytes.size() ? pk.bytes.size() : 256;
     SV_CUDA(cudaMalloc(&e->buf.ptr, e->buf.bytes));
     if (!pk.bytes.empty())
@@ -200,6 +225,13 @@ sv_status get_obs(DeviceCtx *ctx, const sv_pauli_sum &h, int n, sv_dtype dt, Obs
     e->dev.n_terms = (int)e->host.terms.size();
     e->dev.tgroups = (const TermGroup *)(base + o_g);
     e->dev.terms = (const Term *)(base + o_t);
+    const int64_t entries = (int64_t(1) << n) * e->dev.n_tgroups;
+    if (n <= kDtabMaxQubits && entries > 0 && entries <= kDtabMaxEntries) {
+        e->dtab.bytes = (size_t)entries * (dt == SV_C128 ? 16 : 8);
+        SV_CUDA(cudaMalloc(&e->dtab.ptr, e->dtab.bytes));
+        SV_CUDA(launch_build_dtable(dt == SV_C128, e->dev, n, e->dtab.ptr, st));
+        SV_CUDA(cudaStreamSynchronize(st));  // usable from any stream afterwards
+    }
     *out = e.get();
     ctx->obs[key] = std::move(e);
     return SV_OK;
@@ -221,6 +253,20 @@ sv_status get_array(DeviceCtx *ctx, const void *host, size_t bytes, const void *
     if (bytes) SV_CUDA(cudaMemcpy(e->buf.ptr, host, bytes, cudaMemcpyHostToDevice));
     *dev = e->buf.ptr;
     ctx->arrays[key] = std::move(e);
+    return SV_OK;
+}
+
+// A zeroed counter for the energy kernel's last-block gradient assembly (the
+// kernel resets it to zero when it finishes).
+sv_status get_counter(DeviceCtx *ctx, cudaStream_t st, unsigned **out) {
+    auto &c = ctx->counters[st];
+    if (!c) {
+        c.reset(new DeviceBuf());
+        SV_CUDA(cudaMalloc(&c->ptr, 256));
+        c->bytes = 256;
+        SV_CUDA(cudaMemsetAsync(c->ptr, 0, 256, st));
+    }
+    *out = (unsigned *)c->ptr;
     return SV_OK;
 }
 
@@ -259,22 +305,70 @@ bool use_fusion(const sv_plan_opts *o) { return !(o && o->no_fusion); }
 
 // Planner register bits for a kernel kind: the launch shape decides R first.
 sv_status shape_for(int kind, const sv_circuit &c, int n_groups_hint, sv_dtype dt, int n_slots,
-                    const sv_plan_opts *opts, OnchipShape *sh) {
+                    const sv_plan_opts *opts, OnchipShape *sh, int sms, uint32_t const_bytes = 0) {
     const char *err = onchip_shape(kind, c.n_qubits, n_groups_hint, c.n_params, dt == SV_C128,
-                                   n_slots, default_regbits(opts), default_tpb(opts), sh);
+                                   n_slots, default_regbits(opts), default_tpb(opts), sh, sms,
+                                   const_bytes);
     if (err) return fail(SV_ERR_UNSUPPORTED, err);
     return SV_OK;
 }
 
-// Plan + final launch shape (the shape needs the group count of the plan).
+// The arrays a block copies into shared memory before it starts.
+BlockConst make_block_const(const PlanEntry *plan, const ObsEntry *obs, const void *dtab,
+                            bool with_tbase) {
+    BlockConst b{};
+    uint32_t off = 0;
+    auto add = [&](int k, const void *src, size_t bytes) {
+        if (!src || !bytes) return;
+        const uint32_t n16 = (uint32_t)((bytes + 15) / 16);
+        b.src[k] = (const uint4 *)src;
+        b.n16[k] = n16;
+        b.off[k] = off;
+        off += n16 * 16;
+    };
+    const HostProgram &h = plan->host;
+    add(0, plan->dev.stages, h.stages.size() * sizeof(Stage));
+    add(1, plan->dev.ops, h.ops.size() * sizeof(Op));
+    add(2, plan->dev.groups, h.groups.size() * sizeof(Group));
+    add(3, plan->dev.members, h.members.size() * sizeof(Member));
+    if (with_tbase) add(7, plan->dev.tbase, h.tbase.size() * sizeof(ThreadBase));
+    if (obs) {
+        add(4, obs->dev.tgroups, obs->host.tgroups.size() * sizeof(TermGroup));
+        add(5, obs->dev.terms, obs->host.terms.size() * sizeof(Term));
+        if (dtab) add(6, dtab, obs->dtab.bytes);
+    }
+    b.bytes = off;
+    return b;
+}
+
+// Plan + final launch shape (the shape needs the group count of the plan and
+// the size of the block-constant arrays when `bc` is requested).
 sv_status plan_and_shape(DeviceCtx *ctx, int kind, const sv_circuit &c, sv_dtype dt, int n_slots,
-                         const sv_plan_opts *opts, PlanEntry **plan, OnchipShape *sh) {
+                         const sv_plan_opts *opts, PlanEntry **plan, OnchipShape *sh,
+                         const Tuned *tuned = nullptr, const ObsEntry *obs = nullptr,
+                         const void *dtab = nullptr, BlockConst *bc = nullptr) {
+    sv_plan_opts o2{};
+    if (tuned && !(opts && (opts->reg_bits > 0 || opts->threads_per_block > 0))) {
+        if (opts) o2 = *opts;
+        o2.reg_bits = tuned->R;
+        o2.threads_per_block = tuned->tpb;
+        opts = &o2;
+    }
     OnchipShape pre{};
-    sv_status s = shape_for(kind, c, 0, dt, n_slots, opts, &pre);
+    sv_status s = shape_for(kind, c, 0, dt, n_slots, opts, &pre, ctx->sms);
     if (s != SV_OK) return s;
     s = get_plan(ctx, c, pre.R, use_fusion(opts), dt, plan);
     if (s != SV_OK) return s;
-    return shape_for(kind, c, (*plan)->dev.n_groups, dt, n_slots, opts, sh);
+    if (!bc) return shape_for(kind, c, (*plan)->dev.n_groups, dt, n_slots, opts, sh, ctx->sms, 0);
+    // Stage as much as fits: everything, then without the tables, then
+    // without the thread bases, then only the program and terms.
+    for (int variant = 0; variant < 4; ++variant) {
+        *bc = make_block_const(*plan, obs, (variant & 1) ? nullptr : dtab, !(variant & 2));
+        s = shape_for(kind, c, (*plan)->dev.n_groups, dt, n_slots, opts, sh, ctx->sms, bc->bytes);
+        if (s != SV_OK) return s;
+        if (sh->const_bytes || !bc->bytes) return SV_OK;
+    }
+    return SV_OK;
 }
 
 sv_status check_problem(const sv_problem *p, bool need_cost_arrays) {
@@ -298,6 +392,27 @@ sv_status check_problem(const sv_problem *p, bool need_cost_arrays) {
     }
     if (p->cost != SV_COST_LINEAR && p->cost != SV_COST_MSE) return fail(SV_ERR_ARG, "bad cost");
     return SV_OK;
+}
+
+uint64_t tune_key(const sv_problem *p, int kind, int n_slots) {
+    uint64_t k = mix64(hash_circuit(*p->circuit), hash_observable(*p->observable));
+    k = mix64(k, (uint64_t)kind);
+    k = mix64(k, (uint64_t)n_slots);
+    k = mix64(k, (uint64_t)p->dtype);
+    k = mix64(k, (uint64_t)use_fusion(p->opts));
+    return k;
+}
+
+const Tuned *find_tuned(DeviceCtx *ctx, const sv_problem *p, int kind, int n_slots) {
+    auto it = ctx->tuned.find(tune_key(p, kind, n_slots));
+    return it == ctx->tuned.end() ? nullptr : &it->second;
+}
+
+// The expectation epilogue: diagonal tables when requested (or tuned, or by
+// default) and available, otherwise the per-term loop.
+const void *pick_dtab(const ObsEntry *obs, const sv_plan_opts *opts, const Tuned *t) {
+    int epi = (opts && opts->epilogue > 0) ? opts->epilogue : (t && t->epi > 0 ? t->epi : 2);
+    return epi == 2 ? obs->dtab.ptr : nullptr;
 }
 
 CostSource cost_of(const sv_problem *p, const double *ext) {
@@ -465,11 +580,11 @@ sv_status sv_expect_pauli_sum(sv_state state, const sv_pauli_sum *h, int32_t n_r
     if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
     std::lock_guard<std::mutex> lk(ctx->mu);
     ObsEntry *obs = nullptr;
-    sv_status s = get_obs(ctx, *h, state->n, state->dtype, &obs);
+    sv_status s = get_obs(ctx, *h, state->n, state->dtype, &obs, (cudaStream_t)stream);
     if (s != SV_OK) return s;
     OnchipShape sh{};
     const char *err = onchip_shape(ONCHIP_EXPECT, state->n, 0, 0, state->dtype == SV_C128, n_rows,
-                                   0, 0, &sh);
+                                   0, 0, &sh, ctx->sms);
     if (err) return fail(SV_ERR_UNSUPPORTED, err);
     cudaError_t e = launch_onchip_expect(state->dtype == SV_C128, sh, state->n,
                                          swz_bits(state->dtype), obs->dev, state->ptr, n_rows,
@@ -480,16 +595,21 @@ sv_status sv_expect_pauli_sum(sv_state state, const sv_pauli_sum *h, int32_t n_r
 
 namespace {
 
-// Launches the batched energies of every parameter-shift slot into E[B].
+// Launches the batched energies of every parameter-shift slot into E[B]
+// (and, with `fc`, the gradient assembly in the same launch).
 sv_status ps_energies_locked(DeviceCtx *ctx, const sv_problem *p, const double *theta, double *E,
-                             int B, cudaStream_t st) {
+                             int B, cudaStream_t st, const FusedCombine *fc = nullptr) {
     const int I = p->n_instances;
     PlanEntry *plan = nullptr;
     OnchipShape sh{};
-    sv_status s = plan_and_shape(ctx, ONCHIP_ENERGY, *p->circuit, p->dtype, B, p->opts, &plan, &sh);
-    if (s != SV_OK) return s;
     ObsEntry *obs = nullptr;
-    s = get_obs(ctx, *p->observable, p->circuit->n_qubits, p->dtype, &obs);
+    sv_status s = get_obs(ctx, *p->observable, p->circuit->n_qubits, p->dtype, &obs, st);
+    if (s != SV_OK) return s;
+    const Tuned *tn = find_tuned(ctx, p, ONCHIP_ENERGY, B);
+    const void *dtab = pick_dtab(obs, p->opts, tn);
+    BlockConst bc{};
+    s = plan_and_shape(ctx, ONCHIP_ENERGY, *p->circuit, p->dtype, B, p->opts, &plan, &sh, tn, obs,
+                       dtab, &bc);
     if (s != SV_OK) return s;
     const void *drefs = nullptr;
     s = get_array(ctx, p->refs, sizeof(int64_t) * I, &drefs);
@@ -502,7 +622,8 @@ sv_status ps_energies_locked(DeviceCtx *ctx, const sv_problem *p, const double *
     src.theta = theta;
     src.inputs = p->inputs;
     src.input_stride = p->input_stride;
-    cudaError_t e = launch_onchip_energy(p->dtype == SV_C128, sh, plan->dev, obs->dev, src, E, st);
+    cudaError_t e = launch_onchip_energy(p->dtype == SV_C128, sh, plan->dev, obs->dev, src, E, st,
+                                         dtab, fc, &bc);
     if (e != cudaSuccess) return cuda_fail(e, "param-shift energy launch");
     return SV_OK;
 }
@@ -548,12 +669,19 @@ sv_status sv_grad_param_shift(const sv_problem *p, const double *theta, double *
     s = get_scratch(ctx, st, sizeof(double) * ((size_t)B + I), &scr);
     if (s != SV_OK) return s;
     double *E = (double *)scr, *lp = E + B;
-    s = ps_energies_locked(ctx, p, theta, E, B, st);
+    unsigned *counter = nullptr;
+    s = get_counter(ctx, st, &counter);
     if (s != SV_OK) return s;
-    cudaError_t e = launch_ps_combine(E, I, P, cost_of(p, nullptr), lp, energy_out, loss_out,
-                                      grad_out, st);
-    if (e != cudaSuccess) return cuda_fail(e, "param-shift combine launch");
-    return SV_OK;
+    FusedCombine fc{};
+    fc.counter = counter;
+    fc.I = I;
+    fc.P = P;
+    fc.cost = cost_of(p, nullptr);
+    fc.lp = lp;
+    fc.energy_out = energy_out;
+    fc.loss_out = loss_out;
+    fc.grad_out = grad_out;
+    return ps_energies_locked(ctx, p, theta, E, B, st, &fc);
 }
 
 sv_status sv_energies(const sv_problem *p, const double *theta, double *energy_out,
@@ -569,10 +697,13 @@ sv_status sv_energies(const sv_problem *p, const double *theta, double *energy_o
     cudaStream_t st = (cudaStream_t)stream;
     PlanEntry *plan = nullptr;
     OnchipShape sh{};
-    s = plan_and_shape(ctx, ONCHIP_ENERGY, *p->circuit, p->dtype, I, p->opts, &plan, &sh);
-    if (s != SV_OK) return s;
     ObsEntry *obs = nullptr;
-    s = get_obs(ctx, *p->observable, p->circuit->n_qubits, p->dtype, &obs);
+    s = get_obs(ctx, *p->observable, p->circuit->n_qubits, p->dtype, &obs, st);
+    if (s != SV_OK) return s;
+    const void *dtab = pick_dtab(obs, p->opts, nullptr);
+    BlockConst bc{};
+    s = plan_and_shape(ctx, ONCHIP_ENERGY, *p->circuit, p->dtype, I, p->opts, &plan, &sh, nullptr,
+                       obs, dtab, &bc);
     if (s != SV_OK) return s;
     const void *drefs = nullptr;
     s = get_array(ctx, p->refs, sizeof(int64_t) * I, &drefs);
@@ -586,7 +717,7 @@ sv_status sv_energies(const sv_problem *p, const double *theta, double *energy_o
     src.inputs = p->inputs;
     src.input_stride = p->input_stride;
     cudaError_t e = launch_onchip_energy(p->dtype == SV_C128, sh, plan->dev, obs->dev, src,
-                                         energy_out, st);
+                                         energy_out, st, dtab, nullptr, &bc);
     if (e != cudaSuccess) return cuda_fail(e, "energy launch");
     if (loss_out) {
         void *scr = nullptr;
@@ -613,10 +744,12 @@ sv_status sv_grad_adjoint(const sv_problem *p, const double *theta, const double
     cudaStream_t st = (cudaStream_t)stream;
     PlanEntry *plan = nullptr;
     OnchipShape sh{};
-    s = plan_and_shape(ctx, ONCHIP_ADJOINT, *p->circuit, p->dtype, I, p->opts, &plan, &sh);
-    if (s != SV_OK) return s;
     ObsEntry *obs = nullptr;
-    s = get_obs(ctx, *p->observable, p->circuit->n_qubits, p->dtype, &obs);
+    s = get_obs(ctx, *p->observable, p->circuit->n_qubits, p->dtype, &obs, st);
+    if (s != SV_OK) return s;
+    BlockConst bc{};
+    s = plan_and_shape(ctx, ONCHIP_ADJOINT, *p->circuit, p->dtype, I, p->opts, &plan, &sh,
+                       find_tuned(ctx, p, ONCHIP_ADJOINT, I), obs, nullptr, &bc);
     if (s != SV_OK) return s;
     const void *drefs = nullptr;
     s = get_array(ctx, p->refs, sizeof(int64_t) * I, &drefs);
@@ -635,7 +768,7 @@ sv_status sv_grad_adjoint(const sv_problem *p, const double *theta, const double
     src.input_stride = p->input_stride;
     const CostSource cs = cost_of(p, weights);
     cudaError_t e = launch_onchip_adjoint(p->dtype == SV_C128, sh, plan->dev, obs->dev, src, cs,
-                                          G, E, st);
+                                          G, E, st, &bc);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
     e = launch_adjoint_combine(G, E, I, P, cs, energy_out, loss_out, grad_out, st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint combine launch");
@@ -759,6 +892,117 @@ sv_status sv_grad_param_shift_plain(const sv_problem *p, const double *theta, do
     cudaError_t e = launch_ps_combine(E, I, P, cost_of(p, nullptr), lp, energy_out, loss_out,
                                       grad_out, st);
     if (e != cudaSuccess) return cuda_fail(e, "plain combine");
+    return SV_OK;
+}
+
+sv_status sv_autotune(const sv_problem *p, const double *theta, int32_t kinds,
+                      sv_stream_t stream) {
+    sv_status s = check_problem(p, true);
+    if (s != SV_OK) return s;
+    if (p->circuit->n_params > 0 && !theta) return fail(SV_ERR_ARG, "theta is NULL");
+    if (kinds & ~3) return fail(SV_ERR_ARG, "kinds must be a combination of 1 and 2");
+    const int P = p->circuit->n_params, I = p->n_instances, n = p->circuit->n_qubits;
+    int B = 0;
+    s = ps_batch_size(p, &B);
+    if (s != SV_OK) return s;
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    ObsEntry *obs = nullptr;
+    s = get_obs(ctx, *p->observable, n, p->dtype, &obs, st);
+    if (s != SV_OK) return s;
+    const void *drefs = nullptr;
+    s = get_array(ctx, p->refs, sizeof(int64_t) * I, &drefs);
+    if (s != SV_OK) return s;
+    const size_t need = sizeof(double) * ((size_t)B + (size_t)I * (P > 0 ? P : 1) + 2 * I);
+    void *scr = nullptr;
+    s = get_scratch(ctx, st, need, &scr);
+    if (s != SV_OK) return s;
+    double *E = (double *)scr, *G = E + B, *E2 = G + (size_t)I * (P > 0 ? P : 1);
+    cudaEvent_t e0, e1;
+    SV_CUDA(cudaEventCreate(&e0));
+    SV_CUDA(cudaEventCreate(&e1));
+    const int rmax = p->dtype == SV_C128 ? 3 : 4;
+    const int tpbs[] = {32, 64, 128, 256, 512};
+    for (int kind : {ONCHIP_ENERGY, ONCHIP_ADJOINT}) {
+        if (!(kinds & (kind == ONCHIP_ENERGY ? 1 : 2))) continue;
+        const int slots = kind == ONCHIP_ENERGY ? B : I;
+        Tuned best;
+        best.us = 1e30f;
+        for (int epi = 1; epi <= (kind == ONCHIP_ENERGY && obs->dtab.ptr ? 2 : 1); ++epi)
+        for (int R = 1; R <= rmax && R <= n; ++R) {
+            for (int tpb : tpbs) {
+                sv_plan_opts o{};
+                if (p->opts) o = *p->opts;
+                o.reg_bits = R;
+                o.threads_per_block = tpb;
+                PlanEntry *plan = nullptr;
+                OnchipShape sh{};
+                const void *dt = (kind == ONCHIP_ENERGY && epi == 2) ? obs->dtab.ptr : nullptr;
+                BlockConst bc{};
+                if (plan_and_shape(ctx, kind, *p->circuit, p->dtype, slots, &o, &plan, &sh, nullptr,
+                                   obs, dt, &bc) != SV_OK)
+                    continue;
+                SlotSource src{};
+                src.mode = kind == ONCHIP_ENERGY ? SLOTS_PARAM_SHIFT : SLOTS_INSTANCES;
+                src.n_slots = slots;
+                src.n_instances = I;
+                src.refs = (const int64_t *)drefs;
+                src.theta = theta;
+                src.inputs = p->inputs;
+                src.input_stride = p->input_stride;
+                const CostSource cs = cost_of(p, nullptr);
+                auto run = [&]() {
+                    return kind == ONCHIP_ENERGY
+                               ? launch_onchip_energy(p->dtype == SV_C128, sh, plan->dev, obs->dev,
+                                                      src, E, st, dt, nullptr, &bc)
+                               : launch_onchip_adjoint(p->dtype == SV_C128, sh, plan->dev, obs->dev,
+                                                       src, cs, G, E2, st, &bc);
+                };
+                if (run() != cudaSuccess) {
+                    cudaGetLastError();
+                    continue;
+                }
+                float tbest = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    SV_CUDA(cudaEventRecord(e0, st));
+                    SV_CUDA(run());
+                    SV_CUDA(cudaEventRecord(e1, st));
+                    SV_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    SV_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    if (ms < tbest) tbest = ms;
+                }
+                if (tbest * 1e3f < best.us) {
+                    best.us = tbest * 1e3f;
+                    best.R = sh.R;
+                    best.tpb = sh.S * sh.Ts;
+                    best.epi = kind == ONCHIP_ENERGY ? epi : 0;
+                }
+            }
+        }
+        if (best.R > 0) ctx->tuned[tune_key(p, kind, slots)] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return SV_OK;
+}
+
+sv_status sv_tuned_shape(const sv_problem *p, int32_t kind, int32_t *reg_bits,
+                         int32_t *threads_per_block, float *us) {
+    if (!p || !p->circuit || !p->observable) return fail(SV_ERR_ARG, "problem is NULL");
+    if (kind != 1 && kind != 2) return fail(SV_ERR_ARG, "kind must be 1 or 2");
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const int B = (2 * p->circuit->n_params + 1) * p->n_instances;
+    const Tuned *t = kind == 1 ? find_tuned(ctx, p, ONCHIP_ENERGY, B)
+                               : find_tuned(ctx, p, ONCHIP_ADJOINT, p->n_instances);
+    if (!t) return fail(SV_ERR_ARG, "no tuned shape for this problem");
+    if (reg_bits) *reg_bits = t->R;
+    if (threads_per_block) *threads_per_block = t->tpb;
+    if (us) *us = t->us;
     return SV_OK;
 }
 

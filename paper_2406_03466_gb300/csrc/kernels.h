@@ -48,16 +48,48 @@ struct OnchipShape {
     uint32_t smem;   // dynamic shared memory per block
     uint32_t off_lam, off_mats, off_rho, off_grad, off_rhow, off_red;
     uint32_t st_state, st_mats, st_rho, st_grad, st_rhow;
+    uint32_t off_const, const_bytes;  // block-constant region (0 bytes = not staged)
 };
 
-// Shapes (or an error string) for the three on-chip kernels.
+// Block-constant arrays (program, observable, diagonal tables) that a block
+// copies into its shared memory before it starts, so that the stage loop
+// and the epilogue never wait on global memory.  Slot k: 0 stages, 1 ops,
+// 2 groups, 3 members, 4 term groups, 5 terms, 6 diagonal tables, 7 thread
+// bases of every stage.  Sizes are
+// in 16-byte units; the global arrays are padded to whole 16-byte units.
+constexpr int kBlockConst = 8;  // slot 7: per-thread stage bases
+struct BlockConst {
+    const uint4 *src[kBlockConst];
+    uint32_t n16[kBlockConst];
+    uint32_t off[kBlockConst];  // byte offset inside the block-constant region
+    uint32_t base;              // byte offset of the region in dynamic shared memory
+    uint32_t bytes;             // region size (0 = read everything from global memory)
+};
+
+// Shapes (or an error string) for the on-chip kernels; `const_bytes` of
+// block-constant data are appended to the shared-memory layout when they fit.
 const char *onchip_shape(int kind, int n, int n_groups, int n_params, int c128, int n_slots,
-                         int reg_bits, int threads_per_block, OnchipShape *out);
+                         int reg_bits, int threads_per_block, OnchipShape *out,
+                         int num_sms = 152, uint32_t const_bytes = 0);
 enum OnchipKind { ONCHIP_ENERGY = 0, ONCHIP_STORE = 1, ONCHIP_EXPECT = 2, ONCHIP_ADJOINT = 3 };
 
+// Gradient assembly done by the last block of the energy kernel.
+struct FusedCombine {
+    unsigned *counter;  // zero before the launch; the last block resets it
+    int32_t I, P;
+    CostSource cost;
+    double *lp;         // [I] scratch
+    double *energy_out, *loss_out, *grad_out;
+};
+
+// dtab: diagonal tables of the observable ([groups][2^n] complex of the
+// state's precision) or NULL for the per-term epilogue; fc: NULL or the
+// fused gradient assembly.
 cudaError_t launch_onchip_energy(int c128, const OnchipShape &sh, const Program &p,
                                  const Observable &o, const SlotSource &s, double *energies,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const void *dtab = nullptr,
+                                 const FusedCombine *fc = nullptr, const BlockConst *bc = nullptr);
+cudaError_t launch_build_dtable(int c128, const Observable &o, int n, void *out, cudaStream_t st);
 cudaError_t launch_onchip_store(int c128, const OnchipShape &sh, const Program &p,
                                 const SlotSource &s, void *states, cudaStream_t st);
 cudaError_t launch_onchip_expect(int c128, const OnchipShape &sh, int n, int swz_bits,
@@ -65,7 +97,8 @@ cudaError_t launch_onchip_expect(int c128, const OnchipShape &sh, int n, int swz
                                  double *out, cudaStream_t st);
 cudaError_t launch_onchip_adjoint(int c128, const OnchipShape &sh, const Program &p,
                                   const Observable &o, const SlotSource &s, const CostSource &c,
-                                  double *slot_grads, double *slot_energies, cudaStream_t st);
+                                  double *slot_grads, double *slot_energies, cudaStream_t st,
+                                  const BlockConst *bc = nullptr);
 
 cudaError_t launch_ps_combine(const double *E, int I, int P, const CostSource &c,
                               double *lprime_scratch, double *energy_out, double *loss_out,

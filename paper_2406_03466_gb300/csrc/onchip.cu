@@ -263,6 +263,25 @@ struct Bases {
     uint32_t lb, sb, lg;
 };
 
+__device__ __forceinline__ Bases stage_bases(const Stage *sg, int tid);
+
+// Thread bases of stage s.  kMode 0: program in global memory (precomputed
+// table when the plan has one); 1: program staged in shared memory, bases
+// computed from the stage record; 2: table staged in shared memory.
+template <int kMode>
+__device__ __forceinline__ Bases bases_of(const Program &p, int s, int tid, int Ts) {
+    if constexpr (kMode == 2) {
+        const uint4 v = reinterpret_cast<const uint4 *>(p.tbase)[(size_t)s * Ts + tid];
+        return Bases{v.x, v.y, v.z};
+    } else if constexpr (kMode == 0) {
+        if (p.tbase) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p.tbase) + (size_t)s * Ts + tid);
+            return Bases{v.x, v.y, v.z};
+        }
+    }
+    return stage_bases(p.stages + s, tid);
+}
+
 __device__ __forceinline__ Bases stage_bases(const Stage *sg, int tid) {
     Bases b{0u, 0u, 0u};
     const int nt = sg->n_thr;
@@ -292,14 +311,17 @@ __device__ __forceinline__ void apply_stage_ops(const Program &p, const Stage *s
 
 // Runs every stage; the final state is left in shared memory `st` (natural
 // index order, swizzled).  Stage 0 builds |ref> in registers.
-template <typename Real, int R>
+template <typename Real, int R, int kMode>
 __device__ void forward_stages(const Program &p, typename CT<Real>::T *st,
                                const typename CT<Real>::T *mats, int tid, int64_t ref) {
     using C = typename CT<Real>::T;
     C a[1 << R];
+    const int Ts = 1 << (p.n - R);
+    Bases nxt = bases_of<kMode>(p, 0, tid, Ts);
     for (int s = 0; s < p.n_stages; ++s) {
         const Stage *sg = p.stages + s;
-        const Bases bs = stage_bases(sg, tid);
+        const Bases bs = nxt;
+        if (s + 1 < p.n_stages) nxt = bases_of<kMode>(p, s + 1, tid, Ts);
         uint32_t lq[R], sq[R];
         int qq[R];
 #pragma unroll
@@ -395,6 +417,38 @@ __device__ double expect_partial(const Observable &o, const typename CT<Real>::T
     return e;
 }
 
+// Same sum from precomputed diagonals: for each X-mask group g,
+// D_g(j) = sum_{t in g} c_t i^{phase_t} (-1)^{|j & z_t|} (table `dtab`,
+// [groups][2^n] complex in natural index order), E = sum_g sum_j
+// Re(conj(psi_{j^x}) psi_j D_g(j)).
+template <typename Real, int R>
+__device__ double expect_table(const Observable &o, const typename CT<Real>::T *dtab,
+                               const typename CT<Real>::T *st, int tid, int sh, int w, int dim) {
+    using C = typename CT<Real>::T;
+    constexpr int NA = 1 << R;
+    uint32_t v[R];
+    const uint32_t s0 = natural_vectors<R>(tid, sh, w, v);
+    C pj[NA];
+#pragma unroll
+    for (int k = 0; k < NA; ++k) pj[k] = st[s0 ^ xsel<R>(k, v)];
+    double e = 0.0;
+    for (int g = 0; g < o.n_tgroups; ++g) {
+        const uint32_t sx = o.tgroups[g].sx;
+        const C *D = dtab + (size_t)g * dim + tid;
+        Real acc = 0;
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+            const C px = st[s0 ^ xsel<R>(k, v) ^ sx];
+            const C d = D[(size_t)k << sh];  // shared memory when staged, else global
+            const Real wr = fmaR(px.x, pj[k].x, px.y * pj[k].y);
+            const Real wi = fmaR(px.x, pj[k].y, -px.y * pj[k].x);
+            acc = fmaR(wr, d.x, fmaR(-wi, d.y, acc));
+        }
+        e += (double)acc;
+    }
+    return e;
+}
+
 // lambda = H psi for this thread's amplitudes; returns sum Re(conj(psi_j) lambda_j).
 template <typename Real, int R>
 __device__ double apply_h(const Observable &o, const typename CT<Real>::T *psi,
@@ -437,13 +491,78 @@ __device__ double apply_h(const Observable &o, const typename CT<Real>::T *psi,
     return e;
 }
 
+// Parameter-shift combination by one block: dL/dtheta_k = sum_i L'_i
+// (E_{k+,i} - E_{k-,i}) / 2, the energies and the cost.  `red`: 32 doubles.
+__device__ void ps_combine_block(const double *E, int I, int P, const CostSource &c, double *lp,
+                                 double *energy_out, double *loss_out, double *grad_out,
+                                 double *red) {
+    double part = 0.0;
+    for (int i = threadIdx.x; i < I; i += blockDim.x) {
+        const double e = __ldcg(E + i);
+        if (energy_out) energy_out[i] = e;
+        if (c.cost == SV_COST_MSE) {
+            const double d = e - c.targets[i];
+            part += d * d / I;
+        } else {
+            part += c.weights[i] * e;
+        }
+        lp[i] = c.ext_weights ? c.ext_weights[i]
+                              : (c.cost == SV_COST_MSE ? 2.0 * (e - c.targets[i]) / I : c.weights[i]);
+    }
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0 && loss_out) {
+        double s = 0.0;
+        for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) s += red[wi];
+        loss_out[0] = s;
+    }
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        const double *ep = E + I + (int64_t)2 * k * I, *em = ep + I;
+        double g = 0.0;
+#pragma unroll 8
+        for (int i = 0; i < I; ++i) g += lp[i] * 0.5 * (__ldcg(ep + i) - __ldcg(em + i));
+        grad_out[k] = g;
+    }
+}
+
+// Copies the block-constant arrays into shared memory (independent 16-byte
+// loads from every thread) and points the program/observable views at them.
+// (kMode >= 1) Copies the block-constant arrays into shared memory with
+// independent 16-byte loads from every thread and points the program and
+// observable views at the copies.  The pointers are derived from the shared
+// array unconditionally, so every later read compiles to a shared load.
+template <int kMode>
+__device__ __forceinline__ void stage_block_const(const BlockConst &bc, unsigned char *smem,
+                                                  Program &p, Observable &o) {
+    if constexpr (kMode == 0) return;
+    unsigned char *base = smem + bc.base;
+#pragma unroll
+    for (int k = 0; k < kBlockConst; ++k) {
+        uint4 *dst = reinterpret_cast<uint4 *>(base + bc.off[k]);
+        const uint4 *src = bc.src[k];
+        for (uint32_t i = threadIdx.x; i < bc.n16[k]; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    __syncthreads();
+    p.stages = reinterpret_cast<const Stage *>(base + bc.off[0]);
+    p.ops = reinterpret_cast<const Op *>(base + bc.off[1]);
+    p.groups = reinterpret_cast<const Group *>(base + bc.off[2]);
+    p.members = reinterpret_cast<const Member *>(base + bc.off[3]);
+    o.tgroups = reinterpret_cast<const TermGroup *>(base + bc.off[4]);
+    o.terms = reinterpret_cast<const Term *>(base + bc.off[5]);
+    if constexpr (kMode == 2) p.tbase = reinterpret_cast<const ThreadBase *>(base + bc.off[7]);
+}
+
 // ---------------------------------------------------------------- kernels
 
-template <typename Real, int R>
+template <typename Real, int R, int kMode>
 __global__ void __launch_bounds__(512) k_energy(Program p, Observable o, SlotSource src,
-                                                OnchipShape sh, double *energies) {
+                                                OnchipShape sh, double *energies,
+                                                const typename CT<Real>::T *dtab,
+                                                FusedCombine fc, BlockConst bc) {
     using C = typename CT<Real>::T;
     extern __shared__ __align__(16) unsigned char smem[];
+    stage_block_const<kMode>(bc, smem, p, o);
     const int n = p.n, shb = n - R, Ts = 1 << shb;
     const int ls = threadIdx.x >> shb, tid = threadIdx.x & (Ts - 1);
     const int b = blockIdx.x * sh.S + ls;
@@ -455,10 +574,31 @@ __global__ void __launch_bounds__(512) k_energy(Program p, Observable o, SlotSou
     const SlotInfo si = resolve(src, live ? b : 0);
     for (int g = tid; g < p.n_groups; g += Ts) group_matrix<Real, C>(p, g, si, mats + 4 * g);
     __syncthreads();
-    forward_stages<Real, R>(p, st, mats, tid, si.ref);
-    double e = expect_partial<Real, R>(o, st, tid, shb, p.swz_bits);
+    forward_stages<Real, R, kMode>(p, st, mats, tid, si.ref);
+    double e;
+    if (kMode > 0 && bc.n16[6]) {  // diagonal tables staged in shared memory
+        const C *tab = reinterpret_cast<const C *>(smem + bc.base + bc.off[6]);
+        e = expect_table<Real, R>(o, tab, st, tid, shb, p.swz_bits, 1 << n);
+    } else if (dtab) {
+        e = expect_table<Real, R>(o, dtab, st, tid, shb, p.swz_bits, 1 << n);
+    } else {
+        e = expect_partial<Real, R>(o, st, tid, shb, p.swz_bits);
+    }
     e = slot_sum(e, Ts, red);
     if (live && tid == 0) energies[b] = e;
+    if (!fc.counter) return;
+    // The last block to finish assembles the gradient (no second launch).
+    __shared__ unsigned last;
+    __shared__ double cred[32];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(fc.counter, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    ps_combine_block(energies, fc.I, fc.P, fc.cost, fc.lp, fc.energy_out, fc.loss_out,
+                     fc.grad_out, cred);
+    if (threadIdx.x == 0) *fc.counter = 0u;
 }
 
 template <typename Real, int R>
@@ -476,7 +616,7 @@ __global__ void __launch_bounds__(512) k_store(Program p, SlotSource src, Onchip
     const SlotInfo si = resolve(src, live ? b : 0);
     for (int g = tid; g < p.n_groups; g += Ts) group_matrix<Real, C>(p, g, si, mats + 4 * g);
     __syncthreads();
-    forward_stages<Real, R>(p, st, mats, tid, si.ref);
+    forward_stages<Real, R, 0>(p, st, mats, tid, si.ref);
     if (!live) return;
     const int row = src.rows ? src.rows[b] : b;
     C *out = states + ((int64_t)row << n);
@@ -560,13 +700,15 @@ __device__ void group_gradients(const Program &p, int g, const double *rho8, con
     }
 }
 
-template <typename Real, int R>
+template <typename Real, int R, int kMode>
 __global__ void __launch_bounds__(512) k_adjoint(Program p, Observable o, SlotSource src,
                                                  CostSource cs, OnchipShape sh,
-                                                 double *slot_grads, double *slot_E) {
+                                                 double *slot_grads, double *slot_E,
+                                                 BlockConst bc) {
     using C = typename CT<Real>::T;
     constexpr int NA = 1 << R;
     extern __shared__ __align__(16) unsigned char smem[];
+    stage_block_const<kMode>(bc, smem, p, o);
     const int n = p.n, shb = n - R, Ts = 1 << shb;
     const int ls = threadIdx.x >> shb, tid = threadIdx.x & (Ts - 1);
     const int b = blockIdx.x * sh.S + ls;
@@ -585,16 +727,18 @@ __global__ void __launch_bounds__(512) k_adjoint(Program p, Observable o, SlotSo
     for (int g = tid; g < G; g += Ts) group_matrix<Real, C>(p, g, si, mats + 4 * g);
     for (int q = tid; q < P; q += Ts) grad[q] = 0.0;
     __syncthreads();
-    forward_stages<Real, R>(p, psi, mats, tid, si.ref);
+    forward_stages<Real, R, kMode>(p, psi, mats, tid, si.ref);
     double e = apply_h<Real, R>(o, psi, lam, tid, shb, p.swz_bits);
     e = slot_sum(e, Ts, red);
     __syncthreads();
 
     C a[NA], al[NA];
     const int width = Ts < 32 ? Ts : 32;
+    Bases nxt = bases_of<kMode>(p, p.n_stages - 1, tid, Ts);
     for (int s = p.n_stages - 1; s >= 0; --s) {
         const Stage *sg = p.stages + s;
-        const Bases bs = stage_bases(sg, tid);
+        const Bases bs = nxt;
+        if (s > 0) nxt = bases_of<kMode>(p, s - 1, tid, Ts);
         uint32_t lq[R], sq[R];
         int qq[R];
 #pragma unroll
@@ -680,37 +824,11 @@ __global__ void __launch_bounds__(512) k_adjoint(Program p, Observable o, SlotSo
 
 // --------------------------------------------------------- combinations
 
-// Parameter-shift combination: dL/dtheta_k = sum_i L'_i (E_{k+,i} - E_{k-,i}) / 2.
+// Parameter-shift combination as its own launch.
 __global__ void k_ps_combine(const double *E, int I, int P, CostSource c, double *lp,
                              double *energy_out, double *loss_out, double *grad_out) {
     __shared__ double red[32];
-    double part = 0.0;
-    for (int i = threadIdx.x; i < I; i += blockDim.x) {
-        const double e = E[i];
-        if (energy_out) energy_out[i] = e;
-        if (c.cost == SV_COST_MSE) {
-            const double d = e - c.targets[i];
-            part += d * d / I;
-        } else {
-            part += c.weights[i] * e;
-        }
-        lp[i] = c.ext_weights ? c.ext_weights[i]
-                              : (c.cost == SV_COST_MSE ? 2.0 * (e - c.targets[i]) / I : c.weights[i]);
-    }
-    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
-    __syncthreads();
-    if (threadIdx.x == 0 && loss_out) {
-        double s = 0.0;
-        for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) s += red[wi];
-        loss_out[0] = s;
-    }
-    for (int k = threadIdx.x; k < P; k += blockDim.x) {
-        const double *ep = E + I + (int64_t)2 * k * I, *em = ep + I;
-        double g = 0.0;
-        for (int i = 0; i < I; ++i) g += lp[i] * 0.5 * (ep[i] - em[i]);
-        grad_out[k] = g;
-    }
+    ps_combine_block(E, I, P, c, lp, energy_out, loss_out, grad_out, red);
 }
 
 // Adjoint combination: dL/dtheta = sum_i (weighted per-instance gradients).
@@ -759,23 +877,40 @@ template <typename K> cudaError_t prep(K kernel, uint32_t smem) {
 // ----------------------------------------------------------- host side
 
 const char *onchip_shape(int kind, int n, int n_groups, int n_params, int c128, int n_slots,
-                         int reg_bits, int threads_per_block, OnchipShape *out) {
+                         int reg_bits, int threads_per_block, OnchipShape *out, int num_sms,
+                         uint32_t const_bytes) {
     OnchipShape s{};
     const size_t csz = c128 ? 16 : 8, rsz = c128 ? 8 : 4;
-    // Register bits: at most 4 (3 for the two-state complex128 adjoint),
-    // and at most 512 threads per slot.
+    if (num_sms < 1) num_sms = 1;
+    // Register bits: at most 4 (3 for complex128), at most 512 threads per
+    // slot.  By default fewer register bits (more threads per circuit) when
+    // the batch would otherwise leave the schedulers with < 2 warps each.
     const int rmax = c128 ? 3 : 4;
-    int R = reg_bits > 0 ? reg_bits : (kind == ONCHIP_ADJOINT ? 3 : (c128 ? 3 : 4));
+    int R = reg_bits;
+    if (R <= 0) {
+        R = kind == ONCHIP_ADJOINT ? 3 : rmax;
+        const int64_t want = (int64_t)num_sms * 4 * 32 * 2;
+        while (R > 2 && (int64_t)n_slots * (int64_t(1) << (n > R ? n - R : 0)) < want) --R;
+    }
     if (R < 1 || R > rmax) return "reg_bits out of range for this kernel";
     if (R > n) R = n;
     if (n - R > 9) R = n - 9;
     if (R > rmax) return "state too large for the on-chip engine";
     const int Ts = 1 << (n - R);
     if (threads_per_block > 512) return "threads_per_block must be <= 512";
-    int S = threads_per_block > 0 ? threads_per_block / Ts : 256 / Ts;
-    if (threads_per_block > 0 && (threads_per_block % Ts != 0 || S < 1))
-        return "threads_per_block must be a multiple of the threads per slot";
-    if (S < 1) S = 1;
+    int S;
+    if (threads_per_block > 0) {
+        S = threads_per_block / Ts;
+        if (threads_per_block % Ts != 0 || S < 1)
+            return "threads_per_block must be a multiple of the threads per slot";
+    } else {
+        // Enough blocks for two per SM where the batch allows, at least one
+        // warp and at most 256 threads per block.
+        S = (int)((n_slots + 2 * num_sms - 1) / (2 * num_sms));
+        if (S * Ts > 256) S = 256 / Ts;
+        if (S < 1) S = 1;
+    }
+    if (S * Ts < 32) S = 32 / Ts;
     const size_t dim = size_t(1) << n;
     const int wps = Ts >= 32 ? Ts / 32 : 1;
     const uint32_t kLimit = 200 * 1024;
@@ -806,6 +941,12 @@ const char *onchip_shape(int kind, int n, int n_groups, int n_params, int c128, 
         }
         s.off_red = (uint32_t)off;
         off += up16((size_t)((S * Ts + 31) / 32) * 8);
+        s.off_const = (uint32_t)off;
+        s.const_bytes = 0;
+        if (const_bytes && off + const_bytes <= kLimit) {
+            s.const_bytes = const_bytes;
+            off += const_bytes;
+        }
         if (off <= kLimit) {
             s.smem = (uint32_t)off;
             break;
@@ -840,21 +981,79 @@ const char *onchip_shape(int kind, int n, int n_groups, int n_params, int c128, 
 
 template <typename Real, int R>
 static cudaError_t run_energy(const OnchipShape &sh, const Program &p, const Observable &o,
-                              const SlotSource &s, double *E, cudaStream_t st) {
-    auto k = k_energy<Real, R>;
+                              const SlotSource &s, double *E, const void *dtab,
+                              const FusedCombine &fc, const BlockConst &bc, cudaStream_t st) {
+    auto k = !bc.bytes ? k_energy<Real, R, 0> : (bc.n16[7] ? k_energy<Real, R, 2>
+                                                           : k_energy<Real, R, 1>);
     cudaError_t e = prep(k, sh.smem);
     if (e != cudaSuccess) return e;
-    k<<<sh.blocks, sh.S * sh.Ts, sh.smem, st>>>(p, o, s, sh, E);
+    k<<<sh.blocks, sh.S * sh.Ts, sh.smem, st>>>(
+        p, o, s, sh, E, reinterpret_cast<const typename CT<Real>::T *>(dtab), fc, bc);
     return cudaGetLastError();
+}
+
+// The staged block constants live at the end of the shape's layout; a
+// BlockConst without a region in `sh` is ignored (global reads).
+static BlockConst fit_const(const OnchipShape &sh, const BlockConst *bc) {
+    BlockConst b{};
+    if (bc && sh.const_bytes >= bc->bytes && bc->bytes) {
+        b = *bc;
+        b.base = sh.off_const;
+    }
+    return b;
 }
 
 cudaError_t launch_onchip_energy(int c128, const OnchipShape &sh, const Program &p,
                                  const Observable &o, const SlotSource &s, double *E,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, const void *dtab, const FusedCombine *fc,
+                                 const BlockConst *bc) {
     if (sh.blocks == 0) return cudaSuccess;
-    if (c128) { SVK_DISPATCH_R_C128(sh.R, return (run_energy<double, RR>(sh, p, o, s, E, st))); }
-    SVK_DISPATCH_R(sh.R, return (run_energy<float, RR>(sh, p, o, s, E, st)));
+    FusedCombine none{};
+    const FusedCombine &f = fc ? *fc : none;
+    BlockConst b = fit_const(sh, bc);
+    if (!dtab) b.n16[6] = 0;
+    if (c128) {
+        SVK_DISPATCH_R_C128(sh.R, return (run_energy<double, RR>(sh, p, o, s, E, dtab, f, b, st)));
+    }
+    SVK_DISPATCH_R(sh.R, return (run_energy<float, RR>(sh, p, o, s, E, dtab, f, b, st)));
     return cudaSuccess;
+}
+
+// Diagonal tables D_g(j) of an observable, [groups][2^n] complex (Real).
+template <typename Real>
+__global__ void k_build_dtable(Observable o, int n, typename CT<Real>::T *out) {
+    using C = typename CT<Real>::T;
+    const int64_t dim = int64_t(1) << n;
+    const int64_t total = dim * o.n_tgroups;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int g = (int)(i >> n);
+        const uint32_t j = (uint32_t)(i & (dim - 1));
+        const TermGroup tg = o.tgroups[g];
+        double re = 0.0, im = 0.0;
+        for (int t = tg.t_begin; t < tg.t_end; ++t) {
+            const Term tm = o.terms[t];
+            const double c = (__popc(j & tm.z) & 1u) ? -tm.coeff : tm.coeff;
+            if (tm.phase == 0) re += c;
+            else if (tm.phase == 1) im += c;
+            else if (tm.phase == 2) re -= c;
+            else im -= c;
+        }
+        C d;
+        d.x = (Real)re;
+        d.y = (Real)im;
+        out[i] = d;
+    }
+}
+
+cudaError_t launch_build_dtable(int c128, const Observable &o, int n, void *out, cudaStream_t st) {
+    const int64_t total = (int64_t(1) << n) * o.n_tgroups;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    if (c128) k_build_dtable<double><<<blocks, 256, 0, st>>>(o, n, (double2 *)out);
+    else k_build_dtable<float><<<blocks, 256, 0, st>>>(o, n, (float2 *)out);
+    return cudaGetLastError();
 }
 
 template <typename Real, int R>
@@ -902,20 +1101,25 @@ cudaError_t launch_onchip_expect(int c128, const OnchipShape &sh, int n, int swz
 template <typename Real, int R>
 static cudaError_t run_adjoint(const OnchipShape &sh, const Program &p, const Observable &o,
                                const SlotSource &s, const CostSource &c, double *G, double *E,
-                               cudaStream_t st) {
-    auto k = k_adjoint<Real, R>;
+                               const BlockConst &b, cudaStream_t st) {
+    auto k = !b.bytes ? k_adjoint<Real, R, 0> : (b.n16[7] ? k_adjoint<Real, R, 2>
+                                                         : k_adjoint<Real, R, 1>);
     cudaError_t e = prep(k, sh.smem);
     if (e != cudaSuccess) return e;
-    k<<<sh.blocks, sh.S * sh.Ts, sh.smem, st>>>(p, o, s, c, sh, G, E);
+    k<<<sh.blocks, sh.S * sh.Ts, sh.smem, st>>>(p, o, s, c, sh, G, E, b);
     return cudaGetLastError();
 }
 
 cudaError_t launch_onchip_adjoint(int c128, const OnchipShape &sh, const Program &p,
                                   const Observable &o, const SlotSource &s, const CostSource &c,
-                                  double *G, double *E, cudaStream_t st) {
+                                  double *G, double *E, cudaStream_t st, const BlockConst *bc) {
     if (sh.blocks == 0) return cudaSuccess;
-    if (c128) { SVK_DISPATCH_R_C128(sh.R, return (run_adjoint<double, RR>(sh, p, o, s, c, G, E, st))); }
-    SVK_DISPATCH_R(sh.R, return (run_adjoint<float, RR>(sh, p, o, s, c, G, E, st)));
+    BlockConst b = fit_const(sh, bc);
+    b.n16[6] = 0;
+    if (c128) {
+        SVK_DISPATCH_R_C128(sh.R, return (run_adjoint<double, RR>(sh, p, o, s, c, G, E, b, st)));
+    }
+    SVK_DISPATCH_R(sh.R, return (run_adjoint<float, RR>(sh, p, o, s, c, G, E, b, st)));
     return cudaSuccess;
 }
 

@@ -188,6 +188,24 @@ void stage_lops(const std::vector<LOp> &lops, const std::vector<int> &pos, int t
     if (any || (int)P->stages.size() == first_stage) close_stage();
 }
 
+void build_thread_bases(HostProgram *P, int t) {
+    const int T = 1 << (t - P->R);
+    P->tbase.assign((size_t)P->stages.size() * T, ThreadBase{});
+    for (size_t s = 0; s < P->stages.size(); ++s) {
+        const Stage &st = P->stages[s];
+        for (int tid = 0; tid < T; ++tid) {
+            ThreadBase b{0u, 0u, 0u, 0u};
+            for (int k = 0; k < st.n_thr; ++k)
+                if ((tid >> k) & 1) {
+                    b.lb ^= st.ldt[k];
+                    b.sb ^= st.stt[k];
+                    b.lg |= 1u << st.tpos[k];
+                }
+            P->tbase[s * T + tid] = b;
+        }
+    }
+}
+
 std::string plan_circuit(const sv_circuit &c, int reg_bits, bool fuse, int swz_bits,
                          HostProgram *P) {
     if (reg_bits < 1 || reg_bits > kRMax) return "reg_bits must be in [1, 5]";
@@ -206,6 +224,7 @@ std::string plan_circuit(const sv_circuit &c, int reg_bits, bool fuse, int swz_b
     std::vector<int> pos(n);
     for (int q = 0; q < n; ++q) pos[q] = q;
     stage_lops(F.lops, pos, n, P->R, swz_bits, P);
+    build_thread_bases(P, n);
     return "";
 }
 

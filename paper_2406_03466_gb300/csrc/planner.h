@@ -17,7 +17,11 @@ struct HostProgram {
     std::vector<Stage> stages;
     std::vector<std::vector<uint32_t>> perm_cols;  // per stage: f(e_b), b < n
     std::vector<PassDesc> passes;                  // tile passes (device-memory states)
+    std::vector<ThreadBase> tbase;                 // [stages][2^(t-R)] thread bases
 };
+
+// Fills P->tbase for stages whose thread count is 2^(t - R).
+void build_thread_bases(HostProgram *P, int t);
 
 // Logical op stream after single-qubit fusion.
 struct LOp {

@@ -88,6 +88,12 @@ struct Term {
 };
 
 // Device view of a compiled circuit (all pointers are device memory).
+// Per-thread address bases of one stage: x = load base (swizzled), y = store
+// base (swizzled, after the stage's permutation), z = logical index base.
+struct ThreadBase {
+    uint32_t lb, sb, lg, pad;
+};
+
 struct Program {
     int32_t n, R, n_stages, n_groups, n_params, input_dim, swz_bits;
     int32_t pad;
@@ -95,6 +101,7 @@ struct Program {
     const Op *ops;
     const Group *groups;
     const Member *members;
+    const ThreadBase *tbase;  // [n_stages][2^(n-R)] (NULL: computed in the kernel)
 };
 
 struct Observable {

@@ -205,6 +205,34 @@ def test_errors_are_reported(sv):
     assert torch.cuda.is_available()
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_autotune_keeps_results(sv, dtype):
+    """The autotuner picks a launch shape; results under it still match."""
+    w = wl.mcvqe(8, 4)
+    L, E, g = oracle.grad_param_shift(w)
+    prob = sv.Problem.from_spec(w, dtype)
+    sv.sv_autotune(prob, theta_of(w))
+    for kind in (1, 2):
+        R, tpb, us = sv.sv_tuned_shape(prob, kind)
+        assert 1 <= R <= 4 and 32 <= tpb <= 512 and us > 0
+    for fn in (sv.sv_grad_param_shift, sv.sv_grad_adjoint):
+        l_, e_, g_ = fn(prob, theta_of(w))
+        close(g_.cpu().numpy(), g, TOL[dtype]["G"])
+        close(e_.cpu().numpy(), E, TOL[dtype]["E"])
+
+
+def test_energies_entry(sv):
+    w = wl.qcl(8, 2, 11)
+    prob = sv.Problem.from_spec(w, "c64")
+    l_, e_ = sv.sv_energies(prob, theta_of(w))
+    E = oracle.instance_energies(w)
+    close(e_.cpu().numpy(), E, 1e-5)
+    close(l_.cpu().numpy()[0], oracle.cost_from_energies(w, E), 1e-5)
+    B = sv.sv_param_shift_energies(prob, theta_of(w)).cpu().numpy()
+    inst, sp, sh = oracle.param_shift_slots(w)
+    close(B, oracle.energies(w, None, inst, sp, sh), 1e-5)
+
+
 def test_repeatable(sv):
     """A fixed plan gives bitwise identical results run to run."""
     w = wl.mcvqe(8, 4)
