@@ -108,6 +108,11 @@ typedef struct {
     int32_t no_fusion;       /* 1 = apply every gate on its own (no 1-qubit gate fusion) */
     int32_t epilogue;        /* <H> epilogue: 0 = default, 1 = per Pauli term, 2 = per-X-group
                                 diagonal tables (states of at most 13 qubits) */
+    int32_t tile_bits;       /* 0 = states of at most 13 (complex64) / 12 (complex128) qubits
+                                stay on chip, larger ones run as tile passes over device
+                                memory with the default tile; > 0 forces tile passes of
+                                2^tile_bits amplitudes (6..12) */
+    int32_t reserved[3];
 } sv_plan_opts;
 
 /* ---------------------------------------------------------------- states */
@@ -208,9 +213,13 @@ sv_status sv_grad_param_shift(const sv_problem *problem, const double *theta,
  * lambda = H psi, then for each gate in reverse order the derivative
  * Im <lambda| G psi> of its generator G, psi <- U^dag psi, lambda <- U^dag lambda.
  * weights: device [n_instances] dL/dE_i; NULL derives them from the
- * problem's cost.  checkpoint_every: gates between stored forward states
- * for states that do not fit on chip (0 = library choice).  Uses library
- * scratch of I * P doubles. */
+ * problem's cost.  States that do not fit on chip run as tile passes over
+ * device memory; their forward states are stored every `checkpoint_every`
+ * passes (0 = every 4) and the reverse sweep restarts psi from each stored
+ * state instead of carrying the rounding of the un-computation further.
+ * Uses library scratch of I * P doubles, plus for device-memory states
+ * (2 + checkpoints) states per instance processed at once (instances are
+ * processed in groups that fit in free device memory). */
 sv_status sv_grad_adjoint(const sv_problem *problem, const double *theta, const double *weights,
                           double *energy_out, double *loss_out, double *grad_out,
                           int32_t checkpoint_every, sv_stream_t stream);

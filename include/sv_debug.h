@@ -17,12 +17,19 @@
 extern "C" {
 #endif
 
-/* sizes[0..5] = sizeof of Stage, Op, Group, Member, TermGroup, Term. */
+/* sizes[0..6] = sizeof of Stage, Op, Group, Member, TermGroup, Term, PassDesc. */
 void sv_debug_sizes(int32_t *sizes);
 
 sv_status sv_debug_plan(const sv_circuit *circuit, int32_t reg_bits, int32_t fuse,
                         int32_t swz_bits, int32_t *counts, void *stages, void *ops,
                         void *groups, void *members);
+
+/* The same for the tile passes of states in device memory: counts[4] also
+ * receives the number of passes; `passes` gets counts[4] pass descriptors
+ * (sizes[6] bytes each). */
+sv_status sv_debug_passes(const sv_circuit *circuit, int32_t tile_bits, int32_t coalesce_bits,
+                          int32_t reg_bits, int32_t fuse, int32_t swz_bits, int32_t *counts,
+                          void *stages, void *ops, void *groups, void *members, void *passes);
 
 #ifdef __cplusplus
 }

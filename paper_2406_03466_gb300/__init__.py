@@ -58,7 +58,8 @@ class sv_pauli_sum(ctypes.Structure):
 
 class sv_plan_opts(ctypes.Structure):
     _fields_ = [("reg_bits", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
-                ("no_fusion", ctypes.c_int32), ("epilogue", ctypes.c_int32)]
+                ("no_fusion", ctypes.c_int32), ("epilogue", ctypes.c_int32),
+                ("tile_bits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class sv_slot(ctypes.Structure):
@@ -185,8 +186,12 @@ class PauliSum:
                                    self._c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
 
 
-def plan_opts(reg_bits=0, threads_per_block=0, no_fusion=False, epilogue=0) -> sv_plan_opts:
-    return sv_plan_opts(int(reg_bits), int(threads_per_block), int(bool(no_fusion)), int(epilogue))
+def plan_opts(reg_bits=0, threads_per_block=0, no_fusion=False, epilogue=0,
+              tile_bits=0) -> sv_plan_opts:
+    o = sv_plan_opts()
+    o.reg_bits, o.threads_per_block = int(reg_bits), int(threads_per_block)
+    o.no_fusion, o.epilogue, o.tile_bits = int(bool(no_fusion)), int(epilogue), int(tile_bits)
+    return o
 
 
 class Problem:

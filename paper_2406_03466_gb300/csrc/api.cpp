@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -10,6 +11,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "hbm.h"
 #include "kernels.h"
 #include "planner.h"
 #include "sv.h"
@@ -95,6 +97,7 @@ struct DeviceCtx {
     std::unordered_map<uint64_t, std::unique_ptr<ObsEntry>> obs;
     std::unordered_map<uint64_t, std::unique_ptr<ArrayEntry>> arrays;
     std::unordered_map<cudaStream_t, std::unique_ptr<DeviceBuf>> scratch;
+    std::unordered_map<cudaStream_t, std::unique_ptr<DeviceBuf>> scratch_big;  // device-memory states
 };
 
 std::mutex g_mu;
@@ -130,12 +133,15 @@ uint64_t hash_bytes(const void *p, size_t n) {
 int swz_bits(sv_dtype d) { return d == SV_C128 ? 3 : 4; }
 
 // Compiled program of a circuit for (reg_bits, fusion, dtype), cached.
+// tile_bits > 0: the circuit cut into tile passes of 2^tile_bits amplitudes
+// (states in device memory) instead of one on-chip program.
 sv_status get_plan(DeviceCtx *ctx, const sv_circuit &c, int R, bool fuse, sv_dtype dt,
-                   PlanEntry **out) {
+                   PlanEntry **out, int tile_bits = 0) {
     uint64_t key = hash_circuit(c);
     key = mix64(key, (uint64_t)R);
     key = mix64(key, fuse ? 1 : 0);
     key = mix64(key, (uint64_t)swz_bits(dt));
+    key = mix64(key, (uint64_t)(1000 + tile_bits));
     auto it = ctx->plans.find(key);
     if (it != ctx->plans.end()) {
         PlanEntry *e = it->second.get();
@@ -147,7 +153,13 @@ sv_status get_plan(DeviceCtx *ctx, const sv_circuit &c, int R, bool fuse, sv_dty
         }
     }
     std::unique_ptr<PlanEntry> e(new PlanEntry());
-    std::string err = plan_circuit(c, R, fuse, swz_bits(dt), &e->host);
+    std::string err;
+    if (tile_bits > 0) {
+        err = plan_passes(c, tile_bits, dt == SV_C128 ? 3 : 4, R, fuse, swz_bits(dt), &e->host);
+        if (err.empty()) build_thread_bases(&e->host, tile_bits);
+    } else {
+        err = plan_circuit(c, R, fuse, swz_bits(dt), &e->host);
+    }
     if (!err.empty()) return fail(SV_ERR_ARG, "circuit: " + err);
     e->gates.assign(c.gates, c.gates + c.n_gates);
     e->n = c.n_qubits;
@@ -425,6 +437,246 @@ CostSource cost_of(const sv_problem *p, const double *ext) {
     return c;
 }
 
+// ------------------------------------------------ device-memory states
+
+// Second per-stream scratch for tile-pass state buffers (grown on demand).
+sv_status get_big_scratch(DeviceCtx *ctx, cudaStream_t st, size_t bytes, void **out) {
+    auto &s = ctx->scratch_big[st];
+    if (!s) s.reset(new DeviceBuf());
+    if (s->bytes < bytes) {
+        if (s->ptr) {
+            SV_CUDA(cudaStreamSynchronize(st));
+            cudaFree(s->ptr);
+            s->ptr = nullptr;
+            s->bytes = 0;
+        }
+        SV_CUDA(cudaMalloc(&s->ptr, bytes));
+        s->bytes = bytes;
+    }
+    *out = s->ptr;
+    return SV_OK;
+}
+
+// Bytes a tile-pass call may claim: 80 % of what is free plus what its own
+// big scratch already holds.
+size_t big_budget(DeviceCtx *ctx, cudaStream_t st) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    auto it = ctx->scratch_big.find(st);
+    const size_t have = (it != ctx->scratch_big.end() && it->second) ? it->second->bytes : 0;
+    return (size_t)(0.8 * (double)fr) + have;
+}
+
+bool wants_tiles(int n, sv_dtype dt, const sv_plan_opts *o) {
+    if (o && o->tile_bits > 0) return true;
+    return n > (dt == SV_C128 ? 12 : 13);
+}
+
+struct TileCfg {
+    int t, R;
+};
+
+sv_status tile_cfg(int n, sv_dtype dt, const sv_plan_opts *o, TileCfg *cfg) {
+    const int c = dt == SV_C128 ? 3 : 4, rmax = dt == SV_C128 ? 3 : 4;
+    int t = (o && o->tile_bits > 0) ? o->tile_bits : (dt == SV_C128 ? 11 : 12);
+    if (t > n) t = n;
+    if (t < c + 2 || t > 12)
+        return fail(SV_ERR_UNSUPPORTED, "tile passes need 2^tile_bits amplitudes with tile_bits in "
+                                        "[coalesced bits + 2, 12] and at most n_qubits");
+    int R = (o && o->reg_bits > 0) ? o->reg_bits : rmax;
+    if (R < 2 || R > rmax) return fail(SV_ERR_ARG, "reg_bits for tile passes must be 2..4 (2..3 complex128)");
+    if (t - R > 8) R = t - 8;
+    if (R > rmax) return fail(SV_ERR_UNSUPPORTED, "tile too large for the register width");
+    cfg->t = t;
+    cfg->R = R;
+    return SV_OK;
+}
+
+// The program view of one pass: its stages, thread bases and tile size.
+Program pass_view(const PlanEntry *pe, const PassDesc &pd, int R) {
+    Program v = pe->dev;
+    v.n = pd.t;
+    v.R = R;
+    v.n_stages = pd.stage_end - pd.stage_begin;
+    v.stages = pe->dev.stages + pd.stage_begin;
+    const int T = 1 << (pd.t - R);
+    v.tbase = pe->dev.tbase ? pe->dev.tbase + (size_t)pd.stage_begin * T : nullptr;
+    return v;
+}
+
+int pass_blocks(const DeviceCtx *ctx, int64_t tiles, uint32_t smem) {
+    int per_sm = (int)((200u * 1024u) / (smem + 1024u));
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 8) per_sm = 8;
+    int64_t b = (int64_t)ctx->sms * per_sm;
+    if (b > tiles) b = tiles;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// Forward tile passes of `pe` over src.n_slots states (|ref> first when init).
+// After pass i with (i + 1) % every == 0 (and not the last pass) the states
+// are copied to checkpoint (i + 1) / every - 1 of `ck`.
+sv_status tiles_forward(DeviceCtx *ctx, const PlanEntry *pe, int R, sv_dtype dt,
+                        const SlotSource &src, void *states, void *mats, bool init, void *ck,
+                        int every, cudaStream_t st) {
+    const int c128 = dt == SV_C128, n = pe->n, G = pe->dev.n_groups;
+    const size_t sbytes = ((size_t)src.n_slots << n) * (c128 ? 16 : 8);
+    cudaError_t e = launch_group_mats(c128, pe->dev, src, mats, st);
+    if (e != cudaSuccess) return cuda_fail(e, "group matrices");
+    if (init) {
+        e = launch_init_states(c128, states, n, src, st);
+        if (e != cudaSuccess) return cuda_fail(e, "state init");
+    }
+    const auto &passes = pe->host.passes;
+    for (size_t i = 0; i < passes.size(); ++i) {
+        const PassDesc &pd = passes[i];
+        const int64_t tiles = (int64_t)src.n_slots << pd.n_tile_bits;
+        e = launch_pass_fwd(c128, R, pd, pass_view(pe, pd, R), n, src.n_slots, mats, G, states,
+                            pass_blocks(ctx, tiles, pass_fwd_smem(c128, pd.t)), st);
+        if (e != cudaSuccess) return cuda_fail(e, "forward tile pass");
+        if (ck && every > 0 && (i + 1) % every == 0 && i + 1 < passes.size()) {
+            e = cudaMemcpyAsync((char *)ck + ((i + 1) / every - 1) * sbytes, states, sbytes,
+                                cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(e, "checkpoint copy");
+        }
+    }
+    return SV_OK;
+}
+
+// Energies of n_slots slots (parameter-shift or instance slots) of states in
+// device memory, in groups of slots that fit the memory budget.
+sv_status tiles_energies(DeviceCtx *ctx, const sv_problem *p, const double *theta, int mode,
+                         int n_slots, double *E, cudaStream_t st) {
+    const sv_dtype dt = p->dtype;
+    const int c128 = dt == SV_C128, n = p->circuit->n_qubits, I = p->n_instances;
+    TileCfg cfg{};
+    sv_status s = tile_cfg(n, dt, p->opts, &cfg);
+    if (s != SV_OK) return s;
+    PlanEntry *pe = nullptr;
+    s = get_plan(ctx, *p->circuit, cfg.R, use_fusion(p->opts), dt, &pe, cfg.t);
+    if (s != SV_OK) return s;
+    ObsEntry *obs = nullptr;
+    s = get_obs(ctx, *p->observable, n, dt, &obs, st);
+    if (s != SV_OK) return s;
+    const void *drefs = nullptr;
+    s = get_array(ctx, p->refs, sizeof(int64_t) * I, &drefs);
+    if (s != SV_OK) return s;
+    const size_t csz = c128 ? 16 : 8, sb = csz << n;
+    const size_t mb = (size_t)pe->dev.n_groups * 4 * csz;
+    const size_t per = sb + mb;
+    int64_t chunk = (int64_t)(big_budget(ctx, st) / (per + 512));
+    if (chunk < 1) return fail(SV_ERR_OOM, "one state does not fit in free device memory");
+    if (chunk > n_slots) chunk = n_slots;
+    if (chunk > 65535) chunk = 65535;  // one grid row per state in the expectation
+    void *big = nullptr;
+    const size_t mats_off = ((size_t)chunk * sb + 255) & ~size_t(255);
+    s = get_big_scratch(ctx, st, mats_off + (size_t)chunk * mb + 256, &big);
+    if (s != SV_OK) return s;
+    for (int64_t c0 = 0; c0 < n_slots; c0 += chunk) {
+        SlotSource src{};
+        src.mode = mode;
+        src.n_slots = (int)std::min<int64_t>(chunk, n_slots - c0);
+        src.n_instances = I;
+        src.refs = (const int64_t *)drefs;
+        src.theta = theta;
+        src.inputs = p->inputs;
+        src.input_stride = p->input_stride;
+        src.slot_base = (int)c0;
+        s = tiles_forward(ctx, pe, cfg.R, dt, src, big, (char *)big + mats_off, true, nullptr, 0, st);
+        if (s != SV_OK) return s;
+        cudaError_t e = launch_expect_big(c128, obs->dev, n, src.n_slots, big, E + c0, st);
+        if (e != cudaSuccess) return cuda_fail(e, "expectation over device-memory states");
+    }
+    return SV_OK;
+}
+
+// Adjoint gradient of states in device memory: forward passes with stored
+// states every `every` passes, lambda = H psi, reverse passes accumulating the
+// reduced matrices, per-slot gradients, then the sum over instances.
+sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta,
+                        const double *weights, double *energy_out, double *loss_out,
+                        double *grad_out, int every, cudaStream_t st) {
+    const sv_dtype dt = p->dtype;
+    const int c128 = dt == SV_C128, n = p->circuit->n_qubits, I = p->n_instances;
+    const int P = p->circuit->n_params, Pp = P > 0 ? P : 1;
+    TileCfg cfg{};
+    sv_status s = tile_cfg(n, dt, p->opts, &cfg);
+    if (s != SV_OK) return s;
+    PlanEntry *pe = nullptr;
+    s = get_plan(ctx, *p->circuit, cfg.R, use_fusion(p->opts), dt, &pe, cfg.t);
+    if (s != SV_OK) return s;
+    ObsEntry *obs = nullptr;
+    s = get_obs(ctx, *p->observable, n, dt, &obs, st);
+    if (s != SV_OK) return s;
+    const void *drefs = nullptr;
+    s = get_array(ctx, p->refs, sizeof(int64_t) * I, &drefs);
+    if (s != SV_OK) return s;
+    const int G = pe->dev.n_groups;
+    const int npass = (int)pe->host.passes.size();
+    if (every <= 0) every = 4;
+    const int ncp = npass > 1 ? (npass - 1) / every : 0;
+    const size_t csz = c128 ? 16 : 8, sb = csz << n;
+    const size_t per = (2 + (size_t)ncp) * sb + (size_t)G * 4 * csz + (size_t)G * 64;
+    int64_t chunk = (int64_t)(big_budget(ctx, st) / (per + 2048));
+    if (chunk < 1) return fail(SV_ERR_OOM, "psi, lambda and the stored states do not fit");
+    if (chunk > I) chunk = I;
+    if (chunk > 65535) chunk = 65535;
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t o_lam = up((size_t)chunk * sb), o_ck = o_lam + up((size_t)chunk * sb);
+    const size_t o_mats = o_ck + up((size_t)ncp * chunk * sb);
+    const size_t o_rho = o_mats + up((size_t)chunk * G * 4 * csz);
+    const size_t total = o_rho + up((size_t)chunk * G * 64);
+    void *big = nullptr;
+    s = get_big_scratch(ctx, st, total, &big);
+    if (s != SV_OK) return s;
+    char *bb = (char *)big;
+    void *scr = nullptr;
+    s = get_scratch(ctx, st, sizeof(double) * ((size_t)I * Pp + I), &scr);
+    if (s != SV_OK) return s;
+    double *Gs = (double *)scr, *Es = Gs + (size_t)I * Pp;
+    SV_CUDA(cudaMemsetAsync(Gs, 0, sizeof(double) * (size_t)I * Pp, st));
+    const CostSource cs = cost_of(p, weights);
+    const auto &passes = pe->host.passes;
+    for (int64_t c0 = 0; c0 < I; c0 += chunk) {
+        SlotSource src{};
+        src.mode = SLOTS_INSTANCES;
+        src.n_slots = (int)std::min<int64_t>(chunk, I - c0);
+        src.n_instances = I;
+        src.refs = (const int64_t *)drefs;
+        src.theta = theta;
+        src.inputs = p->inputs;
+        src.input_stride = p->input_stride;
+        src.slot_base = (int)c0;
+        const size_t cb = (size_t)src.n_slots * sb;  // bytes of this group's states
+        void *psi = bb, *lam = bb + o_lam, *ck = bb + o_ck, *mats = bb + o_mats;
+        double *rho = (double *)(bb + o_rho);
+        s = tiles_forward(ctx, pe, cfg.R, dt, src, psi, mats, true, ncp ? ck : nullptr, every, st);
+        if (s != SV_OK) return s;
+        cudaError_t e = launch_apply_h_big(c128, obs->dev, n, src.n_slots, psi, lam, Es + c0, st);
+        if (e != cudaSuccess) return cuda_fail(e, "lambda = H psi");
+        SV_CUDA(cudaMemsetAsync(rho, 0, (size_t)src.n_slots * G * 64, st));
+        for (int i = npass - 1; i >= 0; --i) {
+            if ((i + 1) % every == 0 && i + 1 < npass) {
+                // restart psi from the stored forward state after pass i
+                SV_CUDA(cudaMemcpyAsync(psi, (char *)ck + (size_t)((i + 1) / every - 1) * cb, cb,
+                                        cudaMemcpyDeviceToDevice, st));
+            }
+            const PassDesc &pd = passes[i];
+            const int64_t tiles = (int64_t)src.n_slots << pd.n_tile_bits;
+            const uint32_t smem = pass_rev_smem(c128, pd.t, cfg.R, G, pd.n_u1);
+            if (smem > 220u * 1024u) return fail(SV_ERR_UNSUPPORTED, "reverse pass needs too much shared memory");
+            e = launch_pass_rev(c128, cfg.R, pd, pass_view(pe, pd, cfg.R), n, src.n_slots, mats, G,
+                                psi, lam, rho, pass_blocks(ctx, tiles, smem), st);
+            if (e != cudaSuccess) return cuda_fail(e, "reverse tile pass");
+        }
+        e = launch_group_grads(c128, pe->dev, src, rho, cs, Es + c0, Gs + (size_t)c0 * Pp, st);
+        if (e != cudaSuccess) return cuda_fail(e, "per-slot gradients");
+    }
+    cudaError_t e = launch_adjoint_combine(Gs, Es, I, P, cs, energy_out, loss_out, grad_out, st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint combine");
+    return SV_OK;
+}
+
 }  // namespace
 
 struct sv_state_s {
@@ -544,6 +796,38 @@ sv_status sv_apply_circuit_batch(sv_state state, const sv_circuit *circuits, int
                 rows.push_back(b);
             }
         if (sub.empty()) continue;
+        if (wants_tiles(state->n, state->dtype, opts)) {
+            // tile passes run in place on the state rows of this circuit
+            for (size_t k = 1; k < rows.size(); ++k)
+                if (rows[k] != rows[0] + (int32_t)k)
+                    return fail(SV_ERR_UNSUPPORTED, "states in device memory: the slots of one "
+                                                    "circuit must occupy consecutive rows");
+            TileCfg cfg{};
+            sv_status s = tile_cfg(state->n, state->dtype, opts, &cfg);
+            if (s != SV_OK) return s;
+            PlanEntry *pe = nullptr;
+            s = get_plan(ctx, circuits[c], cfg.R, use_fusion(opts), state->dtype, &pe, cfg.t);
+            if (s != SV_OK) return s;
+            const void *dslots = nullptr;
+            s = get_array(ctx, sub.data(), sub.size() * sizeof(sv_slot), &dslots);
+            if (s != SV_OK) return s;
+            const size_t csz = state->dtype == SV_C128 ? 16 : 8;
+            void *mats = nullptr;
+            s = get_big_scratch(ctx, st, sub.size() * pe->dev.n_groups * 4 * csz + 256, &mats);
+            if (s != SV_OK) return s;
+            SlotSource src{};
+            src.mode = SLOTS_EXPLICIT;
+            src.n_slots = (int)sub.size();
+            src.theta = theta;
+            src.theta_stride = theta_stride;
+            src.inputs = inputs;
+            src.input_stride = input_stride;
+            src.slots = (const sv_slot *)dslots;
+            char *rows0 = (char *)state->ptr + (size_t)rows[0] * (csz << state->n);
+            s = tiles_forward(ctx, pe, cfg.R, state->dtype, src, rows0, mats, true, nullptr, 0, st);
+            if (s != SV_OK) return s;
+            continue;
+        }
         PlanEntry *plan = nullptr;
         OnchipShape sh{};
         sv_status s = plan_and_shape(ctx, ONCHIP_STORE, circuits[c], state->dtype,
@@ -582,6 +866,11 @@ sv_status sv_expect_pauli_sum(sv_state state, const sv_pauli_sum *h, int32_t n_r
     ObsEntry *obs = nullptr;
     sv_status s = get_obs(ctx, *h, state->n, state->dtype, &obs, (cudaStream_t)stream);
     if (s != SV_OK) return s;
+    if (wants_tiles(state->n, state->dtype, nullptr)) {
+        cudaError_t e = launch_expect_big(state->dtype == SV_C128, obs->dev, state->n, n_rows,
+                                          state->ptr, out, (cudaStream_t)stream);
+        return e == cudaSuccess ? SV_OK : cuda_fail(e, "expectation launch");
+    }
     OnchipShape sh{};
     const char *err = onchip_shape(ONCHIP_EXPECT, state->n, 0, 0, state->dtype == SV_C128, n_rows,
                                    0, 0, &sh, ctx->sms);
@@ -600,6 +889,13 @@ namespace {
 sv_status ps_energies_locked(DeviceCtx *ctx, const sv_problem *p, const double *theta, double *E,
                              int B, cudaStream_t st, const FusedCombine *fc = nullptr) {
     const int I = p->n_instances;
+    if (wants_tiles(p->circuit->n_qubits, p->dtype, p->opts)) {
+        sv_status s = tiles_energies(ctx, p, theta, SLOTS_PARAM_SHIFT, B, E, st);
+        if (s != SV_OK || !fc) return s;
+        cudaError_t e = launch_ps_combine(E, fc->I, fc->P, fc->cost, fc->lp, fc->energy_out,
+                                          fc->loss_out, fc->grad_out, st);
+        return e == cudaSuccess ? SV_OK : cuda_fail(e, "param-shift combine launch");
+    }
     PlanEntry *plan = nullptr;
     OnchipShape sh{};
     ObsEntry *obs = nullptr;
@@ -695,6 +991,19 @@ sv_status sv_energies(const sv_problem *p, const double *theta, double *energy_o
     if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
     std::lock_guard<std::mutex> lk(ctx->mu);
     cudaStream_t st = (cudaStream_t)stream;
+    if (wants_tiles(p->circuit->n_qubits, p->dtype, p->opts)) {
+        s = tiles_energies(ctx, p, theta, SLOTS_INSTANCES, I, energy_out, st);
+        if (s != SV_OK) return s;
+        if (loss_out) {
+            void *scr = nullptr;
+            s = get_scratch(ctx, st, sizeof(double) * I, &scr);
+            if (s != SV_OK) return s;
+            cudaError_t e = launch_ps_combine(energy_out, I, 0, cost_of(p, nullptr), (double *)scr,
+                                              nullptr, loss_out, nullptr, st);
+            if (e != cudaSuccess) return cuda_fail(e, "loss launch");
+        }
+        return SV_OK;
+    }
     PlanEntry *plan = nullptr;
     OnchipShape sh{};
     ObsEntry *obs = nullptr;
@@ -742,6 +1051,9 @@ sv_status sv_grad_adjoint(const sv_problem *p, const double *theta, const double
     if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
     std::lock_guard<std::mutex> lk(ctx->mu);
     cudaStream_t st = (cudaStream_t)stream;
+    if (wants_tiles(p->circuit->n_qubits, p->dtype, p->opts))
+        return tiles_adjoint(ctx, p, theta, weights, energy_out, loss_out, grad_out,
+                             checkpoint_every, st);
     PlanEntry *plan = nullptr;
     OnchipShape sh{};
     ObsEntry *obs = nullptr;
@@ -902,6 +1214,7 @@ sv_status sv_autotune(const sv_problem *p, const double *theta, int32_t kinds,
     if (p->circuit->n_params > 0 && !theta) return fail(SV_ERR_ARG, "theta is NULL");
     if (kinds & ~3) return fail(SV_ERR_ARG, "kinds must be a combination of 1 and 2");
     const int P = p->circuit->n_params, I = p->n_instances, n = p->circuit->n_qubits;
+    if (wants_tiles(n, p->dtype, p->opts)) return SV_OK;  // tile passes have fixed shapes
     int B = 0;
     s = ps_batch_size(p, &B);
     if (s != SV_OK) return s;

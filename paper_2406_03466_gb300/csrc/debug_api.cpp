@@ -17,6 +17,7 @@ void sv_debug_sizes(int32_t *sizes) {
     sizes[3] = (int32_t)sizeof(Member);
     sizes[4] = (int32_t)sizeof(TermGroup);
     sizes[5] = (int32_t)sizeof(Term);
+    sizes[6] = (int32_t)sizeof(PassDesc);
 }
 
 sv_status sv_debug_plan(const sv_circuit *c, int32_t reg_bits, int32_t fuse, int32_t swz_bits,
@@ -33,6 +34,26 @@ sv_status sv_debug_plan(const sv_circuit *c, int32_t reg_bits, int32_t fuse, int
     if (ops) std::memcpy(ops, h.ops.data(), h.ops.size() * sizeof(Op));
     if (groups) std::memcpy(groups, h.groups.data(), h.groups.size() * sizeof(Group));
     if (members) std::memcpy(members, h.members.data(), h.members.size() * sizeof(Member));
+    return SV_OK;
+}
+
+sv_status sv_debug_passes(const sv_circuit *c, int32_t tile_bits, int32_t coalesce_bits,
+                          int32_t reg_bits, int32_t fuse, int32_t swz_bits, int32_t *counts,
+                          void *stages, void *ops, void *groups, void *members, void *passes) {
+    if (!c || !counts) return SV_ERR_ARG;
+    HostProgram h;
+    std::string err = plan_passes(*c, tile_bits, coalesce_bits, reg_bits, fuse != 0, swz_bits, &h);
+    if (!err.empty()) return SV_ERR_ARG;
+    counts[0] = (int32_t)h.stages.size();
+    counts[1] = (int32_t)h.ops.size();
+    counts[2] = (int32_t)h.groups.size();
+    counts[3] = (int32_t)h.members.size();
+    counts[4] = (int32_t)h.passes.size();
+    if (stages) std::memcpy(stages, h.stages.data(), h.stages.size() * sizeof(Stage));
+    if (ops) std::memcpy(ops, h.ops.data(), h.ops.size() * sizeof(Op));
+    if (groups) std::memcpy(groups, h.groups.data(), h.groups.size() * sizeof(Group));
+    if (members) std::memcpy(members, h.members.data(), h.members.size() * sizeof(Member));
+    if (passes) std::memcpy(passes, h.passes.data(), h.passes.size() * sizeof(PassDesc));
     return SV_OK;
 }
 

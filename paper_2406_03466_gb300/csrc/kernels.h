@@ -22,7 +22,7 @@ struct SlotSource {
     int32_t n_instances;
     int32_t theta_stride;
     int32_t input_stride;
-    int32_t pad;
+    int32_t slot_base;       // slot b of a launch is slot slot_base + b of the batch
     const int64_t *refs;     // per instance (modes 0, 2)
     const double *theta;     // [P] (modes 0, 2) or [rows][theta_stride] (mode 1)
     const double *inputs;    // per instance (modes 0, 2) or per row (mode 1)

@@ -249,7 +249,7 @@ std::string plan_passes(const sv_circuit &c, int tile_bits, int coalesce_bits, i
     const uint32_t forced = (1u << coalesce_bits) - 1u;
     std::vector<int> pending(F.lops.size());
     for (size_t i = 0; i < pending.size(); ++i) pending[i] = (int)i;
-    do {
+    while (!pending.empty()) {
         uint32_t L = forced, blocked = 0;
         std::vector<int> taken, rest;
         for (int idx : pending) {
@@ -293,7 +293,7 @@ std::string plan_passes(const sv_circuit &c, int tile_bits, int coalesce_bits, i
         pd.n_u1 = nu;
         P->passes.push_back(pd);
         pending.swap(rest);
-    } while (!pending.empty());
+    }
     return "";
 }
 

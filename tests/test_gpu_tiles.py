@@ -1,0 +1,129 @@
+"""GPU parity of the tile-pass path (states in device memory) against the oracle.
+
+Small states are forced through tile passes with `tile_bits` so that every
+tile size, register width and checkpoint interval is compared with the CPU
+oracle; 14-qubit states take the path on their own; reduced circuit-learning
+and multi-contracted VQE workloads at 16-20 qubits check sampled gradient
+entries.  Tolerances as in test_gpu_parity.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": dict(E=1e-12, G=1e-12, A=1e-12), "c64": dict(E=1e-5, G=1e-4, A=2e-5)}
+
+
+@pytest.fixture(scope="module")
+def sv():
+    import torch  # noqa: F401
+    import paper_2406_03466_gb300 as m
+    return m
+
+
+def close(got, want, tol):
+    got, want = np.asarray(got), np.asarray(want)
+    scale = max(1.0, float(np.max(np.abs(want))))
+    err = float(np.max(np.abs(got - want)))
+    assert err <= tol * scale, f"max err {err:.3e} > {tol:.1e} x {scale:.3g}"
+
+
+def theta_of(w):
+    import torch
+    return torch.as_tensor(w.theta, dtype=torch.float64, device="cuda")
+
+
+FORCED = {
+    "qcl9": lambda: wl.qcl(9, 3, 3),
+    "mcvqe9_nn": lambda: wl.mcvqe(9, 3, "nn+nnn", n_refs=3),
+    "rand8_enc": lambda: wl.random_workload(8, 90, 7, 3, seed=31, with_encoding=True),
+    "rand10_mse": lambda: wl.random_workload(10, 70, 5, 2, seed=32, cost="mse"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(FORCED))
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("tile_bits,reg_bits", [(7, 2), (7, 3), (8, 3), (6, 2)])
+def test_forced_tiles_gradients(sv, name, dtype, tile_bits, reg_bits):
+    w = FORCED[name]()
+    L, E, g = oracle.grad_param_shift(w)
+    opts = sv.plan_opts(reg_bits=reg_bits, tile_bits=tile_bits)
+    prob = sv.Problem.from_spec(w, dtype, opts=opts)
+    l_, e_, g_ = sv.sv_grad_param_shift(prob, theta_of(w))
+    close(e_.cpu().numpy(), E, TOL[dtype]["E"])
+    close(g_.cpu().numpy()[: w.n_params], g, TOL[dtype]["G"])
+    for every in (1, 2, 0):
+        l_, e_, g_ = sv.sv_grad_adjoint(prob, theta_of(w), checkpoint_every=every)
+        close(e_.cpu().numpy(), E, TOL[dtype]["E"])
+        close(l_.cpu().numpy()[0], L, TOL[dtype]["E"])
+        close(g_.cpu().numpy()[: w.n_params], g, TOL[dtype]["G"])
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_forced_tiles_states_and_energies(sv, dtype):
+    import torch
+    w = wl.random_workload(9, 60, 6, 3, seed=33, with_encoding=True)
+    opts = sv.plan_opts(tile_bits=7)
+    circ = sv.Circuit(w.n_qubits, w.gates, w.n_params, 1)
+    rows = [(0, 0, (2 * i) % w.n_params, i, int(w.refs[i]), 0.3 * (i + 1)) for i in range(3)]
+    st = sv.sv_alloc(w.n_qubits, 3, dtype)
+    xin = torch.as_tensor(w.inputs, device="cuda")
+    sv.sv_apply_circuit_batch(st, [circ], sv.make_slots(rows), theta_of(w).reshape(1, -1), xin, opts)
+    amps = st.tensor.cpu().numpy()
+    for i, r in enumerate(rows):
+        close(amps[i], oracle.state(w, instance=i, shift_param=r[2], shift=r[5]), TOL[dtype]["A"])
+    prob = sv.Problem.from_spec(w, dtype, opts=opts)
+    l_, e_ = sv.sv_energies(prob, theta_of(w))
+    close(e_.cpu().numpy(), oracle.instance_energies(w), TOL[dtype]["E"])
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_fourteen_qubits_take_tiles(sv, dtype):
+    """Just beyond the on-chip limit: the default tile path, full gradient."""
+    w = wl.mcvqe(14, 2, "nn+nnn", n_refs=2)
+    L, E, g = oracle.grad_param_shift(w)
+    prob = sv.Problem.from_spec(w, dtype)
+    for fn in (sv.sv_grad_param_shift, sv.sv_grad_adjoint):
+        l_, e_, g_ = fn(prob, theta_of(w))
+        close(e_.cpu().numpy(), E, TOL[dtype]["E"])
+        close(g_.cpu().numpy(), g, TOL[dtype]["G"])
+
+
+def test_expect_pauli_sum_large_state(sv):
+    import torch
+    w = wl.mcvqe(15, 1, "nn+nnn", n_refs=2)
+    circ = sv.Circuit(w.n_qubits, w.gates, w.n_params, 0)
+    obs = sv.PauliSum(w.n_qubits, w.pauli_letters, w.pauli_coeffs)
+    st = sv.sv_alloc(w.n_qubits, 2, "c64")
+    rows = [(0, 0, -1, -1, int(w.refs[i]), 0.0) for i in range(2)]
+    sv.sv_apply_circuit_batch(st, [circ], sv.make_slots(rows), theta_of(w).reshape(1, -1))
+    out = sv.sv_expect_pauli_sum(st, obs)
+    close(out.cpu().numpy(), oracle.instance_energies(w), 1e-5)
+
+
+def test_circuit_learning_20_qubits_sampled(sv):
+    """Reduced circuit learning at 20 qubits (2 layers, 3 inputs): the adjoint
+    gradient against oracle parameter-shift entries."""
+    w = wl.qcl(20, 2, 3)
+    prob = sv.Problem.from_spec(w, "c64")
+    l_, e_, g_ = sv.sv_grad_adjoint(prob, theta_of(w), checkpoint_every=2)
+    E = oracle.instance_energies(w)
+    close(e_.cpu().numpy(), E, 1e-5)
+    ks = [0, 17, 60, 119]
+    _, _, gs = oracle.grad_param_shift(w, params=ks)
+    close(g_.cpu().numpy()[ks], gs, 1e-4)
+
+
+def test_mcvqe_16_qubits_adjoint_vs_param_shift(sv):
+    w = wl.mcvqe(16, 2, "nn+nnn", n_refs=3)
+    prob = sv.Problem.from_spec(w, "c64")
+    la, ea, ga = sv.sv_grad_adjoint(prob, theta_of(w))
+    lp, ep, gp = sv.sv_grad_param_shift(prob, theta_of(w))
+    close(ga.cpu().numpy(), gp.cpu().numpy(), 1e-4)
+    close(ea.cpu().numpy(), oracle.instance_energies(w), 1e-5)
+    ks = [0, 9, 31]
+    _, _, gs = oracle.grad_param_shift(w, params=ks)
+    close(ga.cpu().numpy()[ks], gs, 1e-4)

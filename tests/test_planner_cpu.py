@@ -40,6 +40,11 @@ class Member(ctypes.Structure):
     _fields_ = [("kind", I32), ("param", I32), ("angle", ctypes.c_double)]
 
 
+class PassDesc(ctypes.Structure):
+    _fields_ = [("stage_begin", I32), ("stage_end", I32), ("t", I32), ("n_tile_bits", I32),
+                ("n_u1", I32), ("local_mask", U32), ("gl", U32 * 30), ("gt", U32 * 30)]
+
+
 def lib():
     L = sv.library()
     L.sv_debug_plan.argtypes = [ctypes.c_void_p, I32, I32, I32, ctypes.POINTER(I32)] + [ctypes.c_void_p] * 4
@@ -59,10 +64,11 @@ def test_header_symbols_exported():
 
 
 def test_struct_sizes_match():
-    sizes = (I32 * 6)()
+    sizes = (I32 * 7)()
     lib().sv_debug_sizes(sizes)
     assert list(sizes)[:4] == [ctypes.sizeof(Stage), ctypes.sizeof(Op), ctypes.sizeof(Group),
                                ctypes.sizeof(Member)]
+    assert sizes[6] == ctypes.sizeof(PassDesc)
 
 
 def export_plan(circ, R, fuse, w):
@@ -107,18 +113,22 @@ def member_matrix(m, theta, x, sp, sh):
     return rot(2, np.arccos(x[m.param] ** 2))
 
 
-def run_plan(plan, n, R, w, theta, x, ref, sp=-1, sh=0.0):
-    stages, ops, groups, members = plan
+def group_mats(groups, members, theta, x, sp, sh):
     mats = []
     for g in groups:
         M = np.eye(2, dtype=complex)
         for m in members[g.m_begin:g.m_end]:
             M = member_matrix(m, theta, x, sp, sh) @ M
         mats.append(M)
-    R = min(R, n)
-    T = 1 << (n - R)
+    return mats
+
+
+def run_stages(smem, stages, ops, mats, t, R, ref=None):
+    """Executes register stages thread by thread on a 2^t shared-memory image
+    (swizzled addresses); stage 0 builds |ref> when ref is given."""
+    R = min(R, t)
+    T = 1 << (t - R)
     tid = np.arange(T)
-    smem = np.zeros(1 << n, dtype=complex)
     for s, sg in enumerate(stages):
         lb = np.zeros(T, np.int64); sb = np.zeros(T, np.int64); lg = np.zeros(T, np.int64)
         for k in range(sg.n_thr):
@@ -131,7 +141,7 @@ def run_plan(plan, n, R, w, theta, x, ref, sp=-1, sh=0.0):
                     lo[r] ^= sg.ldq[i]; so[r] ^= sg.stq[i]; lj[r] |= 1 << sg.q[i]
         a = np.zeros((T, 1 << R), dtype=complex)
         for r in range(1 << R):
-            if s == 0:
+            if s == 0 and ref is not None:
                 a[:, r] = ((lg | lj[r]) == ref).astype(float)
             else:
                 a[:, r] = smem[lb ^ lo[r]]
@@ -150,15 +160,65 @@ def run_plan(plan, n, R, w, theta, x, ref, sp=-1, sh=0.0):
                     j = lg | lj[r]
                     flip = ((j >> op.a) & 1) & ((j >> op.b) & 1)
                     a[:, r] = np.where(flip == 1, -a[:, r], a[:, r])
-        new = np.full(1 << n, np.nan, dtype=complex)
+        new = np.full(1 << t, np.nan, dtype=complex)
         addrs = []
         for r in range(1 << R):
             new[sb ^ so[r]] = a[:, r]
             addrs.append(sb ^ so[r])
         addrs = np.concatenate(addrs)
-        assert len(np.unique(addrs)) == 1 << n, "stage store is not a bijection"
+        assert len(np.unique(addrs)) == 1 << t, "stage store is not a bijection"
         smem = new
+    return smem
+
+
+def run_plan(plan, n, R, w, theta, x, ref, sp=-1, sh=0.0):
+    stages, ops, groups, members = plan
+    mats = group_mats(groups, members, theta, x, sp, sh)
+    smem = run_stages(np.zeros(1 << n, dtype=complex), stages, ops, mats, n, R, ref)
     return np.array([smem[swz(j, w)] for j in range(1 << n)])
+
+
+def export_passes(circ, t, c, R, fuse, w):
+    L = sv.library()
+    L.sv_debug_passes.argtypes = [ctypes.c_void_p, I32, I32, I32, I32, I32, ctypes.POINTER(I32)] + [ctypes.c_void_p] * 5
+    L.sv_debug_passes.restype = I32
+    counts = (I32 * 5)()
+    st = L.sv_debug_passes(ctypes.byref(circ.struct), t, c, R, int(fuse), w, counts, None, None, None, None, None)
+    assert st == 0, sv.sv_status_string(st)
+    arrays = [(Stage * max(1, counts[0]))(), (Op * max(1, counts[1]))(), (Group * max(1, counts[2]))(),
+              (Member * max(1, counts[3]))(), (PassDesc * max(1, counts[4]))()]
+    assert L.sv_debug_passes(ctypes.byref(circ.struct), t, c, R, int(fuse), w, counts, *arrays) == 0
+    return [a[:k] for a, k in zip(arrays, counts)]
+
+
+def run_passes(plan, n, R, w, theta, x, ref, sp=-1, sh=0.0):
+    stages, ops, groups, members, passes = plan
+    mats = group_mats(groups, members, theta, x, sp, sh)
+    state = np.zeros(1 << n, dtype=complex)
+    state[ref] = 1.0
+    for pd in passes:
+        t = pd.t
+        loc = np.zeros(1 << t, np.int64)
+        for i in range(1 << t):
+            for b in range(t):
+                if i >> b & 1:
+                    loc[i] ^= pd.gl[b]
+        sw = np.array([swz(i, w) for i in range(1 << t)])
+        covered = np.zeros(1 << n, bool)
+        for tile in range(1 << pd.n_tile_bits):
+            tb = 0
+            for k in range(pd.n_tile_bits):
+                if tile >> k & 1:
+                    tb ^= pd.gt[k]
+            gidx = tb ^ loc
+            assert not covered[gidx].any(), "tiles overlap"
+            covered[gidx] = True
+            smem = np.zeros(1 << t, dtype=complex)
+            smem[sw] = state[gidx]
+            smem = run_stages(smem, stages[pd.stage_begin:pd.stage_end], ops, mats, t, R)
+            state[gidx] = smem[sw]
+        assert covered.all(), "tiles do not cover the state"
+    return state
 
 
 CASES = [
@@ -199,3 +259,39 @@ def test_stage_limits():
     assert len(groups) == 12 * 6
     # 12 rotations per layer with 4 register bits -> 3 stages per layer
     assert len(stages) == 18
+
+
+PASS_CASES = [
+    (lambda: wl.qcl(9, 3, 2), 7, 3),
+    (lambda: wl.mcvqe(9, 3, "nn+nnn", n_refs=3), 6, 3),
+    (lambda: wl.random_workload(8, 80, 3, 2, seed=21, with_encoding=True), 6, 3),
+    (lambda: wl.mcvqe(7, 2), 7, 3),
+]
+
+
+@pytest.mark.parametrize("case", range(len(PASS_CASES)))
+@pytest.mark.parametrize("R", [2, 3])
+def test_tile_passes_match_oracle(case, R):
+    make, t, c = PASS_CASES[case]
+    w = make()
+    d = 0 if w.inputs is None else w.inputs.shape[1]
+    circ = sv.Circuit(w.n_qubits, w.gates, w.n_params, d)
+    for swz_bits in (3, 4):
+        plan = export_passes(circ, t, c, R, True, swz_bits)
+        passes = plan[4]
+        assert all(((p.local_mask & ((1 << c) - 1)) == (1 << c) - 1) for p in passes)
+        for i in range(min(2, w.n_instances)):
+            x = None if w.inputs is None else w.inputs[i]
+            sp = (5 * i + 1) % w.n_params
+            got = run_passes(plan, w.n_qubits, R, swz_bits, w.theta, x, int(w.refs[i]), sp, -0.4)
+            want = oracle.state(w, instance=i, shift_param=sp, shift=-0.4)
+            assert np.allclose(got, want, atol=1e-12), (case, R, swz_bits, i)
+
+
+def test_pass_counts_at_scale():
+    # 20-qubit circuit learning: encoding + 10 layers of Rx-Rz-Rx + CNOT ring
+    w = wl.qcl(20, 10, 1)
+    circ = sv.Circuit(20, w.gates, w.n_params, 1)
+    stages, ops, groups, members, passes = export_passes(circ, 12, 4, 4, True, 4)
+    assert 10 <= len(passes) <= 40
+    assert sum(p.n_u1 for p in passes) == len(groups)
