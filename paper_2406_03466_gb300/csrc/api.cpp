@@ -478,18 +478,27 @@ struct TileCfg {
 
 sv_status tile_cfg(int n, sv_dtype dt, const sv_plan_opts *o, TileCfg *cfg) {
     const int c = dt == SV_C128 ? 3 : 4, rmax = dt == SV_C128 ? 3 : 4;
-    int t = (o && o->tile_bits > 0) ? o->tile_bits : (dt == SV_C128 ? 11 : 12);
+    // Default: 2^11 (complex64) / 2^10 (complex128) amplitudes per tile with
+    // 3 / 2 register bits: 256 threads per block, no register spills.
+    int t = (o && o->tile_bits > 0) ? o->tile_bits : (dt == SV_C128 ? 10 : 11);
     if (t > n) t = n;
     if (t < c + 2 || t > 12)
         return fail(SV_ERR_UNSUPPORTED, "tile passes need 2^tile_bits amplitudes with tile_bits in "
                                         "[coalesced bits + 2, 12] and at most n_qubits");
-    int R = (o && o->reg_bits > 0) ? o->reg_bits : rmax;
+    int R = (o && o->reg_bits > 0) ? o->reg_bits : (dt == SV_C128 ? 2 : 3);
     if (R < 2 || R > rmax) return fail(SV_ERR_ARG, "reg_bits for tile passes must be 2..4 (2..3 complex128)");
     if (t - R > 8) R = t - 8;
     if (R > rmax) return fail(SV_ERR_UNSUPPORTED, "tile too large for the register width");
     cfg->t = t;
     cfg->R = R;
     return SV_OK;
+}
+
+// The op range [first, first + count) used by the stages of one pass.
+void pass_ops(const PlanEntry *pe, const PassDesc &pd, int *first, int *count) {
+    const auto &st = pe->host.stages;
+    *first = st[pd.stage_begin].op_begin;
+    *count = st[pd.stage_end - 1].op_end - *first;
 }
 
 // The program view of one pass: its stages, thread bases and tile size.
@@ -531,8 +540,13 @@ sv_status tiles_forward(DeviceCtx *ctx, const PlanEntry *pe, int R, sv_dtype dt,
     for (size_t i = 0; i < passes.size(); ++i) {
         const PassDesc &pd = passes[i];
         const int64_t tiles = (int64_t)src.n_slots << pd.n_tile_bits;
-        e = launch_pass_fwd(c128, R, pd, pass_view(pe, pd, R), n, src.n_slots, mats, G, states,
-                            pass_blocks(ctx, tiles, pass_fwd_smem(c128, pd.t)), st);
+        int op0 = 0, nops = 0;
+        pass_ops(pe, pd, &op0, &nops);
+        const Program pv = pass_view(pe, pd, R);
+        const uint32_t smem = pass_fwd_smem(c128, pd.t, R, G, pv.n_stages, nops);
+        if (smem > 220u * 1024u) return fail(SV_ERR_UNSUPPORTED, "tile pass needs too much shared memory");
+        e = launch_pass_fwd(c128, R, pd, pv, op0, nops, n, src.n_slots, mats, G, states,
+                            pass_blocks(ctx, tiles, smem), st);
         if (e != cudaSuccess) return cuda_fail(e, "forward tile pass");
         if (ck && every > 0 && (i + 1) % every == 0 && i + 1 < passes.size()) {
             e = cudaMemcpyAsync((char *)ck + ((i + 1) / every - 1) * sbytes, states, sbytes,
@@ -663,10 +677,13 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
             }
             const PassDesc &pd = passes[i];
             const int64_t tiles = (int64_t)src.n_slots << pd.n_tile_bits;
-            const uint32_t smem = pass_rev_smem(c128, pd.t, cfg.R, G, pd.n_u1);
+            int op0 = 0, nops = 0;
+            pass_ops(pe, pd, &op0, &nops);
+            const Program pv = pass_view(pe, pd, cfg.R);
+            const uint32_t smem = pass_rev_smem(c128, pd.t, cfg.R, G, pd.n_u1, pv.n_stages, nops);
             if (smem > 220u * 1024u) return fail(SV_ERR_UNSUPPORTED, "reverse pass needs too much shared memory");
-            e = launch_pass_rev(c128, cfg.R, pd, pass_view(pe, pd, cfg.R), n, src.n_slots, mats, G,
-                                psi, lam, rho, pass_blocks(ctx, tiles, smem), st);
+            e = launch_pass_rev(c128, cfg.R, pd, pv, op0, nops, n, src.n_slots, mats, G, psi, lam,
+                                rho, pass_blocks(ctx, tiles, smem), st);
             if (e != cudaSuccess) return cuda_fail(e, "reverse tile pass");
         }
         e = launch_group_grads(c128, pe->dev, src, rho, cs, Es + c0, Gs + (size_t)c0 * Pp, st);

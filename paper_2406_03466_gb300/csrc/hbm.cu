@@ -68,30 +68,124 @@ __device__ __forceinline__ uint32_t tile_base(const PassDesc &pd, uint32_t tile)
 
 // One forward pass over every tile of every slot.  `pv` is the pass's view
 // of the program (n = t, its own stages); `mats` holds [slots][G][4].
+// Asynchronous global -> shared copies (bypass registers) so that the next
+// tile is in flight while the current one is computed.
+__device__ __forceinline__ void cp_async(void *smem_dst, const void *gsrc, int bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if (bytes == 16)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// The pass's program in shared memory: stage records, its op range, the
+// thread bases of its stages and every group record.  `pv` must carry thread
+// bases (tile plans always do).  Byte offsets follow `base`.
+struct PassSmem {
+    uint32_t stages, ops, tbase, groups, end;
+};
+
+__host__ __device__ inline PassSmem pass_smem_layout(uint32_t base, int n_st, int n_ops, int T,
+                                                     int G) {
+    PassSmem L{};
+    auto up = [](uint32_t x) { return (x + 15u) & ~15u; };
+    L.stages = up(base);
+    L.ops = up(L.stages + (uint32_t)n_st * (uint32_t)sizeof(Stage));
+    L.tbase = up(L.ops + (uint32_t)n_ops * (uint32_t)sizeof(Op));
+    L.groups = up(L.tbase + (uint32_t)n_st * T * (uint32_t)sizeof(ThreadBase));
+    L.end = up(L.groups + (uint32_t)G * (uint32_t)sizeof(Group));
+    return L;
+}
+
+template <typename T>
+__device__ __forceinline__ void copy_words(T *dst, const T *src, int count) {
+    const int words = (int)(count * sizeof(T) / 4);
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = s[i];
+}
+
+// Copies the pass program into shared memory and returns a view whose
+// pointers all derive from the shared array (so reads compile to shared loads).
+__device__ __forceinline__ Program stage_pass_program(const Program &pv, int op0, int n_ops, int G,
+                                                      unsigned char *smem, const PassSmem &L) {
+    const int T = 1 << (pv.n - pv.R);
+    Stage *st = reinterpret_cast<Stage *>(smem + L.stages);
+    Op *ops = reinterpret_cast<Op *>(smem + L.ops);
+    ThreadBase *tb = reinterpret_cast<ThreadBase *>(smem + L.tbase);
+    Group *gr = reinterpret_cast<Group *>(smem + L.groups);
+    copy_words(st, pv.stages, pv.n_stages);
+    copy_words(ops, pv.ops + op0, n_ops);
+    copy_words(tb, pv.tbase, pv.n_stages * T);
+    copy_words(gr, pv.groups, G);
+    __syncthreads();
+    Program ps = pv;
+    ps.stages = st;
+    ps.ops = ops - op0;
+    ps.tbase = tb;
+    ps.groups = gr;
+    return ps;
+}
+
+// Copies slot b's fused group matrices ([G][4] complex) into shared memory.
+template <typename C>
+__device__ __forceinline__ void load_mats(C *dst, const C *mats, int b, int G) {
+    __syncthreads();
+    const C *src = mats + (size_t)b * G * 4;
+    for (int i = threadIdx.x; i < 4 * G; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+}
+
 template <typename Real, int R>
-__global__ void __launch_bounds__(256) k_pass_fwd(PassDesc pd, Program pv, int n, int n_slots,
-                                                  const typename CT<Real>::T *mats, int G,
-                                                  typename CT<Real>::T *states) {
+__global__ void __launch_bounds__(256, 3) k_pass_fwd(PassDesc pd, Program pv, int op0, int n_ops,
+                                                     int n, int n_slots,
+                                                     const typename CT<Real>::T *mats, int G,
+                                                     typename CT<Real>::T *states) {
     using C = typename CT<Real>::T;
     constexpr int NA = 1 << R;
     extern __shared__ __align__(16) unsigned char smem[];
-    C *tile = reinterpret_cast<C *>(smem);
+    const size_t tbytes = (size_t)sizeof(C) << pd.t;
+    C *buf[2] = {reinterpret_cast<C *>(smem), reinterpret_cast<C *>(smem + tbytes)};
+    C *smats = reinterpret_cast<C *>(smem + 2 * tbytes);
+    const PassSmem PL = pass_smem_layout((uint32_t)(2 * tbytes + (size_t)G * 4 * sizeof(C)),
+                                         pv.n_stages, n_ops, 1 << (pd.t - R), G);
+    const Program ps = stage_pass_program(pv, op0, n_ops, G, smem, PL);
     const int tid = threadIdx.x, t = pd.t, w = pv.swz_bits;
     uint32_t gk[R], sv[R];
     const uint32_t g0 = tile_vectors<R>(pd, tid, gk);
     const uint32_t s0 = natural_vectors<R>(tid, t - R, w, sv);
+    // contiguous tile ranges per block: the slot (and its matrices) rarely changes
     const int64_t tiles = (int64_t)n_slots << pd.n_tile_bits;
-    for (int64_t tix = blockIdx.x; tix < tiles; tix += gridDim.x) {
-        const int b = (int)(tix >> pd.n_tile_bits);
-        const uint32_t tb = tile_base(pd, (uint32_t)(tix & ((int64_t(1) << pd.n_tile_bits) - 1)));
-        C *S = states + ((int64_t)b << n);
+    const int64_t per = (tiles + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = per * blockIdx.x, t_end = min(tiles, t0 + per);
+    const int64_t tmask = (int64_t(1) << pd.n_tile_bits) - 1;
+    auto fetch = [&](int64_t tix, C *dst) {
+        const C *S = states + ((tix >> pd.n_tile_bits) << n);
+        const uint32_t tb = tile_base(pd, (uint32_t)(tix & tmask));
 #pragma unroll
-        for (int k = 0; k < NA; ++k) tile[s0 ^ xsel<R>(k, sv)] = S[tb ^ g0 ^ xsel<R>(k, gk)];
+        for (int k = 0; k < NA; ++k)
+            cp_async(dst + (s0 ^ xsel<R>(k, sv)), S + (tb ^ g0 ^ xsel<R>(k, gk)), (int)sizeof(C));
+        cp_async_commit();
+    };
+    if (t0 < t_end) fetch(t0, buf[0]);
+    int cur = -1;
+    for (int64_t tix = t0, i = 0; tix < t_end; ++tix, ++i) {
+        const int b = (int)(tix >> pd.n_tile_bits);
+        if (b != cur) {
+            load_mats(smats, mats, b, G);
+            cur = b;
+        }
+        C *tile = buf[i & 1];
+        cp_async_wait_all();
         __syncthreads();
-        forward_stages<Real, R, 0>(pv, tile, mats + (size_t)b * G * 4, tid, -1);
+        if (tix + 1 < t_end) fetch(tix + 1, buf[(i + 1) & 1]);
+        forward_stages<Real, R, 2>(ps, tile, smats, tid, -1);
+        C *S = states + ((int64_t)b << n);
+        const uint32_t tb = tile_base(pd, (uint32_t)(tix & tmask));
 #pragma unroll
         for (int k = 0; k < NA; ++k) S[tb ^ g0 ^ xsel<R>(k, gk)] = tile[s0 ^ xsel<R>(k, sv)];
-        __syncthreads();
     }
 }
 
@@ -131,15 +225,20 @@ __device__ void flush_rho(const Program &pv, const int *u2g, int n_u1, double *r
 // One reverse pass: un-applies the pass on psi and lambda tiles and sums the
 // reduced matrices of its groups (FP64) into rho_g[slot][group][8].
 template <typename Real, int R>
-__global__ void __launch_bounds__(256) k_pass_rev(PassDesc pd, Program pv, int n, int n_slots,
+__global__ void __launch_bounds__(256, 2) k_pass_rev(PassDesc pd, Program pv_g, int op0, int n_ops,
+                                                  int n, int n_slots,
                                                   const typename CT<Real>::T *mats, int G,
                                                   typename CT<Real>::T *psi,
                                                   typename CT<Real>::T *lam, double *rho_g) {
     using C = typename CT<Real>::T;
     constexpr int NA = 1 << R;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int tid = threadIdx.x, t = pd.t, w = pv.swz_bits, T = blockDim.x;
+    const int tid = threadIdx.x, t = pd.t, w = pv_g.swz_bits, T = blockDim.x;
     const RevLayout L = rev_layout(t, R, (int)sizeof(C), (int)sizeof(Real), G, pd.n_u1);
+    C *smats = reinterpret_cast<C *>(smem + L.total);
+    const PassSmem PL = pass_smem_layout(L.total + (uint32_t)(G * 4 * sizeof(C)), pv_g.n_stages,
+                                         n_ops, 1 << (pd.t - R), G);
+    const Program pv = stage_pass_program(pv_g, op0, n_ops, G, smem, PL);
     C *tp = reinterpret_cast<C *>(smem);
     C *tl = reinterpret_cast<C *>(smem + L.tile);
     Real *rhow = reinterpret_cast<Real *>(smem + L.rhow);
@@ -166,6 +265,7 @@ __global__ void __launch_bounds__(256) k_pass_rev(PassDesc pd, Program pv, int n
         const int b = (int)(tix >> pd.n_tile_bits);
         if (b != cur) {
             if (cur >= 0) flush_rho(pv, u2g, pd.n_u1, rho_blk, rho_g, cur, G);
+            load_mats(smats, mats, b, G);
             cur = b;
         }
         const uint32_t tb = tile_base(pd, (uint32_t)(tix & ((int64_t(1) << pd.n_tile_bits) - 1)));
@@ -177,7 +277,7 @@ __global__ void __launch_bounds__(256) k_pass_rev(PassDesc pd, Program pv, int n
             tl[sa] = Lm[ga];
         }
         __syncthreads();
-        reverse_stages<Real, R, 0>(pv, tp, tl, mats + (size_t)b * G * 4, tid, T, rhow, rho_blk);
+        reverse_stages<Real, R, 2>(pv, tp, tl, smats, tid, T, rhow, rho_blk);
 #pragma unroll
         for (int k = 0; k < NA; ++k) {
             const uint32_t ga = tb ^ g0 ^ xsel<R>(k, gk), sa = s0 ^ xsel<R>(k, sv);
@@ -358,39 +458,45 @@ cudaError_t launch_init_states(int c128, void *states, int n, const SlotSource &
     return cudaGetLastError();
 }
 
-uint32_t pass_fwd_smem(int c128, int t) { return (uint32_t)((c128 ? 16 : 8) << t); }
-
-uint32_t pass_rev_smem(int c128, int t, int R, int G, int n_u1) {
-    return rev_layout(t, R, c128 ? 16 : 8, c128 ? 8 : 4, G, n_u1).total;
+uint32_t pass_fwd_smem(int c128, int t, int R, int G, int n_st, int n_ops) {
+    const uint32_t base = 2u * (uint32_t)((c128 ? 16 : 8) << t) + (uint32_t)(G * 4 * (c128 ? 16 : 8));
+    return pass_smem_layout(base, n_st, n_ops, 1 << (t - R), G).end;
 }
 
-cudaError_t launch_pass_fwd(int c128, int R, const PassDesc &pd, const Program &pv, int n,
-                            int n_slots, const void *mats, int G, void *states, int blocks,
-                            cudaStream_t st) {
-    const uint32_t smem = pass_fwd_smem(c128, pd.t);
+uint32_t pass_rev_smem(int c128, int t, int R, int G, int n_u1, int n_st, int n_ops) {
+    const uint32_t base = rev_layout(t, R, c128 ? 16 : 8, c128 ? 8 : 4, G, n_u1).total +
+                          (uint32_t)(G * 4 * (c128 ? 16 : 8));
+    return pass_smem_layout(base, n_st, n_ops, 1 << (t - R), G).end;
+}
+
+cudaError_t launch_pass_fwd(int c128, int R, const PassDesc &pd, const Program &pv, int op0,
+                            int n_ops, int n, int n_slots, const void *mats, int G, void *states,
+                            int blocks, cudaStream_t st) {
+    const uint32_t smem = pass_fwd_smem(c128, pd.t, R, G, pv.n_stages, n_ops);
     const int threads = 1 << (pd.t - R);
     HBM_DISPATCH_R(c128, R, {
         using C = typename CT<Real>::T;
         auto k = k_pass_fwd<Real, RR>;
         cudaError_t e = allow_smem(k, smem);
         if (e != cudaSuccess) return e;
-        k<<<blocks, threads, smem, st>>>(pd, pv, n, n_slots, (const C *)mats, G, (C *)states);
+        k<<<blocks, threads, smem, st>>>(pd, pv, op0, n_ops, n, n_slots, (const C *)mats, G,
+                                         (C *)states);
     });
     return cudaGetLastError();
 }
 
-cudaError_t launch_pass_rev(int c128, int R, const PassDesc &pd, const Program &pv, int n,
-                            int n_slots, const void *mats, int G, void *psi, void *lam,
-                            double *rho_g, int blocks, cudaStream_t st) {
-    const uint32_t smem = pass_rev_smem(c128, pd.t, R, G, pd.n_u1);
+cudaError_t launch_pass_rev(int c128, int R, const PassDesc &pd, const Program &pv, int op0,
+                            int n_ops, int n, int n_slots, const void *mats, int G, void *psi,
+                            void *lam, double *rho_g, int blocks, cudaStream_t st) {
+    const uint32_t smem = pass_rev_smem(c128, pd.t, R, G, pd.n_u1, pv.n_stages, n_ops);
     const int threads = 1 << (pd.t - R);
     HBM_DISPATCH_R(c128, R, {
         using C = typename CT<Real>::T;
         auto k = k_pass_rev<Real, RR>;
         cudaError_t e = allow_smem(k, smem);
         if (e != cudaSuccess) return e;
-        k<<<blocks, threads, smem, st>>>(pd, pv, n, n_slots, (const C *)mats, G, (C *)psi,
-                                         (C *)lam, rho_g);
+        k<<<blocks, threads, smem, st>>>(pd, pv, op0, n_ops, n, n_slots, (const C *)mats, G,
+                                         (C *)psi, (C *)lam, rho_g);
     });
     return cudaGetLastError();
 }
