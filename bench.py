@@ -44,8 +44,12 @@ L2_FLUSH_BYTES = 256 << 20   # larger than the 126.5 MiB L2
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4000)
-    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=None)
+    ap.add_argument("--workload", default="mcvqe8", choices=["mcvqe8", "qcl20", "mcvqe28"],
+                    help="mcvqe8 (default): batched parameter-shift gradient of the 8-qubit "
+                         "MC-VQE; qcl20 / mcvqe28: adjoint gradient of the 20-qubit circuit "
+                         "learning / 28-qubit MC-VQE workload (states in device memory)")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true", help="skip adjoint/plain/c128 side runs")
@@ -163,9 +167,153 @@ def fp32_peak_tflops():
     return 152 * 128 * 2 * 2.07e9 / 1e12
 
 
+def measured_hbm_gbs():
+    """The measured copy bandwidth of the GB300s, else the
+    recipe's fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def forward_passes_roofline(sv, w, dev, flush, stream, reps=5):
+    """Times the forward simulation of workload `w` (all instances, states in
+    device memory) and reports it against the HBM roofline: each tile pass
+    reads and writes every state once, the |ref> initialisation writes them."""
+    import torch
+    d = 0 if w.inputs is None else 1
+    circ = sv.Circuit(w.n_qubits, w.gates, w.n_params, d)
+    info = sv.sv_plan_info(circ, "c64")
+    n, I = w.n_qubits, w.n_instances
+    st = sv.sv_alloc(n, I, "c64", device=dev)
+    theta = torch.as_tensor(w.theta, dtype=torch.float64, device=dev).reshape(1, -1)
+    xin = None if w.inputs is None else torch.as_tensor(w.inputs, device=dev)
+    slots = sv.make_slots([(0, 0, -1, i if d else -1, int(w.refs[i]), 0.0) for i in range(I)])
+    fn = lambda: sv.sv_apply_circuit_batch(st, [circ], slots, theta, xin)  # noqa: E731
+    fn()
+    t = timed_loop(fn, reps, flush, stream) / reps
+    nbytes = (2 * info["n_passes"] + 1) * I * (8 << n)
+    peak, src = measured_hbm_gbs()
+    achieved = nbytes / t / 1e9
+    st.free()
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": f"k_pass_fwd<float,3> x {info['n_passes']} tile passes of 2^{info['tile_bits']} "
+                      f"amplitudes ({w.name}: {I} states of {n} qubits)",
+            "forward_ms": t * 1e3, "bytes_per_forward": nbytes, "peak_source": src}
+
+
+def cpu_baseline_device_memory(w, seconds):
+    """The oracle on a bounded sample of a large workload: whole circuits
+    (each with its full <H>) for about `seconds`, scaled to parameter-shift
+    gradients (2P + 1 circuits per instance)."""
+    import oracle
+    threads = oracle.max_threads()
+    # Above 22 qubits one oracle circuit per core already runs for minutes:
+    # time the same family at 20 qubits and scale by the state size and the
+    # gate + term count.
+    ws, scale = w, 1.0
+    if w.n_qubits > 22:
+        ws = wl.mcvqe(20, w.meta.get("layers", 8), w.meta.get("pairs", "nn+nnn"),
+                      n_refs=w.n_instances)
+        cost = lambda x: (1 << x.n_qubits) * (len(x.gates) + 3 * x.n_terms)  # noqa: E731
+        scale = cost(w) / cost(ws)
+    t0 = time.perf_counter()
+    n_done = 0
+    while True:
+        k = max(1, threads)
+        oracle.energies(ws, None, np.arange(k) % ws.n_instances)
+        n_done += k
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    per_circuit = dt / n_done * scale
+    circuits = w.n_slots_param_shift
+    how = (f"{n_done} full circuits of {ws.name} in {dt:.1f} s" +
+           (f", scaled x{scale:.0f} to {w.name} by 2^n x (gates + 3 terms)" if ws is not w else "") +
+           f"; scaled to {circuits} circuits per parameter-shift gradient (extrapolated)")
+    return {"value": 1.0 / (per_circuit * circuits), "unit": "gradients/s", "cores": threads,
+            "kind": "oracle", "sample": how}
+
+
+def run_device_memory(args, sv, dev, stream, dist, world, rank):
+    """Adjoint gradient of a workload whose states live in device memory."""
+    import torch
+    w = wl.config(3 if args.workload == "qcl20" else 4)
+    prob = sv.Problem.from_spec(w, "c64", device=dev)
+    theta = torch.as_tensor(w.theta, dtype=torch.float64, device=dev)
+    out = sv._outputs(prob, dev, None, None, None)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        sv.sv_grad_adjoint(prob, theta, None, *out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    t_dev = timed_loop(step, args.steps, flush, stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([t_dev], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev = float(t.item())
+    gps = world * args.steps / t_dev
+    d = 0 if w.inputs is None else 1
+    info = sv.sv_plan_info(sv.Circuit(w.n_qubits, w.gates, w.n_params, d), "c64")
+    result = {"metric": METRIC, "value": gps, "unit": "gradients/s", "n_gpus": world,
+              "steps": args.steps, "warmup": args.warmup,
+              "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+              "config": {"workload": f"{w.name}: adjoint gradient, {w.n_instances} states of "
+                                     f"{w.n_qubits} qubits in device memory, {w.n_params} "
+                                     f"params, {info['n_passes']} tile passes per sweep",
+                         "l2": "states larger than L2; 256 MiB flush before each step",
+                         "parallelism": f"replicas x{world}"},
+              # per adjoint: group matrices, init (memset + |ref>), forward and reverse
+              # passes, lambda = H psi, per-slot gradients, combination
+              "gpu_launches": args.steps * (2 * info["n_passes"] + 5),
+              "clocks": clk, "wall_s_timed_region": t_wall}
+    if rank == 0:
+        result["roofline"] = forward_passes_roofline(sv, w, dev, flush, stream,
+                                                     reps=3 if w.n_qubits > 24 else 5)
+        th_host = torch.as_tensor(w.theta, dtype=torch.float64).pin_memory()
+        g_host = torch.empty(w.n_params, dtype=torch.float64).pin_memory()
+        th_dev = torch.empty_like(theta)
+        t0 = time.perf_counter()
+        reps = max(1, args.steps // 2)
+        for _ in range(reps):
+            th_dev.copy_(th_host, non_blocking=True)
+            l_, e_, g_ = sv.sv_grad_adjoint(prob, th_dev, None, *out)
+            g_host.copy_(g_[: w.n_params], non_blocking=True)
+            stream.synchronize()
+        result["e2e"] = {"value": reps / (time.perf_counter() - t0), "unit": "gradients/s",
+                         "h2d_bytes_per_step": 8 * w.n_params,
+                         "d2h_bytes_per_step": 8 * w.n_params}
+        result["cpu_baseline"] = cpu_baseline_device_memory(w, min(args.cpu_seconds, 10.0))
+        print(json.dumps(result))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     rank, world, local = rank_info()
+    if args.steps is None:
+        args.steps = {"mcvqe8": 4000, "qcl20": 20, "mcvqe28": 2}[args.workload]
+    if args.warmup is None:
+        args.warmup = {"mcvqe8": 50, "qcl20": 3, "mcvqe28": 1}[args.workload]
 
     if args.impl == "reference":
         if rank != 0:
@@ -194,6 +342,8 @@ def main():
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
+    if args.workload != "mcvqe8":
+        return run_device_memory(args, sv, dev, stream, dist, world, rank)
 
     w = wl.config(1)
     B = w.n_slots_param_shift
@@ -289,6 +439,9 @@ def main():
                          "timing": "host wall clock incl. stream synchronize per step"}
 
         if not args.no_extras:
+            # the metric's "% HBM roofline": forward tile passes of the
+            # 20-qubit circuit-learning batch (64 states, 512 MiB)
+            result["hbm_gate_passes"] = forward_passes_roofline(sv, wl.config(3), dev, flush, stream)
             extras = {}
             fn = lambda: sv.sv_grad_adjoint(prob, theta, None, *out)  # noqa: E731
             for _ in range(20):

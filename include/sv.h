@@ -262,6 +262,16 @@ sv_status sv_grad_param_shift_noalloc(const sv_problem *problem, const double *t
                                       double *energy_out, double *loss_out, double *grad_out,
                                       sv_stream_t stream);
 
+/* How a circuit will run for a state precision and options: on_chip = 1 when
+ * the whole state stays in one block's shared memory, else the number of tile
+ * passes over device memory and their tile size (2^tile_bits amplitudes);
+ * n_stages: register stages of the program; n_groups: fused single-qubit
+ * groups.  Host-only (plans the circuit, launches nothing).  Any out-pointer
+ * may be NULL. */
+sv_status sv_plan_info(const sv_circuit *circuit, sv_dtype dtype, const sv_plan_opts *opts,
+                       int32_t *on_chip, int32_t *n_passes, int32_t *tile_bits,
+                       int32_t *n_stages, int32_t *n_groups);
+
 /* ------------------------------------------------------------- autotune */
 
 /* Times the launch shapes (register bits 1..4, 32..512 threads per block) of

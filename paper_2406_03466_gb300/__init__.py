@@ -80,7 +80,7 @@ class sv_problem(ctypes.Structure):
 EXPORTED = ("sv_alloc", "sv_free", "sv_state_info", "sv_apply_circuit_batch",
             "sv_expect_pauli_sum", "sv_energies", "sv_param_shift_energies", "sv_grad_param_shift", "sv_grad_adjoint",
             "sv_grad_param_shift_plain", "sv_grad_param_shift_noalloc", "sv_autotune",
-            "sv_tuned_shape", "sv_status_string",
+            "sv_tuned_shape", "sv_plan_info", "sv_status_string",
             "sv_last_error",
             "sv_sync_status", "sv_shutdown", "sv_version")
 
@@ -104,6 +104,7 @@ def _load():
     lib.sv_grad_param_shift_plain.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_grad_param_shift_noalloc.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_autotune.argtypes = [P(sv_problem), V, I32, V]
+    lib.sv_plan_info.argtypes = [P(sv_circuit), I32, P(sv_plan_opts)] + [P(I32)] * 5
     lib.sv_tuned_shape.argtypes = [P(sv_problem), I32, P(I32), P(I32), P(ctypes.c_float)]
     lib.sv_status_string.argtypes = [I32]
     lib.sv_status_string.restype = ctypes.c_char_p
@@ -394,6 +395,16 @@ def sv_tuned_shape(problem: Problem, kind: int):
     _check(_lib.sv_tuned_shape(ctypes.byref(problem.struct), int(kind), ctypes.byref(r),
                                ctypes.byref(t), ctypes.byref(us)), "sv_tuned_shape")
     return r.value, t.value, us.value
+
+
+def sv_plan_info(circuit: Circuit, dtype="c64", opts: Optional[sv_plan_opts] = None) -> dict:
+    """How the circuit runs: on chip, or as tile passes (count, tile size)."""
+    vals = [ctypes.c_int32() for _ in range(5)]
+    _check(_lib.sv_plan_info(ctypes.byref(circuit.struct), _dtype_code(dtype),
+                             None if opts is None else ctypes.byref(opts),
+                             *[ctypes.byref(v) for v in vals]), "sv_plan_info")
+    keys = ("on_chip", "n_passes", "tile_bits", "n_stages", "n_groups")
+    return {k: v.value for k, v in zip(keys, vals)}
 
 
 def sv_status_string(status: int) -> str:

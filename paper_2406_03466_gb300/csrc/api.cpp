@@ -1319,6 +1319,34 @@ sv_status sv_autotune(const sv_problem *p, const double *theta, int32_t kinds,
     return SV_OK;
 }
 
+sv_status sv_plan_info(const sv_circuit *c, sv_dtype dt, const sv_plan_opts *o, int32_t *on_chip,
+                       int32_t *n_passes, int32_t *tile_bits, int32_t *n_stages,
+                       int32_t *n_groups) {
+    sv_status s = check_circuit(c, dt == SV_C128 ? 29 : 30);
+    if (s != SV_OK) return s;
+    HostProgram h;
+    std::string err;
+    const bool tiles = wants_tiles(c->n_qubits, dt, o);
+    int t = 0;
+    if (tiles) {
+        TileCfg cfg{};
+        s = tile_cfg(c->n_qubits, dt, o, &cfg);
+        if (s != SV_OK) return s;
+        t = cfg.t;
+        err = plan_passes(*c, cfg.t, dt == SV_C128 ? 3 : 4, cfg.R, use_fusion(o), swz_bits(dt), &h);
+    } else {
+        err = plan_circuit(*c, (o && o->reg_bits > 0) ? o->reg_bits : (dt == SV_C128 ? 3 : 4),
+                           use_fusion(o), swz_bits(dt), &h);
+    }
+    if (!err.empty()) return fail(SV_ERR_ARG, "circuit: " + err);
+    if (on_chip) *on_chip = tiles ? 0 : 1;
+    if (n_passes) *n_passes = (int32_t)h.passes.size();
+    if (tile_bits) *tile_bits = t;
+    if (n_stages) *n_stages = (int32_t)h.stages.size();
+    if (n_groups) *n_groups = (int32_t)h.groups.size();
+    return SV_OK;
+}
+
 sv_status sv_tuned_shape(const sv_problem *p, int32_t kind, int32_t *reg_bits,
                          int32_t *threads_per_block, float *us) {
     if (!p || !p->circuit || !p->observable) return fail(SV_ERR_ARG, "problem is NULL");

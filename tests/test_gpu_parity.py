@@ -199,8 +199,9 @@ def test_errors_are_reported(sv):
     with pytest.raises(sv.SvError):
         sv.sv_grad_adjoint(sv.Problem.from_spec(bad, "c64"), theta_of(w))
     big = wl.random_workload(16, 10, 2, 1, seed=1)
-    with pytest.raises(sv.SvError):
-        sv.sv_grad_adjoint(sv.Problem.from_spec(big, "c64"), theta_of(big))
+    with pytest.raises(sv.SvError):  # tiles larger than 2^12 amplitudes are not offered
+        sv.sv_grad_adjoint(sv.Problem.from_spec(big, "c64", opts=sv.plan_opts(tile_bits=13)),
+                           theta_of(big))
     sv.sv_sync_status()
     assert torch.cuda.is_available()
 
