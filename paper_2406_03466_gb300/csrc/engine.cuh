@@ -191,6 +191,21 @@ __device__ __forceinline__ void u1_bit(C (&a)[1 << R], const C m0, const C m1, c
     }
 }
 
+// Real 2x2 matrix [[m0, m1], [m2, m3]] on register bit I: 4 FMAs per amplitude.
+template <typename C, typename Real, int R, int I>
+__device__ __forceinline__ void u1r_bit(C (&a)[1 << R], const Real m0, const Real m1,
+                                        const Real m2, const Real m3) {
+#pragma unroll
+    for (int r = 0; r < (1 << R); ++r) {
+        if (r & (1 << I)) continue;
+        const C x = a[r], y = a[r | (1 << I)];
+        a[r].x = fmaR(m0, x.x, m1 * y.x);
+        a[r].y = fmaR(m0, x.y, m1 * y.y);
+        a[r | (1 << I)].x = fmaR(m2, x.x, m3 * y.x);
+        a[r | (1 << I)].y = fmaR(m2, x.y, m3 * y.y);
+    }
+}
+
 template <typename C, int R>
 __device__ __forceinline__ void u1_reg(C (&a)[1 << R], int i, const C m0, const C m1, const C m2,
                                        const C m3) {
@@ -288,9 +303,32 @@ __device__ __forceinline__ Bases stage_bases(const Stage *sg, int tid) {
     return b;
 }
 
+// The ops of register bit I (sorted stages): compile-time register indices,
+// no dispatch; real matrices take the half-cost path.
+template <typename C, int R, int I>
+__device__ __forceinline__ void bit_ops_fwd(const Program &p, const Stage *sg, const C *mats,
+                                            C (&a)[1 << R]) {
+    if constexpr (I < R) {
+        const int e = sg->op_begin + sg->bit_begin[I + 1];
+        for (int o = sg->op_begin + sg->bit_begin[I]; o < e; ++o) {
+            const Op op = p.ops[o];
+            const C *m = mats + 4 * op.group;
+            if (p.groups[op.group].real)
+                u1r_bit<C, decltype(m[0].x), R, I>(a, m[0].x, m[1].x, m[2].x, m[3].x);
+            else
+                u1_bit<C, R, I>(a, m[0], m[1], m[2], m[3]);
+        }
+        bit_ops_fwd<C, R, I + 1>(p, sg, mats, a);
+    }
+}
+
 template <typename C, int R>
 __device__ __forceinline__ void apply_stage_ops(const Program &p, const Stage *sg, const C *mats,
                                                 C (&a)[1 << R], uint32_t lg, const int (&qq)[R]) {
+    if (sg->sorted) {
+        bit_ops_fwd<C, R, 0>(p, sg, mats, a);
+        return;
+    }
     for (int o = sg->op_begin; o < sg->op_end; ++o) {
         const Op op = p.ops[o];
         if (op.kind == OP_U1) {
@@ -597,6 +635,46 @@ __device__ void group_gradients(const Program &p, int g, const double *rho8, con
     }
 }
 
+// Reverse of bit_ops_fwd for bits I, I-1, ..., 0: per op, the partial reduced
+// matrix of bit I (reduced over the warp, written to rw[u]) then the inverse
+// gate on psi and lambda.  u counts the stage's ops downwards.
+template <typename C, typename Real, int R, int I>
+__device__ __forceinline__ void bit_ops_rev(const Program &p, const Stage *sg, const C *mats,
+                                            C (&a)[1 << R], C (&al)[1 << R], int &u, int width,
+                                            int tid, int wps, Real *rw) {
+    if constexpr (I >= 0) {
+        const int b0 = sg->op_begin + sg->bit_begin[I];
+        for (int o = sg->op_begin + sg->bit_begin[I + 1] - 1; o >= b0; --o) {
+            const Op op = p.ops[o];
+            --u;
+            const Group grp = p.groups[op.group];
+            if (grp.has_param) {
+                Real rh[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                rho_bit<C, Real, R, I>(a, al, rh);
+#pragma unroll
+                for (int v = 0; v < 8; ++v)
+                    for (int off = width >> 1; off > 0; off >>= 1)
+                        rh[v] += __shfl_xor_sync(0xffffffffu, rh[v], off);
+                if ((tid & 31) == 0) {
+                    Real *dst = rw + (u * wps + (tid >> 5)) * 8;
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) dst[v] = rh[v];
+                }
+            }
+            const C *m = mats + 4 * op.group;
+            if (grp.real) {
+                u1r_bit<C, Real, R, I>(a, m[0].x, m[2].x, m[1].x, m[3].x);
+                u1r_bit<C, Real, R, I>(al, m[0].x, m[2].x, m[1].x, m[3].x);
+            } else {
+                const C d0 = cconj(m[0]), d1 = cconj(m[2]), d2 = cconj(m[1]), d3 = cconj(m[3]);
+                u1_bit<C, R, I>(a, d0, d1, d2, d3);
+                u1_bit<C, R, I>(al, d0, d1, d2, d3);
+            }
+        }
+        bit_ops_rev<C, Real, R, I - 1>(p, sg, mats, a, al, u, width, tid, wps, rw);
+    }
+}
+
 // Reverse sweep over every stage of `p` on psi and lambda (both in shared
 // memory, natural order, swizzled): un-applies each stage, and for every
 // fused group with parameters adds the reduced matrix
@@ -633,6 +711,9 @@ __device__ void reverse_stages(const Program &p, typename CT<Real>::T *psi,
         }
         Real *rw = rhow + (s & 1) * (kMaxGroupOpsPerStage * wps * 8);
         int u = sg->n_u1;
+        if (sg->sorted)
+            bit_ops_rev<C, Real, R, R - 1>(p, sg, mats, a, al, u, width, tid, wps, rw);
+        else
         for (int oi = sg->op_end - 1; oi >= sg->op_begin; --oi) {
             const Op op = p.ops[oi];
             if (op.kind == OP_U1) {

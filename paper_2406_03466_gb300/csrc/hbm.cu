@@ -46,6 +46,19 @@ __global__ void k_set_ref(C *states, int n, SlotSource src) {
     }
 }
 
+// Shared-memory addresses of this thread's tile amplitudes through the
+// pass's load permutation: returns the tid part, fills the k part.
+template <int R>
+__device__ __forceinline__ uint32_t perm_vectors(const PassDesc &pd, int tid, uint32_t (&pk)[R]) {
+    const int tb = pd.t - R;
+    uint32_t g = 0;
+    for (int b = 0; b < tb; ++b)
+        if ((tid >> b) & 1) g ^= pd.ldperm[b];
+#pragma unroll
+    for (int j = 0; j < R; ++j) pk[j] = pd.ldperm[tb + j];
+    return g;
+}
+
 // Global offsets (within one state) of this thread's 2^R tile amplitudes:
 // local index i = tid + k * 2^(t-R); returns the tid part, fills the k part.
 template <int R>
@@ -153,9 +166,10 @@ __global__ void __launch_bounds__(256, 3) k_pass_fwd(PassDesc pd, Program pv, in
                                          pv.n_stages, n_ops, 1 << (pd.t - R), G);
     const Program ps = stage_pass_program(pv, op0, n_ops, G, smem, PL);
     const int tid = threadIdx.x, t = pd.t, w = pv.swz_bits;
-    uint32_t gk[R], sv[R];
+    uint32_t gk[R], sv[R], pk[R];
     const uint32_t g0 = tile_vectors<R>(pd, tid, gk);
     const uint32_t s0 = natural_vectors<R>(tid, t - R, w, sv);
+    const uint32_t p0 = perm_vectors<R>(pd, tid, pk);
     // contiguous tile ranges per block: the slot (and its matrices) rarely changes
     const int64_t tiles = (int64_t)n_slots << pd.n_tile_bits;
     const int64_t per = (tiles + gridDim.x - 1) / gridDim.x;
@@ -166,7 +180,7 @@ __global__ void __launch_bounds__(256, 3) k_pass_fwd(PassDesc pd, Program pv, in
         const uint32_t tb = tile_base(pd, (uint32_t)(tix & tmask));
 #pragma unroll
         for (int k = 0; k < NA; ++k)
-            cp_async(dst + (s0 ^ xsel<R>(k, sv)), S + (tb ^ g0 ^ xsel<R>(k, gk)), (int)sizeof(C));
+            cp_async(dst + (p0 ^ xsel<R>(k, pk)), S + (tb ^ g0 ^ xsel<R>(k, gk)), (int)sizeof(C));
         cp_async_commit();
     };
     if (t0 < t_end) fetch(t0, buf[0]);
@@ -252,9 +266,10 @@ __global__ void __launch_bounds__(256, 2) k_pass_rev(PassDesc pd, Program pv_g, 
                 if (pv.ops[oi].kind == OP_U1 && u < pd.n_u1) u2g[u++] = pv.ops[oi].group;
     }
     __syncthreads();
-    uint32_t gk[R], sv[R];
+    uint32_t gk[R], sv[R], pk[R];
     const uint32_t g0 = tile_vectors<R>(pd, tid, gk);
     const uint32_t s0 = natural_vectors<R>(tid, t - R, w, sv);
+    const uint32_t p0 = perm_vectors<R>(pd, tid, pk);
     // Each block walks one contiguous range of tiles (few slot changes, so
     // few flushes of its rho sums).
     const int64_t tiles = (int64_t)n_slots << pd.n_tile_bits;
@@ -279,8 +294,8 @@ __global__ void __launch_bounds__(256, 2) k_pass_rev(PassDesc pd, Program pv_g, 
         __syncthreads();
         reverse_stages<Real, R, 2>(pv, tp, tl, smats, tid, T, rhow, rho_blk);
 #pragma unroll
-        for (int k = 0; k < NA; ++k) {
-            const uint32_t ga = tb ^ g0 ^ xsel<R>(k, gk), sa = s0 ^ xsel<R>(k, sv);
+        for (int k = 0; k < NA; ++k) {  // back through the pass's load permutation
+            const uint32_t ga = tb ^ g0 ^ xsel<R>(k, gk), sa = p0 ^ xsel<R>(k, pk);
             P[ga] = tp[sa];
             Lm[ga] = tl[sa];
         }

@@ -94,9 +94,12 @@ std::string fuse_circuit(const sv_circuit &c, bool fuse, FusedCircuit *F) {
         Group grp{};
         grp.m_begin = (int)F->members.size();
         grp.qubit = gq[g];
+        grp.real = 1;
         for (const Member &m : gm[g]) {
             F->members.push_back(m);
             if (m.kind <= M_RZ && m.param >= 0) grp.has_param = 1;
+            if (!(m.kind == M_RY || m.kind == M_X || m.kind == M_H || m.kind == M_ENC_RY_ASIN))
+                grp.real = 0;
         }
         grp.m_end = (int)F->members.size();
         F->groups.push_back(grp);
@@ -126,6 +129,20 @@ void stage_lops(const std::vector<LOp> &lops, const std::vector<int> &pos, int t
         for (int p = 0; (int)Q.size() < R && p < t; ++p)
             if (find_pos(Q, p) < 0) Q.push_back(p);
         Stage st{};
+        bool any_cz = false;
+        for (const Op &o : sops) any_cz |= o.kind != OP_U1;
+        if (!any_cz) {
+            // fused groups on different register bits commute: order by bit
+            std::stable_sort(sops.begin(), sops.end(),
+                             [](const Op &x, const Op &y) { return x.a < y.a; });
+            st.sorted = 1;
+            int k = 0;
+            for (int i = 0; i <= kRMax; ++i) {
+                while (k < (int)sops.size() && sops[k].a < i) ++k;
+                st.bit_begin[i] = k;
+            }
+            st.bit_begin[kRMax] = (int)sops.size();
+        }
         st.op_begin = (int)P->ops.size();
         for (const Op &o : sops) P->ops.push_back(o);
         st.op_end = (int)P->ops.size();
@@ -288,6 +305,17 @@ std::string plan_passes(const sv_circuit &c, int tile_bits, int coalesce_bits, i
         for (int idx : taken) sub.push_back(F.lops[idx]);
         stage_lops(sub, pos, t, reg_bits, swz_bits, P);
         pd.stage_end = (int)P->stages.size();
+        // A leading stage without ops is only a permutation: fold it into
+        // the tile load (and the reverse pass's tile store).
+        for (int b = 0; b < t; ++b) pd.ldperm[b] = swizzle(1u << b, swz_bits);
+        const Stage &s0 = P->stages[pd.stage_begin];
+        if (s0.op_begin == s0.op_end) {
+            const std::vector<uint32_t> &col = P->perm_cols[pd.stage_begin];
+            for (int b = 0; b < t; ++b) pd.ldperm[b] = swizzle(col[b], swz_bits);
+            P->stages.erase(P->stages.begin() + pd.stage_begin);
+            P->perm_cols.erase(P->perm_cols.begin() + pd.stage_begin);
+            --pd.stage_end;
+        }
         int nu = 0;
         for (int s = pd.stage_begin; s < pd.stage_end; ++s) nu += P->stages[s].n_u1;
         pd.n_u1 = nu;

@@ -37,6 +37,7 @@ struct Group {
     int32_t m_begin, m_end;  // members [m_begin, m_end) in time order
     int32_t qubit;
     int32_t has_param;       // 1 if some member reads theta (needs a gradient)
+    int32_t real;            // 1 if the fused matrix is real (Ry, X, H, Ry encodings only)
 };
 
 enum OpKind : int32_t { OP_U1 = 0, OP_CZ = 1 };
@@ -58,6 +59,11 @@ struct Stage {
     uint32_t stq[kRMax];        // swizzled address vector of register bit i, store layout
     uint32_t ldt[kNMax];        // same for thread bit k
     uint32_t stt[kNMax];
+    // sorted = 1: the stage's ops are all fused groups, ordered by register
+    // bit (ops on different bits commute), and bit i owns the ops
+    // [op_begin + bit_begin[i], op_begin + bit_begin[i + 1]).
+    int32_t sorted;
+    int32_t bit_begin[kRMax + 1];
 };
 
 // One tile pass over states in device memory: a tile is the 2^t amplitudes
@@ -71,6 +77,10 @@ struct PassDesc {
     uint32_t local_mask;             // qubits local to the pass
     uint32_t gl[kNMax];
     uint32_t gt[kNMax];
+    // Shared-memory address vector of tile-local bit b when the tile is
+    // loaded (forward) or stored back (reverse): swizzle(f(e_b)) for the
+    // pass's leading CNOT permutation f (identity if it has none).
+    uint32_t ldperm[kNMax];
 };
 
 // Pauli terms grouped by X-mask: <psi|P|psi> = Re(i^phase sum_j (-1)^{|j & z|}

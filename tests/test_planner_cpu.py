@@ -25,7 +25,7 @@ I32, U32 = ctypes.c_int32, ctypes.c_uint32
 class Stage(ctypes.Structure):
     _fields_ = [("op_begin", I32), ("op_end", I32), ("n_thr", I32), ("n_u1", I32),
                 ("q", I32 * 5), ("tpos", I32 * 30), ("ldq", U32 * 5), ("stq", U32 * 5),
-                ("ldt", U32 * 30), ("stt", U32 * 30)]
+                ("ldt", U32 * 30), ("stt", U32 * 30), ("sorted", I32), ("bit_begin", I32 * 6)]
 
 
 class Op(ctypes.Structure):
@@ -33,7 +33,8 @@ class Op(ctypes.Structure):
 
 
 class Group(ctypes.Structure):
-    _fields_ = [("m_begin", I32), ("m_end", I32), ("qubit", I32), ("has_param", I32)]
+    _fields_ = [("m_begin", I32), ("m_end", I32), ("qubit", I32), ("has_param", I32),
+                ("real", I32)]
 
 
 class Member(ctypes.Structure):
@@ -42,7 +43,8 @@ class Member(ctypes.Structure):
 
 class PassDesc(ctypes.Structure):
     _fields_ = [("stage_begin", I32), ("stage_end", I32), ("t", I32), ("n_tile_bits", I32),
-                ("n_u1", I32), ("local_mask", U32), ("gl", U32 * 30), ("gt", U32 * 30)]
+                ("n_u1", I32), ("local_mask", U32), ("gl", U32 * 30), ("gt", U32 * 30),
+                ("ldperm", U32 * 30)]
 
 
 def lib():
@@ -204,6 +206,11 @@ def run_passes(plan, n, R, w, theta, x, ref, sp=-1, sh=0.0):
                 if i >> b & 1:
                     loc[i] ^= pd.gl[b]
         sw = np.array([swz(i, w) for i in range(1 << t)])
+        lp = np.zeros(1 << t, np.int64)  # load through the pass's leading permutation
+        for i in range(1 << t):
+            for b in range(t):
+                if i >> b & 1:
+                    lp[i] ^= pd.ldperm[b]
         covered = np.zeros(1 << n, bool)
         for tile in range(1 << pd.n_tile_bits):
             tb = 0
@@ -213,8 +220,9 @@ def run_passes(plan, n, R, w, theta, x, ref, sp=-1, sh=0.0):
             gidx = tb ^ loc
             assert not covered[gidx].any(), "tiles overlap"
             covered[gidx] = True
-            smem = np.zeros(1 << t, dtype=complex)
-            smem[sw] = state[gidx]
+            smem = np.full(1 << t, np.nan, dtype=complex)
+            smem[lp] = state[gidx]
+            assert not np.isnan(smem).any(), "load permutation is not a bijection"
             smem = run_stages(smem, stages[pd.stage_begin:pd.stage_end], ops, mats, t, R)
             state[gidx] = smem[sw]
         assert covered.all(), "tiles do not cover the state"
