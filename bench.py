@@ -199,7 +199,7 @@ def forward_passes_roofline(sv, w, dev, flush, stream, reps=5):
     st.free()
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": None,
-            "kernel": f"k_pass_fwd<float,3> x {info['n_passes']} tile passes of 2^{info['tile_bits']} "
+            "kernel": f"k_tile_fwd x {info['n_passes']} tile passes of 2^{info['tile_bits']} "
                       f"amplitudes ({w.name}: {I} states of {n} qubits)",
             "forward_ms": t * 1e3, "bytes_per_forward": nbytes, "peak_source": src}
 

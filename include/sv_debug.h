@@ -17,7 +17,7 @@
 extern "C" {
 #endif
 
-/* sizes[0..6] = sizeof of Stage, Op, Group, Member, TermGroup, Term, PassDesc. */
+/* sizes[0..7] = sizeof of Stage, Op, Group, Member, TermGroup, Term, PassDesc, TilePass. */
 void sv_debug_sizes(int32_t *sizes);
 
 sv_status sv_debug_plan(const sv_circuit *circuit, int32_t reg_bits, int32_t fuse,
@@ -30,6 +30,13 @@ sv_status sv_debug_plan(const sv_circuit *circuit, int32_t reg_bits, int32_t fus
 sv_status sv_debug_passes(const sv_circuit *circuit, int32_t tile_bits, int32_t coalesce_bits,
                           int32_t reg_bits, int32_t fuse, int32_t swz_bits, int32_t *counts,
                           void *stages, void *ops, void *groups, void *members, void *passes);
+
+/* The kernel descriptors of the tile passes exactly as the GPU entry points
+ * build them for `dtype` (SV_C64 / SV_C128): counts[0..2] = groups, members,
+ * passes; `tile_passes` gets counts[2] descriptors of sizes[7] bytes. */
+sv_status sv_debug_tile_passes(const sv_circuit *circuit, int32_t tile_bits, int32_t reg_bits,
+                               int32_t fuse, int32_t dtype, int32_t *counts, void *groups,
+                               void *members, void *tile_passes);
 
 #ifdef __cplusplus
 }

@@ -64,6 +64,7 @@ struct PlanEntry {
     std::vector<sv_gate> gates;  // exact key check against hash collisions
     int n = 0, n_params = 0, input_dim = 0;
     HostProgram host;
+    std::vector<TilePass> tiles;  // tile plans: one kernel descriptor per pass
     DeviceBuf buf;
     Program dev{};
 };
@@ -156,7 +157,7 @@ sv_status get_plan(DeviceCtx *ctx, const sv_circuit &c, int R, bool fuse, sv_dty
     std::string err;
     if (tile_bits > 0) {
         err = plan_passes(c, tile_bits, dt == SV_C128 ? 3 : 4, R, fuse, swz_bits(dt), &e->host);
-        if (err.empty()) build_thread_bases(&e->host, tile_bits);
+        if (err.empty()) err = build_tile_passes(e->host, dt == SV_C128 ? 16 : 8, &e->tiles);
     } else {
         err = plan_circuit(c, R, fuse, swz_bits(dt), &e->host);
     }
@@ -485,41 +486,22 @@ sv_status tile_cfg(int n, sv_dtype dt, const sv_plan_opts *o, TileCfg *cfg) {
     if (t < c + 2 || t > 12)
         return fail(SV_ERR_UNSUPPORTED, "tile passes need 2^tile_bits amplitudes with tile_bits in "
                                         "[coalesced bits + 2, 12] and at most n_qubits");
-    int R = (o && o->reg_bits > 0) ? o->reg_bits : (dt == SV_C128 ? 2 : 3);
+    int R = (o && o->reg_bits > 0) ? o->reg_bits : std::min(dt == SV_C128 ? 2 : 3, t - 5);
     if (R < 2 || R > rmax) return fail(SV_ERR_ARG, "reg_bits for tile passes must be 2..4 (2..3 complex128)");
     if (t - R > 8) R = t - 8;
     if (R > rmax) return fail(SV_ERR_UNSUPPORTED, "tile too large for the register width");
+    if (t - R < 5)
+        return fail(SV_ERR_UNSUPPORTED, "tile passes need tile_bits - reg_bits >= 5 (a warp of threads)");
     cfg->t = t;
     cfg->R = R;
     return SV_OK;
 }
 
-// The op range [first, first + count) used by the stages of one pass.
-void pass_ops(const PlanEntry *pe, const PassDesc &pd, int *first, int *count) {
-    const auto &st = pe->host.stages;
-    *first = st[pd.stage_begin].op_begin;
-    *count = st[pd.stage_end - 1].op_end - *first;
-}
-
-// The program view of one pass: its stages, thread bases and tile size.
-Program pass_view(const PlanEntry *pe, const PassDesc &pd, int R) {
-    Program v = pe->dev;
-    v.n = pd.t;
-    v.R = R;
-    v.n_stages = pd.stage_end - pd.stage_begin;
-    v.stages = pe->dev.stages + pd.stage_begin;
-    const int T = 1 << (pd.t - R);
-    v.tbase = pe->dev.tbase ? pe->dev.tbase + (size_t)pd.stage_begin * T : nullptr;
-    return v;
-}
-
-int pass_blocks(const DeviceCtx *ctx, int64_t tiles, uint32_t smem) {
-    int per_sm = (int)((200u * 1024u) / (smem + 1024u));
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm > 8) per_sm = 8;
-    int64_t b = (int64_t)ctx->sms * per_sm;
-    if (b > tiles) b = tiles;
-    return (int)(b < 1 ? 1 : b);
+// Upper bound on the blocks of a tile-pass launch (the launcher caps it by
+// the kernel's occupancy): at most one block per tile.
+int64_t tile_blocks(const DeviceCtx *ctx, int64_t tiles) {
+    const int64_t b = (int64_t)ctx->sms * 8;
+    return b < tiles ? b : tiles;
 }
 
 // Forward tile passes of `pe` over src.n_slots states (|ref> first when init).
@@ -536,17 +518,13 @@ sv_status tiles_forward(DeviceCtx *ctx, const PlanEntry *pe, int R, sv_dtype dt,
         e = launch_init_states(c128, states, n, src, st);
         if (e != cudaSuccess) return cuda_fail(e, "state init");
     }
-    const auto &passes = pe->host.passes;
+    const auto &passes = pe->tiles;
     for (size_t i = 0; i < passes.size(); ++i) {
-        const PassDesc &pd = passes[i];
-        const int64_t tiles = (int64_t)src.n_slots << pd.n_tile_bits;
-        int op0 = 0, nops = 0;
-        pass_ops(pe, pd, &op0, &nops);
-        const Program pv = pass_view(pe, pd, R);
-        const uint32_t smem = pass_fwd_smem(c128, pd.t, R, G, pv.n_stages, nops);
+        const TilePass &tp = passes[i];
+        const int64_t tiles = (int64_t)src.n_slots << tp.n_tile_bits;
+        const uint32_t smem = tile_fwd_smem(c128, tp);
         if (smem > 220u * 1024u) return fail(SV_ERR_UNSUPPORTED, "tile pass needs too much shared memory");
-        e = launch_pass_fwd(c128, R, pd, pv, op0, nops, n, src.n_slots, mats, G, states,
-                            pass_blocks(ctx, tiles, smem), st);
+        e = launch_tile_fwd(c128, tp, n, src.n_slots, mats, G, states, tile_blocks(ctx, tiles), st);
         if (e != cudaSuccess) return cuda_fail(e, "forward tile pass");
         if (ck && every > 0 && (i + 1) % every == 0 && i + 1 < passes.size()) {
             e = cudaMemcpyAsync((char *)ck + ((i + 1) / every - 1) * sbytes, states, sbytes,
@@ -626,7 +604,7 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
     s = get_array(ctx, p->refs, sizeof(int64_t) * I, &drefs);
     if (s != SV_OK) return s;
     const int G = pe->dev.n_groups;
-    const int npass = (int)pe->host.passes.size();
+    const int npass = (int)pe->tiles.size();
     if (every <= 0) every = 4;
     const int ncp = npass > 1 ? (npass - 1) / every : 0;
     const size_t csz = c128 ? 16 : 8, sb = csz << n;
@@ -650,7 +628,7 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
     double *Gs = (double *)scr, *Es = Gs + (size_t)I * Pp;
     SV_CUDA(cudaMemsetAsync(Gs, 0, sizeof(double) * (size_t)I * Pp, st));
     const CostSource cs = cost_of(p, weights);
-    const auto &passes = pe->host.passes;
+    const auto &passes = pe->tiles;
     for (int64_t c0 = 0; c0 < I; c0 += chunk) {
         SlotSource src{};
         src.mode = SLOTS_INSTANCES;
@@ -675,15 +653,12 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
                 SV_CUDA(cudaMemcpyAsync(psi, (char *)ck + (size_t)((i + 1) / every - 1) * cb, cb,
                                         cudaMemcpyDeviceToDevice, st));
             }
-            const PassDesc &pd = passes[i];
-            const int64_t tiles = (int64_t)src.n_slots << pd.n_tile_bits;
-            int op0 = 0, nops = 0;
-            pass_ops(pe, pd, &op0, &nops);
-            const Program pv = pass_view(pe, pd, cfg.R);
-            const uint32_t smem = pass_rev_smem(c128, pd.t, cfg.R, G, pd.n_u1, pv.n_stages, nops);
+            const TilePass &tp = passes[i];
+            const int64_t tiles = (int64_t)src.n_slots << tp.n_tile_bits;
+            const uint32_t smem = tile_rev_smem(c128, tp);
             if (smem > 220u * 1024u) return fail(SV_ERR_UNSUPPORTED, "reverse pass needs too much shared memory");
-            e = launch_pass_rev(c128, cfg.R, pd, pv, op0, nops, n, src.n_slots, mats, G, psi, lam,
-                                rho, pass_blocks(ctx, tiles, smem), st);
+            e = launch_tile_rev(c128, tp, n, src.n_slots, mats, G, psi, lam, rho,
+                                tile_blocks(ctx, tiles), st);
             if (e != cudaSuccess) return cuda_fail(e, "reverse tile pass");
         }
         e = launch_group_grads(c128, pe->dev, src, rho, cs, Es + c0, Gs + (size_t)c0 * Pp, st);

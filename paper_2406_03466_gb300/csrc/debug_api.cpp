@@ -1,6 +1,7 @@
 // Test hooks declared in sv_debug.h: host-side planner output, no GPU needed.
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "planner.h"
 #include "sv_debug.h"
@@ -18,6 +19,7 @@ void sv_debug_sizes(int32_t *sizes) {
     sizes[4] = (int32_t)sizeof(TermGroup);
     sizes[5] = (int32_t)sizeof(Term);
     sizes[6] = (int32_t)sizeof(PassDesc);
+    sizes[7] = (int32_t)sizeof(TilePass);
 }
 
 sv_status sv_debug_plan(const sv_circuit *c, int32_t reg_bits, int32_t fuse, int32_t swz_bits,
@@ -54,6 +56,25 @@ sv_status sv_debug_passes(const sv_circuit *c, int32_t tile_bits, int32_t coales
     if (groups) std::memcpy(groups, h.groups.data(), h.groups.size() * sizeof(Group));
     if (members) std::memcpy(members, h.members.data(), h.members.size() * sizeof(Member));
     if (passes) std::memcpy(passes, h.passes.data(), h.passes.size() * sizeof(PassDesc));
+    return SV_OK;
+}
+
+sv_status sv_debug_tile_passes(const sv_circuit *c, int32_t tile_bits, int32_t reg_bits,
+                               int32_t fuse, int32_t dtype, int32_t *counts, void *groups,
+                               void *members, void *tile_passes) {
+    if (!c || !counts) return SV_ERR_ARG;
+    const bool c128 = dtype == SV_C128;
+    HostProgram h;
+    std::string err = plan_passes(*c, tile_bits, c128 ? 3 : 4, reg_bits, fuse != 0, c128 ? 3 : 4, &h);
+    std::vector<TilePass> tp;
+    if (err.empty()) err = build_tile_passes(h, c128 ? 16 : 8, &tp);
+    if (!err.empty()) return SV_ERR_ARG;
+    counts[0] = (int32_t)h.groups.size();
+    counts[1] = (int32_t)h.members.size();
+    counts[2] = (int32_t)tp.size();
+    if (groups) std::memcpy(groups, h.groups.data(), h.groups.size() * sizeof(Group));
+    if (members) std::memcpy(members, h.members.data(), h.members.size() * sizeof(Member));
+    if (tile_passes) std::memcpy(tile_passes, tp.data(), tp.size() * sizeof(TilePass));
     return SV_OK;
 }
 

@@ -46,262 +46,357 @@ __global__ void k_set_ref(C *states, int n, SlotSource src) {
     }
 }
 
-// Shared-memory addresses of this thread's tile amplitudes through the
-// pass's load permutation: returns the tid part, fills the k part.
-template <int R>
-__device__ __forceinline__ uint32_t perm_vectors(const PassDesc &pd, int tid, uint32_t (&pk)[R]) {
-    const int tb = pd.t - R;
-    uint32_t g = 0;
-    for (int b = 0; b < tb; ++b)
-        if ((tid >> b) & 1) g ^= pd.ldperm[b];
-#pragma unroll
-    for (int j = 0; j < R; ++j) pk[j] = pd.ldperm[tb + j];
-    return g;
-}
+// ------------------------------------------------------------ tile passes
+//
+// A block owns one contiguous range of (slot, tile) pairs.  Tiles arrive by
+// cp.async in one of two buffers, so the next tile is in flight while the
+// current one is computed.  Every register stage loads the thread's 2^R
+// amplitudes from shared memory, applies the fused 2x2 group of each of its
+// register bits (at most one per bit) and stores them back in place.  The
+// pass descriptor is a __grid_constant__ parameter: its stage vectors are
+// read with warp-uniform indices through the constant cache.  Each thread
+// computes its per-stage address bases once per launch.
 
-// Global offsets (within one state) of this thread's 2^R tile amplitudes:
-// local index i = tid + k * 2^(t-R); returns the tid part, fills the k part.
-template <int R>
-__device__ __forceinline__ uint32_t tile_vectors(const PassDesc &pd, int tid, uint32_t (&gk)[R]) {
-    const int tb = pd.t - R;
-    uint32_t g = 0;
-    for (int b = 0; b < tb; ++b)
-        if ((tid >> b) & 1) g ^= pd.gl[b];
-#pragma unroll
-    for (int j = 0; j < R; ++j) gk[j] = pd.gl[tb + j];
-    return g;
+__device__ __forceinline__ void cp_async_amp(uint32_t sdst, const float2 *g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sdst), "l"(g) : "memory");
 }
-
-__device__ __forceinline__ uint32_t tile_base(const PassDesc &pd, uint32_t tile) {
-    uint32_t g = 0;
-    for (int k = 0; k < pd.n_tile_bits; ++k)
-        if ((tile >> k) & 1) g ^= pd.gt[k];
-    return g;
-}
-
-// One forward pass over every tile of every slot.  `pv` is the pass's view
-// of the program (n = t, its own stages); `mats` holds [slots][G][4].
-// Asynchronous global -> shared copies (bypass registers) so that the next
-// tile is in flight while the current one is computed.
-__device__ __forceinline__ void cp_async(void *smem_dst, const void *gsrc, int bytes) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    if (bytes == 16)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+__device__ __forceinline__ void cp_async_amp(uint32_t sdst, const double2 *g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst), "l"(g) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// The pass's program in shared memory: stage records, its op range, the
-// thread bases of its stages and every group record.  `pv` must carry thread
-// bases (tile plans always do).  Byte offsets follow `base`.
-struct PassSmem {
-    uint32_t stages, ops, tbase, groups, end;
+// Offsets of this thread's amplitudes (tile-local index tid + k 2^(t-R))
+// through the per-bit vector table v: returns the tid part and fills the
+// parts of the R register bits.
+template <int R>
+__device__ __forceinline__ uint32_t bit_vectors(const uint32_t *v, int t, int tid,
+                                                uint32_t (&k)[R]) {
+    const int tb = t - R;
+    uint32_t g = 0;
+    for (int b = 0; b < tb; ++b)
+        if ((tid >> b) & 1) g ^= v[b];
+#pragma unroll
+    for (int j = 0; j < R; ++j) k[j] = v[tb + j];
+    return g;
+}
+
+// Position of one tile in the walk over (slot, tile): global offset of the
+// tile's first amplitude within its state.
+struct TileCursor {
+    int slot;
+    uint32_t local, base;
 };
 
-__host__ __device__ inline PassSmem pass_smem_layout(uint32_t base, int n_st, int n_ops, int T,
-                                                     int G) {
-    PassSmem L{};
-    auto up = [](uint32_t x) { return (x + 15u) & ~15u; };
-    L.stages = up(base);
-    L.ops = up(L.stages + (uint32_t)n_st * (uint32_t)sizeof(Stage));
-    L.tbase = up(L.ops + (uint32_t)n_ops * (uint32_t)sizeof(Op));
-    L.groups = up(L.tbase + (uint32_t)n_st * T * (uint32_t)sizeof(ThreadBase));
-    L.end = up(L.groups + (uint32_t)G * (uint32_t)sizeof(Group));
-    return L;
+__device__ __forceinline__ TileCursor tile_cursor(const TilePass &P, int64_t tix) {
+    TileCursor c;
+    c.slot = (int)(tix >> P.n_tile_bits);
+    c.local = (uint32_t)(tix & ((int64_t(1) << P.n_tile_bits) - 1));
+    c.base = 0;
+    for (int k = 0; k < P.n_tile_bits; ++k)
+        if ((c.local >> k) & 1u) c.base ^= P.gpre[k] ^ (k ? P.gpre[k - 1] : 0u);
+    return c;
 }
 
-template <typename T>
-__device__ __forceinline__ void copy_words(T *dst, const T *src, int count) {
-    const int words = (int)(count * sizeof(T) / 4);
-    const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
-    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
-    for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = s[i];
+// Next tile: counting up flips tile-number bits 0..ctz(local + 1).
+__device__ __forceinline__ TileCursor tile_next(const TilePass &P, TileCursor c) {
+    ++c.local;
+    if ((c.local >> P.n_tile_bits) != 0u) {
+        c.local = 0;
+        c.base = 0;
+        ++c.slot;
+    } else {
+        c.base ^= P.gpre[__ffs((int)c.local) - 1];
+    }
+    return c;
 }
 
-// Copies the pass program into shared memory and returns a view whose
-// pointers all derive from the shared array (so reads compile to shared loads).
-__device__ __forceinline__ Program stage_pass_program(const Program &pv, int op0, int n_ops, int G,
-                                                      unsigned char *smem, const PassSmem &L) {
-    const int T = 1 << (pv.n - pv.R);
-    Stage *st = reinterpret_cast<Stage *>(smem + L.stages);
-    Op *ops = reinterpret_cast<Op *>(smem + L.ops);
-    ThreadBase *tb = reinterpret_cast<ThreadBase *>(smem + L.tbase);
-    Group *gr = reinterpret_cast<Group *>(smem + L.groups);
-    copy_words(st, pv.stages, pv.n_stages);
-    copy_words(ops, pv.ops + op0, n_ops);
-    copy_words(tb, pv.tbase, pv.n_stages * T);
-    copy_words(gr, pv.groups, G);
-    __syncthreads();
-    Program ps = pv;
-    ps.stages = st;
-    ps.ops = ops - op0;
-    ps.tbase = tb;
-    ps.groups = gr;
-    return ps;
-}
-
-// Copies slot b's fused group matrices ([G][4] complex) into shared memory.
-template <typename C>
-__device__ __forceinline__ void load_mats(C *dst, const C *mats, int b, int G) {
-    __syncthreads();
-    const C *src = mats + (size_t)b * G * 4;
-    for (int i = threadIdx.x; i < 4 * G; i += blockDim.x) dst[i] = src[i];
-    __syncthreads();
-}
-
-template <typename Real, int R>
-__global__ void __launch_bounds__(256, 3) k_pass_fwd(PassDesc pd, Program pv, int op0, int n_ops,
-                                                     int n, int n_slots,
-                                                     const typename CT<Real>::T *mats, int G,
-                                                     typename CT<Real>::T *states) {
-    using C = typename CT<Real>::T;
-    constexpr int NA = 1 << R;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const size_t tbytes = (size_t)sizeof(C) << pd.t;
-    C *buf[2] = {reinterpret_cast<C *>(smem), reinterpret_cast<C *>(smem + tbytes)};
-    C *smats = reinterpret_cast<C *>(smem + 2 * tbytes);
-    const PassSmem PL = pass_smem_layout((uint32_t)(2 * tbytes + (size_t)G * 4 * sizeof(C)),
-                                         pv.n_stages, n_ops, 1 << (pd.t - R), G);
-    const Program ps = stage_pass_program(pv, op0, n_ops, G, smem, PL);
-    const int tid = threadIdx.x, t = pd.t, w = pv.swz_bits;
-    uint32_t gk[R], sv[R], pk[R];
-    const uint32_t g0 = tile_vectors<R>(pd, tid, gk);
-    const uint32_t s0 = natural_vectors<R>(tid, t - R, w, sv);
-    const uint32_t p0 = perm_vectors<R>(pd, tid, pk);
-    // contiguous tile ranges per block: the slot (and its matrices) rarely changes
-    const int64_t tiles = (int64_t)n_slots << pd.n_tile_bits;
-    const int64_t per = (tiles + gridDim.x - 1) / gridDim.x;
-    const int64_t t0 = per * blockIdx.x, t_end = min(tiles, t0 + per);
-    const int64_t tmask = (int64_t(1) << pd.n_tile_bits) - 1;
-    auto fetch = [&](int64_t tix, C *dst) {
-        const C *S = states + ((tix >> pd.n_tile_bits) << n);
-        const uint32_t tb = tile_base(pd, (uint32_t)(tix & tmask));
-#pragma unroll
-        for (int k = 0; k < NA; ++k)
-            cp_async(dst + (p0 ^ xsel<R>(k, pk)), S + (tb ^ g0 ^ xsel<R>(k, gk)), (int)sizeof(C));
-        cp_async_commit();
-    };
-    if (t0 < t_end) fetch(t0, buf[0]);
-    int cur = -1;
-    for (int64_t tix = t0, i = 0; tix < t_end; ++tix, ++i) {
-        const int b = (int)(tix >> pd.n_tile_bits);
-        if (b != cur) {
-            load_mats(smats, mats, b, G);
-            cur = b;
+// The group ops of one stage, register bits I..R-1 in order.
+template <typename C, int R, int I>
+__device__ __forceinline__ void tile_ops_fwd(const TilePass &P, const TileStage &sg, const C *sm,
+                                             C (&a)[1 << R]) {
+    if constexpr (I < R) {
+        const int u = sg.op[I];
+        if (u >= 0) {
+            const C m0 = sm[4 * u], m1 = sm[4 * u + 1], m2 = sm[4 * u + 2], m3 = sm[4 * u + 3];
+            if ((P.real_mask >> u) & 1ull)
+                u1r_bit<C, decltype(m0.x), R, I>(a, m0.x, m1.x, m2.x, m3.x);
+            else
+                u1_bit<C, R, I>(a, m0, m1, m2, m3);
         }
-        C *tile = buf[i & 1];
-        cp_async_wait_all();
-        __syncthreads();
-        if (tix + 1 < t_end) fetch(tix + 1, buf[(i + 1) & 1]);
-        forward_stages<Real, R, 2>(ps, tile, smats, tid, -1);
-        C *S = states + ((int64_t)b << n);
-        const uint32_t tb = tile_base(pd, (uint32_t)(tix & tmask));
-#pragma unroll
-        for (int k = 0; k < NA; ++k) S[tb ^ g0 ^ xsel<R>(k, gk)] = tile[s0 ^ xsel<R>(k, sv)];
+        tile_ops_fwd<C, R, I + 1>(P, sg, sm, a);
     }
 }
 
-// Shared-memory layout of the reverse pass: psi tile, lambda tile, per-warp
-// rho partials (two buffers), per-block FP64 rho sums by group, group ids of
-// the pass's fused ops.
-struct RevLayout {
-    uint32_t tile, rhow, rho, u2g, total;
-};
-
-__host__ __device__ inline RevLayout rev_layout(int t, int R, int csz, int rsz, int G, int n_u1) {
-    RevLayout L{};
-    const uint32_t tile = (uint32_t)(csz << t);
-    const int T = 1 << (t - R), wps = T >= 32 ? T / 32 : 1;
-    L.tile = tile;
-    L.rhow = 2 * tile;
-    L.rho = L.rhow + (uint32_t)((2 * kMaxGroupOpsPerStage * wps * 8 * rsz + 15) & ~15);
-    L.u2g = L.rho + (uint32_t)(G * 64);
-    L.total = L.u2g + (uint32_t)((n_u1 * 4 + 15) & ~15);
-    return L;
+// One forward pass over every tile of every slot.  mats: [slots][G][4].
+template <typename Real, int R>
+__global__ void __launch_bounds__(256, 3)
+k_tile_fwd(const __grid_constant__ TilePass P, int n, int n_slots,
+           const typename CT<Real>::T *mats, int G, typename CT<Real>::T *states) {
+    using C = typename CT<Real>::T;
+    constexpr int NA = 1 << R;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x, T = blockDim.x, t = P.t, S = P.n_stages;
+    const uint32_t tbytes = (uint32_t)sizeof(C) << t;
+    uint2 *tb = reinterpret_cast<uint2 *>(smem + 2 * tbytes);
+    C *sm = reinterpret_cast<C *>(smem + 2 * tbytes + (uint32_t)S * T * 8u);
+    for (int s = 0; s < S; ++s) {
+        const TileStage &sg = P.st[s];
+        uint32_t lb = 0, sb = 0;
+        for (int k = 0; k < t - R; ++k)
+            if ((tid >> k) & 1) {
+                lb ^= sg.ldt[k];
+                sb ^= sg.stt[k];
+            }
+        tb[s * T + tid] = make_uint2(lb, sb);
+    }
+    uint32_t gk[R], pk[R], nk[R];
+    const uint32_t g0 = bit_vectors<R>(P.gl, t, tid, gk);
+    const uint32_t p0 = bit_vectors<R>(P.ldperm, t, tid, pk);
+    const uint32_t n0 = bit_vectors<R>(P.nat, t, tid, nk);
+    const uint32_t sh = (uint32_t)__cvta_generic_to_shared(smem);
+    const int64_t tiles = (int64_t)n_slots << P.n_tile_bits;
+    const int64_t per = (tiles + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = per * blockIdx.x, t_end = min(tiles, t0 + per);
+    if (t0 >= t_end) return;
+    auto fetch = [&](const TileCursor &c, int buf) {
+        const C *src = states + ((int64_t)c.slot << n) + c.base;
+        const uint32_t d = sh + (uint32_t)buf * tbytes;
+#pragma unroll
+        for (int k = 0; k < NA; ++k) cp_async_amp(d + (p0 ^ xsel<R>(k, pk)), src + (g0 ^ xsel<R>(k, gk)));
+        cp_async_commit();
+    };
+    TileCursor cur = tile_cursor(P, t0);
+    fetch(cur, 0);
+    TileCursor nxt = tile_next(P, cur);
+    int mslot = -1;
+    for (int64_t tix = t0, i = 0; tix < t_end; ++tix, ++i) {
+        const int buf = (int)(i & 1);
+        if (cur.slot != mslot) {  // the previous tile's stages are past their last barrier
+            for (int x = tid; x < 4 * P.n_ops; x += T)
+                sm[x] = mats[((size_t)cur.slot * G + P.grp[x >> 2]) * 4 + (x & 3)];
+            mslot = cur.slot;
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (tix + 1 < t_end) fetch(nxt, buf ^ 1);
+        unsigned char *tile = smem + (uint32_t)buf * tbytes;
+        for (int s = 0; s < S; ++s) {
+            const TileStage &sg = P.st[s];
+            const uint2 bb = tb[s * T + tid];
+            uint32_t lq[R], sq[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                lq[j] = sg.ldq[j];
+                sq[j] = sg.stq[j];
+            }
+            C a[NA];
+#pragma unroll
+            for (int r = 0; r < NA; ++r) a[r] = *reinterpret_cast<const C *>(tile + (bb.x ^ xsel<R>(r, lq)));
+            tile_ops_fwd<C, R, 0>(P, sg, sm, a);
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < NA; ++r) *reinterpret_cast<C *>(tile + (bb.y ^ xsel<R>(r, sq))) = a[r];
+            __syncthreads();
+        }
+        C *dst = states + ((int64_t)cur.slot << n) + cur.base;
+#pragma unroll
+        for (int k = 0; k < NA; ++k)
+            dst[g0 ^ xsel<R>(k, gk)] = *reinterpret_cast<const C *>(tile + (n0 ^ xsel<R>(k, nk)));
+        cur = nxt;
+        nxt = tile_next(P, nxt);
+    }
 }
 
-// Adds the block's rho sums of slot b for the pass's groups to rho_g and clears them.
-__device__ void flush_rho(const Program &pv, const int *u2g, int n_u1, double *rho_blk,
-                          double *rho_g, int b, int G) {
+// Sum over the 32 lanes of the 8 values rh[0..7]: lane l ends with the total
+// of value l & 7 (reduce-scatter over lane bits 0-2, then lane bits 3-4).
+template <typename Real>
+__device__ __forceinline__ Real warp_reduce8(const Real (&rh)[8], int lane) {
+    constexpr unsigned full = 0xffffffffu;
+    Real y[4], z[2];
+    const bool b0 = lane & 1, b1 = lane & 2, b2 = lane & 4;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const Real keep = b0 ? rh[2 * j + 1] : rh[2 * j], give = b0 ? rh[2 * j] : rh[2 * j + 1];
+        y[j] = keep + __shfl_xor_sync(full, give, 1);
+    }
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const Real keep = b1 ? y[2 * m + 1] : y[2 * m], give = b1 ? y[2 * m] : y[2 * m + 1];
+        z[m] = keep + __shfl_xor_sync(full, give, 2);
+    }
+    const Real keep = b2 ? z[1] : z[0], give = b2 ? z[0] : z[1];
+    Real v = keep + __shfl_xor_sync(full, give, 4);
+    v += __shfl_xor_sync(full, v, 8);
+    v += __shfl_xor_sync(full, v, 16);
+    return v;
+}
+
+// Reverse of tile_ops_fwd, register bits I, I-1, ..., 0: per op, first the
+// reduced matrix rho_ab = sum psi_a conj(lambda_b) of its bit (at the point
+// after the group) into the warp's accumulator acc[u][warp][8], then the
+// inverse group (sm holds the adjoint matrices) on psi and lambda.
+template <typename C, typename Real, int R, int I>
+__device__ __forceinline__ void tile_ops_rev(const TilePass &P, const TileStage &sg, const C *sm,
+                                             C (&a)[1 << R], C (&al)[1 << R], Real *accw,
+                                             int wps, int lane) {
+    if constexpr (I >= 0) {
+        const int u = sg.op[I];
+        if (u >= 0) {
+            if ((P.param_mask >> u) & 1ull) {
+                Real rh[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                rho_bit<C, Real, R, I>(a, al, rh);
+                const Real v = warp_reduce8<Real>(rh, lane);
+                if (lane < 8) accw[u * wps * 8 + lane] += v;
+            }
+            const C m0 = sm[4 * u], m1 = sm[4 * u + 1], m2 = sm[4 * u + 2], m3 = sm[4 * u + 3];
+            if ((P.real_mask >> u) & 1ull) {
+                u1r_bit<C, Real, R, I>(a, m0.x, m1.x, m2.x, m3.x);
+                u1r_bit<C, Real, R, I>(al, m0.x, m1.x, m2.x, m3.x);
+            } else {
+                u1_bit<C, R, I>(a, m0, m1, m2, m3);
+                u1_bit<C, R, I>(al, m0, m1, m2, m3);
+            }
+        }
+        tile_ops_rev<C, Real, R, I - 1>(P, sg, sm, a, al, accw, wps, lane);
+    }
+}
+
+// Adds the block's reduced-matrix sums of slot b (FP64 over warps) to
+// rho_g[b][group][8] and clears them.  Called by every thread.
+template <typename Real>
+__device__ void flush_acc(const TilePass &P, Real *acc, int wps, double *rho_g, int b, int G) {
     __syncthreads();
-    for (int idx = threadIdx.x; idx < n_u1 * 8; idx += blockDim.x) {
-        const int gi = u2g[idx >> 3], v = idx & 7;
-        if (!pv.groups[gi].has_param) continue;
-        const double x = rho_blk[gi * 8 + v];
-        if (x != 0.0) atomicAdd(&rho_g[((size_t)b * G + gi) * 8 + v], x);
-        rho_blk[gi * 8 + v] = 0.0;
+    for (int x = threadIdx.x; x < P.n_ops * 8; x += blockDim.x) {
+        const int u = x >> 3, v = x & 7;
+        if (!((P.param_mask >> u) & 1ull)) continue;
+        double s = 0.0;
+        for (int w = 0; w < wps; ++w) {
+            Real &r = acc[(u * wps + w) * 8 + v];
+            s += (double)r;
+            r = 0;
+        }
+        if (s != 0.0) atomicAdd(&rho_g[((size_t)b * G + P.grp[u]) * 8 + v], s);
     }
     __syncthreads();
 }
 
 // One reverse pass: un-applies the pass on psi and lambda tiles and sums the
-// reduced matrices of its groups (FP64) into rho_g[slot][group][8].
+// reduced matrices of its parametrised groups into rho_g[slot][group][8].
+// Reduced-matrix partials are summed in the state's precision over one
+// warp and at most 64 tiles, then in FP64.
 template <typename Real, int R>
-__global__ void __launch_bounds__(256, 2) k_pass_rev(PassDesc pd, Program pv_g, int op0, int n_ops,
-                                                  int n, int n_slots,
-                                                  const typename CT<Real>::T *mats, int G,
-                                                  typename CT<Real>::T *psi,
-                                                  typename CT<Real>::T *lam, double *rho_g) {
+__global__ void __launch_bounds__(256, 2)
+k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
+           const typename CT<Real>::T *mats, int G, typename CT<Real>::T *psi,
+           typename CT<Real>::T *lam, double *rho_g) {
     using C = typename CT<Real>::T;
     constexpr int NA = 1 << R;
+    constexpr int kFlushTiles = 64;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int tid = threadIdx.x, t = pd.t, w = pv_g.swz_bits, T = blockDim.x;
-    const RevLayout L = rev_layout(t, R, (int)sizeof(C), (int)sizeof(Real), G, pd.n_u1);
-    C *smats = reinterpret_cast<C *>(smem + L.total);
-    const PassSmem PL = pass_smem_layout(L.total + (uint32_t)(G * 4 * sizeof(C)), pv_g.n_stages,
-                                         n_ops, 1 << (pd.t - R), G);
-    const Program pv = stage_pass_program(pv_g, op0, n_ops, G, smem, PL);
-    C *tp = reinterpret_cast<C *>(smem);
-    C *tl = reinterpret_cast<C *>(smem + L.tile);
-    Real *rhow = reinterpret_cast<Real *>(smem + L.rhow);
-    double *rho_blk = reinterpret_cast<double *>(smem + L.rho);
-    int *u2g = reinterpret_cast<int *>(smem + L.u2g);
-    for (int i = tid; i < G * 8; i += T) rho_blk[i] = 0.0;
-    if (tid == 0) {
-        int u = 0;
-        for (int s = 0; s < pv.n_stages; ++s)
-            for (int oi = pv.stages[s].op_begin; oi < pv.stages[s].op_end; ++oi)
-                if (pv.ops[oi].kind == OP_U1 && u < pd.n_u1) u2g[u++] = pv.ops[oi].group;
+    const int tid = threadIdx.x, T = blockDim.x, t = P.t, S = P.n_stages;
+    const int lane = tid & 31, wps = T >> 5;
+    const uint32_t tbytes = (uint32_t)sizeof(C) << t;
+    uint2 *tb = reinterpret_cast<uint2 *>(smem + 4 * tbytes);
+    C *sm = reinterpret_cast<C *>(smem + 4 * tbytes + (uint32_t)S * T * 8u);
+    Real *acc = reinterpret_cast<Real *>(sm + 4 * P.n_ops);
+    for (int s = 0; s < S; ++s) {
+        const TileStage &sg = P.st[s];
+        uint32_t lb = 0, sb = 0;
+        for (int k = 0; k < t - R; ++k)
+            if ((tid >> k) & 1) {
+                lb ^= sg.ldt[k];
+                sb ^= sg.stt[k];
+            }
+        tb[s * T + tid] = make_uint2(lb, sb);
     }
-    __syncthreads();
-    uint32_t gk[R], sv[R], pk[R];
-    const uint32_t g0 = tile_vectors<R>(pd, tid, gk);
-    const uint32_t s0 = natural_vectors<R>(tid, t - R, w, sv);
-    const uint32_t p0 = perm_vectors<R>(pd, tid, pk);
-    // Each block walks one contiguous range of tiles (few slot changes, so
-    // few flushes of its rho sums).
-    const int64_t tiles = (int64_t)n_slots << pd.n_tile_bits;
+    for (int x = tid; x < P.n_ops * wps * 8; x += T) acc[x] = 0;
+    Real *accw = acc + (tid >> 5) * 8;
+    uint32_t gk[R], pk[R], nk[R];
+    const uint32_t g0 = bit_vectors<R>(P.gl, t, tid, gk);
+    const uint32_t p0 = bit_vectors<R>(P.ldperm, t, tid, pk);
+    const uint32_t n0 = bit_vectors<R>(P.nat, t, tid, nk);
+    const uint32_t sh = (uint32_t)__cvta_generic_to_shared(smem);
+    const int64_t tiles = (int64_t)n_slots << P.n_tile_bits;
     const int64_t per = (tiles + gridDim.x - 1) / gridDim.x;
-    const int64_t t_end = min(tiles, per * (blockIdx.x + 1));
-    int cur = -1;
-    for (int64_t tix = per * blockIdx.x; tix < t_end; ++tix) {
-        const int b = (int)(tix >> pd.n_tile_bits);
-        if (b != cur) {
-            if (cur >= 0) flush_rho(pv, u2g, pd.n_u1, rho_blk, rho_g, cur, G);
-            load_mats(smats, mats, b, G);
-            cur = b;
-        }
-        const uint32_t tb = tile_base(pd, (uint32_t)(tix & ((int64_t(1) << pd.n_tile_bits) - 1)));
-        C *P = psi + ((int64_t)b << n), *Lm = lam + ((int64_t)b << n);
+    const int64_t t0 = per * blockIdx.x, t_end = min(tiles, t0 + per);
+    if (t0 >= t_end) return;
+    // psi tile of buffer j at [j tbytes], lambda tile at [(2 + j) tbytes]
+    auto fetch = [&](const TileCursor &c, int buf) {
+        const int64_t off = ((int64_t)c.slot << n) + c.base;
+        const C *sp = psi + off, *sl = lam + off;
+        const uint32_t dp = sh + (uint32_t)buf * tbytes, dl = dp + 2 * tbytes;
 #pragma unroll
         for (int k = 0; k < NA; ++k) {
-            const uint32_t ga = tb ^ g0 ^ xsel<R>(k, gk), sa = s0 ^ xsel<R>(k, sv);
-            tp[sa] = P[ga];
-            tl[sa] = Lm[ga];
+            const uint32_t so = n0 ^ xsel<R>(k, nk), go = g0 ^ xsel<R>(k, gk);
+            cp_async_amp(dp + so, sp + go);
+            cp_async_amp(dl + so, sl + go);
         }
+        cp_async_commit();
+    };
+    TileCursor cur = tile_cursor(P, t0);
+    fetch(cur, 0);
+    TileCursor nxt = tile_next(P, cur);
+    int mslot = -1, since = 0;
+    for (int64_t tix = t0, i = 0; tix < t_end; ++tix, ++i) {
+        const int buf = (int)(i & 1);
+        if (cur.slot != mslot || since == kFlushTiles) {
+            if (mslot >= 0) flush_acc<Real>(P, acc, wps, rho_g, mslot, G);
+            since = 0;
+        }
+        if (cur.slot != mslot) {  // adjoint matrices of this slot's groups
+            for (int x = tid; x < 4 * P.n_ops; x += T) {
+                const C *m = mats + ((size_t)cur.slot * G + P.grp[x >> 2]) * 4;
+                const int e = x & 3, te = e == 1 ? 2 : (e == 2 ? 1 : e);
+                C d = m[te];
+                d.y = -d.y;
+                sm[x] = d;
+            }
+            mslot = cur.slot;
+        }
+        cp_async_wait_all();
         __syncthreads();
-        reverse_stages<Real, R, 2>(pv, tp, tl, smats, tid, T, rhow, rho_blk);
+        if (tix + 1 < t_end) fetch(nxt, buf ^ 1);
+        unsigned char *tp = smem + (uint32_t)buf * tbytes, *tl = tp + 2 * tbytes;
+        for (int s = S - 1; s >= 0; --s) {
+            const TileStage &sg = P.st[s];
+            const uint2 bb = tb[s * T + tid];
+            uint32_t lq[R], sq[R];
 #pragma unroll
-        for (int k = 0; k < NA; ++k) {  // back through the pass's load permutation
-            const uint32_t ga = tb ^ g0 ^ xsel<R>(k, gk), sa = p0 ^ xsel<R>(k, pk);
-            P[ga] = tp[sa];
-            Lm[ga] = tl[sa];
+            for (int j = 0; j < R; ++j) {
+                lq[j] = sg.ldq[j];
+                sq[j] = sg.stq[j];
+            }
+            C a[NA], al[NA];
+#pragma unroll
+            for (int r = 0; r < NA; ++r) {
+                const uint32_t ad = bb.y ^ xsel<R>(r, sq);
+                a[r] = *reinterpret_cast<const C *>(tp + ad);
+                al[r] = *reinterpret_cast<const C *>(tl + ad);
+            }
+            tile_ops_rev<C, Real, R, R - 1>(P, sg, sm, a, al, accw, wps, lane);
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < NA; ++r) {
+                const uint32_t ad = bb.x ^ xsel<R>(r, lq);
+                *reinterpret_cast<C *>(tp + ad) = a[r];
+                *reinterpret_cast<C *>(tl + ad) = al[r];
+            }
+            __syncthreads();
         }
-        __syncthreads();
+        const int64_t off = ((int64_t)cur.slot << n) + cur.base;
+        C *dp = psi + off, *dl = lam + off;
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+            const uint32_t so = p0 ^ xsel<R>(k, pk), go = g0 ^ xsel<R>(k, gk);
+            dp[go] = *reinterpret_cast<const C *>(tp + so);
+            dl[go] = *reinterpret_cast<const C *>(tl + so);
+        }
+        ++since;
+        cur = nxt;
+        nxt = tile_next(P, nxt);
     }
-    if (cur >= 0) flush_rho(pv, u2g, pd.n_u1, rho_blk, rho_g, cur, G);
+    flush_acc<Real>(P, acc, wps, rho_g, mslot, G);
 }
 
 // D_g(j) = sum_{t in g} c_t i^{phase_t} (-1)^{|j & z_t|} for one amplitude.
@@ -424,6 +519,19 @@ template <typename K> cudaError_t allow_smem(K kernel, uint32_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Resident blocks of kernel k on the whole GPU, at most max_blocks.
+template <typename K> int fill_blocks(K kernel, int threads, uint32_t smem, int64_t max_blocks) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess ||
+        per < 1)
+        per = 1;
+    int64_t b = (int64_t)sms * per;
+    if (b > max_blocks) b = max_blocks;
+    return b < 1 ? 1 : (int)b;
+}
+
 int grid_1d(int64_t work, int threads) {
     int64_t b = (work + threads - 1) / threads;
     if (b > 8192) b = 8192;
@@ -473,45 +581,45 @@ cudaError_t launch_init_states(int c128, void *states, int n, const SlotSource &
     return cudaGetLastError();
 }
 
-uint32_t pass_fwd_smem(int c128, int t, int R, int G, int n_st, int n_ops) {
-    const uint32_t base = 2u * (uint32_t)((c128 ? 16 : 8) << t) + (uint32_t)(G * 4 * (c128 ? 16 : 8));
-    return pass_smem_layout(base, n_st, n_ops, 1 << (t - R), G).end;
+uint32_t tile_fwd_smem(int c128, const TilePass &P) {
+    const uint32_t csz = c128 ? 16u : 8u, T = 1u << (P.t - P.R);
+    return 2u * (csz << P.t) + (uint32_t)P.n_stages * T * 8u + (uint32_t)P.n_ops * 4u * csz;
 }
 
-uint32_t pass_rev_smem(int c128, int t, int R, int G, int n_u1, int n_st, int n_ops) {
-    const uint32_t base = rev_layout(t, R, c128 ? 16 : 8, c128 ? 8 : 4, G, n_u1).total +
-                          (uint32_t)(G * 4 * (c128 ? 16 : 8));
-    return pass_smem_layout(base, n_st, n_ops, 1 << (t - R), G).end;
+uint32_t tile_rev_smem(int c128, const TilePass &P) {
+    const uint32_t csz = c128 ? 16u : 8u, rsz = c128 ? 8u : 4u, T = 1u << (P.t - P.R);
+    return 4u * (csz << P.t) + (uint32_t)P.n_stages * T * 8u + (uint32_t)P.n_ops * 4u * csz +
+           (uint32_t)P.n_ops * (T / 32u) * 8u * rsz;
 }
 
-cudaError_t launch_pass_fwd(int c128, int R, const PassDesc &pd, const Program &pv, int op0,
-                            int n_ops, int n, int n_slots, const void *mats, int G, void *states,
-                            int blocks, cudaStream_t st) {
-    const uint32_t smem = pass_fwd_smem(c128, pd.t, R, G, pv.n_stages, n_ops);
-    const int threads = 1 << (pd.t - R);
-    HBM_DISPATCH_R(c128, R, {
+cudaError_t launch_tile_fwd(int c128, const TilePass &P, int n, int n_slots, const void *mats,
+                            int G, void *states, int64_t max_blocks, cudaStream_t st) {
+    const uint32_t smem = tile_fwd_smem(c128, P);
+    const int threads = 1 << (P.t - P.R);
+    HBM_DISPATCH_R(c128, P.R, {
         using C = typename CT<Real>::T;
-        auto k = k_pass_fwd<Real, RR>;
+        auto k = k_tile_fwd<Real, RR>;
         cudaError_t e = allow_smem(k, smem);
         if (e != cudaSuccess) return e;
-        k<<<blocks, threads, smem, st>>>(pd, pv, op0, n_ops, n, n_slots, (const C *)mats, G,
-                                         (C *)states);
+        const int blocks = fill_blocks(k, threads, smem, max_blocks);
+        k<<<blocks, threads, smem, st>>>(P, n, n_slots, (const C *)mats, G, (C *)states);
     });
     return cudaGetLastError();
 }
 
-cudaError_t launch_pass_rev(int c128, int R, const PassDesc &pd, const Program &pv, int op0,
-                            int n_ops, int n, int n_slots, const void *mats, int G, void *psi,
-                            void *lam, double *rho_g, int blocks, cudaStream_t st) {
-    const uint32_t smem = pass_rev_smem(c128, pd.t, R, G, pd.n_u1, pv.n_stages, n_ops);
-    const int threads = 1 << (pd.t - R);
-    HBM_DISPATCH_R(c128, R, {
+cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, const void *mats,
+                            int G, void *psi, void *lam, double *rho_g, int64_t max_blocks,
+                            cudaStream_t st) {
+    const uint32_t smem = tile_rev_smem(c128, P);
+    const int threads = 1 << (P.t - P.R);
+    HBM_DISPATCH_R(c128, P.R, {
         using C = typename CT<Real>::T;
-        auto k = k_pass_rev<Real, RR>;
+        auto k = k_tile_rev<Real, RR>;
         cudaError_t e = allow_smem(k, smem);
         if (e != cudaSuccess) return e;
-        k<<<blocks, threads, smem, st>>>(pd, pv, op0, n_ops, n, n_slots, (const C *)mats, G,
-                                         (C *)psi, (C *)lam, rho_g);
+        const int blocks = fill_blocks(k, threads, smem, max_blocks);
+        k<<<blocks, threads, smem, st>>>(P, n, n_slots, (const C *)mats, G, (C *)psi, (C *)lam,
+                                         rho_g);
     });
     return cudaGetLastError();
 }

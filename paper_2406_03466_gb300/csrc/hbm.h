@@ -1,6 +1,7 @@
 // Launchers of the tile-pass kernels (hbm.cu): states in device memory.
 #pragma once
 #include <cuda_runtime.h>
+#include <cstdint>
 
 #include "kernels.h"
 #include "svk_types.h"
@@ -13,16 +14,17 @@ cudaError_t launch_group_mats(int c128, const Program &p, const SlotSource &src,
 // Zeroes the slot states and sets amplitude |ref> of each to 1.
 cudaError_t launch_init_states(int c128, void *states, int n, const SlotSource &src,
                                cudaStream_t st);
-uint32_t pass_fwd_smem(int c128, int t, int R, int G, int n_st, int n_ops);
-uint32_t pass_rev_smem(int c128, int t, int R, int G, int n_u1, int n_st, int n_ops);
-// pv: the program view of one pass (n = t, the pass's stages and thread bases);
-// its ops are [op0, op0 + n_ops) of the plan's op array.
-cudaError_t launch_pass_fwd(int c128, int R, const PassDesc &pd, const Program &pv, int op0,
-                            int n_ops, int n, int n_slots, const void *mats, int G, void *states,
-                            int blocks, cudaStream_t st);
-cudaError_t launch_pass_rev(int c128, int R, const PassDesc &pd, const Program &pv, int op0,
-                            int n_ops, int n, int n_slots, const void *mats, int G, void *psi,
-                            void *lam, double *rho_g, int blocks, cudaStream_t st);
+// Shared memory of one block of the forward / reverse kernels of pass P.
+uint32_t tile_fwd_smem(int c128, const TilePass &P);
+uint32_t tile_rev_smem(int c128, const TilePass &P);
+// Forward pass P over n_slots states of n qubits (mats: [slots][G][4]).
+cudaError_t launch_tile_fwd(int c128, const TilePass &P, int n, int n_slots, const void *mats,
+                            int G, void *states, int64_t max_blocks, cudaStream_t st);
+// Reverse pass P on psi and lambda; adds the reduced matrices of its
+// parametrised groups to rho_g[slot][G][8].
+cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, const void *mats,
+                            int G, void *psi, void *lam, double *rho_g, int64_t max_blocks,
+                            cudaStream_t st);
 // out[r] = <psi_r|H|psi_r> (zeroed here first).
 cudaError_t launch_expect_big(int c128, const Observable &o, int n, int n_rows,
                               const void *states, double *out, cudaStream_t st);

@@ -108,7 +108,7 @@ std::string fuse_circuit(const sv_circuit &c, bool fuse, FusedCircuit *F) {
 }
 
 void stage_lops(const std::vector<LOp> &lops, const std::vector<int> &pos, int t, int R, int w,
-                HostProgram *P) {
+                HostProgram *P, bool one_per_bit) {
     // lops act on positions pos[qubit] in [0, t); R <= t register bits.
     std::vector<int> Q;
     std::vector<Op> sops;
@@ -182,6 +182,14 @@ void stage_lops(const std::vector<LOp> &lops, const std::vector<int> &pos, int t
             const int q = pos[o.a];
             if (((dirty >> q) & 1u) || n_u1 >= kMaxGroupOpsPerStage) close_stage();
             int idx = find_pos(Q, q);
+            if (idx >= 0 && one_per_bit) {
+                bool taken = false;
+                for (const Op &x : sops) taken |= x.kind == OP_U1 && x.a == idx;
+                if (taken) {
+                    close_stage();
+                    idx = -1;
+                }
+            }
             if (idx < 0) {
                 if ((int)Q.size() >= R) close_stage();
                 Q.push_back(q);
@@ -240,18 +248,45 @@ std::string plan_circuit(const sv_circuit &c, int reg_bits, bool fuse, int swz_b
     P->groups = F.groups;
     std::vector<int> pos(n);
     for (int q = 0; q < n; ++q) pos[q] = q;
-    stage_lops(F.lops, pos, n, P->R, swz_bits, P);
+    stage_lops(F.lops, pos, n, P->R, swz_bits, P, false);
     build_thread_bases(P, n);
     return "";
 }
 
-std::string plan_passes(const sv_circuit &c, int tile_bits, int coalesce_bits, int reg_bits,
+std::string plan_passes(const sv_circuit &c0, int tile_bits, int coalesce_bits, int reg_bits,
                         bool fuse, int swz_bits, HostProgram *P) {
+    // CZ(a, b) = H_b CNOT(a -> b) H_b: tile passes run fused single-qubit
+    // groups and CNOT permutations only.
+    std::vector<sv_gate> gates;
+    if (c0.n_gates > 0 && c0.gates) {
+        for (int g = 0; g < c0.n_gates; ++g) {
+            sv_gate G = c0.gates[g];
+            if (G.op == SV_GATE_CZ) {
+                sv_gate h{};
+                h.op = SV_GATE_H;
+                h.target = G.target;
+                h.control = -1;
+                h.param = -1;
+                sv_gate cx = G;
+                cx.op = SV_GATE_CNOT;
+                gates.push_back(h);
+                gates.push_back(cx);
+                gates.push_back(h);
+            } else {
+                gates.push_back(G);
+            }
+        }
+    }
+    sv_circuit c = c0;
+    if (!gates.empty()) {
+        c.gates = gates.data();
+        c.n_gates = (int)gates.size();
+    }
     FusedCircuit F;
     std::string err = fuse_circuit(c, fuse, &F);
     if (!err.empty()) return err;
     const int n = c.n_qubits;
-    if (tile_bits < 2 || tile_bits > n) return "tile_bits must be in [2, n]";
+    if (tile_bits < 2 || tile_bits > n || tile_bits > kTileBitsMax) return "tile_bits must be in [2, min(n, 13)]";
     if (coalesce_bits < 0 || coalesce_bits + 2 > tile_bits) return "coalesce_bits too large";
     if (reg_bits < 1 || reg_bits > kRMax || reg_bits > tile_bits) return "bad reg_bits";
     const int t = tile_bits;
@@ -300,27 +335,98 @@ std::string plan_passes(const sv_circuit &c, int tile_bits, int coalesce_bits, i
         pd.t = t;
         pd.n_tile_bits = n - t;
         pd.local_mask = L;
-        pd.stage_begin = (int)P->stages.size();
-        std::vector<LOp> sub;
-        for (int idx : taken) sub.push_back(F.lops[idx]);
-        stage_lops(sub, pos, t, reg_bits, swz_bits, P);
-        pd.stage_end = (int)P->stages.size();
-        // A leading stage without ops is only a permutation: fold it into
-        // the tile load (and the reverse pass's tile store).
-        for (int b = 0; b < t; ++b) pd.ldperm[b] = swizzle(1u << b, swz_bits);
-        const Stage &s0 = P->stages[pd.stage_begin];
-        if (s0.op_begin == s0.op_end) {
-            const std::vector<uint32_t> &col = P->perm_cols[pd.stage_begin];
-            for (int b = 0; b < t; ++b) pd.ldperm[b] = swizzle(col[b], swz_bits);
-            P->stages.erase(P->stages.begin() + pd.stage_begin);
-            P->perm_cols.erase(P->perm_cols.begin() + pd.stage_begin);
-            --pd.stage_end;
+        // Stage the taken ops; a pass holds at most kPassStages stages and
+        // kPassOps group ops, so an over-long pass keeps a prefix of them (a
+        // prefix of the taken ops in circuit order is closed under
+        // dependencies) and returns the rest to the pending list.
+        size_t keep = taken.size();
+        const size_t st0 = P->stages.size(), op0 = P->ops.size();
+        for (;;) {
+            pd.stage_begin = (int)st0;
+            std::vector<LOp> sub;
+            for (size_t i = 0; i < keep; ++i) sub.push_back(F.lops[taken[i]]);
+            stage_lops(sub, pos, t, reg_bits, swz_bits, P, true);
+            pd.stage_end = (int)P->stages.size();
+            // A leading stage without ops is only a permutation: fold it into
+            // the tile load (and the reverse pass's tile store).
+            for (int bb = 0; bb < t; ++bb) pd.ldperm[bb] = swizzle(1u << bb, swz_bits);
+            const Stage &s0 = P->stages[pd.stage_begin];
+            if (s0.op_begin == s0.op_end && pd.stage_end - pd.stage_begin > 1) {
+                const std::vector<uint32_t> &col = P->perm_cols[pd.stage_begin];
+                for (int bb = 0; bb < t; ++bb) pd.ldperm[bb] = swizzle(col[bb], swz_bits);
+                P->stages.erase(P->stages.begin() + pd.stage_begin);
+                P->perm_cols.erase(P->perm_cols.begin() + pd.stage_begin);
+                --pd.stage_end;
+            }
+            int nu = 0;
+            for (int si = pd.stage_begin; si < pd.stage_end; ++si) nu += P->stages[si].n_u1;
+            pd.n_u1 = nu;
+            if ((pd.stage_end - pd.stage_begin <= kPassStages && nu <= kPassOps) || keep <= 1) break;
+            P->stages.resize(st0);
+            P->perm_cols.resize(st0);
+            P->ops.resize(op0);
+            keep = keep * 3 / 4;
         }
-        int nu = 0;
-        for (int s = pd.stage_begin; s < pd.stage_end; ++s) nu += P->stages[s].n_u1;
-        pd.n_u1 = nu;
+        if (pd.stage_end - pd.stage_begin > kPassStages || pd.n_u1 > kPassOps)
+            return "internal: a tile pass exceeds the stage or op limit";
+        for (size_t i = keep; i < taken.size(); ++i) rest.push_back(taken[i]);
+        std::sort(rest.begin(), rest.end());
         P->passes.push_back(pd);
         pending.swap(rest);
+    }
+    return "";
+}
+
+// Kernel descriptors of every pass of a tile plan (amplitudes of csz bytes).
+std::string build_tile_passes(const HostProgram &P, int csz, std::vector<TilePass> *out) {
+    out->clear();
+    const int R = P.R, w = P.swz_bits;
+    for (const PassDesc &pd : P.passes) {
+        TilePass tp{};
+        tp.t = pd.t;
+        tp.R = R;
+        tp.n_stages = pd.stage_end - pd.stage_begin;
+        tp.n_tile_bits = pd.n_tile_bits;
+        if (tp.n_stages > kPassStages) return "too many stages in a tile pass";
+        if (pd.t - R < 5) return "tile passes need at least 32 threads (tile_bits - reg_bits >= 5)";
+        for (int b = 0; b < pd.t; ++b) {
+            tp.gl[b] = pd.gl[b];
+            tp.ldperm[b] = pd.ldperm[b] * (uint32_t)csz;
+            tp.nat[b] = swizzle(1u << b, w) * (uint32_t)csz;
+        }
+        uint32_t acc = 0;
+        for (int k = 0; k < pd.n_tile_bits; ++k) {
+            acc ^= pd.gt[k];
+            tp.gpre[k] = acc;
+        }
+        int u = 0;
+        for (int si = 0; si < tp.n_stages; ++si) {
+            const Stage &sg = P.stages[pd.stage_begin + si];
+            TileStage &ts = tp.st[si];
+            for (int i = 0; i < kRMax; ++i) {
+                ts.op[i] = -1;
+                ts.ldq[i] = i < R ? sg.ldq[i] * (uint32_t)csz : 0u;
+                ts.stq[i] = i < R ? sg.stq[i] * (uint32_t)csz : 0u;
+            }
+            for (int k = 0; k < pd.t - R; ++k) {
+                ts.ldt[k] = sg.ldt[k] * (uint32_t)csz;
+                ts.stt[k] = sg.stt[k] * (uint32_t)csz;
+            }
+            for (int oi = sg.op_begin; oi < sg.op_end; ++oi) {
+                const Op &op = P.ops[oi];
+                if (op.kind != OP_U1) return "tile pass stage holds a non-group op";
+                if (op.a < 0 || op.a >= R || ts.op[op.a] >= 0)
+                    return "tile pass stage holds two ops on one register bit";
+                if (u >= kPassOps) return "too many ops in a tile pass";
+                ts.op[op.a] = u;
+                tp.grp[u] = op.group;
+                if (P.groups[op.group].real) tp.real_mask |= 1ull << u;
+                if (P.groups[op.group].has_param) tp.param_mask |= 1ull << u;
+                ++u;
+            }
+        }
+        tp.n_ops = u;
+        out->push_back(tp);
     }
     return "";
 }

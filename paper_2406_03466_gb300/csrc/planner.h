@@ -37,12 +37,16 @@ struct FusedCircuit {
 
 std::string fuse_circuit(const sv_circuit &c, bool fuse, FusedCircuit *out);
 // Appends the register stages of `lops` (qubit q at tile position pos[q] < t).
+// one_per_bit: close a stage rather than put a second op on a register bit.
 void stage_lops(const std::vector<LOp> &lops, const std::vector<int> &pos, int t, int R, int w,
-                HostProgram *P);
+                HostProgram *P, bool one_per_bit);
 // Cuts a circuit into tile passes of 2^tile_bits amplitudes whose local
 // qubits always include the lowest coalesce_bits qubits.
 std::string plan_passes(const sv_circuit &c, int tile_bits, int coalesce_bits, int reg_bits,
                         bool fuse, int swz_bits, HostProgram *P);
+
+// Kernel descriptors of every pass of a tile plan (amplitudes of csz bytes).
+std::string build_tile_passes(const HostProgram &P, int csz, std::vector<TilePass> *out);
 
 struct HostObservable {
     int n = 0;

@@ -83,6 +83,32 @@ struct PassDesc {
     uint32_t ldperm[kNMax];
 };
 
+// Device descriptor of one tile pass, passed to the pass kernels as a
+// __grid_constant__ parameter.  Shared-memory addresses are byte offsets
+// within one tile buffer (swizzled, times the amplitude size); global
+// offsets are amplitude indices within one state.
+constexpr int kTileBitsMax = 13;  // largest tile: 2^13 amplitudes
+constexpr int kPassStages = 16;   // register stages per pass
+constexpr int kPassOps = 64;      // fused-group ops per pass
+
+struct TileStage {
+    uint32_t ldq[kRMax], stq[kRMax];                // register bit i: load / store vector
+    uint32_t ldt[kTileBitsMax], stt[kTileBitsMax];  // thread bit k: load / store vector
+    int32_t op[kRMax];                              // pass-local op on register bit i, or -1
+};
+
+struct TilePass {
+    int32_t t, R, n_stages, n_ops, n_tile_bits, pad;
+    uint64_t real_mask;             // bit u: op u has a real matrix
+    uint64_t param_mask;            // bit u: op u's group has parameters
+    uint32_t gl[kTileBitsMax];      // tile-local bit b -> global offset bit
+    uint32_t gpre[kNMax];           // gt[0] ^ ... ^ gt[k] for tile-number bit k
+    uint32_t ldperm[kTileBitsMax];  // tile-local bit b -> shared address at load (forward)
+    uint32_t nat[kTileBitsMax];     // tile-local bit b -> natural shared address
+    int32_t grp[kPassOps];          // pass-local op u -> fused group
+    TileStage st[kPassStages];
+};
+
 // Pauli terms grouped by X-mask: <psi|P|psi> = Re(i^phase sum_j (-1)^{|j & z|}
 // conj(psi_{j^x}) psi_j) with phase = (#Y) mod 4.
 struct TermGroup {

@@ -46,7 +46,7 @@ FORCED = {
 
 @pytest.mark.parametrize("name", sorted(FORCED))
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
-@pytest.mark.parametrize("tile_bits,reg_bits", [(7, 2), (7, 3), (8, 3), (6, 2)])
+@pytest.mark.parametrize("tile_bits,reg_bits", [(7, 2), (8, 3), (8, 2), (9, 3)])
 def test_forced_tiles_gradients(sv, name, dtype, tile_bits, reg_bits):
     w = FORCED[name]()
     L, E, g = oracle.grad_param_shift(w)

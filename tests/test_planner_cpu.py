@@ -66,7 +66,7 @@ def test_header_symbols_exported():
 
 
 def test_struct_sizes_match():
-    sizes = (I32 * 7)()
+    sizes = (I32 * 8)()
     lib().sv_debug_sizes(sizes)
     assert list(sizes)[:4] == [ctypes.sizeof(Stage), ctypes.sizeof(Op), ctypes.sizeof(Group),
                                ctypes.sizeof(Member)]

@@ -1,0 +1,355 @@
+"""Host-side checks of the tile-pass kernel descriptors, on CPU.
+
+libsv.so exports the TilePass descriptors exactly as the GPU entry points
+build them.  Here they drive a numpy model of the two pass kernels, thread
+by thread and tile by tile, with the kernels' byte addresses, tile walk
+(per-block contiguous tile ranges, incremental tile bases) and op order:
+the forward passes must reproduce the oracle's states, and the reverse
+passes (adjoint sweep with per-group reduced matrices, then the member walk
+that turns them into derivatives) the oracle's parameter-shift gradient.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import dense
+import workloads as wl
+
+sv = pytest.importorskip("paper_2406_03466_gb300")
+
+I32, U32, U64 = ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64
+KT = 13  # largest tile bits
+
+
+class Group(ctypes.Structure):
+    _fields_ = [("m_begin", I32), ("m_end", I32), ("qubit", I32), ("has_param", I32),
+                ("real", I32)]
+
+
+class Member(ctypes.Structure):
+    _fields_ = [("kind", I32), ("param", I32), ("angle", ctypes.c_double)]
+
+
+class TileStage(ctypes.Structure):
+    _fields_ = [("ldq", U32 * 5), ("stq", U32 * 5), ("ldt", U32 * KT), ("stt", U32 * KT),
+                ("op", I32 * 5)]
+
+
+class TilePass(ctypes.Structure):
+    _fields_ = [("t", I32), ("R", I32), ("n_stages", I32), ("n_ops", I32), ("n_tile_bits", I32),
+                ("pad", I32), ("real_mask", U64), ("param_mask", U64), ("gl", U32 * KT),
+                ("gpre", U32 * 30), ("ldperm", U32 * KT), ("nat", U32 * KT), ("grp", I32 * 64),
+                ("st", TileStage * 16)]
+
+
+def export(circ, t, R, fuse=True, dtype=0):
+    L = sv.library()
+    L.sv_debug_tile_passes.argtypes = [ctypes.c_void_p, I32, I32, I32, I32, ctypes.POINTER(I32),
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.sv_debug_tile_passes.restype = I32
+    counts = (I32 * 3)()
+    st = L.sv_debug_tile_passes(ctypes.byref(circ.struct), t, R, int(fuse), dtype, counts,
+                                None, None, None)
+    assert st == 0, sv.sv_status_string(st)
+    arrs = [(Group * max(1, counts[0]))(), (Member * max(1, counts[1]))(),
+            (TilePass * max(1, counts[2]))()]
+    assert L.sv_debug_tile_passes(ctypes.byref(circ.struct), t, R, int(fuse), dtype, counts,
+                                  *arrs) == 0
+    return [a[:k] for a, k in zip(arrs, counts)]
+
+
+def test_descriptor_size_matches():
+    sizes = (I32 * 8)()
+    sv.library().sv_debug_sizes(sizes)
+    assert sizes[7] == ctypes.sizeof(TilePass)
+
+
+# --------------------------------------------------------------- numpy model
+
+def rot(axis, a):
+    c, s = np.cos(a / 2), np.sin(a / 2)
+    if axis == 0:
+        return np.array([[c, -1j * s], [-1j * s, c]])
+    if axis == 1:
+        return np.array([[c, -s], [s, c]], dtype=complex)
+    return np.array([[np.exp(-0.5j * a), 0], [0, np.exp(0.5j * a)]])
+
+
+def member_matrix(m, theta, x, sp, sh):
+    if m.kind <= 2:
+        a = m.angle if m.param < 0 else theta[m.param] + (sh if m.param == sp else 0.0)
+        return rot(m.kind, a)
+    if m.kind == 3:
+        return np.array([[0, 1], [1, 0]], dtype=complex)
+    if m.kind == 4:
+        return np.array([[1, 1], [1, -1]], dtype=complex) / np.sqrt(2)
+    if m.kind == 5:
+        return rot(1, np.arcsin(x[m.param]))
+    return rot(2, np.arccos(x[m.param] ** 2))
+
+
+def group_mats(groups, members, theta, x, sp=-1, sh=0.0):
+    out = []
+    for g in groups:
+        M = np.eye(2, dtype=complex)
+        for m in members[g.m_begin:g.m_end]:
+            M = member_matrix(m, theta, x, sp, sh) @ M
+        out.append(M)
+    return out
+
+
+def xsel(r, v):
+    a = 0
+    for i, x in enumerate(v):
+        if r >> i & 1:
+            a ^= x
+    return a
+
+
+def thread_vectors(v, t, R, tid):
+    g = np.zeros(len(tid), np.int64)
+    for b in range(t - R):
+        g ^= ((tid >> b) & 1) * int(v[b])
+    return g, [int(v[t - R + j]) for j in range(R)]
+
+
+def tile_walk(P, n_slots, n_blocks):
+    """The (slot, base) sequence of every block, walked as the kernels do."""
+    ntb = P.n_tile_bits
+    tiles = n_slots << ntb
+    per = -(-tiles // n_blocks)
+    gt = [P.gpre[k] ^ (P.gpre[k - 1] if k else 0) for k in range(ntb)]
+    out = []
+    for blk in range(n_blocks):
+        t0, t1 = per * blk, min(tiles, per * (blk + 1))
+        if t0 >= t1:
+            continue
+        slot, local = t0 >> ntb, t0 & ((1 << ntb) - 1)
+        base = 0
+        for k in range(ntb):
+            if local >> k & 1:
+                base ^= gt[k]
+        for _ in range(t0, t1):
+            out.append((slot, base))
+            local += 1
+            if local >> ntb:
+                slot, local, base = slot + 1, 0, 0
+            else:
+                base ^= P.gpre[(local & -local).bit_length() - 1]
+    return out
+
+
+def apply_bit(a, I, M):
+    """2x2 matrix M on register bit I of a[thread, r]."""
+    for r in range(a.shape[1]):
+        if r >> I & 1:
+            continue
+        x, y = a[:, r].copy(), a[:, r | 1 << I].copy()
+        a[:, r] = M[0, 0] * x + M[0, 1] * y
+        a[:, r | 1 << I] = M[1, 0] * x + M[1, 1] * y
+
+
+def stage_bases(sg, t, R, tid):
+    lb = np.zeros(len(tid), np.int64)
+    sb = np.zeros(len(tid), np.int64)
+    for k in range(t - R):
+        bit = (tid >> k) & 1
+        lb ^= bit * int(sg.ldt[k])
+        sb ^= bit * int(sg.stt[k])
+    return lb, sb
+
+
+def run_fwd(P, states, mats, csz, n_blocks=3):
+    t, R = P.t, P.R
+    tid = np.arange(1 << (t - R))
+    g0, gk = thread_vectors(P.gl, t, R, tid)
+    p0, pk = thread_vectors(P.ldperm, t, R, tid)
+    n0, nk = thread_vectors(P.nat, t, R, tid)
+    NA = 1 << R
+    for slot, base in tile_walk(P, states.shape[0], n_blocks):
+        S = states[slot]
+        sm = np.full(1 << t, np.nan, dtype=complex)
+        for k in range(NA):
+            sm[(p0 ^ xsel(k, pk)) // csz] = S[base + (g0 ^ xsel(k, gk))]
+        assert not np.isnan(sm).any(), "tile load misses shared-memory words"
+        for s in range(P.n_stages):
+            sg = P.st[s]
+            lb, sb = stage_bases(sg, t, R, tid)
+            a = np.stack([sm[(lb ^ xsel(r, sg.ldq[:R])) // csz] for r in range(NA)], axis=1)
+            for I in range(R):
+                u = sg.op[I]
+                if u >= 0:
+                    M = mats[slot][P.grp[u]]
+                    if P.real_mask >> u & 1:
+                        assert np.all(M.imag == 0)
+                    apply_bit(a, I, M)
+            new = np.full(1 << t, np.nan, dtype=complex)
+            for r in range(NA):
+                new[(sb ^ xsel(r, sg.stq[:R])) // csz] = a[:, r]
+            assert not np.isnan(new).any(), "stage store misses shared-memory words"
+            sm = new
+        for k in range(NA):
+            S[base + (g0 ^ xsel(k, gk))] = sm[(n0 ^ xsel(k, nk)) // csz]
+
+
+def run_rev(P, psi, lam, mats, rho, csz, n_blocks=2):
+    t, R = P.t, P.R
+    tid = np.arange(1 << (t - R))
+    g0, gk = thread_vectors(P.gl, t, R, tid)
+    p0, pk = thread_vectors(P.ldperm, t, R, tid)
+    n0, nk = thread_vectors(P.nat, t, R, tid)
+    NA = 1 << R
+    for slot, base in tile_walk(P, psi.shape[0], n_blocks):
+        sp = np.zeros(1 << t, complex)
+        sl = np.zeros(1 << t, complex)
+        for k in range(NA):
+            so, go = (n0 ^ xsel(k, nk)) // csz, base + (g0 ^ xsel(k, gk))
+            sp[so] = psi[slot][go]
+            sl[so] = lam[slot][go]
+        for s in range(P.n_stages - 1, -1, -1):
+            sg = P.st[s]
+            lb, sb = stage_bases(sg, t, R, tid)
+            ad = [(sb ^ xsel(r, sg.stq[:R])) // csz for r in range(NA)]
+            a = np.stack([sp[x] for x in ad], axis=1)
+            al = np.stack([sl[x] for x in ad], axis=1)
+            for I in range(R - 1, -1, -1):
+                u = sg.op[I]
+                if u < 0:
+                    continue
+                g = P.grp[u]
+                if P.param_mask >> u & 1:
+                    for r in range(NA):
+                        if r >> I & 1:
+                            continue
+                        ps = (a[:, r], a[:, r | 1 << I])
+                        ls = (al[:, r], al[:, r | 1 << I])
+                        for x in range(2):
+                            for y in range(2):
+                                rho[slot][g][x, y] += np.sum(ps[x] * np.conj(ls[y]))
+                Md = mats[slot][g].conj().T
+                apply_bit(a, I, Md)
+                apply_bit(al, I, Md)
+            for r in range(NA):
+                x = (lb ^ xsel(r, sg.ldq[:R])) // csz
+                sp[x] = a[:, r]
+                sl[x] = al[:, r]
+        for k in range(NA):
+            so, go = (p0 ^ xsel(k, pk)) // csz, base + (g0 ^ xsel(k, gk))
+            psi[slot][go] = sp[so]
+            lam[slot][go] = sl[so]
+
+
+def group_gradients(groups, members, rho, theta, x, grad, weight):
+    """dE/dtheta = Im tr(P rho) member by member, rho <- G^dag rho G between."""
+    for gi, g in enumerate(groups):
+        if not g.has_param:
+            continue
+        r = rho[gi].copy() * weight
+        ms = list(members[g.m_begin:g.m_end])
+        first = next(i for i, m in enumerate(ms) if m.kind <= 2 and m.param >= 0)
+        for i in range(len(ms) - 1, first - 1, -1):
+            m = ms[i]
+            if m.kind <= 2 and m.param >= 0:
+                Pm = [np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]),
+                      np.diag([1, -1])][m.kind]
+                grad[m.param] += np.imag(np.trace(Pm @ r))
+            if i > first:
+                G = member_matrix(m, theta, x, -1, 0.0)
+                r = G.conj().T @ r @ G
+
+
+def init_states(w, n_inst):
+    S = np.zeros((n_inst, 1 << w.n_qubits), complex)
+    for i in range(n_inst):
+        S[i, int(w.refs[i])] = 1.0
+    return S
+
+
+CASES = {
+    "qcl8": lambda: wl.qcl(8, 2, 2),
+    "mcvqe8": lambda: wl.mcvqe(8, 2, "nn+nnn", n_refs=2),
+    "rand8_cz": lambda: wl.random_workload(8, 70, 5, 2, seed=41, with_encoding=True),
+    "rand9": lambda: wl.random_workload(9, 60, 4, 2, seed=42, cost="mse"),
+}
+
+
+def circuit_of(w):
+    d = 0 if w.inputs is None else w.inputs.shape[1]
+    return sv.Circuit(w.n_qubits, w.gates, w.n_params, d)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("t,R,dtype", [(7, 2, 0), (8, 3, 0), (7, 2, 1), (8, 3, 1), (6, 1, 0)])
+def test_forward_passes_match_oracle(name, t, R, dtype):
+    w = CASES[name]()
+    circ = circuit_of(w)
+    groups, members, passes = export(circ, t, R, dtype=dtype)
+    csz = 16 if dtype else 8
+    I = min(2, w.n_instances)
+    xs = [None if w.inputs is None else w.inputs[i] for i in range(I)]
+    mats = [group_mats(groups, members, w.theta, xs[i]) for i in range(I)]
+    S = init_states(w, I)
+    for P in passes:
+        assert P.n_stages >= 1 and P.t == t and P.R == R
+        run_fwd(P, S, mats, csz)
+    for i in range(I):
+        np.testing.assert_allclose(S[i], oracle.state(w, instance=i), atol=1e-12)
+
+
+def test_tile_walk_covers_every_tile_once():
+    w = wl.qcl(12, 1, 1)
+    groups, members, passes = export(circuit_of(w), 8, 3)
+    for P in passes[:4]:
+        for nb in (1, 3, 7, 40):
+            seen = tile_walk(P, 3, nb)
+            assert len(seen) == 3 << P.n_tile_bits
+            assert len(set(seen)) == len(seen)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("t,R,dtype", [(7, 2, 0), (8, 3, 1)])
+def test_reverse_passes_give_oracle_gradient(name, t, R, dtype):
+    w = CASES[name]()
+    circ = circuit_of(w)
+    groups, members, passes = export(circ, t, R, dtype=dtype)
+    csz = 16 if dtype else 8
+    I = w.n_instances
+    xs = [None if w.inputs is None else w.inputs[i] for i in range(I)]
+    mats = [group_mats(groups, members, w.theta, xs[i]) for i in range(I)]
+    psi = init_states(w, I)
+    for P in passes:
+        run_fwd(P, psi, mats, csz)
+    H = dense.hamiltonian(w.n_qubits, w.pauli_letters, w.pauli_coeffs)
+    lam = np.stack([H @ psi[i] for i in range(I)])
+    E = np.array([np.vdot(psi[i], lam[i]).real for i in range(I)])
+    rho = [[np.zeros((2, 2), complex) for _ in groups] for _ in range(I)]
+    for P in reversed(passes):
+        run_rev(P, psi, lam, mats, rho, csz)
+    for i in range(I):  # the reverse sweep returns psi to |ref>
+        np.testing.assert_allclose(psi[i], init_states(w, I)[i], atol=1e-12)
+    wts = oracle.cost_weights(w, E)
+    grad = np.zeros(w.n_params)
+    for i in range(I):
+        group_gradients(groups, members, rho[i], w.theta, xs[i], grad, wts[i])
+    L, E_o, g_o = oracle.grad_param_shift(w)
+    np.testing.assert_allclose(E, E_o, atol=1e-12)
+    np.testing.assert_allclose(grad, g_o, atol=1e-11)
+
+
+def test_cz_is_planned_as_h_cnot_h():
+    w = wl.random_workload(8, 70, 5, 2, seed=41, with_encoding=True)
+    assert any(g.op == "CZ" for g in w.gates)
+    groups, members, passes = export(circuit_of(w), 7, 2)
+    assert any(m.kind == 4 for m in members)  # H members absorbed into groups
+
+
+def test_rejects_tiles_narrower_than_a_warp():
+    w = wl.qcl(8, 1, 1)
+    L = sv.library()
+    counts = (I32 * 3)()
+    L.sv_debug_tile_passes.argtypes = [ctypes.c_void_p, I32, I32, I32, I32, ctypes.POINTER(I32),
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert L.sv_debug_tile_passes(ctypes.byref(circuit_of(w).struct), 7, 3, 1, 0, counts,
+                                  None, None, None) != 0
