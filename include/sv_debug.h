@@ -38,6 +38,13 @@ sv_status sv_debug_tile_passes(const sv_circuit *circuit, int32_t tile_bits, int
                                int32_t fuse, int32_t dtype, int32_t *counts, void *groups,
                                void *members, void *tile_passes);
 
+/* The tile passes of lambda = H psi: counts[0..3] = passes, groups, classes,
+ * terms.  In the exported pass records the three array pointers hold the
+ * pass's first index into `groups`, `classes` and `terms`. */
+sv_status sv_debug_h_passes(const sv_pauli_sum *h, int32_t tile_bits, int32_t coalesce_bits,
+                            int32_t *counts, void *passes, void *groups, void *classes,
+                            void *terms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstring>
 #include <memory>
+#include <map>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -69,6 +70,13 @@ struct PlanEntry {
     Program dev{};
 };
 
+// Tile passes of lambda = H psi for one tile size, uploaded.
+struct HPlanEntry {
+    HostHPlan host;
+    DeviceBuf buf;
+    std::vector<HPass> passes;  // with device pointers
+};
+
 struct ObsEntry {
     std::vector<uint64_t> xm, zm;
     std::vector<double> c;
@@ -76,6 +84,7 @@ struct ObsEntry {
     DeviceBuf buf;
     Observable dev{};
     DeviceBuf dtab;  // diagonal tables D_g(j) for on-chip sizes, or empty
+    std::map<int, std::unique_ptr<HPlanEntry>> hplans;  // by tile bits
 };
 
 struct ArrayEntry {
@@ -468,6 +477,62 @@ size_t big_budget(DeviceCtx *ctx, cudaStream_t st) {
     return (size_t)(0.8 * (double)fr) + have;
 }
 
+// lambda = H psi and <H> for states in device memory: tiles of 2^12
+// (complex64) / 2^11 (complex128) amplitudes, or the whole state below that.
+int h_tile_bits(int n, sv_dtype dt) {
+    const int t = dt == SV_C128 ? 11 : 12;
+    return n < t ? n : t;
+}
+
+sv_status get_hplan(ObsEntry *obs, int n, sv_dtype dt, HPlanEntry **out) {
+    const int t = h_tile_bits(n, dt);
+    std::unique_ptr<HPlanEntry> &slot = obs->hplans[t];
+    if (!slot) {
+        std::unique_ptr<HPlanEntry> e(new HPlanEntry());
+        std::string err = plan_h_passes(obs->host, t, dt == SV_C128 ? 3 : 4, &e->host);
+        if (!err.empty()) return fail(SV_ERR_ARG, "observable: " + err);
+        const HostHPlan &h = e->host;
+        Packer pk;
+        const size_t og = pk.add(h.groups.data(), h.groups.size() * sizeof(HGroup));
+        const size_t oc = pk.add(h.classes.data(), h.classes.size() * sizeof(HClass));
+        const size_t ot = pk.add(h.terms.data(), h.terms.size() * sizeof(HTerm));
+        e->buf.bytes = pk.bytes.size() ? pk.bytes.size() : 256;
+        SV_CUDA(cudaMalloc(&e->buf.ptr, e->buf.bytes));
+        if (!pk.bytes.empty())
+            SV_CUDA(cudaMemcpy(e->buf.ptr, pk.bytes.data(), pk.bytes.size(), cudaMemcpyHostToDevice));
+        const unsigned char *base = (const unsigned char *)e->buf.ptr;
+        for (size_t i = 0; i < h.passes.size(); ++i) {
+            HPass P = h.passes[i];
+            P.groups = (const HGroup *)(base + og) + h.g_begin[i];
+            P.classes = (const HClass *)(base + oc) + h.c_begin[i];
+            P.terms = (const HTerm *)(base + ot) + h.t_begin[i];
+            e->passes.push_back(P);
+        }
+        slot = std::move(e);
+    }
+    *out = slot.get();
+    return SV_OK;
+}
+
+int64_t tile_blocks(const DeviceCtx *ctx, int64_t tiles);
+
+// E[r] = <psi_r|H|psi_r> for n_rows states (and lam = H psi unless lam is
+// null) by tile passes.
+sv_status h_tiles(DeviceCtx *ctx, ObsEntry *obs, int n, sv_dtype dt, int n_rows, const void *psi,
+                  void *lam, double *E, cudaStream_t st) {
+    HPlanEntry *hp = nullptr;
+    sv_status s = get_hplan(obs, n, dt, &hp);
+    if (s != SV_OK) return s;
+    SV_CUDA(cudaMemsetAsync(E, 0, sizeof(double) * (size_t)n_rows, st));
+    for (const HPass &P : hp->passes) {
+        const int64_t tiles = (int64_t)n_rows << P.n_tile_bits;
+        cudaError_t e = launch_tile_h(dt == SV_C128, P, n, n_rows, psi, lam, E,
+                                      tile_blocks(ctx, tiles), st);
+        if (e != cudaSuccess) return cuda_fail(e, "H tile pass");
+    }
+    return SV_OK;
+}
+
 bool wants_tiles(int n, sv_dtype dt, const sv_plan_opts *o) {
     if (o && o->tile_bits > 0) return true;
     return n > (dt == SV_C128 ? 12 : 13);
@@ -480,13 +545,13 @@ struct TileCfg {
 sv_status tile_cfg(int n, sv_dtype dt, const sv_plan_opts *o, TileCfg *cfg) {
     const int c = dt == SV_C128 ? 3 : 4, rmax = dt == SV_C128 ? 3 : 4;
     // Default: 2^11 (complex64) / 2^10 (complex128) amplitudes per tile with
-    // 3 / 2 register bits: 256 threads per block, no register spills.
+    // 4 / 2 register bits: 128 / 256 threads per block.
     int t = (o && o->tile_bits > 0) ? o->tile_bits : (dt == SV_C128 ? 10 : 11);
     if (t > n) t = n;
     if (t < c + 2 || t > 12)
         return fail(SV_ERR_UNSUPPORTED, "tile passes need 2^tile_bits amplitudes with tile_bits in "
                                         "[coalesced bits + 2, 12] and at most n_qubits");
-    int R = (o && o->reg_bits > 0) ? o->reg_bits : std::min(dt == SV_C128 ? 2 : 3, t - 5);
+    int R = (o && o->reg_bits > 0) ? o->reg_bits : std::min(dt == SV_C128 ? 2 : 4, t - 5);
     if (R < 2 || R > rmax) return fail(SV_ERR_ARG, "reg_bits for tile passes must be 2..4 (2..3 complex128)");
     if (t - R > 8) R = t - 8;
     if (R > rmax) return fail(SV_ERR_UNSUPPORTED, "tile too large for the register width");
@@ -576,8 +641,8 @@ sv_status tiles_energies(DeviceCtx *ctx, const sv_problem *p, const double *thet
         src.slot_base = (int)c0;
         s = tiles_forward(ctx, pe, cfg.R, dt, src, big, (char *)big + mats_off, true, nullptr, 0, st);
         if (s != SV_OK) return s;
-        cudaError_t e = launch_expect_big(c128, obs->dev, n, src.n_slots, big, E + c0, st);
-        if (e != cudaSuccess) return cuda_fail(e, "expectation over device-memory states");
+        s = h_tiles(ctx, obs, n, dt, src.n_slots, big, nullptr, E + c0, st);
+        if (s != SV_OK) return s;
     }
     return SV_OK;
 }
@@ -644,8 +709,9 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
         double *rho = (double *)(bb + o_rho);
         s = tiles_forward(ctx, pe, cfg.R, dt, src, psi, mats, true, ncp ? ck : nullptr, every, st);
         if (s != SV_OK) return s;
-        cudaError_t e = launch_apply_h_big(c128, obs->dev, n, src.n_slots, psi, lam, Es + c0, st);
-        if (e != cudaSuccess) return cuda_fail(e, "lambda = H psi");
+        s = h_tiles(ctx, obs, n, dt, src.n_slots, psi, lam, Es + c0, st);
+        if (s != SV_OK) return s;
+        cudaError_t e = cudaSuccess;
         SV_CUDA(cudaMemsetAsync(rho, 0, (size_t)src.n_slots * G * 64, st));
         for (int i = npass - 1; i >= 0; --i) {
             if ((i + 1) % every == 0 && i + 1 < npass) {
@@ -858,11 +924,9 @@ sv_status sv_expect_pauli_sum(sv_state state, const sv_pauli_sum *h, int32_t n_r
     ObsEntry *obs = nullptr;
     sv_status s = get_obs(ctx, *h, state->n, state->dtype, &obs, (cudaStream_t)stream);
     if (s != SV_OK) return s;
-    if (wants_tiles(state->n, state->dtype, nullptr)) {
-        cudaError_t e = launch_expect_big(state->dtype == SV_C128, obs->dev, state->n, n_rows,
-                                          state->ptr, out, (cudaStream_t)stream);
-        return e == cudaSuccess ? SV_OK : cuda_fail(e, "expectation launch");
-    }
+    if (wants_tiles(state->n, state->dtype, nullptr))
+        return h_tiles(ctx, obs, state->n, state->dtype, n_rows, state->ptr, nullptr, out,
+                       (cudaStream_t)stream);
     OnchipShape sh{};
     const char *err = onchip_shape(ONCHIP_EXPECT, state->n, 0, 0, state->dtype == SV_C128, n_rows,
                                    0, 0, &sh, ctx->sms);

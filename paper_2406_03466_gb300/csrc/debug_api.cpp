@@ -1,4 +1,5 @@
 // Test hooks declared in sv_debug.h: host-side planner output, no GPU needed.
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -75,6 +76,34 @@ sv_status sv_debug_tile_passes(const sv_circuit *c, int32_t tile_bits, int32_t r
     if (groups) std::memcpy(groups, h.groups.data(), h.groups.size() * sizeof(Group));
     if (members) std::memcpy(members, h.members.data(), h.members.size() * sizeof(Member));
     if (tile_passes) std::memcpy(tile_passes, tp.data(), tp.size() * sizeof(TilePass));
+    return SV_OK;
+}
+
+sv_status sv_debug_h_passes(const sv_pauli_sum *h, int32_t tile_bits, int32_t coalesce_bits,
+                            int32_t *counts, void *passes, void *groups, void *classes,
+                            void *terms) {
+    if (!h || !counts) return SV_ERR_ARG;
+    HostObservable ho;
+    std::string err = plan_observable(*h, h->n_qubits, 4, &ho);
+    HostHPlan hp;
+    if (err.empty()) err = plan_h_passes(ho, tile_bits, coalesce_bits, &hp);
+    if (!err.empty()) return SV_ERR_ARG;
+    counts[0] = (int32_t)hp.passes.size();
+    counts[1] = (int32_t)hp.groups.size();
+    counts[2] = (int32_t)hp.classes.size();
+    counts[3] = (int32_t)hp.terms.size();
+    if (passes) {
+        std::vector<HPass> ps = hp.passes;
+        for (size_t i = 0; i < ps.size(); ++i) {  // offsets into the arrays, as pointers
+            ps[i].groups = (const HGroup *)(uintptr_t)hp.g_begin[i];
+            ps[i].classes = (const HClass *)(uintptr_t)hp.c_begin[i];
+            ps[i].terms = (const HTerm *)(uintptr_t)hp.t_begin[i];
+        }
+        std::memcpy(passes, ps.data(), ps.size() * sizeof(HPass));
+    }
+    if (groups) std::memcpy(groups, hp.groups.data(), hp.groups.size() * sizeof(HGroup));
+    if (classes) std::memcpy(classes, hp.classes.data(), hp.classes.size() * sizeof(HClass));
+    if (terms) std::memcpy(terms, hp.terms.data(), hp.terms.size() * sizeof(HTerm));
     return SV_OK;
 }
 

@@ -15,6 +15,8 @@
 // states, and the per-slot gradient assembly.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "engine.cuh"
 #include "hbm.h"
 
@@ -111,35 +113,93 @@ __device__ __forceinline__ TileCursor tile_next(const TilePass &P, TileCursor c)
     return c;
 }
 
-// The group ops of one stage, register bits I..R-1 in order.
+// Shared-memory record of one stage (32 bytes, read with warp-uniform
+// addresses): word 0 holds one op byte per register bit, (u + 1) | real << 6
+// | parametrised << 7 for pass-local op u (0: no op); word 1 + i holds
+// ldq[i] | stq[i] << 16 (byte offsets, < 2^16 for every supported tile).
+__device__ __forceinline__ void build_stage_recs(const TilePass &P, uint4 *rec) {
+    for (int s = threadIdx.x; s < P.n_stages; s += blockDim.x) {
+        const TileStage &sg = P.st[s];
+        uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int i = 0; i < P.R && i < 4; ++i) {
+            const int u = sg.op[i];
+            if (u >= 0) {
+                const uint32_t ob = (uint32_t)(u + 1) | (((P.real_mask >> u) & 1ull) ? 64u : 0u) |
+                                    (((P.param_mask >> u) & 1ull) ? 128u : 0u);
+                w[0] |= ob << (8 * i);
+            }
+            w[1 + i] = sg.ldq[i] | (sg.stq[i] << 16);
+        }
+        rec[2 * s] = make_uint4(w[0], w[1], w[2], w[3]);
+        rec[2 * s + 1] = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+}
+
+template <int R>
+__device__ __forceinline__ uint32_t read_stage_rec(const uint4 *rec, int s, uint32_t (&lq)[R],
+                                                   uint32_t (&sq)[R]) {
+    static_assert(R <= 4, "stage records hold four register bits");
+    const uint4 a = rec[2 * s];
+    uint32_t w[4] = {a.y, a.z, a.w, 0u};
+    if constexpr (R > 3) w[3] = rec[2 * s + 1].x;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        lq[j] = w[j] & 0xffffu;
+        sq[j] = w[j] >> 16;
+    }
+    return a.x;
+}
+
+// The four entries of matrix u (32-byte aligned records) as two 16-byte loads.
+__device__ __forceinline__ void load_mat(const float2 *sm, int u, float2 &m0, float2 &m1,
+                                         float2 &m2, float2 &m3) {
+    const float4 *p = reinterpret_cast<const float4 *>(sm) + 2 * u;
+    const float4 x = p[0], y = p[1];
+    m0 = make_float2(x.x, x.y);
+    m1 = make_float2(x.z, x.w);
+    m2 = make_float2(y.x, y.y);
+    m3 = make_float2(y.z, y.w);
+}
+__device__ __forceinline__ void load_mat(const double2 *sm, int u, double2 &m0, double2 &m1,
+                                         double2 &m2, double2 &m3) {
+    m0 = sm[4 * u];
+    m1 = sm[4 * u + 1];
+    m2 = sm[4 * u + 2];
+    m3 = sm[4 * u + 3];
+}
+
+// The group ops of one stage (op bytes `ops`), register bits I..R-1 in order.
 template <typename C, int R, int I>
-__device__ __forceinline__ void tile_ops_fwd(const TilePass &P, const TileStage &sg, const C *sm,
-                                             C (&a)[1 << R]) {
+__device__ __forceinline__ void tile_ops_fwd(uint32_t ops, const C *sm, C (&a)[1 << R]) {
     if constexpr (I < R) {
-        const int u = sg.op[I];
-        if (u >= 0) {
-            const C m0 = sm[4 * u], m1 = sm[4 * u + 1], m2 = sm[4 * u + 2], m3 = sm[4 * u + 3];
-            if ((P.real_mask >> u) & 1ull)
+        const uint32_t ob = (ops >> (8 * I)) & 0xffu;
+        if (ob) {
+            C m0, m1, m2, m3;
+            load_mat(sm, (int)(ob & 63u) - 1, m0, m1, m2, m3);
+            if (ob & 64u)
                 u1r_bit<C, decltype(m0.x), R, I>(a, m0.x, m1.x, m2.x, m3.x);
             else
                 u1_bit<C, R, I>(a, m0, m1, m2, m3);
         }
-        tile_ops_fwd<C, R, I + 1>(P, sg, sm, a);
+        tile_ops_fwd<C, R, I + 1>(ops, sm, a);
     }
 }
 
 // One forward pass over every tile of every slot.  mats: [slots][G][4].
 template <typename Real, int R>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, R >= 4 ? 2 : 3)
 k_tile_fwd(const __grid_constant__ TilePass P, int n, int n_slots,
            const typename CT<Real>::T *mats, int G, typename CT<Real>::T *states) {
     using C = typename CT<Real>::T;
     constexpr int NA = 1 << R;
+    constexpr uint32_t kBufs = 2u;
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, T = blockDim.x, t = P.t, S = P.n_stages;
     const uint32_t tbytes = (uint32_t)sizeof(C) << t;
-    uint2 *tb = reinterpret_cast<uint2 *>(smem + 2 * tbytes);
-    C *sm = reinterpret_cast<C *>(smem + 2 * tbytes + (uint32_t)S * T * 8u);
+    uint2 *tb = reinterpret_cast<uint2 *>(smem + kBufs * tbytes);
+    uint4 *rec = reinterpret_cast<uint4 *>(smem + kBufs * tbytes + (uint32_t)S * T * 8u);
+    C *sm = reinterpret_cast<C *>(rec + 2 * S);
+    build_stage_recs(P, rec);
     for (int s = 0; s < S; ++s) {
         const TileStage &sg = P.st[s];
         uint32_t lb = 0, sb = 0;
@@ -182,18 +242,13 @@ k_tile_fwd(const __grid_constant__ TilePass P, int n, int n_slots,
         if (tix + 1 < t_end) fetch(nxt, buf ^ 1);
         unsigned char *tile = smem + (uint32_t)buf * tbytes;
         for (int s = 0; s < S; ++s) {
-            const TileStage &sg = P.st[s];
             const uint2 bb = tb[s * T + tid];
             uint32_t lq[R], sq[R];
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-                lq[j] = sg.ldq[j];
-                sq[j] = sg.stq[j];
-            }
+            const uint32_t ops = read_stage_rec<R>(rec, s, lq, sq);
             C a[NA];
 #pragma unroll
             for (int r = 0; r < NA; ++r) a[r] = *reinterpret_cast<const C *>(tile + (bb.x ^ xsel<R>(r, lq)));
-            tile_ops_fwd<C, R, 0>(P, sg, sm, a);
+            tile_ops_fwd<C, R, 0>(ops, sm, a);
             __syncthreads();
 #pragma unroll
             for (int r = 0; r < NA; ++r) *reinterpret_cast<C *>(tile + (bb.y ^ xsel<R>(r, sq))) = a[r];
@@ -208,49 +263,59 @@ k_tile_fwd(const __grid_constant__ TilePass P, int n, int n_slots,
     }
 }
 
-// Sum over the 32 lanes of the 8 values rh[0..7]: lane l ends with the total
-// of value l & 7 (reduce-scatter over lane bits 0-2, then lane bits 3-4).
-template <typename Real>
-__device__ __forceinline__ Real warp_reduce8(const Real (&rh)[8], int lane) {
-    constexpr unsigned full = 0xffffffffu;
-    Real y[4], z[2];
-    const bool b0 = lane & 1, b1 = lane & 2, b2 = lane & 4;
+// The derivative of a rotation exp(-i theta P / 2) inside a fused group is
+// Im tr(Q rho) for a Hermitian Q, with rho_ab = sum psi_a conj(lambda_b) over
+// the amplitude pairs of the group's qubit.  Only the Hermitian matrix
+// K = (rho - rho^dag) / 2i enters (Im tr(Q rho) = tr(Q K)), and i K gives
+// the same derivatives as rho, also after conjugation by the group's
+// members.  Four sums fix K:
+//   k0 = Im rho_00, k1 = Im rho_11, k2 = Im rho_01 + Im rho_10,
+//   k3 = Re rho_01 - Re rho_10,
+// and i K = [[i k0, (k3 + i k2) / 2], [(-k3 + i k2) / 2, i k1]].
+template <typename C, typename Real, int R, int I>
+__device__ __forceinline__ void kmat_bit(const C (&a)[1 << R], const C (&l)[1 << R], Real *k) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const Real keep = b0 ? rh[2 * j + 1] : rh[2 * j], give = b0 ? rh[2 * j] : rh[2 * j + 1];
-        y[j] = keep + __shfl_xor_sync(full, give, 1);
+    for (int r = 0; r < (1 << R); ++r) {
+        if (r & (1 << I)) continue;
+        const C p0 = a[r], p1 = a[r | (1 << I)], l0 = l[r], l1 = l[r | (1 << I)];
+        k[0] = fmaR(p0.y, l0.x, fmaR(-p0.x, l0.y, k[0]));
+        k[1] = fmaR(p1.y, l1.x, fmaR(-p1.x, l1.y, k[1]));
+        k[2] = fmaR(p0.y, l1.x, fmaR(-p0.x, l1.y, fmaR(p1.y, l0.x, fmaR(-p1.x, l0.y, k[2]))));
+        k[3] = fmaR(p0.x, l1.x, fmaR(p0.y, l1.y, fmaR(-p1.x, l0.x, fmaR(-p1.y, l0.y, k[3]))));
     }
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-        const Real keep = b1 ? y[2 * m + 1] : y[2 * m], give = b1 ? y[2 * m] : y[2 * m + 1];
-        z[m] = keep + __shfl_xor_sync(full, give, 2);
-    }
-    const Real keep = b2 ? z[1] : z[0], give = b2 ? z[0] : z[1];
-    Real v = keep + __shfl_xor_sync(full, give, 4);
-    v += __shfl_xor_sync(full, v, 8);
-    v += __shfl_xor_sync(full, v, 16);
-    return v;
 }
 
-// Reverse of tile_ops_fwd, register bits I, I-1, ..., 0: per op, first the
-// reduced matrix rho_ab = sum psi_a conj(lambda_b) of its bit (at the point
-// after the group) into the warp's accumulator acc[u][warp][8], then the
-// inverse group (sm holds the adjoint matrices) on psi and lambda.
-template <typename C, typename Real, int R, int I>
-__device__ __forceinline__ void tile_ops_rev(const TilePass &P, const TileStage &sg, const C *sm,
-                                             C (&a)[1 << R], C (&al)[1 << R], Real *accw,
-                                             int wps, int lane) {
+// Partial sum over the lanes of NV values x[0..NV-1] (NV = 8 or 16):
+// afterwards x[m] (m < NV / 4) holds value 4 m + (lane & 3) summed over the
+// four lanes that differ in lane bits 0-1 (a reduce-scatter of two levels;
+// the kept half follows the lane bit).
+template <typename Real, int NV>
+__device__ __forceinline__ void warp_reduce_quad(Real (&x)[NV], int lane) {
+    constexpr unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int j = 0, M = NV; j < 2; ++j, M >>= 1) {
+        const bool b = (lane >> j) & 1;
+#pragma unroll
+        for (int m = 0; m < M / 2; ++m) {
+            const Real keep = b ? x[2 * m + 1] : x[2 * m], give = b ? x[2 * m] : x[2 * m + 1];
+            x[m] = keep + __shfl_xor_sync(full, give, 1 << j);
+        }
+    }
+}
+
+// Reverse of tile_ops_fwd, register bits I, I-1, ..., 0: per op, first its
+// sums k0..k3 (at the point after the group) into k[4 I .. 4 I + 3], then
+// the inverse group (sm holds the adjoint matrices) on psi and lambda.
+template <typename C, typename Real, int R, int I, int NV>
+__device__ __forceinline__ void tile_ops_rev(uint32_t ops, const C *sm, C (&a)[1 << R],
+                                             C (&al)[1 << R], Real (&k)[NV]) {
     if constexpr (I >= 0) {
-        const int u = sg.op[I];
-        if (u >= 0) {
-            if ((P.param_mask >> u) & 1ull) {
-                Real rh[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                rho_bit<C, Real, R, I>(a, al, rh);
-                const Real v = warp_reduce8<Real>(rh, lane);
-                if (lane < 8) accw[u * wps * 8 + lane] += v;
-            }
-            const C m0 = sm[4 * u], m1 = sm[4 * u + 1], m2 = sm[4 * u + 2], m3 = sm[4 * u + 3];
-            if ((P.real_mask >> u) & 1ull) {
+        const uint32_t ob = (ops >> (8 * I)) & 0xffu;
+        if (ob) {
+            if (ob & 128u) kmat_bit<C, Real, R, I>(a, al, &k[4 * I]);
+            C m0, m1, m2, m3;
+            load_mat(sm, (int)(ob & 63u) - 1, m0, m1, m2, m3);
+            if (ob & 64u) {
                 u1r_bit<C, Real, R, I>(a, m0.x, m1.x, m2.x, m3.x);
                 u1r_bit<C, Real, R, I>(al, m0.x, m1.x, m2.x, m3.x);
             } else {
@@ -258,35 +323,50 @@ __device__ __forceinline__ void tile_ops_rev(const TilePass &P, const TileStage 
                 u1_bit<C, R, I>(al, m0, m1, m2, m3);
             }
         }
-        tile_ops_rev<C, Real, R, I - 1>(P, sg, sm, a, al, accw, wps, lane);
+        tile_ops_rev<C, Real, R, I - 1, NV>(ops, sm, a, al, k);
     }
 }
 
-// Adds the block's reduced-matrix sums of slot b (FP64 over warps) to
-// rho_g[b][group][8] and clears them.  Called by every thread.
+// Adds the block's sums of slot b (FP64 over warps and lane quads), as i K
+// in reduced-matrix form, to rho_g[b][group][8] and clears them.  Called by
+// every thread.
 template <typename Real>
 __device__ void flush_acc(const TilePass &P, Real *acc, int wps, double *rho_g, int b, int G) {
     __syncthreads();
-    for (int x = threadIdx.x; x < P.n_ops * 8; x += blockDim.x) {
-        const int u = x >> 3, v = x & 7;
+    for (int x = threadIdx.x; x < P.n_ops * 4; x += blockDim.x) {
+        const int u = x >> 2, c = x & 3;
         if (!((P.param_mask >> u) & 1ull)) continue;
-        double s = 0.0;
-        for (int w = 0; w < wps; ++w) {
-            Real &r = acc[(u * wps + w) * 8 + v];
-            s += (double)r;
-            r = 0;
+        double k = 0.0;
+        for (int w = 0; w < wps; ++w)
+            for (int q = c; q < 32; q += 4) {
+                Real &r = acc[(u * wps + w) * 32 + q];
+                k += (double)r;
+                r = 0;
+            }
+        if (k == 0.0) continue;
+        // i K = [[i k0, (k3 + i k2) / 2], [(-k3 + i k2) / 2, i k1]]
+        double *dst = rho_g + ((size_t)b * G + P.grp[u]) * 8;
+        if (c == 0) {
+            atomicAdd(dst + 1, k);
+        } else if (c == 1) {
+            atomicAdd(dst + 7, k);
+        } else if (c == 2) {
+            atomicAdd(dst + 3, 0.5 * k);
+            atomicAdd(dst + 5, 0.5 * k);
+        } else {
+            atomicAdd(dst + 2, 0.5 * k);
+            atomicAdd(dst + 4, -0.5 * k);
         }
-        if (s != 0.0) atomicAdd(&rho_g[((size_t)b * G + P.grp[u]) * 8 + v], s);
     }
     __syncthreads();
 }
 
 // One reverse pass: un-applies the pass on psi and lambda tiles and sums the
-// reduced matrices of its parametrised groups into rho_g[slot][group][8].
-// Reduced-matrix partials are summed in the state's precision over one
+// reduced matrices of its parametrised groups (as i K) into
+// rho_g[slot][group][8].  The sums run in the state's precision over one
 // warp and at most 64 tiles, then in FP64.
 template <typename Real, int R>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, R >= 4 ? 1 : 2)
 k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
            const typename CT<Real>::T *mats, int G, typename CT<Real>::T *psi,
            typename CT<Real>::T *lam, double *rho_g) {
@@ -298,8 +378,10 @@ k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
     const int lane = tid & 31, wps = T >> 5;
     const uint32_t tbytes = (uint32_t)sizeof(C) << t;
     uint2 *tb = reinterpret_cast<uint2 *>(smem + 4 * tbytes);
-    C *sm = reinterpret_cast<C *>(smem + 4 * tbytes + (uint32_t)S * T * 8u);
+    uint4 *rec = reinterpret_cast<uint4 *>(smem + 4 * tbytes + (uint32_t)S * T * 8u);
+    C *sm = reinterpret_cast<C *>(rec + 2 * S);
     Real *acc = reinterpret_cast<Real *>(sm + 4 * P.n_ops);
+    build_stage_recs(P, rec);
     for (int s = 0; s < S; ++s) {
         const TileStage &sg = P.st[s];
         uint32_t lb = 0, sb = 0;
@@ -310,8 +392,8 @@ k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
             }
         tb[s * T + tid] = make_uint2(lb, sb);
     }
-    for (int x = tid; x < P.n_ops * wps * 8; x += T) acc[x] = 0;
-    Real *accw = acc + (tid >> 5) * 8;
+    for (int x = tid; x < P.n_ops * wps * 32; x += T) acc[x] = 0;
+    Real *accw = acc + (tid >> 5) * 32 + lane;  // [op][warp][lane]: sum k_(lane & 3)
     uint32_t gk[R], pk[R], nk[R];
     const uint32_t g0 = bit_vectors<R>(P.gl, t, tid, gk);
     const uint32_t p0 = bit_vectors<R>(P.ldperm, t, tid, pk);
@@ -359,14 +441,9 @@ k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
         if (tix + 1 < t_end) fetch(nxt, buf ^ 1);
         unsigned char *tp = smem + (uint32_t)buf * tbytes, *tl = tp + 2 * tbytes;
         for (int s = S - 1; s >= 0; --s) {
-            const TileStage &sg = P.st[s];
             const uint2 bb = tb[s * T + tid];
             uint32_t lq[R], sq[R];
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-                lq[j] = sg.ldq[j];
-                sq[j] = sg.stq[j];
-            }
+            const uint32_t ops = read_stage_rec<R>(rec, s, lq, sq);
             C a[NA], al[NA];
 #pragma unroll
             for (int r = 0; r < NA; ++r) {
@@ -374,7 +451,19 @@ k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
                 a[r] = *reinterpret_cast<const C *>(tp + ad);
                 al[r] = *reinterpret_cast<const C *>(tl + ad);
             }
-            tile_ops_rev<C, Real, R, R - 1>(P, sg, sm, a, al, accw, wps, lane);
+            // the stage's sums: over lane quads in registers, then per lane
+            // into the warp's accumulators
+            constexpr int NV = 4 * R <= 8 ? 8 : 16;
+            Real kk[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) kk[v] = 0;
+            tile_ops_rev<C, Real, R, R - 1, NV>(ops, sm, a, al, kk);
+            warp_reduce_quad<Real, NV>(kk, lane);
+#pragma unroll
+            for (int m = 0; m < R; ++m) {
+                const uint32_t ob = (ops >> (8 * m)) & 0xffu;
+                if (ob & 128u) accw[((int)(ob & 63u) - 1) * wps * 32] += kk[m];
+            }
             __syncthreads();
 #pragma unroll
             for (int r = 0; r < NA; ++r) {
@@ -399,6 +488,201 @@ k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
     flush_acc<Real>(P, acc, wps, rho_g, mslot, G);
 }
 
+// Sum of v over the block (every thread gets it); red: one double per warp.
+__device__ __forceinline__ double block_sum(double v, double *red) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    return s;
+}
+
+// ------------------------------------------------------ H over tile passes
+
+// Tile walk of an H pass (the same counting as TileCursor).
+__device__ __forceinline__ TileCursor h_cursor(const HPass &P, int64_t tix) {
+    TileCursor c;
+    c.slot = (int)(tix >> P.n_tile_bits);
+    c.local = (uint32_t)(tix & ((int64_t(1) << P.n_tile_bits) - 1));
+    c.base = 0;
+    for (int k = 0; k < P.n_tile_bits; ++k)
+        if ((c.local >> k) & 1u) c.base ^= P.gpre[k] ^ (k ? P.gpre[k - 1] : 0u);
+    return c;
+}
+
+__device__ __forceinline__ TileCursor h_next(const HPass &P, TileCursor c) {
+    ++c.local;
+    if ((c.local >> P.n_tile_bits) != 0u) {
+        c.local = 0;
+        c.base = 0;
+        ++c.slot;
+    } else {
+        c.base ^= P.gpre[__ffs((int)c.local) - 1];
+    }
+    return c;
+}
+
+// Per-tile record of one class of terms: its coefficient sum_t c_t i^phase_t
+// times the term's sign on the tile's non-local bits and the class's sign
+// on the group's flip bits, the Z mask on the thread bits, and the class's
+// sign for each of the thread's amplitude slots k (parity of k & the Z mask
+// on the register bits).
+template <typename Real> struct HCoef {
+    uint32_t zt, kpat;
+    Real re, im;
+};
+
+// One H pass: for the pass's X-mask groups g,
+//   lambda_j (+)= sum_g D_g(j ^ x_g) psi_(j ^ x_g),
+//   D_g(k) = sum_(t in g) c_t i^phase_t (-1)^|k & z_t|,
+// and E[slot] += sum_j Re(conj(psi_j) lambda_j) over this pass's part of
+// lambda.  psi tiles arrive by cp.async (double-buffered) in natural order;
+// the thread's amplitudes are j = tid + k 2^(t-R), handled 8 at a time.
+// Products in the state's precision, sums over the block's amplitudes in
+// FP64.  kLam = false: energies only.
+template <typename Real, int R, bool kLam>
+__global__ void __launch_bounds__(256)
+k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<Real>::T *psi,
+         typename CT<Real>::T *lam, double *E) {
+    using C = typename CT<Real>::T;
+    constexpr int NA = 1 << R, KC = NA < 8 ? NA : 8;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x, T = blockDim.x, t = P.t;
+    const uint32_t tbytes = (uint32_t)sizeof(C) << t;
+    HCoef<Real> *coef = reinterpret_cast<HCoef<Real> *>(smem + 2 * tbytes);
+    HGroup *grp = reinterpret_cast<HGroup *>(coef + P.n_classes);
+    HClass *cls = reinterpret_cast<HClass *>(grp + P.n_groups);
+    double *red = reinterpret_cast<double *>(cls + P.n_classes);
+    for (int i = tid; i < P.n_groups; i += T) grp[i] = P.groups[i];
+    for (int i = tid; i < P.n_classes; i += T) cls[i] = P.classes[i];
+    uint32_t gk[R];
+    const uint32_t g0 = bit_vectors<R>(P.gl, t, tid, gk);
+    const uint32_t sh = (uint32_t)__cvta_generic_to_shared(smem);
+    const int64_t tiles = (int64_t)n_slots << P.n_tile_bits;
+    const int64_t per = (tiles + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = per * blockIdx.x, t_end = min(tiles, t0 + per);
+    if (t0 >= t_end) return;
+    const bool real = P.real != 0;
+    auto fetch = [&](const TileCursor &c, int buf) {
+        const C *src = psi + ((int64_t)c.slot << n) + c.base;
+        const uint32_t d = sh + (uint32_t)buf * tbytes;
+#pragma unroll
+        for (int k = 0; k < NA; ++k)
+            cp_async_amp(d + (uint32_t)(tid + k * T) * (uint32_t)sizeof(C), src + (g0 ^ xsel<R>(k, gk)));
+        cp_async_commit();
+    };
+    TileCursor cur = h_cursor(P, t0);
+    fetch(cur, 0);
+    TileCursor nxt = h_next(P, cur);
+    double e_acc = 0.0;
+    int eslot = cur.slot;
+    for (int64_t tix = t0, i = 0; tix < t_end; ++tix, ++i) {
+        const int buf = (int)(i & 1);
+        if (cur.slot != eslot) {  // the slot's energy so far
+            const double s = block_sum(e_acc, red);
+            if (tid == 0) atomicAdd(&E[eslot], s);
+            e_acc = 0.0;
+            eslot = cur.slot;
+        }
+        for (int c = tid; c < P.n_classes; c += T) {  // this tile's class records
+            const HClass cl = cls[c];
+            Real re = 0, im = 0;
+            for (int ti = cl.t_begin; ti < cl.t_end; ++ti) {
+                const HTerm tm = P.terms[ti];
+                const Real v =
+                    (__popc((cur.base ^ cl.xnl) & tm.z) & 1u) ? (Real)-tm.coeff : (Real)tm.coeff;
+                if (tm.phase == 0) re += v;
+                else if (tm.phase == 1) im += v;
+                else if (tm.phase == 2) re -= v;
+                else im -= v;
+            }
+            if (__popc(cl.xl & cl.zl) & 1u) {
+                re = -re;
+                im = -im;
+            }
+            const uint32_t zh = cl.zl >> (t - R);
+            uint32_t kp = 0;
+            for (int k = 0; k < NA; ++k) kp |= (uint32_t)(__popc((uint32_t)k & zh) & 1) << k;
+            HCoef<Real> h;
+            h.zt = cl.zl & (uint32_t)(T - 1);
+            h.kpat = kp;
+            h.re = re;
+            h.im = im;
+            coef[c] = h;
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (tix + 1 < t_end) fetch(nxt, buf ^ 1);
+        const C *tile = reinterpret_cast<const C *>(smem + (uint32_t)buf * tbytes);
+        C *L = lam + ((int64_t)cur.slot << n) + cur.base;
+        const C *Sg = psi + ((int64_t)cur.slot << n);
+        Real part = 0;
+#pragma unroll
+        for (int k0 = 0; k0 < NA; k0 += KC) {
+            Real lr[KC], li[KC];
+#pragma unroll
+            for (int k = 0; k < KC; ++k) lr[k] = li[k] = 0;
+            for (int g = 0; g < P.n_groups; ++g) {
+                const HGroup gr = grp[g];
+                C p[KC];
+#pragma unroll
+                for (int k = 0; k < KC; ++k) {
+                    const uint32_t j = (uint32_t)(tid + (k0 + k) * T);
+                    p[k] = gr.xfar ? Sg[(cur.base ^ g0 ^ xsel<R>(k0 + k, gk)) ^ gr.xfar]
+                                   : tile[j ^ gr.xl];
+                }
+                Real dr[KC], di[KC];
+#pragma unroll
+                for (int k = 0; k < KC; ++k) dr[k] = di[k] = 0;
+                for (int c = gr.c_begin; c < gr.c_end; ++c) {
+                    const HCoef<Real> h = coef[c];
+                    const bool nt = __popc((uint32_t)tid & h.zt) & 1u;
+                    const Real vr = nt ? -h.re : h.re;
+                    const uint32_t kp = h.kpat >> k0;
+#pragma unroll
+                    for (int k = 0; k < KC; ++k) dr[k] += ((kp >> k) & 1u) ? -vr : vr;
+                    if (!real) {
+                        const Real vi = nt ? -h.im : h.im;
+#pragma unroll
+                        for (int k = 0; k < KC; ++k) di[k] += ((kp >> k) & 1u) ? -vi : vi;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < KC; ++k) {
+                    lr[k] = fmaR(dr[k], p[k].x, fmaR(-di[k], p[k].y, lr[k]));
+                    li[k] = fmaR(dr[k], p[k].y, fmaR(di[k], p[k].x, li[k]));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < KC; ++k) {
+                const C pj = tile[tid + (k0 + k) * T];
+                part = fmaR(pj.x, lr[k], fmaR(pj.y, li[k], part));
+                if constexpr (kLam) {
+                    const uint32_t go = g0 ^ xsel<R>(k0 + k, gk);
+                    C out;
+                    out.x = lr[k];
+                    out.y = li[k];
+                    if (!P.first) {
+                        const C old = L[go];
+                        out.x += old.x;
+                        out.y += old.y;
+                    }
+                    L[go] = out;
+                }
+            }
+        }
+        e_acc += (double)part;
+        __syncthreads();  // coef and this buffer are rewritten next
+        cur = nxt;
+        nxt = h_next(P, nxt);
+    }
+    const double s = block_sum(e_acc, red);
+    if (tid == 0) atomicAdd(&E[eslot], s);
+}
+
 // D_g(j) = sum_{t in g} c_t i^{phase_t} (-1)^{|j & z_t|} for one amplitude.
 template <typename Real>
 __device__ __forceinline__ void diag_of(const Observable &o, const TermGroup &tg, uint32_t j,
@@ -415,16 +699,6 @@ __device__ __forceinline__ void diag_of(const Observable &o, const TermGroup &tg
     }
 }
 
-__device__ __forceinline__ double block_sum(double v, double *red) {
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-    return s;
-}
 
 // out[b] += sum_j sum_g Re(conj(psi_{j^x_g}) psi_j D_g(j)); grid.y = slot.
 // Products in the state's precision over 8 amplitudes, sums in FP64.
@@ -583,13 +857,13 @@ cudaError_t launch_init_states(int c128, void *states, int n, const SlotSource &
 
 uint32_t tile_fwd_smem(int c128, const TilePass &P) {
     const uint32_t csz = c128 ? 16u : 8u, T = 1u << (P.t - P.R);
-    return 2u * (csz << P.t) + (uint32_t)P.n_stages * T * 8u + (uint32_t)P.n_ops * 4u * csz;
+    return 2u * (csz << P.t) + (uint32_t)P.n_stages * (T * 8u + 32u) + (uint32_t)P.n_ops * 4u * csz;
 }
 
 uint32_t tile_rev_smem(int c128, const TilePass &P) {
     const uint32_t csz = c128 ? 16u : 8u, rsz = c128 ? 8u : 4u, T = 1u << (P.t - P.R);
-    return 4u * (csz << P.t) + (uint32_t)P.n_stages * T * 8u + (uint32_t)P.n_ops * 4u * csz +
-           (uint32_t)P.n_ops * (T / 32u) * 8u * rsz;
+    return 4u * (csz << P.t) + (uint32_t)P.n_stages * (T * 8u + 32u) + (uint32_t)P.n_ops * 4u * csz +
+           (uint32_t)P.n_ops * T * rsz;
 }
 
 cudaError_t launch_tile_fwd(int c128, const TilePass &P, int n, int n_slots, const void *mats,
@@ -622,6 +896,40 @@ cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, con
                                          rho_g);
     });
     return cudaGetLastError();
+}
+
+uint32_t tile_h_smem(int c128, const HPass &P) {
+    const uint32_t csz = c128 ? 16u : 8u;
+    return 2u * (csz << P.t) + (uint32_t)P.n_classes * (csz + 8u + (uint32_t)sizeof(HClass)) +
+           (uint32_t)P.n_groups * (uint32_t)sizeof(HGroup) + 32u * 8u + 16u;
+}
+
+cudaError_t launch_tile_h(int c128, const HPass &P, int n, int n_slots, const void *psi, void *lam,
+                          double *E, int64_t max_blocks, cudaStream_t st) {
+    const uint32_t smem = tile_h_smem(c128, P);
+    // 2^R amplitudes per thread: 256 threads for t >= 10, at least 32 below
+    const int R = P.t >= 12 ? 4 : (P.t == 11 ? 3 : 2);
+    const int threads = 1 << (P.t - R);
+    if (P.t < 7 || P.t > 12) return cudaErrorInvalidValue;
+    auto go = [&](auto k, auto *psi_t, auto *lam_t) -> cudaError_t {
+        cudaError_t e = allow_smem(k, smem);
+        if (e != cudaSuccess) return e;
+        const int blocks = fill_blocks(k, threads, smem, max_blocks);
+        k<<<blocks, threads, smem, st>>>(P, n, n_slots, psi_t, lam_t, E);
+        return cudaGetLastError();
+    };
+    auto pick = [&](auto rr) -> cudaError_t {
+        constexpr int RR = decltype(rr)::value;
+        if (c128) {
+            if (lam) return go(k_tile_h<double, RR, true>, (const double2 *)psi, (double2 *)lam);
+            return go(k_tile_h<double, RR, false>, (const double2 *)psi, (double2 *)nullptr);
+        }
+        if (lam) return go(k_tile_h<float, RR, true>, (const float2 *)psi, (float2 *)lam);
+        return go(k_tile_h<float, RR, false>, (const float2 *)psi, (float2 *)nullptr);
+    };
+    if (R == 4) return pick(std::integral_constant<int, 4>());
+    if (R == 3) return pick(std::integral_constant<int, 3>());
+    return pick(std::integral_constant<int, 2>());
 }
 
 static dim3 whole_state_grid(int n, int rows) {

@@ -25,6 +25,11 @@ cudaError_t launch_tile_fwd(int c128, const TilePass &P, int n, int n_slots, con
 cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, const void *mats,
                             int G, void *psi, void *lam, double *rho_g, int64_t max_blocks,
                             cudaStream_t st);
+// One tile pass of lambda = H psi (lam may be null: energies only); adds this
+// pass's part of <psi|H|psi> to E[slot] (zero E before the first pass).
+uint32_t tile_h_smem(int c128, const HPass &P);
+cudaError_t launch_tile_h(int c128, const HPass &P, int n, int n_slots, const void *psi, void *lam,
+                          double *E, int64_t max_blocks, cudaStream_t st);
 // out[r] = <psi_r|H|psi_r> (zeroed here first).
 cudaError_t launch_expect_big(int c128, const Observable &o, int n, int n_rows,
                               const void *states, double *out, cudaStream_t st);

@@ -431,6 +431,107 @@ std::string build_tile_passes(const HostProgram &P, int csz, std::vector<TilePas
     return "";
 }
 
+std::string plan_h_passes(const HostObservable &h, int tile_bits, int coalesce_bits,
+                          HostHPlan *out) {
+    const int n = h.n, t = tile_bits;
+    if (t < coalesce_bits + 1 || t > n || t > kTileBitsMax) return "bad tile_bits for H passes";
+    *out = HostHPlan();
+    const uint32_t forced = (1u << coalesce_bits) - 1u;
+    std::vector<int> pending(h.tgroups.size());
+    for (size_t i = 0; i < pending.size(); ++i) pending[i] = (int)i;
+    while (!pending.empty()) {
+        uint32_t L = forced;
+        std::vector<int> taken, rest;
+        std::vector<int> far;  // flip masks that fit no tile: partners from global memory
+        for (int gi : pending) {
+            const uint32_t x = h.tgroups[gi].x;
+            if (__builtin_popcount(forced | x) > t) {
+                far.push_back(gi);
+            } else if (__builtin_popcount(L | x) <= t) {
+                L |= x;
+                taken.push_back(gi);
+            } else {
+                rest.push_back(gi);
+            }
+        }
+        if (taken.empty() && far.empty()) return "internal: H pass planner made no progress";
+        for (int gi : far) taken.push_back(gi);
+        for (int q = 0; __builtin_popcount(L) < t && q < n; ++q) L |= 1u << q;
+        HPass P{};
+        P.t = t;
+        P.n_tile_bits = n - t;
+        P.first = out->passes.empty() ? 1 : 0;
+        std::vector<int> pos(n, -1);
+        int b = 0, k = 0;
+        uint32_t acc = 0;
+        for (int q = 0; q < n; ++q) {
+            if ((L >> q) & 1u) {
+                pos[q] = b;
+                P.gl[b++] = 1u << q;
+            } else {
+                acc ^= 1u << q;
+                P.gpre[k++] = acc;
+            }
+        }
+        auto local = [&](uint32_t m) {
+            uint32_t r = 0;
+            for (int q = 0; q < n; ++q)
+                if (((m >> q) & 1u) && pos[q] >= 0) r |= 1u << pos[q];
+            return r;
+        };
+        out->g_begin.push_back((int)out->groups.size());
+        out->c_begin.push_back((int)out->classes.size());
+        out->t_begin.push_back((int)out->terms.size());
+        const int g0 = (int)out->groups.size(), c0 = (int)out->classes.size(),
+                  t0 = (int)out->terms.size();
+        for (int gi : taken) {
+            const TermGroup &tg = h.tgroups[gi];
+            HGroup G{};
+            G.xl = local(tg.x);
+            const uint32_t xnl = tg.x & ~L;
+            G.xfar = xnl ? tg.x : 0u;
+            G.c_begin = (int)out->classes.size() - c0;
+            std::vector<int> order;
+            for (int ti = tg.t_begin; ti < tg.t_end; ++ti) order.push_back(ti);
+            std::stable_sort(order.begin(), order.end(), [&](int a, int bb) {
+                return local(h.terms[a].z) < local(h.terms[bb].z);
+            });
+            for (size_t i = 0; i < order.size(); ++i) {
+                const Term &tm = h.terms[order[i]];
+                const uint32_t zl = local(tm.z);
+                if (i == 0 || zl != out->classes.back().zl ||
+                    (int)out->classes.size() - c0 == G.c_begin) {
+                    HClass C{};
+                    C.zl = zl;
+                    C.xnl = xnl;
+                    C.xl = G.xl;
+                    C.t_begin = (int)out->terms.size() - t0;
+                    out->classes.push_back(C);
+                }
+                HTerm ht{};
+                ht.z = tm.z;
+                ht.phase = tm.phase;
+                ht.coeff = tm.coeff;
+                out->terms.push_back(ht);
+                out->classes.back().t_end = (int)out->terms.size() - t0;
+            }
+            G.c_end = (int)out->classes.size() - c0;
+            out->groups.push_back(G);
+        }
+        P.real = 1;
+        for (size_t i = (size_t)t0; i < out->terms.size(); ++i) P.real &= (out->terms[i].phase & 1) == 0;
+        P.n_groups = (int)out->groups.size() - g0;
+        P.n_classes = (int)out->classes.size() - c0;
+        P.n_terms = (int)out->terms.size() - t0;
+        out->passes.push_back(P);
+        pending.swap(rest);
+    }
+    out->g_begin.push_back((int)out->groups.size());
+    out->c_begin.push_back((int)out->classes.size());
+    out->t_begin.push_back((int)out->terms.size());
+    return "";
+}
+
 std::string plan_observable(const sv_pauli_sum &h, int n, int swz_bits, HostObservable *out) {
     if (h.n_terms < 0) return "negative n_terms";
     if (h.n_terms > 0 && (!h.x_mask || !h.z_mask || !h.coeff)) return "observable arrays missing";

@@ -54,6 +54,18 @@ struct HostObservable {
     std::vector<Term> terms;
 };
 
+// Tile passes of lambda = H psi: pass i uses groups[g_begin[i]..g_begin[i+1])
+// etc.  Device pointers of HPass are left null (set after upload).
+struct HostHPlan {
+    std::vector<HPass> passes;
+    std::vector<int> g_begin, c_begin, t_begin;  // per pass, plus an end entry
+    std::vector<HGroup> groups;
+    std::vector<HClass> classes;
+    std::vector<HTerm> terms;
+};
+std::string plan_h_passes(const HostObservable &h, int tile_bits, int coalesce_bits,
+                          HostHPlan *out);
+
 // Returns "" on success, otherwise the reason the circuit was rejected.
 std::string plan_circuit(const sv_circuit &c, int reg_bits, bool fuse, int swz_bits,
                          HostProgram *out);

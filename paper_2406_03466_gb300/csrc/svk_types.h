@@ -89,7 +89,7 @@ struct PassDesc {
 // offsets are amplitude indices within one state.
 constexpr int kTileBitsMax = 13;  // largest tile: 2^13 amplitudes
 constexpr int kPassStages = 16;   // register stages per pass
-constexpr int kPassOps = 64;      // fused-group ops per pass
+constexpr int kPassOps = 48;      // fused-group ops per pass (< 63: kernels pack u + 1 in 6 bits)
 
 struct TileStage {
     uint32_t ldq[kRMax], stq[kRMax];                // register bit i: load / store vector
@@ -144,6 +144,43 @@ struct Observable {
     int32_t n_tgroups, n_terms;
     const TermGroup *tgroups;
     const Term *terms;
+};
+
+// lambda = H psi (and <H>) over tiles of 2^t amplitudes.  A pass covers the
+// X-mask groups whose flip mask lies inside its local qubits; inside a
+// group, terms with the same Z mask on the local qubits form a class whose
+// coefficient is summed once per tile (the Z mask's tile-number bits only
+// give each term a sign per tile).
+struct HGroup {
+    uint32_t xl;              // flip mask on tile-local bits
+    int32_t c_begin, c_end;   // its classes
+    uint32_t xfar;            // whole flip mask when it leaves the tile (partner read from
+                              // global memory), else 0
+};
+
+struct HClass {
+    uint32_t zl;              // Z mask on tile-local bits
+    int32_t t_begin, t_end;   // its terms
+    uint32_t xnl;             // the group's flip bits outside the tile (sign of the partner)
+    uint32_t xl;              // the group's flip bits on tile-local bits
+    int32_t pad;
+};
+
+struct HTerm {
+    uint32_t z;               // Z mask (global index bits)
+    int32_t phase;            // i^phase, phase = #Y mod 4
+    double coeff;
+};
+
+struct HPass {
+    int32_t t, n_tile_bits, n_groups, n_classes, n_terms, first;  // first: writes lambda
+    int32_t real;               // every coefficient c_t i^phase_t is real
+    int32_t pad;
+    uint32_t gl[kTileBitsMax];  // tile-local bit b -> global offset bit
+    uint32_t gpre[kNMax];       // gt[0] ^ ... ^ gt[k] for tile-number bit k
+    const HGroup *groups;       // device arrays of this pass
+    const HClass *classes;
+    const HTerm *terms;
 };
 
 // GF(2)-linear swizzle of a shared-memory amplitude index: the low `w` bits

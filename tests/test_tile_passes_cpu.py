@@ -40,7 +40,7 @@ class TileStage(ctypes.Structure):
 class TilePass(ctypes.Structure):
     _fields_ = [("t", I32), ("R", I32), ("n_stages", I32), ("n_ops", I32), ("n_tile_bits", I32),
                 ("pad", I32), ("real_mask", U64), ("param_mask", U64), ("gl", U32 * KT),
-                ("gpre", U32 * 30), ("ldperm", U32 * KT), ("nat", U32 * KT), ("grp", I32 * 64),
+                ("gpre", U32 * 30), ("ldperm", U32 * KT), ("nat", U32 * KT), ("grp", I32 * 48),
                 ("st", TileStage * 16)]
 
 
@@ -220,14 +220,20 @@ def run_rev(P, psi, lam, mats, rho, csz, n_blocks=2):
                     continue
                 g = P.grp[u]
                 if P.param_mask >> u & 1:
+                    # the kernel keeps K = (rho - rho^dag) / 2i as four sums
+                    # and stores i K in place of rho
+                    k = np.zeros(4)
                     for r in range(NA):
                         if r >> I & 1:
                             continue
-                        ps = (a[:, r], a[:, r | 1 << I])
-                        ls = (al[:, r], al[:, r | 1 << I])
-                        for x in range(2):
-                            for y in range(2):
-                                rho[slot][g][x, y] += np.sum(ps[x] * np.conj(ls[y]))
+                        x0, x1 = a[:, r], a[:, r | 1 << I]
+                        y0, y1 = al[:, r], al[:, r | 1 << I]
+                        k[0] += np.sum(x0 * np.conj(y0)).imag
+                        k[1] += np.sum(x1 * np.conj(y1)).imag
+                        k[2] += np.sum(x0 * np.conj(y1) + x1 * np.conj(y0)).imag
+                        k[3] += np.sum(x0 * np.conj(y1) - x1 * np.conj(y0)).real
+                    rho[slot][g] += np.array([[1j * k[0], 0.5 * (k[3] + 1j * k[2])],
+                                              [0.5 * (-k[3] + 1j * k[2]), 1j * k[1]]])
                 Md = mats[slot][g].conj().T
                 apply_bit(a, I, Md)
                 apply_bit(al, I, Md)
@@ -353,3 +359,103 @@ def test_rejects_tiles_narrower_than_a_warp():
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     assert L.sv_debug_tile_passes(ctypes.byref(circuit_of(w).struct), 7, 3, 1, 0, counts,
                                   None, None, None) != 0
+
+
+# ------------------------------------------------------------ lambda = H psi
+
+class HPassRec(ctypes.Structure):
+    _fields_ = [("t", I32), ("n_tile_bits", I32), ("n_groups", I32), ("n_classes", I32),
+                ("n_terms", I32), ("first", I32), ("real", I32), ("pad", I32), ("gl", U32 * KT),
+                ("gpre", U32 * 30),
+                ("groups", ctypes.c_void_p), ("classes", ctypes.c_void_p),
+                ("terms", ctypes.c_void_p)]
+
+
+class HGroup(ctypes.Structure):
+    _fields_ = [("xl", U32), ("c_begin", I32), ("c_end", I32), ("xfar", U32)]
+
+
+class HClass(ctypes.Structure):
+    _fields_ = [("zl", U32), ("t_begin", I32), ("t_end", I32), ("xnl", U32), ("xl", U32),
+                ("pad", I32)]
+
+
+class HTerm(ctypes.Structure):
+    _fields_ = [("z", U32), ("phase", I32), ("coeff", ctypes.c_double)]
+
+
+def export_h(obs, t, c):
+    L = sv.library()
+    L.sv_debug_h_passes.argtypes = [ctypes.c_void_p, I32, I32, ctypes.POINTER(I32)] + [ctypes.c_void_p] * 4
+    L.sv_debug_h_passes.restype = I32
+    counts = (I32 * 4)()
+    assert L.sv_debug_h_passes(ctypes.byref(obs.struct), t, c, counts, None, None, None, None) == 0
+    arrs = [(HPassRec * counts[0])(), (HGroup * max(1, counts[1]))(),
+            (HClass * max(1, counts[2]))(), (HTerm * max(1, counts[3]))()]
+    assert L.sv_debug_h_passes(ctypes.byref(obs.struct), t, c, counts, *arrs) == 0
+    return [a[:k] for a, k in zip(arrs, counts)]
+
+
+def run_h(plan, psi, n):
+    """The tile H kernel, tile by tile: returns lambda = H psi and <psi|H|psi>."""
+    passes, groups, classes, terms = plan
+    lam = np.zeros_like(psi)
+    E = 0.0
+    for P in passes:
+        t, ntb = P.t, P.n_tile_bits
+        g0, c0, t0 = P.groups or 0, P.classes or 0, P.terms or 0
+        loc = np.zeros(1 << t, np.int64)
+        for i in range(1 << t):
+            for b in range(t):
+                if i >> b & 1:
+                    loc[i] ^= P.gl[b]
+        j = np.arange(1 << t)
+        for slot, base in tile_walk(P, 1, 3):
+            tile = psi[base + loc]
+            coef = []
+            for cl in classes[c0:c0 + P.n_classes]:
+                v = 0j
+                for tm in terms[t0 + cl.t_begin:t0 + cl.t_end]:
+                    sgn = -1.0 if bin((base ^ cl.xnl) & tm.z).count("1") & 1 else 1.0
+                    v += sgn * tm.coeff * 1j ** tm.phase
+                coef.append(v)
+            part = np.zeros(1 << t, complex)
+            for gr in groups[g0:g0 + P.n_groups]:
+                jx = j ^ gr.xl
+                D = np.zeros(1 << t, complex)
+                for c in range(gr.c_begin, gr.c_end):
+                    par = np.array([bin(v).count("1") & 1 for v in (jx & classes[c0 + c].zl)])
+                    D += np.where(par == 1, -coef[c], coef[c])
+                part += D * (psi[(base + loc) ^ gr.xfar] if gr.xfar else tile[jx])
+            E += float(np.sum(np.conj(tile) * part).real)
+            if P.first:
+                lam[base + loc] = part
+            else:
+                lam[base + loc] += part
+    return lam, E
+
+
+@pytest.mark.parametrize("n,t,c,kind", [(9, 7, 4, "mcvqe"), (10, 8, 4, "mcvqe"), (8, 7, 3, "random"),
+                                        (9, 9, 4, "random"), (10, 7, 4, "mcvqe")])
+def test_h_passes_match_dense(n, t, c, kind):
+    if kind == "mcvqe":
+        w = wl.mcvqe(n, 1, "nn+nnn", n_refs=1)
+    else:
+        w = wl.vqe_random_pauli(n, 1, 40)
+    obs = sv.PauliSum(n, w.pauli_letters, w.pauli_coeffs)
+    plan = export_h(obs, t, c)
+    passes = plan[0]
+    assert passes[0].first == 1 and all(p.first == 0 for p in passes[1:])
+    # every X-mask group is covered by exactly one pass
+    xs = {}
+    for row in np.asarray(w.pauli_letters).reshape(-1, n):
+        x = sum(1 << q for q in range(n) if row[q] in (1, 2))
+        xs[x] = 1
+    assert len(plan[1]) == len(xs)
+    rng = np.random.default_rng(n + t)
+    psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    psi /= np.linalg.norm(psi)
+    H = dense.hamiltonian(n, w.pauli_letters, w.pauli_coeffs)
+    lam, E = run_h(plan, psi, n)
+    np.testing.assert_allclose(lam, H @ psi, atol=1e-12)
+    assert abs(E - np.vdot(psi, H @ psi).real) < 1e-12
