@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true", help="skip adjoint/plain/c128 side runs")
+    ap.add_argument("--qubits", type=int, default=0,
+                    help="qcl20 / mcvqe28 only: the same workload family at this qubit count "
+                         "(a smaller case for profiler captures; not a bench line)")
     return ap.parse_args()
 
 
@@ -204,6 +207,36 @@ def forward_passes_roofline(sv, w, dev, flush, stream, reps=5):
             "forward_ms": t * 1e3, "bytes_per_forward": nbytes, "peak_source": src}
 
 
+def adjoint_phases(sv, w, prob, theta, out, info, flush, stream, reps):
+    """Per-phase CUDA-event times of the device-memory adjoint (the library's
+    phase timer records events on the call's stream), each step after an L2
+    flush; the reverse tile passes are the dominant kernel: per pass they
+    read and write psi and lambda of every state."""
+    import torch
+    sv.sv_phase_timing(True)
+    ph = {"forward_ms": 0.0, "h_ms": 0.0, "reverse_ms": 0.0}
+    for _ in range(reps):
+        flush.fill_(1.0)
+        sv.sv_grad_adjoint(prob, theta, None, *out)
+        got = sv.sv_last_phase_ms()
+        for k in ph:
+            ph[k] += got[k] / reps
+    sv.sv_phase_timing(False)
+    torch.cuda.synchronize()
+    n, I = w.n_qubits, w.n_instances
+    state = I * (8 << n)
+    nbytes = 4 * info["n_passes"] * state
+    peak, src = measured_hbm_gbs()
+    achieved = nbytes / (ph["reverse_ms"] * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": f"k_tile_rev x {info['n_passes']} reverse tile passes of "
+                      f"2^{info['tile_bits']} amplitudes ({w.name}: {I} states of {n} qubits; "
+                      "psi and lambda read and written per pass)",
+            "reverse_ms": ph["reverse_ms"], "bytes_per_reverse": nbytes, "peak_source": src,
+            "phases_ms": ph}
+
+
 def cpu_baseline_device_memory(w, seconds):
     """The oracle on a bounded sample of a large workload: whole circuits
     (each with its full <H>) for about `seconds`, scaled to parameter-shift
@@ -241,6 +274,10 @@ def run_device_memory(args, sv, dev, stream, dist, world, rank):
     """Adjoint gradient of a workload whose states live in device memory."""
     import torch
     w = wl.config(3 if args.workload == "qcl20" else 4)
+    if args.qubits:
+        w = (wl.qcl(args.qubits, w.meta.get("layers", 10), w.n_instances) if args.workload == "qcl20"
+             else wl.mcvqe(args.qubits, w.meta.get("layers", 8), w.meta.get("pairs", "nn+nnn"),
+                           n_refs=w.n_instances))
     prob = sv.Problem.from_spec(w, "c64", device=dev)
     theta = torch.as_tensor(w.theta, dtype=torch.float64, device=dev)
     out = sv._outputs(prob, dev, None, None, None)
@@ -271,6 +308,7 @@ def run_device_memory(args, sv, dev, stream, dist, world, rank):
     gps = world * args.steps / t_dev
     d = 0 if w.inputs is None else 1
     info = sv.sv_plan_info(sv.Circuit(w.n_qubits, w.gates, w.n_params, d), "c64")
+    hinfo = sv.sv_h_plan_info(sv.PauliSum(w.n_qubits, w.pauli_letters, w.pauli_coeffs), "c64")
     result = {"metric": METRIC, "value": gps, "unit": "gradients/s", "n_gpus": world,
               "steps": args.steps, "warmup": args.warmup,
               "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
@@ -280,13 +318,15 @@ def run_device_memory(args, sv, dev, stream, dist, world, rank):
                                      f"params, {info['n_passes']} tile passes per sweep",
                          "l2": "states larger than L2; 256 MiB flush before each step",
                          "parallelism": f"replicas x{world}"},
-              # per adjoint: group matrices, init (memset + |ref>), forward and reverse
-              # passes, lambda = H psi, per-slot gradients, combination
-              "gpu_launches": args.steps * (2 * info["n_passes"] + 5),
+              # per adjoint: group matrices, |ref>, forward and reverse passes, the
+              # passes of lambda = H psi, per-slot gradients, combination
+              "gpu_launches": args.steps * (2 * info["n_passes"] + hinfo["n_passes"] + 4),
               "clocks": clk, "wall_s_timed_region": t_wall}
     if rank == 0:
-        result["roofline"] = forward_passes_roofline(sv, w, dev, flush, stream,
-                                                     reps=3 if w.n_qubits > 24 else 5)
+        result["roofline"] = adjoint_phases(sv, w, prob, theta, out, info, flush, stream,
+                                            reps=2 if w.n_qubits > 24 else 5)
+        result["roofline_forward"] = forward_passes_roofline(sv, w, dev, flush, stream,
+                                                             reps=3 if w.n_qubits > 24 else 5)
         th_host = torch.as_tensor(w.theta, dtype=torch.float64).pin_memory()
         g_host = torch.empty(w.n_params, dtype=torch.float64).pin_memory()
         th_dev = torch.empty_like(theta)

@@ -272,6 +272,22 @@ sv_status sv_plan_info(const sv_circuit *circuit, sv_dtype dtype, const sv_plan_
                        int32_t *on_chip, int32_t *n_passes, int32_t *tile_bits,
                        int32_t *n_stages, int32_t *n_groups);
 
+/* How lambda = H psi and <H> run for states that take the tile path: the
+ * number of tile passes over device memory and their tile size (2^tile_bits
+ * amplitudes).  Host-only.  Any out-pointer may be NULL. */
+sv_status sv_h_plan_info(const sv_pauli_sum *observable, sv_dtype dtype, int32_t *n_passes,
+                         int32_t *tile_bits);
+
+/* Phase timing of the adjoint gradient of states in device memory (the
+ * forward tile passes, lambda = H psi, the reverse tile passes), taken with
+ * CUDA events on the call's stream.  sv_phase_timing(1) turns it on for the
+ * current device (it adds event records to every such call); after a call,
+ * sv_last_phase_ms synchronizes on its events and returns the milliseconds
+ * of each phase summed over the call's chunks of instances, or
+ * SV_ERR_ARG when no timed call has run since timing was turned on. */
+sv_status sv_phase_timing(int32_t on);
+sv_status sv_last_phase_ms(float *forward_ms, float *h_ms, float *reverse_ms);
+
 /* ------------------------------------------------------------- autotune */
 
 /* Times the launch shapes (register bits 1..4, 32..512 threads per block) of

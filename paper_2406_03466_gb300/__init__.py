@@ -80,7 +80,8 @@ class sv_problem(ctypes.Structure):
 EXPORTED = ("sv_alloc", "sv_free", "sv_state_info", "sv_apply_circuit_batch",
             "sv_expect_pauli_sum", "sv_energies", "sv_param_shift_energies", "sv_grad_param_shift", "sv_grad_adjoint",
             "sv_grad_param_shift_plain", "sv_grad_param_shift_noalloc", "sv_autotune",
-            "sv_tuned_shape", "sv_plan_info", "sv_status_string",
+            "sv_tuned_shape", "sv_plan_info", "sv_h_plan_info", "sv_phase_timing",
+            "sv_last_phase_ms", "sv_status_string",
             "sv_last_error",
             "sv_sync_status", "sv_shutdown", "sv_version")
 
@@ -106,6 +107,9 @@ def _load():
     lib.sv_autotune.argtypes = [P(sv_problem), V, I32, V]
     lib.sv_plan_info.argtypes = [P(sv_circuit), I32, P(sv_plan_opts)] + [P(I32)] * 5
     lib.sv_tuned_shape.argtypes = [P(sv_problem), I32, P(I32), P(I32), P(ctypes.c_float)]
+    lib.sv_h_plan_info.argtypes = [P(sv_pauli_sum), I32, P(I32), P(I32)]
+    lib.sv_phase_timing.argtypes = [I32]
+    lib.sv_last_phase_ms.argtypes = [P(ctypes.c_float)] * 3
     lib.sv_status_string.argtypes = [I32]
     lib.sv_status_string.restype = ctypes.c_char_p
     lib.sv_last_error.restype = ctypes.c_char_p
@@ -405,6 +409,26 @@ def sv_plan_info(circuit: Circuit, dtype="c64", opts: Optional[sv_plan_opts] = N
                              *[ctypes.byref(v) for v in vals]), "sv_plan_info")
     keys = ("on_chip", "n_passes", "tile_bits", "n_stages", "n_groups")
     return {k: v.value for k, v in zip(keys, vals)}
+
+
+def sv_h_plan_info(observable: PauliSum, dtype="c64") -> dict:
+    """How lambda = H psi runs for states on the tile path: passes, tile size."""
+    vals = [ctypes.c_int32() for _ in range(2)]
+    _check(_lib.sv_h_plan_info(ctypes.byref(observable.struct), _dtype_code(dtype),
+                               *[ctypes.byref(v) for v in vals]), "sv_h_plan_info")
+    return {"n_passes": vals[0].value, "tile_bits": vals[1].value}
+
+
+def sv_phase_timing(on: bool = True) -> None:
+    """Turn CUDA-event phase timing of device-memory adjoint gradients on/off."""
+    _check(_lib.sv_phase_timing(int(bool(on))), "sv_phase_timing")
+
+
+def sv_last_phase_ms() -> dict:
+    """Milliseconds of the last timed adjoint's forward, H and reverse phases."""
+    vals = [ctypes.c_float() for _ in range(3)]
+    _check(_lib.sv_last_phase_ms(*[ctypes.byref(v) for v in vals]), "sv_last_phase_ms")
+    return {"forward_ms": vals[0].value, "h_ms": vals[1].value, "reverse_ms": vals[2].value}
 
 
 def sv_status_string(status: int) -> str:

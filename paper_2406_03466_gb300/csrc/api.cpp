@@ -108,7 +108,23 @@ struct DeviceCtx {
     std::unordered_map<uint64_t, std::unique_ptr<ArrayEntry>> arrays;
     std::unordered_map<cudaStream_t, std::unique_ptr<DeviceBuf>> scratch;
     std::unordered_map<cudaStream_t, std::unique_ptr<DeviceBuf>> scratch_big;  // device-memory states
+    // Phase timing of tile adjoints: per chunk, events before the forward,
+    // H and reverse phases and after the reverse.
+    bool timing = false;
+    std::vector<cudaEvent_t> phase_ev;
+    int phase_used = 0;
 };
+
+// Records phase event `i` of the current timed call (creating it on first use).
+void phase_mark(DeviceCtx *ctx, cudaStream_t st) {
+    if (!ctx->timing) return;
+    if (ctx->phase_used == (int)ctx->phase_ev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        ctx->phase_ev.push_back(e);
+    }
+    cudaEventRecord(ctx->phase_ev[ctx->phase_used++], st);
+}
 
 std::mutex g_mu;
 std::unordered_map<int, std::unique_ptr<DeviceCtx>> g_ctx;
@@ -653,6 +669,7 @@ sv_status tiles_energies(DeviceCtx *ctx, const sv_problem *p, const double *thet
 sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta,
                         const double *weights, double *energy_out, double *loss_out,
                         double *grad_out, int every, cudaStream_t st) {
+    ctx->phase_used = 0;
     const sv_dtype dt = p->dtype;
     const int c128 = dt == SV_C128, n = p->circuit->n_qubits, I = p->n_instances;
     const int P = p->circuit->n_params, Pp = P > 0 ? P : 1;
@@ -707,10 +724,13 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
         const size_t cb = (size_t)src.n_slots * sb;  // bytes of this group's states
         void *psi = bb, *lam = bb + o_lam, *ck = bb + o_ck, *mats = bb + o_mats;
         double *rho = (double *)(bb + o_rho);
+        phase_mark(ctx, st);
         s = tiles_forward(ctx, pe, cfg.R, dt, src, psi, mats, true, ncp ? ck : nullptr, every, st);
         if (s != SV_OK) return s;
+        phase_mark(ctx, st);
         s = h_tiles(ctx, obs, n, dt, src.n_slots, psi, lam, Es + c0, st);
         if (s != SV_OK) return s;
+        phase_mark(ctx, st);
         cudaError_t e = cudaSuccess;
         SV_CUDA(cudaMemsetAsync(rho, 0, (size_t)src.n_slots * G * 64, st));
         for (int i = npass - 1; i >= 0; --i) {
@@ -727,6 +747,7 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
                                 tile_blocks(ctx, tiles), st);
             if (e != cudaSuccess) return cuda_fail(e, "reverse tile pass");
         }
+        phase_mark(ctx, st);
         e = launch_group_grads(c128, pe->dev, src, rho, cs, Es + c0, Gs + (size_t)c0 * Pp, st);
         if (e != cudaSuccess) return cuda_fail(e, "per-slot gradients");
     }
@@ -1383,6 +1404,50 @@ sv_status sv_plan_info(const sv_circuit *c, sv_dtype dt, const sv_plan_opts *o, 
     if (tile_bits) *tile_bits = t;
     if (n_stages) *n_stages = (int32_t)h.stages.size();
     if (n_groups) *n_groups = (int32_t)h.groups.size();
+    return SV_OK;
+}
+
+sv_status sv_h_plan_info(const sv_pauli_sum *h, sv_dtype dt, int32_t *n_passes,
+                         int32_t *tile_bits) {
+    if (!h) return fail(SV_ERR_ARG, "observable is NULL");
+    if (h->n_qubits < 1 || h->n_qubits > 30) return fail(SV_ERR_ARG, "n_qubits must be in [1, 30]");
+    HostObservable ho;
+    std::string err = plan_observable(*h, h->n_qubits, swz_bits(dt), &ho);
+    const int t = h_tile_bits(h->n_qubits, dt);
+    HostHPlan hp;
+    if (err.empty()) err = plan_h_passes(ho, t, dt == SV_C128 ? 3 : 4, &hp);
+    if (!err.empty()) return fail(SV_ERR_ARG, "observable: " + err);
+    if (n_passes) *n_passes = (int32_t)hp.passes.size();
+    if (tile_bits) *tile_bits = t;
+    return SV_OK;
+}
+
+sv_status sv_phase_timing(int32_t on) {
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->timing = on != 0;
+    ctx->phase_used = 0;
+    return SV_OK;
+}
+
+sv_status sv_last_phase_ms(float *forward_ms, float *h_ms, float *reverse_ms) {
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->timing || ctx->phase_used < 4 || ctx->phase_used % 4)
+        return fail(SV_ERR_ARG, "no timed call since phase timing was turned on");
+    float ph[3] = {0.f, 0.f, 0.f};
+    for (int c = 0; c < ctx->phase_used; c += 4)
+        for (int k = 0; k < 3; ++k) {
+            float ms = 0.f;
+            SV_CUDA(cudaEventSynchronize(ctx->phase_ev[c + k + 1]));
+            SV_CUDA(cudaEventElapsedTime(&ms, ctx->phase_ev[c + k], ctx->phase_ev[c + k + 1]));
+            ph[k] += ms;
+        }
+    if (forward_ms) *forward_ms = ph[0];
+    if (h_ms) *h_ms = ph[1];
+    if (reverse_ms) *reverse_ms = ph[2];
     return SV_OK;
 }
 

@@ -67,6 +67,8 @@ __device__ __forceinline__ void cp_async_amp(uint32_t sdst, const double2 *g) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// Waits for all but the most recently committed group.
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // Offsets of this thread's amplitudes (tile-local index tid + k 2^(t-R))
 // through the per-bit vector table v: returns the tid part and fills the
@@ -116,7 +118,8 @@ __device__ __forceinline__ TileCursor tile_next(const TilePass &P, TileCursor c)
 // Shared-memory record of one stage (32 bytes, read with warp-uniform
 // addresses): word 0 holds one op byte per register bit, (u + 1) | real << 6
 // | parametrised << 7 for pass-local op u (0: no op); word 1 + i holds
-// ldq[i] | stq[i] << 16 (byte offsets, < 2^16 for every supported tile).
+// ldq[i] | stq[i] << 16 (byte offsets, < 2^16 for every supported tile);
+// word 5 holds the ops' fmode bytes.
 __device__ __forceinline__ void build_stage_recs(const TilePass &P, uint4 *rec) {
     for (int s = threadIdx.x; s < P.n_stages; s += blockDim.x) {
         const TileStage &sg = P.st[s];
@@ -129,6 +132,7 @@ __device__ __forceinline__ void build_stage_recs(const TilePass &P, uint4 *rec) 
                 w[0] |= ob << (8 * i);
             }
             w[1 + i] = sg.ldq[i] | (sg.stq[i] << 16);
+            if (u >= 0) w[5] |= (uint32_t)(P.fmode[u] & 3) << (8 * i);
         }
         rec[2 * s] = make_uint4(w[0], w[1], w[2], w[3]);
         rec[2 * s + 1] = make_uint4(w[4], w[5], w[6], w[7]);
@@ -303,16 +307,54 @@ __device__ __forceinline__ void warp_reduce_quad(Real (&x)[NV], int lane) {
     }
 }
 
+// The one sum a group needs when its only rotation is its last member
+// (fmode md): 1: k3 (RY), 2: k2 (RX), 3: k0 - k1 (RZ), over the pairs of
+// register bit I.
+template <typename C, typename Real, int R, int I>
+__device__ __forceinline__ Real single_sum(const C (&a)[1 << R], const C (&l)[1 << R],
+                                           uint32_t md) {
+    Real v = 0;
+    if (md == 1) {
+#pragma unroll
+        for (int r = 0; r < (1 << R); ++r) {
+            if (r & (1 << I)) continue;
+            const C x0 = a[r], x1 = a[r | (1 << I)], y0 = l[r], y1 = l[r | (1 << I)];
+            v = fmaR(x0.x, y1.x, fmaR(x0.y, y1.y, fmaR(-x1.x, y0.x, fmaR(-x1.y, y0.y, v))));
+        }
+    } else if (md == 2) {
+#pragma unroll
+        for (int r = 0; r < (1 << R); ++r) {
+            if (r & (1 << I)) continue;
+            const C x0 = a[r], x1 = a[r | (1 << I)], y0 = l[r], y1 = l[r | (1 << I)];
+            v = fmaR(x0.y, y1.x, fmaR(-x0.x, y1.y, fmaR(x1.y, y0.x, fmaR(-x1.x, y0.y, v))));
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < (1 << R); ++r) {
+            if (r & (1 << I)) continue;
+            const C x0 = a[r], x1 = a[r | (1 << I)], y0 = l[r], y1 = l[r | (1 << I)];
+            v = fmaR(x0.y, y0.x, fmaR(-x0.x, y0.y, fmaR(-x1.y, y1.x, fmaR(x1.x, y1.y, v))));
+        }
+    }
+    return v;
+}
+
 // Reverse of tile_ops_fwd, register bits I, I-1, ..., 0: per op, first its
-// sums k0..k3 (at the point after the group) into k[4 I .. 4 I + 3], then
-// the inverse group (sm holds the adjoint matrices) on psi and lambda.
-template <typename C, typename Real, int R, int I, int NV>
-__device__ __forceinline__ void tile_ops_rev(uint32_t ops, const C *sm, C (&a)[1 << R],
-                                             C (&al)[1 << R], Real (&k)[NV]) {
+// sums (at the point after the group) into k — k0..k3 at k[4 I ..], or with
+// kSingle the one sum of its fmode at k[I] — then the inverse group (sm
+// holds the adjoint matrices) on psi and lambda.
+template <typename C, typename Real, int R, int I, int NV, bool kSingle>
+__device__ __forceinline__ void tile_ops_rev(uint32_t ops, uint32_t modes, const C *sm,
+                                             C (&a)[1 << R], C (&al)[1 << R], Real (&k)[NV]) {
     if constexpr (I >= 0) {
         const uint32_t ob = (ops >> (8 * I)) & 0xffu;
         if (ob) {
-            if (ob & 128u) kmat_bit<C, Real, R, I>(a, al, &k[4 * I]);
+            if (ob & 128u) {
+                if constexpr (kSingle)
+                    k[I] = single_sum<C, Real, R, I>(a, al, (modes >> (8 * I)) & 3u);
+                else
+                    kmat_bit<C, Real, R, I>(a, al, &k[4 * I]);
+            }
             C m0, m1, m2, m3;
             load_mat(sm, (int)(ob & 63u) - 1, m0, m1, m2, m3);
             if (ob & 64u) {
@@ -323,22 +365,26 @@ __device__ __forceinline__ void tile_ops_rev(uint32_t ops, const C *sm, C (&a)[1
                 u1_bit<C, R, I>(al, m0, m1, m2, m3);
             }
         }
-        tile_ops_rev<C, Real, R, I - 1, NV>(ops, sm, a, al, k);
+        tile_ops_rev<C, Real, R, I - 1, NV, kSingle>(ops, modes, sm, a, al, k);
     }
 }
 
 // Adds the block's sums of slot b (FP64 over warps and lane quads), as i K
 // in reduced-matrix form, to rho_g[b][group][8] and clears them.  Called by
 // every thread.
-template <typename Real>
+template <typename Real, bool kSingle>
 __device__ void flush_acc(const TilePass &P, Real *acc, int wps, double *rho_g, int b, int G) {
     __syncthreads();
     for (int x = threadIdx.x; x < P.n_ops * 4; x += blockDim.x) {
-        const int u = x >> 2, c = x & 3;
+        const int u = x >> 2;
         if (!((P.param_mask >> u) & 1ull)) continue;
+        // kSingle: one sum per op in all lanes, stored as the component of
+        // its fmode; otherwise lane q holds component q & 3.
+        const int c = kSingle ? (P.fmode[u] == 1 ? 3 : (P.fmode[u] == 2 ? 2 : 0)) : (x & 3);
+        if (kSingle && (x & 3)) continue;
         double k = 0.0;
         for (int w = 0; w < wps; ++w)
-            for (int q = c; q < 32; q += 4) {
+            for (int q = kSingle ? 0 : c; q < 32; q += kSingle ? 1 : 4) {
                 Real &r = acc[(u * wps + w) * 32 + q];
                 k += (double)r;
                 r = 0;
@@ -365,7 +411,7 @@ __device__ void flush_acc(const TilePass &P, Real *acc, int wps, double *rho_g, 
 // reduced matrices of its parametrised groups (as i K) into
 // rho_g[slot][group][8].  The sums run in the state's precision over one
 // warp and at most 64 tiles, then in FP64.
-template <typename Real, int R>
+template <typename Real, int R, bool kSingle>
 __global__ void __launch_bounds__(256, R >= 4 ? 1 : 2)
 k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
            const typename CT<Real>::T *mats, int G, typename CT<Real>::T *psi,
@@ -423,7 +469,7 @@ k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
     for (int64_t tix = t0, i = 0; tix < t_end; ++tix, ++i) {
         const int buf = (int)(i & 1);
         if (cur.slot != mslot || since == kFlushTiles) {
-            if (mslot >= 0) flush_acc<Real>(P, acc, wps, rho_g, mslot, G);
+            if (mslot >= 0) flush_acc<Real, kSingle>(P, acc, wps, rho_g, mslot, G);
             since = 0;
         }
         if (cur.slot != mslot) {  // adjoint matrices of this slot's groups
@@ -444,6 +490,7 @@ k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
             const uint2 bb = tb[s * T + tid];
             uint32_t lq[R], sq[R];
             const uint32_t ops = read_stage_rec<R>(rec, s, lq, sq);
+            const uint32_t modes = kSingle ? rec[2 * s + 1].y : 0u;
             C a[NA], al[NA];
 #pragma unroll
             for (int r = 0; r < NA; ++r) {
@@ -453,16 +500,22 @@ k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
             }
             // the stage's sums: over lane quads in registers, then per lane
             // into the warp's accumulators
-            constexpr int NV = 4 * R <= 8 ? 8 : 16;
+            constexpr int NV = kSingle ? 4 : (4 * R <= 8 ? 8 : 16);
             Real kk[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) kk[v] = 0;
-            tile_ops_rev<C, Real, R, R - 1, NV>(ops, sm, a, al, kk);
+            tile_ops_rev<C, Real, R, R - 1, NV, kSingle>(ops, modes, sm, a, al, kk);
             warp_reduce_quad<Real, NV>(kk, lane);
+            if constexpr (kSingle) {  // lane: the sum of register bit lane & 3
+                const int m = lane & 3;
+                const uint32_t ob = m < R ? (ops >> (8 * m)) & 0xffu : 0u;
+                if (ob & 128u) accw[((int)(ob & 63u) - 1) * wps * 32] += kk[0];
+            } else {
 #pragma unroll
-            for (int m = 0; m < R; ++m) {
-                const uint32_t ob = (ops >> (8 * m)) & 0xffu;
-                if (ob & 128u) accw[((int)(ob & 63u) - 1) * wps * 32] += kk[m];
+                for (int m = 0; m < R; ++m) {
+                    const uint32_t ob = (ops >> (8 * m)) & 0xffu;
+                    if (ob & 128u) accw[((int)(ob & 63u) - 1) * wps * 32] += kk[m];
+                }
             }
             __syncthreads();
 #pragma unroll
@@ -485,7 +538,7 @@ k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
         cur = nxt;
         nxt = tile_next(P, nxt);
     }
-    flush_acc<Real>(P, acc, wps, rho_g, mslot, G);
+    flush_acc<Real, kSingle>(P, acc, wps, rho_g, mslot, G);
 }
 
 // Sum of v over the block (every thread gets it); red: one double per warp.
@@ -552,12 +605,17 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, T = blockDim.x, t = P.t;
     const uint32_t tbytes = (uint32_t)sizeof(C) << t;
-    HCoef<Real> *coef = reinterpret_cast<HCoef<Real> *>(smem + 2 * tbytes);
+    // psi tiles at [0, 2 tbytes), the lambda tile being added to at [2 tbytes, 3 tbytes)
+    HTerm *trm = reinterpret_cast<HTerm *>(smem + 3 * tbytes);
+    HCoef<Real> *coef = reinterpret_cast<HCoef<Real> *>(trm + P.n_terms);
     HGroup *grp = reinterpret_cast<HGroup *>(coef + P.n_classes);
     HClass *cls = reinterpret_cast<HClass *>(grp + P.n_groups);
     double *red = reinterpret_cast<double *>(cls + P.n_classes);
+    for (int i = tid; i < P.n_terms; i += T) trm[i] = P.terms[i];
     for (int i = tid; i < P.n_groups; i += T) grp[i] = P.groups[i];
     for (int i = tid; i < P.n_classes; i += T) cls[i] = P.classes[i];
+    __syncthreads();
+    const bool add = kLam && !P.first;
     uint32_t gk[R];
     const uint32_t g0 = bit_vectors<R>(P.gl, t, tid, gk);
     const uint32_t sh = (uint32_t)__cvta_generic_to_shared(smem);
@@ -591,7 +649,7 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
             const HClass cl = cls[c];
             Real re = 0, im = 0;
             for (int ti = cl.t_begin; ti < cl.t_end; ++ti) {
-                const HTerm tm = P.terms[ti];
+                const HTerm tm = trm[ti];
                 const Real v =
                     (__popc((cur.base ^ cl.xnl) & tm.z) & 1u) ? (Real)-tm.coeff : (Real)tm.coeff;
                 if (tm.phase == 0) re += v;
@@ -615,11 +673,21 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
         }
         cp_async_wait_all();
         __syncthreads();
-        if (tix + 1 < t_end) fetch(nxt, buf ^ 1);
-        const C *tile = reinterpret_cast<const C *>(smem + (uint32_t)buf * tbytes);
         C *L = lam + ((int64_t)cur.slot << n) + cur.base;
+        C *lt = reinterpret_cast<C *>(smem + 2 * tbytes);
+        if (add) {  // this tile's lambda so far, in flight during the sums
+            const uint32_t d = sh + 2 * tbytes;
+#pragma unroll
+            for (int k = 0; k < NA; ++k)
+                cp_async_amp(d + (uint32_t)(tid + k * T) * (uint32_t)sizeof(C), L + (g0 ^ xsel<R>(k, gk)));
+            cp_async_commit();
+        }
+        if (tix + 1 < t_end) fetch(nxt, buf ^ 1);
+        else cp_async_commit();  // keeps "all but the newest group" meaning the lambda tile
+        const C *tile = reinterpret_cast<const C *>(smem + (uint32_t)buf * tbytes);
         const C *Sg = psi + ((int64_t)cur.slot << n);
         Real part = 0;
+        bool lam_ready = false;
 #pragma unroll
         for (int k0 = 0; k0 < NA; k0 += KC) {
             Real lr[KC], li[KC];
@@ -656,6 +724,10 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
                     li[k] = fmaR(dr[k], p[k].y, fmaR(di[k], p[k].x, li[k]));
                 }
             }
+            if (add && !lam_ready) {
+                cp_async_wait_prior();  // own copies of the lambda tile have landed
+                lam_ready = true;
+            }
 #pragma unroll
             for (int k = 0; k < KC; ++k) {
                 const C pj = tile[tid + (k0 + k) * T];
@@ -665,8 +737,8 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
                     C out;
                     out.x = lr[k];
                     out.y = li[k];
-                    if (!P.first) {
-                        const C old = L[go];
+                    if (add) {  // each thread reads back only its own copies
+                        const C old = lt[tid + (k0 + k) * T];
                         out.x += old.x;
                         out.y += old.y;
                     }
@@ -888,7 +960,7 @@ cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, con
     const int threads = 1 << (P.t - P.R);
     HBM_DISPATCH_R(c128, P.R, {
         using C = typename CT<Real>::T;
-        auto k = k_tile_rev<Real, RR>;
+        auto k = P.all_single ? k_tile_rev<Real, RR, true> : k_tile_rev<Real, RR, false>;
         cudaError_t e = allow_smem(k, smem);
         if (e != cudaSuccess) return e;
         const int blocks = fill_blocks(k, threads, smem, max_blocks);
@@ -900,7 +972,8 @@ cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, con
 
 uint32_t tile_h_smem(int c128, const HPass &P) {
     const uint32_t csz = c128 ? 16u : 8u;
-    return 2u * (csz << P.t) + (uint32_t)P.n_classes * (csz + 8u + (uint32_t)sizeof(HClass)) +
+    return 3u * (csz << P.t) + (uint32_t)P.n_terms * (uint32_t)sizeof(HTerm) +
+           (uint32_t)P.n_classes * (csz + 8u + (uint32_t)sizeof(HClass)) +
            (uint32_t)P.n_groups * (uint32_t)sizeof(HGroup) + 32u * 8u + 16u;
 }
 

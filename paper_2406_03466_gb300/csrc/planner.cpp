@@ -420,12 +420,30 @@ std::string build_tile_passes(const HostProgram &P, int csz, std::vector<TilePas
                 if (u >= kPassOps) return "too many ops in a tile pass";
                 ts.op[op.a] = u;
                 tp.grp[u] = op.group;
-                if (P.groups[op.group].real) tp.real_mask |= 1ull << u;
-                if (P.groups[op.group].has_param) tp.param_mask |= 1ull << u;
+                const Group &gr = P.groups[op.group];
+                if (gr.real) tp.real_mask |= 1ull << u;
+                if (gr.has_param) {
+                    tp.param_mask |= 1ull << u;
+                    int n_par = 0, last_par = -1;
+                    for (int m = gr.m_begin; m < gr.m_end; ++m) {
+                        const Member &mb = P.members[m];
+                        if (mb.kind <= M_RZ && mb.param >= 0) {
+                            ++n_par;
+                            last_par = m;
+                        }
+                    }
+                    if (n_par == 1 && last_par == gr.m_end - 1) {
+                        const int k = P.members[last_par].kind;
+                        tp.fmode[u] = (int8_t)(k == M_RY ? 1 : (k == M_RX ? 2 : 3));
+                    }
+                }
                 ++u;
             }
         }
         tp.n_ops = u;
+        tp.all_single = 1;
+        for (int v = 0; v < u; ++v)
+            if (((tp.param_mask >> v) & 1ull) && tp.fmode[v] == 0) tp.all_single = 0;
         out->push_back(tp);
     }
     return "";

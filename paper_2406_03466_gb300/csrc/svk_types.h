@@ -98,7 +98,8 @@ struct TileStage {
 };
 
 struct TilePass {
-    int32_t t, R, n_stages, n_ops, n_tile_bits, pad;
+    int32_t t, R, n_stages, n_ops, n_tile_bits;
+    int32_t all_single;             // every parametrised op has fmode > 0
     uint64_t real_mask;             // bit u: op u has a real matrix
     uint64_t param_mask;            // bit u: op u's group has parameters
     uint32_t gl[kTileBitsMax];      // tile-local bit b -> global offset bit
@@ -107,6 +108,10 @@ struct TilePass {
     uint32_t nat[kTileBitsMax];     // tile-local bit b -> natural shared address
     int32_t grp[kPassOps];          // pass-local op u -> fused group
     TileStage st[kPassStages];
+    // The derivative of op u's group needs one sum of the reduced matrix
+    // when its only rotation is the group's last member: fmode 1 = RY (k3),
+    // 2 = RX (k2), 3 = RZ (k0 - k1); 0 = all four.
+    int8_t fmode[kPassOps];
 };
 
 // Pauli terms grouped by X-mask: <psi|P|psi> = Re(i^phase sum_j (-1)^{|j & z|}

@@ -39,9 +39,9 @@ class TileStage(ctypes.Structure):
 
 class TilePass(ctypes.Structure):
     _fields_ = [("t", I32), ("R", I32), ("n_stages", I32), ("n_ops", I32), ("n_tile_bits", I32),
-                ("pad", I32), ("real_mask", U64), ("param_mask", U64), ("gl", U32 * KT),
+                ("all_single", I32), ("real_mask", U64), ("param_mask", U64), ("gl", U32 * KT),
                 ("gpre", U32 * 30), ("ldperm", U32 * KT), ("nat", U32 * KT), ("grp", I32 * 48),
-                ("st", TileStage * 16)]
+                ("st", TileStage * 16), ("fmode", ctypes.c_int8 * 48)]
 
 
 def export(circ, t, R, fuse=True, dtype=0):
@@ -232,6 +232,11 @@ def run_rev(P, psi, lam, mats, rho, csz, n_blocks=2):
                         k[1] += np.sum(x1 * np.conj(y1)).imag
                         k[2] += np.sum(x0 * np.conj(y1) + x1 * np.conj(y0)).imag
                         k[3] += np.sum(x0 * np.conj(y1) - x1 * np.conj(y0)).real
+                    if P.all_single:
+                        # one sum per op, stored as the component its fmode needs
+                        md = P.fmode[u]
+                        assert md in (1, 2, 3)
+                        k = {1: [0, 0, 0, k[3]], 2: [0, 0, k[2], 0], 3: [k[0] - k[1], 0, 0, 0]}[md]
                     rho[slot][g] += np.array([[1j * k[0], 0.5 * (k[3] + 1j * k[2])],
                                               [0.5 * (-k[3] + 1j * k[2]), 1j * k[1]]])
                 Md = mats[slot][g].conj().T
@@ -459,3 +464,13 @@ def test_h_passes_match_dense(n, t, c, kind):
     lam, E = run_h(plan, psi, n)
     np.testing.assert_allclose(lam, H @ psi, atol=1e-12)
     assert abs(E - np.vdot(psi, H @ psi).real) < 1e-12
+
+
+def test_single_sum_mode_chosen_for_one_rotation_groups():
+    w = wl.mcvqe(8, 2, "nn+nnn", n_refs=2)  # one Ry per group
+    groups, members, passes = export(circuit_of(w), 8, 3)
+    assert all(P.all_single for P in passes)
+    assert all(P.fmode[u] == 1 for P in passes for u in range(P.n_ops) if P.param_mask >> u & 1)
+    w = wl.qcl(8, 2, 2)  # Rx Rz Rx groups
+    groups, members, passes = export(circuit_of(w), 8, 3)
+    assert not any(P.all_single for P in passes)
