@@ -59,6 +59,19 @@ def parse():
     return ap.parse_args()
 
 
+def job_throughput(t_dev, units_per_rank, dist, device):
+    """Whole-job rate of a replicas run: every rank did `units_per_rank` units
+    in its own t_dev seconds; the job took the slowest rank's time."""
+    import torch
+    world = 1
+    if dist:
+        t = torch.tensor([t_dev], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev = float(t.item())
+        world = dist.get_world_size()
+    return world * units_per_rank / t_dev, t_dev
+
+
 def rank_info():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -301,11 +314,7 @@ def run_device_memory(args, sv, dev, stream, dist, world, rank):
         dist.barrier()
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([t_dev], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev = float(t.item())
-    gps = world * args.steps / t_dev
+    gps, t_dev = job_throughput(t_dev, args.steps, dist, dev)
     d = 0 if w.inputs is None else 1
     info = sv.sv_plan_info(sv.Circuit(w.n_qubits, w.gates, w.n_params, d), "c64")
     hinfo = sv.sv_h_plan_info(sv.PauliSum(w.n_qubits, w.pauli_letters, w.pauli_coeffs), "c64")
@@ -416,11 +425,7 @@ def main():
         dist.barrier()
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([t_dev], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev = float(t.item())
-    grads_per_s = world * args.steps / t_dev
+    grads_per_s, t_dev = job_throughput(t_dev, args.steps, dist, dev)
 
     result = {"metric": METRIC, "value": grads_per_s, "unit": "gradients/s", "n_gpus": world,
               "steps": args.steps, "warmup": args.warmup,
