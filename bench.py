@@ -283,14 +283,25 @@ def cpu_baseline_device_memory(w, seconds):
             "kind": "oracle", "sample": how}
 
 
-def run_device_memory(args, sv, dev, stream, dist, world, rank):
-    """Adjoint gradient of a workload whose states live in device memory."""
-    import torch
+def device_workload(args):
+    """Config 4 (qcl20) or 5 (mcvqe28), or the same family at --qubits."""
     w = wl.config(3 if args.workload == "qcl20" else 4)
     if args.qubits:
         w = (wl.qcl(args.qubits, w.meta.get("layers", 10), w.n_instances) if args.workload == "qcl20"
              else wl.mcvqe(args.qubits, w.meta.get("layers", 8), w.meta.get("pairs", "nn+nnn"),
                            n_refs=w.n_instances))
+    return w
+
+
+def device_workload_name(w):
+    return (f"{w.name}: adjoint gradient, {w.n_instances} states of {w.n_qubits} qubits in "
+            f"device memory, {w.n_params} params")
+
+
+def run_device_memory(args, sv, dev, stream, dist, world, rank):
+    """Adjoint gradient of a workload whose states live in device memory."""
+    import torch
+    w = device_workload(args)
     prob = sv.Problem.from_spec(w, "c64", device=dev)
     theta = torch.as_tensor(w.theta, dtype=torch.float64, device=dev)
     out = sv._outputs(prob, dev, None, None, None)
@@ -322,9 +333,8 @@ def run_device_memory(args, sv, dev, stream, dist, world, rank):
               "steps": args.steps, "warmup": args.warmup,
               "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
               "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-              "config": {"workload": f"{w.name}: adjoint gradient, {w.n_instances} states of "
-                                     f"{w.n_qubits} qubits in device memory, {w.n_params} "
-                                     f"params, {info['n_passes']} tile passes per sweep",
+              "config": {"workload": device_workload_name(w), "tile_passes": info["n_passes"],
+                         "h_passes": hinfo["n_passes"],
                          "l2": "states larger than L2; 256 MiB flush before each step",
                          "parallelism": f"replicas x{world}"},
               # per adjoint: group matrices, |ref>, forward and reverse passes, the
@@ -367,13 +377,18 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        cb = cpu_baseline(args.cpu_seconds)
+        if args.workload == "mcvqe8":
+            cb, workload = cpu_baseline(args.cpu_seconds), WORKLOAD
+        else:
+            w = device_workload(args)
+            cb = cpu_baseline_device_memory(w, min(args.cpu_seconds, 10.0))
+            workload = device_workload_name(w)
         v = cb["value"]
         line = {"metric": METRIC, "value": v, "unit": "gradients/s", "impl": "reference",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-                "config": {"workload": WORKLOAD}, "cpu_baseline": cb,
+                "config": {"workload": workload}, "cpu_baseline": cb,
                 "e2e": {"value": v, "unit": "gradients/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
