@@ -193,20 +193,20 @@ def measured_hbm_gbs():
         return 6800.0, "fallback 6.8 TB/s"
 
 
-def forward_passes_roofline(sv, w, dev, flush, stream, reps=5):
+def forward_passes_roofline(sv, w, dev, flush, stream, reps=5, opts=None):
     """Times the forward simulation of workload `w` (all instances, states in
     device memory) and reports it against the HBM roofline: each tile pass
     reads and writes every state once, the |ref> initialisation writes them."""
     import torch
     d = 0 if w.inputs is None else 1
     circ = sv.Circuit(w.n_qubits, w.gates, w.n_params, d)
-    info = sv.sv_plan_info(circ, "c64")
+    info = sv.sv_plan_info(circ, "c64", opts)
     n, I = w.n_qubits, w.n_instances
     st = sv.sv_alloc(n, I, "c64", device=dev)
     theta = torch.as_tensor(w.theta, dtype=torch.float64, device=dev).reshape(1, -1)
     xin = None if w.inputs is None else torch.as_tensor(w.inputs, device=dev)
     slots = sv.make_slots([(0, 0, -1, i if d else -1, int(w.refs[i]), 0.0) for i in range(I)])
-    fn = lambda: sv.sv_apply_circuit_batch(st, [circ], slots, theta, xin)  # noqa: E731
+    fn = lambda: sv.sv_apply_circuit_batch(st, [circ], slots, theta, xin, opts)  # noqa: E731
     fn()
     t = timed_loop(fn, reps, flush, stream) / reps
     nbytes = (2 * info["n_passes"] + 1) * I * (8 << n)
@@ -306,6 +306,11 @@ def run_device_memory(args, sv, dev, stream, dist, world, rank):
     theta = torch.as_tensor(w.theta, dtype=torch.float64, device=dev)
     out = sv._outputs(prob, dev, None, None, None)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    # tile shape (tile bits, register bits) picked by timing
+    sv.sv_autotune(prob, theta, 2)
+    R, tpb, _ = sv.sv_tuned_shape(prob, 2)
+    tile_bits = R + tpb.bit_length() - 1
+    opts = sv.plan_opts(reg_bits=R, tile_bits=tile_bits)
 
     def step():
         sv.sv_grad_adjoint(prob, theta, None, *out)
@@ -327,13 +332,14 @@ def run_device_memory(args, sv, dev, stream, dist, world, rank):
     clk = clocks.stop()
     gps, t_dev = job_throughput(t_dev, args.steps, dist, dev)
     d = 0 if w.inputs is None else 1
-    info = sv.sv_plan_info(sv.Circuit(w.n_qubits, w.gates, w.n_params, d), "c64")
+    info = sv.sv_plan_info(sv.Circuit(w.n_qubits, w.gates, w.n_params, d), "c64", opts)
     hinfo = sv.sv_h_plan_info(sv.PauliSum(w.n_qubits, w.pauli_letters, w.pauli_coeffs), "c64")
     result = {"metric": METRIC, "value": gps, "unit": "gradients/s", "n_gpus": world,
               "steps": args.steps, "warmup": args.warmup,
               "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
               "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
               "config": {"workload": device_workload_name(w), "tile_passes": info["n_passes"],
+                         "tuned_tile": {"tile_bits": tile_bits, "reg_bits": R},
                          "h_passes": hinfo["n_passes"],
                          "l2": "states larger than L2; 256 MiB flush before each step",
                          "parallelism": f"replicas x{world}"},
@@ -345,7 +351,8 @@ def run_device_memory(args, sv, dev, stream, dist, world, rank):
         result["roofline"] = adjoint_phases(sv, w, prob, theta, out, info, flush, stream,
                                             reps=2 if w.n_qubits > 24 else 5)
         result["roofline_forward"] = forward_passes_roofline(sv, w, dev, flush, stream,
-                                                             reps=3 if w.n_qubits > 24 else 5)
+                                                             reps=3 if w.n_qubits > 24 else 5,
+                                                             opts=opts)
         th_host = torch.as_tensor(w.theta, dtype=torch.float64).pin_memory()
         g_host = torch.empty(w.n_params, dtype=torch.float64).pin_memory()
         th_dev = torch.empty_like(theta)

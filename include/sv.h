@@ -294,11 +294,17 @@ sv_status sv_last_phase_ms(float *forward_ms, float *h_ms, float *reverse_ms);
  * the batched parameter-shift energy kernel (kinds bit 1) and of the adjoint
  * kernel (kinds bit 2) on this problem and remembers the fastest per problem
  * structure; later calls whose opts leave reg_bits and threads_per_block at
- * zero use it.  Host-synchronous: launches and times kernels on `stream`,
- * so do not call it during stream capture.  theta: device [P]. */
+ * zero use it.  For states in device memory (tile passes) it times tile
+ * shapes instead — 2^t-amplitude tiles with R register bits, t in 9..12 —
+ * for the instance energies (bit 1) and the adjoint gradient (bit 2), and
+ * later calls whose opts leave tile_bits and reg_bits at zero use them.
+ * Host-synchronous: launches and times kernels on `stream`, so do not call
+ * it during stream capture.  theta: device [P]. */
 sv_status sv_autotune(const sv_problem *problem, const double *theta, int32_t kinds,
                       sv_stream_t stream);
-/* The remembered shape for kind 1 (parameter-shift energies) or 2 (adjoint). */
+/* The remembered shape for kind 1 (parameter-shift energies; instance
+ * energies for tile passes) or 2 (adjoint).  For tile passes
+ * threads_per_block is 2^(tile_bits - reg_bits). */
 sv_status sv_tuned_shape(const sv_problem *problem, int32_t kind, int32_t *reg_bits,
                          int32_t *threads_per_block, float *microseconds);
 

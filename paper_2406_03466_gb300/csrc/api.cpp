@@ -558,7 +558,20 @@ struct TileCfg {
     int t, R;
 };
 
-sv_status tile_cfg(int n, sv_dtype dt, const sv_plan_opts *o, TileCfg *cfg) {
+// Tuning keys of the tile tier (by instance count), beside the on-chip kinds.
+constexpr int kTileEnergyKey = 10 + ONCHIP_ENERGY, kTileAdjointKey = 10 + ONCHIP_ADJOINT;
+
+// tn: a tuned tile shape (R = register bits, tpb = 2^(t - R) threads), used
+// when opts leave tile_bits and reg_bits at zero.
+sv_status tile_cfg(int n, sv_dtype dt, const sv_plan_opts *o, TileCfg *cfg,
+                   const Tuned *tn = nullptr) {
+    if (tn && tn->R > 0 && (!o || (o->tile_bits <= 0 && o->reg_bits <= 0))) {
+        sv_plan_opts t{};
+        if (o) t = *o;
+        t.reg_bits = tn->R;
+        t.tile_bits = tn->R + __builtin_ctz((unsigned)tn->tpb);
+        return tile_cfg(n, dt, &t, cfg, nullptr);
+    }
     const int c = dt == SV_C128 ? 3 : 4, rmax = dt == SV_C128 ? 3 : 4;
     // Default: 2^11 (complex64) / 2^10 (complex128) amplitudes per tile with
     // 4 / 2 register bits: 128 / 256 threads per block.
@@ -623,7 +636,7 @@ sv_status tiles_energies(DeviceCtx *ctx, const sv_problem *p, const double *thet
     const sv_dtype dt = p->dtype;
     const int c128 = dt == SV_C128, n = p->circuit->n_qubits, I = p->n_instances;
     TileCfg cfg{};
-    sv_status s = tile_cfg(n, dt, p->opts, &cfg);
+    sv_status s = tile_cfg(n, dt, p->opts, &cfg, find_tuned(ctx, p, kTileEnergyKey, p->n_instances));
     if (s != SV_OK) return s;
     PlanEntry *pe = nullptr;
     s = get_plan(ctx, *p->circuit, cfg.R, use_fusion(p->opts), dt, &pe, cfg.t);
@@ -674,7 +687,7 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
     const int c128 = dt == SV_C128, n = p->circuit->n_qubits, I = p->n_instances;
     const int P = p->circuit->n_params, Pp = P > 0 ? P : 1;
     TileCfg cfg{};
-    sv_status s = tile_cfg(n, dt, p->opts, &cfg);
+    sv_status s = tile_cfg(n, dt, p->opts, &cfg, find_tuned(ctx, p, kTileAdjointKey, I));
     if (s != SV_OK) return s;
     PlanEntry *pe = nullptr;
     s = get_plan(ctx, *p->circuit, cfg.R, use_fusion(p->opts), dt, &pe, cfg.t);
@@ -1284,6 +1297,71 @@ sv_status sv_grad_param_shift_plain(const sv_problem *p, const double *theta, do
     return SV_OK;
 }
 
+// Tile shapes (tile bits t, register bits R) for the energies of the
+// instances (kinds bit 1) and the adjoint gradient (bit 2) of a problem whose
+// states live in device memory: each candidate runs once to plan and warm,
+// then the faster of two CUDA-event-timed calls counts.
+sv_status tune_tiles(const sv_problem *p, const double *theta, int32_t kinds, cudaStream_t st) {
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    if (p->opts && (p->opts->tile_bits > 0 || p->opts->reg_bits > 0)) return SV_OK;  // fixed by the caller
+    const int n = p->circuit->n_qubits, I = p->n_instances, Pp = p->circuit->n_params > 0 ? p->circuit->n_params : 1;
+    const bool c128 = p->dtype == SV_C128;
+    const int cand_c64[][2] = {{11, 4}, {11, 3}, {12, 4}, {10, 3}, {10, 4}};
+    const int cand_c128[][2] = {{10, 2}, {10, 3}, {11, 3}, {9, 2}};
+    void *out = nullptr;
+    const size_t need = sizeof(double) * (2 * (size_t)I + Pp + 2);
+    if (cudaMalloc(&out, need) != cudaSuccess) return fail(SV_ERR_OOM, "tuning outputs");
+    double *E = (double *)out, *L = E + I, *G = L + 1;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    sv_status result = SV_OK;
+    for (int key : {kTileEnergyKey, kTileAdjointKey}) {
+        if (!(kinds & (key == kTileEnergyKey ? 1 : 2))) continue;
+        Tuned best;
+        best.us = 1e30f;
+        const int nc = c128 ? 4 : 5;
+        for (int ci = 0; ci < nc; ++ci) {
+            const int t = c128 ? cand_c128[ci][0] : cand_c64[ci][0];
+            const int R = c128 ? cand_c128[ci][1] : cand_c64[ci][1];
+            if (t > n || t - R < 5) continue;
+            sv_plan_opts o{};
+            if (p->opts) o = *p->opts;
+            o.tile_bits = t;
+            o.reg_bits = R;
+            sv_problem q = *p;
+            q.opts = &o;
+            auto run = [&]() {
+                return key == kTileEnergyKey ? sv_energies(&q, theta, E, L, st)
+                                             : sv_grad_adjoint(&q, theta, nullptr, E, L, G, 0, st);
+            };
+            if (run() != SV_OK) continue;  // unsupported shape for this problem
+            float tbest = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaEventRecord(e0, st);
+                if (run() != SV_OK) break;
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < tbest) tbest = ms;
+            }
+            if (tbest * 1e3f < best.us) {
+                best.us = tbest * 1e3f;
+                best.R = R;
+                best.tpb = 1 << (t - R);
+            }
+        }
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (best.R > 0) ctx->tuned[tune_key(p, key, I)] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    return result;
+}
+
 sv_status sv_autotune(const sv_problem *p, const double *theta, int32_t kinds,
                       sv_stream_t stream) {
     sv_status s = check_problem(p, true);
@@ -1291,7 +1369,7 @@ sv_status sv_autotune(const sv_problem *p, const double *theta, int32_t kinds,
     if (p->circuit->n_params > 0 && !theta) return fail(SV_ERR_ARG, "theta is NULL");
     if (kinds & ~3) return fail(SV_ERR_ARG, "kinds must be a combination of 1 and 2");
     const int P = p->circuit->n_params, I = p->n_instances, n = p->circuit->n_qubits;
-    if (wants_tiles(n, p->dtype, p->opts)) return SV_OK;  // tile passes have fixed shapes
+    if (wants_tiles(n, p->dtype, p->opts)) return tune_tiles(p, theta, kinds, (cudaStream_t)stream);
     int B = 0;
     s = ps_batch_size(p, &B);
     if (s != SV_OK) return s;
@@ -1459,8 +1537,12 @@ sv_status sv_tuned_shape(const sv_problem *p, int32_t kind, int32_t *reg_bits,
     if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
     std::lock_guard<std::mutex> lk(ctx->mu);
     const int B = (2 * p->circuit->n_params + 1) * p->n_instances;
-    const Tuned *t = kind == 1 ? find_tuned(ctx, p, ONCHIP_ENERGY, B)
-                               : find_tuned(ctx, p, ONCHIP_ADJOINT, p->n_instances);
+    const Tuned *t = nullptr;
+    if (wants_tiles(p->circuit->n_qubits, p->dtype, p->opts))
+        t = find_tuned(ctx, p, kind == 1 ? kTileEnergyKey : kTileAdjointKey, p->n_instances);
+    else
+        t = kind == 1 ? find_tuned(ctx, p, ONCHIP_ENERGY, B)
+                      : find_tuned(ctx, p, ONCHIP_ADJOINT, p->n_instances);
     if (!t) return fail(SV_ERR_ARG, "no tuned shape for this problem");
     if (reg_bits) *reg_bits = t->R;
     if (threads_per_block) *threads_per_block = t->tpb;

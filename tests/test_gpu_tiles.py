@@ -127,3 +127,22 @@ def test_mcvqe_16_qubits_adjoint_vs_param_shift(sv):
     ks = [0, 9, 31]
     _, _, gs = oracle.grad_param_shift(w, params=ks)
     close(ga.cpu().numpy()[ks], gs, 1e-4)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_autotuned_tile_shape(sv, dtype):
+    """sv_autotune picks a tile shape for device-memory states; later calls
+    use it and still match the oracle."""
+    w = wl.mcvqe(14, 2, "nn+nnn", n_refs=2)
+    prob = sv.Problem.from_spec(w, dtype)
+    sv.sv_autotune(prob, theta_of(w), 3)
+    for kind in (1, 2):
+        R, tpb, us = sv.sv_tuned_shape(prob, kind)
+        t = R + tpb.bit_length() - 1
+        assert tpb == 1 << (t - R) and t - R >= 5 and 9 <= t <= 12 and us > 0
+    L, E, g = oracle.grad_param_shift(w)
+    l_, e_, g_ = sv.sv_grad_adjoint(prob, theta_of(w))
+    close(e_.cpu().numpy(), E, TOL[dtype]["E"])
+    close(g_.cpu().numpy(), g, TOL[dtype]["G"])
+    l_, e_ = sv.sv_energies(prob, theta_of(w))
+    close(e_.cpu().numpy(), E, TOL[dtype]["E"])
