@@ -173,24 +173,31 @@ __device__ __forceinline__ void load_mat(const double2 *sm, int u, double2 &m0, 
 }
 
 // The group ops of one stage (op bytes `ops`), register bits I..R-1 in order.
-template <typename C, int R, int I>
+// kReal: every op of the pass has a real matrix (no complex path compiled).
+template <typename C, int R, int I, bool kReal>
 __device__ __forceinline__ void tile_ops_fwd(uint32_t ops, const C *sm, C (&a)[1 << R]) {
     if constexpr (I < R) {
         const uint32_t ob = (ops >> (8 * I)) & 0xffu;
         if (ob) {
             C m0, m1, m2, m3;
             load_mat(sm, (int)(ob & 63u) - 1, m0, m1, m2, m3);
-            if (ob & 64u)
+            if (kReal || (ob & 64u))
                 u1r_bit<C, decltype(m0.x), R, I>(a, m0.x, m1.x, m2.x, m3.x);
             else
                 u1_bit<C, R, I>(a, m0, m1, m2, m3);
         }
-        tile_ops_fwd<C, R, I + 1>(ops, sm, a);
+        tile_ops_fwd<C, R, I + 1, kReal>(ops, sm, a);
     }
 }
 
+// Every op of pass P has a real matrix.
+__host__ __device__ inline bool pass_all_real(const TilePass &P) {
+    const uint64_t all = P.n_ops >= 64 ? ~0ull : ((1ull << P.n_ops) - 1ull);
+    return (P.real_mask & all) == all;
+}
+
 // One forward pass over every tile of every slot.  mats: [slots][G][4].
-template <typename Real, int R>
+template <typename Real, int R, bool kReal>
 __global__ void __launch_bounds__(256, R >= 4 ? 2 : 3)
 k_tile_fwd(const __grid_constant__ TilePass P, int n, int n_slots,
            const typename CT<Real>::T *mats, int G, typename CT<Real>::T *states) {
@@ -252,7 +259,7 @@ k_tile_fwd(const __grid_constant__ TilePass P, int n, int n_slots,
             C a[NA];
 #pragma unroll
             for (int r = 0; r < NA; ++r) a[r] = *reinterpret_cast<const C *>(tile + (bb.x ^ xsel<R>(r, lq)));
-            tile_ops_fwd<C, R, 0>(ops, sm, a);
+            tile_ops_fwd<C, R, 0, kReal>(ops, sm, a);
             __syncthreads();
 #pragma unroll
             for (int r = 0; r < NA; ++r) *reinterpret_cast<C *>(tile + (bb.y ^ xsel<R>(r, sq))) = a[r];
@@ -343,7 +350,7 @@ __device__ __forceinline__ Real single_sum(const C (&a)[1 << R], const C (&l)[1 
 // sums (at the point after the group) into k — k0..k3 at k[4 I ..], or with
 // kSingle the one sum of its fmode at k[I] — then the inverse group (sm
 // holds the adjoint matrices) on psi and lambda.
-template <typename C, typename Real, int R, int I, int NV, bool kSingle>
+template <typename C, typename Real, int R, int I, int NV, bool kSingle, bool kReal>
 __device__ __forceinline__ void tile_ops_rev(uint32_t ops, uint32_t modes, const C *sm,
                                              C (&a)[1 << R], C (&al)[1 << R], Real (&k)[NV]) {
     if constexpr (I >= 0) {
@@ -357,7 +364,7 @@ __device__ __forceinline__ void tile_ops_rev(uint32_t ops, uint32_t modes, const
             }
             C m0, m1, m2, m3;
             load_mat(sm, (int)(ob & 63u) - 1, m0, m1, m2, m3);
-            if (ob & 64u) {
+            if (kReal || (ob & 64u)) {
                 u1r_bit<C, Real, R, I>(a, m0.x, m1.x, m2.x, m3.x);
                 u1r_bit<C, Real, R, I>(al, m0.x, m1.x, m2.x, m3.x);
             } else {
@@ -365,7 +372,7 @@ __device__ __forceinline__ void tile_ops_rev(uint32_t ops, uint32_t modes, const
                 u1_bit<C, R, I>(al, m0, m1, m2, m3);
             }
         }
-        tile_ops_rev<C, Real, R, I - 1, NV, kSingle>(ops, modes, sm, a, al, k);
+        tile_ops_rev<C, Real, R, I - 1, NV, kSingle, kReal>(ops, modes, sm, a, al, k);
     }
 }
 
@@ -411,7 +418,7 @@ __device__ void flush_acc(const TilePass &P, Real *acc, int wps, double *rho_g, 
 // reduced matrices of its parametrised groups (as i K) into
 // rho_g[slot][group][8].  The sums run in the state's precision over one
 // warp and at most 64 tiles, then in FP64.
-template <typename Real, int R, bool kSingle>
+template <typename Real, int R, bool kSingle, bool kReal>
 __global__ void __launch_bounds__(256, R >= 4 ? 1 : 2)
 k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
            const typename CT<Real>::T *mats, int G, typename CT<Real>::T *psi,
@@ -504,7 +511,7 @@ k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
             Real kk[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) kk[v] = 0;
-            tile_ops_rev<C, Real, R, R - 1, NV, kSingle>(ops, modes, sm, a, al, kk);
+            tile_ops_rev<C, Real, R, R - 1, NV, kSingle, kReal>(ops, modes, sm, a, al, kk);
             warp_reduce_quad<Real, NV>(kk, lane);
             if constexpr (kSingle) {  // lane: the sum of register bit lane & 3
                 const int m = lane & 3;
@@ -944,7 +951,7 @@ cudaError_t launch_tile_fwd(int c128, const TilePass &P, int n, int n_slots, con
     const int threads = 1 << (P.t - P.R);
     HBM_DISPATCH_R(c128, P.R, {
         using C = typename CT<Real>::T;
-        auto k = k_tile_fwd<Real, RR>;
+        auto k = pass_all_real(P) ? k_tile_fwd<Real, RR, true> : k_tile_fwd<Real, RR, false>;
         cudaError_t e = allow_smem(k, smem);
         if (e != cudaSuccess) return e;
         const int blocks = fill_blocks(k, threads, smem, max_blocks);
@@ -960,7 +967,10 @@ cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, con
     const int threads = 1 << (P.t - P.R);
     HBM_DISPATCH_R(c128, P.R, {
         using C = typename CT<Real>::T;
-        auto k = P.all_single ? k_tile_rev<Real, RR, true> : k_tile_rev<Real, RR, false>;
+        auto k = P.all_single ? (pass_all_real(P) ? k_tile_rev<Real, RR, true, true>
+                                                  : k_tile_rev<Real, RR, true, false>)
+                              : (pass_all_real(P) ? k_tile_rev<Real, RR, false, true>
+                                                  : k_tile_rev<Real, RR, false, false>);
         cudaError_t e = allow_smem(k, smem);
         if (e != cudaSuccess) return e;
         const int blocks = fill_blocks(k, threads, smem, max_blocks);
