@@ -46,10 +46,13 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=None)
-    ap.add_argument("--workload", default="mcvqe8", choices=["mcvqe8", "qcl20", "mcvqe28"],
+    ap.add_argument("--workload", default="mcvqe8",
+                    choices=["mcvqe8", "qcl20", "mcvqe28", "qcl-uneven"],
                     help="mcvqe8 (default): batched parameter-shift gradient of the 8-qubit "
                          "MC-VQE; qcl20 / mcvqe28: adjoint gradient of the 20-qubit circuit "
-                         "learning / 28-qubit MC-VQE workload (states in device memory)")
+                         "learning / 28-qubit MC-VQE workload (states in device memory); "
+                         "qcl-uneven: adjoint gradients of 8 circuit-learning circuits of "
+                         "20-24 qubits and depth 4-12 in one graph launch")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true", help="skip adjoint/plain/c128 side runs")
@@ -373,19 +376,135 @@ def run_device_memory(args, sv, dev, stream, dist, world, rank):
         dist.destroy_process_group()
 
 
+def uneven_workload_name(ws):
+    return (f"qcl-uneven: adjoint gradients of {len(ws)} circuit-learning circuits (n, layers) = "
+            + ", ".join(f"({w.n_qubits},{w.meta['layers']})" for w in ws)
+            + f", {ws[0].n_instances} inputs each, one CUDA graph launch")
+
+
+def uneven_cost_model(w):
+    return (1 << w.n_qubits) * (len(w.gates) + 3 * w.n_terms)
+
+
+def cpu_baseline_uneven(ws, seconds):
+    """The oracle on whole circuits of the batch's smallest circuit for about
+    `seconds`, scaled by 2^n x (gates + 3 terms) to every circuit of the
+    batch and to one parameter-shift gradient per circuit (extrapolated)."""
+    import oracle
+    threads = oracle.max_threads()
+    ws0 = min(ws, key=uneven_cost_model)
+    t0 = time.perf_counter()
+    n_done = 0
+    while True:
+        k = max(1, threads)
+        oracle.energies(ws0, None, np.arange(k) % ws0.n_instances)
+        n_done += k
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    per = dt / n_done / uneven_cost_model(ws0)
+    total = sum(w.n_slots_param_shift * uneven_cost_model(w) * per for w in ws)
+    return {"value": len(ws) / total, "unit": "gradients/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n_done} full circuits of {ws0.name} in {dt:.1f} s; scaled by 2^n x "
+                      f"(gates + 3 terms) to the {len(ws)} circuits' parameter-shift gradients "
+                      "(extrapolated)"}
+
+
+def run_uneven(args, sv, dev, stream, dist, world, rank):
+    """Adjoint gradients of the uneven circuit-learning batch in one graph launch."""
+    import torch
+    ws = wl.qcl_uneven()
+    probs = [sv.Problem.from_spec(w, "c64", device=dev) for w in ws]
+    thetas = [torch.as_tensor(w.theta, dtype=torch.float64, device=dev) for w in ws]
+    outs = sv.sv_grad_adjoint_multi(probs, thetas)  # plans, runs, captures
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        sv.sv_grad_adjoint_multi(probs, thetas, outputs=outs)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    t_dev = timed_loop(step, args.steps, flush, stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    gps, t_dev = job_throughput(t_dev, args.steps * len(ws), dist, dev)
+    # algorithmic HBM bytes of one step: |ref> writes, forward passes (read +
+    # write), lambda = H psi passes, reverse passes (psi and lambda, read + write)
+    nbytes, launches, max_pass = 0, 0, 0
+    for w in ws:
+        circ = sv.Circuit(w.n_qubits, w.gates, w.n_params, 1)
+        npass = sv.sv_plan_info(circ, "c64")["n_passes"]
+        nh = sv.sv_h_plan_info(sv.PauliSum(w.n_qubits, w.pauli_letters, w.pauli_coeffs))["n_passes"]
+        state = w.n_instances * (8 << w.n_qubits)
+        nbytes += state * (1 + 2 * npass + 2 + 3 * (nh - 1) + 4 * npass)
+        launches += 4 + nh
+        max_pass = max(max_pass, npass)
+    launches += 2 * max_pass
+    peak, src = measured_hbm_gbs()
+    achieved = nbytes * args.steps / t_dev / 1e9 / world
+    result = {"metric": METRIC, "value": gps, "unit": "gradients/s", "n_gpus": world,
+              "steps": args.steps, "warmup": args.warmup,
+              "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+              "config": {"workload": uneven_workload_name(ws),
+                         "l2": "states larger than L2; 256 MiB flush before each step",
+                         "parallelism": f"replicas x{world}"},
+              "gpu_launches": args.steps * launches,
+              "clocks": clk, "wall_s_timed_region": t_wall,
+              "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                           "frac": achieved / peak, "traffic": None,
+                           "kernel": "whole step: k_tile_fwd_multi + k_tile_h + k_tile_rev_multi "
+                                     "(pass-major launches of all circuits, one graph)",
+                           "bytes_per_step": nbytes, "peak_source": src}}
+    if rank == 0:
+        th_host = [torch.as_tensor(w.theta, dtype=torch.float64).pin_memory() for w in ws]
+        g_host = [torch.empty(w.n_params, dtype=torch.float64).pin_memory() for w in ws]
+        t0 = time.perf_counter()
+        reps = max(1, args.steps // 2)
+        for _ in range(reps):
+            for th_d, th_h in zip(thetas, th_host):
+                th_d.copy_(th_h, non_blocking=True)
+            step()
+            for o, gh, w in zip(outs, g_host, ws):
+                gh.copy_(o[2][: w.n_params], non_blocking=True)
+            stream.synchronize()
+        result["e2e"] = {"value": reps * len(ws) / (time.perf_counter() - t0), "unit": "gradients/s",
+                         "h2d_bytes_per_step": sum(8 * w.n_params for w in ws),
+                         "d2h_bytes_per_step": sum(8 * w.n_params for w in ws)}
+        result["cpu_baseline"] = cpu_baseline_uneven(ws, min(args.cpu_seconds, 10.0))
+        print(json.dumps(result))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     rank, world, local = rank_info()
     if args.steps is None:
-        args.steps = {"mcvqe8": 4000, "qcl20": 20, "mcvqe28": 2}[args.workload]
+        args.steps = {"mcvqe8": 4000, "qcl20": 20, "mcvqe28": 2, "qcl-uneven": 5}[args.workload]
     if args.warmup is None:
-        args.warmup = {"mcvqe8": 50, "qcl20": 3, "mcvqe28": 1}[args.workload]
+        args.warmup = {"mcvqe8": 50, "qcl20": 3, "mcvqe28": 1, "qcl-uneven": 3}[args.workload]
 
     if args.impl == "reference":
         if rank != 0:
             return
         if args.workload == "mcvqe8":
             cb, workload = cpu_baseline(args.cpu_seconds), WORKLOAD
+        elif args.workload == "qcl-uneven":
+            ws = wl.qcl_uneven()
+            cb = cpu_baseline_uneven(ws, min(args.cpu_seconds, 10.0))
+            workload = uneven_workload_name(ws)
         else:
             w = device_workload(args)
             cb = cpu_baseline_device_memory(w, min(args.cpu_seconds, 10.0))
@@ -413,6 +532,8 @@ def main():
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
+    if args.workload == "qcl-uneven":
+        return run_uneven(args, sv, dev, stream, dist, world, rank)
     if args.workload != "mcvqe8":
         return run_device_memory(args, sv, dev, stream, dist, world, rank)
 

@@ -262,6 +262,25 @@ sv_status sv_grad_param_shift_noalloc(const sv_problem *problem, const double *t
                                       double *energy_out, double *loss_out, double *grad_out,
                                       sv_stream_t stream);
 
+/* Adjoint gradients of several problems at once: circuits of different qubit
+ * counts and depths whose states take the tile path (14..30 qubits; all
+ * problems share the dtype and the tile shape), each with its own
+ * observable, instances, theta and outputs.  The forward and reverse sweeps
+ * run pass-major — one launch per pass index covers that pass of every
+ * problem that has it — and the whole sequence (group matrices, |ref>,
+ * forward passes, lambda = H psi, reverse passes, gradients) is captured
+ * into one CUDA graph per configuration (the problems' structures and every
+ * pointer), replayed by a single graph launch on `stream`.  The first call
+ * for a configuration plans, allocates, runs eagerly and captures
+ * (host-synchronous); later calls only launch the graph.  No checkpoints.
+ * theta[j]: device [P_j]; energy_out[j]: device [I_j] or NULL; loss_out[j]:
+ * device [1] or NULL; grad_out[j]: device [P_j].  Arrays of n_problems host
+ * pointers.  SV_ERR_OOM when the states of all problems do not fit. */
+sv_status sv_grad_adjoint_multi(const sv_problem *problems, int32_t n_problems,
+                                const double *const *theta, double *const *energy_out,
+                                double *const *loss_out, double *const *grad_out,
+                                sv_stream_t stream);
+
 /* How a circuit will run for a state precision and options: on_chip = 1 when
  * the whole state stays in one block's shared memory, else the number of tile
  * passes over device memory and their tile size (2^tile_bits amplitudes);

@@ -81,6 +81,7 @@ EXPORTED = ("sv_alloc", "sv_free", "sv_state_info", "sv_apply_circuit_batch",
             "sv_expect_pauli_sum", "sv_energies", "sv_param_shift_energies", "sv_grad_param_shift", "sv_grad_adjoint",
             "sv_grad_param_shift_plain", "sv_grad_param_shift_noalloc", "sv_autotune",
             "sv_tuned_shape", "sv_plan_info", "sv_h_plan_info", "sv_phase_timing",
+            "sv_grad_adjoint_multi",
             "sv_last_phase_ms", "sv_status_string",
             "sv_last_error",
             "sv_sync_status", "sv_shutdown", "sv_version")
@@ -102,6 +103,7 @@ def _load():
     lib.sv_param_shift_energies.argtypes = [P(sv_problem), V, V, V]
     lib.sv_grad_param_shift.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_grad_adjoint.argtypes = [P(sv_problem), V, V, V, V, V, I32, V]
+    lib.sv_grad_adjoint_multi.argtypes = [P(sv_problem), I32, P(V), P(V), P(V), P(V), V]
     lib.sv_grad_param_shift_plain.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_grad_param_shift_noalloc.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_autotune.argtypes = [P(sv_problem), V, I32, V]
@@ -361,6 +363,23 @@ def sv_grad_adjoint(problem: Problem, theta, weights=None, energy_out=None, loss
                                 _ptr(e), _ptr(l), _ptr(g), int(checkpoint_every),
                                 _stream(stream)), "sv_grad_adjoint")
     return l, e, g
+
+
+def sv_grad_adjoint_multi(problems, thetas, outputs=None, stream=None):
+    """Adjoint gradients of several tile-path problems of different qubit counts
+    and depths at once (replayed as one CUDA graph after the first call).
+    Returns [(loss[1], energies[I], grad[P])] per problem; ``outputs`` (the
+    same list, preallocated) keeps the graph's output pointers fixed."""
+    n = len(problems)
+    if outputs is None:
+        outputs = [(l, e, g) for e, l, g in
+                   (_outputs(p, th.device, None, None, None) for p, th in zip(problems, thetas))]
+    arr = (sv_problem * n)(*[p.struct for p in problems])
+    ptrs = lambda xs: (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])  # noqa: E731
+    _check(_lib.sv_grad_adjoint_multi(arr, n, ptrs(thetas), ptrs([o[1] for o in outputs]),
+                                      ptrs([o[0] for o in outputs]), ptrs([o[2] for o in outputs]),
+                                      _stream(stream)), "sv_grad_adjoint_multi")
+    return outputs
 
 
 def sv_grad_param_shift_plain(problem: Problem, theta, energy_out=None, loss_out=None,

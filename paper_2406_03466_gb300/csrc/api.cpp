@@ -113,6 +113,18 @@ struct DeviceCtx {
     bool timing = false;
     std::vector<cudaEvent_t> phase_ev;
     int phase_used = 0;
+    // Uneven batches: one instantiated graph per configuration, and the
+    // stream the captures run on.
+    std::unordered_map<uint64_t, std::unique_ptr<struct MultiGraph>> graphs;
+    cudaStream_t capture_stream = nullptr;
+};
+
+struct MultiGraph {
+    cudaGraphExec_t exec = nullptr;
+    DeviceBuf buf;  // descriptors, item tables and every problem's states and sums
+    ~MultiGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
 };
 
 // Records phase event `i` of the current timed call (creating it on first use).
@@ -769,6 +781,248 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
     return SV_OK;
 }
 
+// ------------------------------------------------------- uneven batches
+
+// One problem of an uneven batch, planned and placed in the batch's buffer.
+struct MultiProblem {
+    const sv_problem *p = nullptr;
+    PlanEntry *pe = nullptr;
+    ObsEntry *obs = nullptr;
+    const void *drefs = nullptr;
+    int n = 0, I = 0, P = 0, G = 0, npass = 0;
+    size_t o_tp = 0, o_psi = 0, o_lam = 0, o_mats = 0, o_rho = 0, o_E = 0, o_G = 0;
+    SlotSource src{};
+};
+
+// Launches the whole multi-problem adjoint on st (eagerly, or into a capture).
+sv_status multi_sequence(DeviceCtx *ctx, std::vector<MultiProblem> &mp, sv_dtype dt, int R,
+                         unsigned char *base, const std::vector<size_t> &o_items,
+                         const std::vector<int> &n_items, const std::vector<int> &blocks,
+                         const std::vector<uint32_t> &smem, const double *const *theta,
+                         double *const *E_out, double *const *L_out, double *const *G_out,
+                         cudaStream_t st) {
+    const int c128 = dt == SV_C128;
+    const int nsteps = (int)n_items.size() / 2;  // forward steps, then reverse steps
+    for (MultiProblem &m : mp) {
+        m.src.theta = theta[&m - &mp[0]];
+        cudaError_t e = launch_group_mats(c128, m.pe->dev, m.src, base + m.o_mats, st);
+        if (e == cudaSuccess) e = launch_init_states(c128, base + m.o_psi, m.n, m.src, st);
+        if (e != cudaSuccess) return cuda_fail(e, "uneven batch: group matrices / init");
+    }
+    const int threads = 1 << (mp[0].pe->tiles[0].t - R);
+    for (int k = 0; k < 2 * nsteps; ++k) {
+        if (k == nsteps) {  // between the sweeps: lambda = H psi, cleared sums
+            for (MultiProblem &m : mp) {
+                sv_status s = h_tiles(ctx, m.obs, m.n, dt, m.I, base + m.o_psi, base + m.o_lam,
+                                      (double *)(base + m.o_E), st);
+                if (s != SV_OK) return s;
+                SV_CUDA(cudaMemsetAsync(base + m.o_rho, 0, (size_t)m.I * m.G * 64, st));
+                SV_CUDA(cudaMemsetAsync(base + m.o_G, 0, sizeof(double) * (size_t)m.I * (m.P > 0 ? m.P : 1), st));
+            }
+        }
+        if (n_items[k] == 0) continue;
+        cudaError_t e = launch_tile_multi(c128, R, k >= nsteps, (const MultiItem *)(base + o_items[k]),
+                                          n_items[k], blocks[k], threads, smem[k], st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, ("uneven batch: tile pass step " + std::to_string(k) + " (" +
+                                    std::to_string(n_items[k]) + " items, " +
+                                    std::to_string(blocks[k]) + " blocks of " +
+                                    std::to_string(threads) + " threads, " +
+                                    std::to_string(smem[k]) + " B shared)").c_str());
+    }
+    for (size_t j = 0; j < mp.size(); ++j) {
+        MultiProblem &m = mp[j];
+        const CostSource cs = cost_of(m.p, nullptr);
+        const double *Es = (const double *)(base + m.o_E);
+        double *Gs = (double *)(base + m.o_G);
+        cudaError_t e = launch_group_grads(c128, m.pe->dev, m.src, (const double *)(base + m.o_rho),
+                                           cs, Es, Gs, st);
+        if (e == cudaSuccess)
+            e = launch_adjoint_combine(Gs, Es, m.I, m.P, cs, E_out ? E_out[j] : nullptr,
+                                       L_out ? L_out[j] : nullptr, G_out[j], st);
+        if (e != cudaSuccess) return cuda_fail(e, "uneven batch: gradients");
+    }
+    return SV_OK;
+}
+
+sv_status multi_adjoint(DeviceCtx *ctx, const sv_problem *problems, int np,
+                        const double *const *theta, double *const *E_out, double *const *L_out,
+                        double *const *G_out, cudaStream_t st) {
+    const sv_dtype dt = problems[0].dtype;
+    const int c128 = dt == SV_C128;
+    const size_t csz = c128 ? 16 : 8;
+    TileCfg cfg{};
+    uint64_t key = mix64(0x5e17ull, (uint64_t)np);
+    for (int j = 0; j < np; ++j) {
+        const sv_problem *p = &problems[j];
+        if (p->dtype != dt) return fail(SV_ERR_ARG, "uneven batch: problems differ in dtype");
+        if (!wants_tiles(p->circuit->n_qubits, dt, p->opts))
+            return fail(SV_ERR_UNSUPPORTED, "uneven batch: every problem must take the tile path");
+        TileCfg c{};
+        sv_status s = tile_cfg(p->circuit->n_qubits, dt, p->opts, &c);
+        if (s != SV_OK) return s;
+        if (j == 0) cfg = c;
+        else if (c.t != cfg.t || c.R != cfg.R)
+            return fail(SV_ERR_UNSUPPORTED, "uneven batch: problems need one tile shape");
+        key = mix64(key, mix64(hash_circuit(*p->circuit), hash_observable(*p->observable)));
+        key = mix64(key, (uint64_t)p->n_instances);
+        key = mix64(key, (uint64_t)p->cost);
+        for (int i = 0; i < p->n_instances; ++i) key = mix64(key, (uint64_t)p->refs[i]);
+        for (const void *ptr : {(const void *)theta[j], (const void *)(E_out ? E_out[j] : nullptr),
+                                (const void *)(L_out ? L_out[j] : nullptr), (const void *)G_out[j],
+                                (const void *)p->inputs, (const void *)p->weights,
+                                (const void *)p->targets})
+            key = mix64(key, (uint64_t)(uintptr_t)ptr);
+        key = mix64(key, (uint64_t)p->input_stride);
+    }
+    key = mix64(key, mix64((uint64_t)dt, (uint64_t)(cfg.t * 8 + cfg.R)));
+    std::unique_ptr<MultiGraph> &g = ctx->graphs[key];
+    if (g && g->exec) {
+        SV_CUDA(cudaGraphLaunch(g->exec, st));
+        return SV_OK;
+    }
+    // plan every problem and lay out one buffer
+    std::vector<MultiProblem> mp(np);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~size_t(255);
+        return o;
+    };
+    int max_pass = 0;
+    for (int j = 0; j < np; ++j) {
+        MultiProblem &m = mp[j];
+        m.p = &problems[j];
+        m.n = m.p->circuit->n_qubits;
+        m.I = m.p->n_instances;
+        m.P = m.p->circuit->n_params;
+        sv_status s = get_plan(ctx, *m.p->circuit, cfg.R, use_fusion(m.p->opts), dt, &m.pe, cfg.t);
+        if (s == SV_OK) s = get_obs(ctx, *m.p->observable, m.n, dt, &m.obs, st);
+        if (s == SV_OK) s = get_array(ctx, m.p->refs, sizeof(int64_t) * m.I, &m.drefs);
+        HPlanEntry *hp = nullptr;
+        if (s == SV_OK) s = get_hplan(m.obs, m.n, dt, &hp);
+        if (s != SV_OK) return s;
+        m.G = m.pe->dev.n_groups;
+        m.npass = (int)m.pe->tiles.size();
+        max_pass = std::max(max_pass, m.npass);
+        m.src.mode = SLOTS_INSTANCES;
+        m.src.n_slots = m.I;
+        m.src.n_instances = m.I;
+        m.src.refs = (const int64_t *)m.drefs;
+        m.src.inputs = m.p->inputs;
+        m.src.input_stride = m.p->input_stride;
+        m.o_tp = take(sizeof(TilePass) * (size_t)m.npass);
+        m.o_psi = take(((size_t)m.I << m.n) * csz);
+        m.o_lam = take(((size_t)m.I << m.n) * csz);
+        m.o_mats = take((size_t)m.I * m.G * 4 * csz);
+        m.o_rho = take((size_t)m.I * m.G * 64);
+        m.o_E = take(sizeof(double) * (size_t)m.I);
+        m.o_G = take(sizeof(double) * (size_t)m.I * (m.P > 0 ? m.P : 1));
+    }
+    // item tables: forward step k runs pass k, reverse step k pass npass - 1 - k
+    std::vector<std::vector<MultiItem>> steps(2 * max_pass);
+    std::vector<uint32_t> smem(2 * max_pass, 0);
+    std::vector<int> blocks(2 * max_pass, 0), n_items(2 * max_pass, 0);
+    std::vector<size_t> o_items(2 * max_pass, 0);
+    const int threads = 1 << (cfg.t - cfg.R);
+    for (int k = 0; k < 2 * max_pass; ++k) {
+        const bool rev = k >= max_pass;
+        int64_t total = 0;
+        for (const MultiProblem &m : mp) {
+            const int pi = rev ? m.npass - 1 - (k - max_pass) : k;
+            if (pi < 0 || pi >= m.npass) continue;
+            const TilePass &tp = m.pe->tiles[pi];
+            smem[k] = std::max(smem[k], tile_multi_smem(c128, rev, tp));
+            total += (int64_t)m.I << tp.n_tile_bits;
+        }
+        if (total == 0) continue;
+        if (smem[k] > 220u * 1024u) return fail(SV_ERR_UNSUPPORTED, "uneven batch: pass needs too much shared memory");
+        const int per_sm = tile_multi_blocks_per_sm(c128, cfg.R, rev, smem[k], threads);
+        if (per_sm < 1) return fail(SV_ERR_UNSUPPORTED, "uneven batch: pass kernel does not fit an SM");
+        int64_t budget = (int64_t)ctx->sms * per_sm;
+        int b0 = 0;
+        for (MultiProblem &m : mp) {
+            const int pi = rev ? m.npass - 1 - (k - max_pass) : k;
+            if (pi < 0 || pi >= m.npass) continue;
+            const TilePass &tp = m.pe->tiles[pi];
+            const int64_t tiles = (int64_t)m.I << tp.n_tile_bits;
+            int64_t nb = budget * tiles / total;
+            nb = std::max<int64_t>(1, std::min<int64_t>(nb, tiles));
+            MultiItem it{};
+            it.P = nullptr;  // set after the buffer exists: base + o_tp + pi
+            it.pad = pi;
+            it.n = m.n;
+            it.n_slots = m.I;
+            it.G = m.G;
+            it.block_begin = b0;
+            it.block_end = b0 + (int)nb;
+            b0 += (int)nb;
+            steps[k].push_back(it);
+        }
+        blocks[k] = b0;
+        n_items[k] = (int)steps[k].size();
+        o_items[k] = take(sizeof(MultiItem) * steps[k].size());
+    }
+    std::unique_ptr<MultiGraph> ng(new MultiGraph());
+    if (cudaMalloc(&ng->buf.ptr, off ? off : 256) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SV_ERR_OOM, "uneven batch: states of all problems do not fit (" +
+                                    std::to_string(off >> 20) + " MiB)");
+    }
+    ng->buf.bytes = off;
+    unsigned char *base = (unsigned char *)ng->buf.ptr;
+    for (MultiProblem &m : mp)
+        SV_CUDA(cudaMemcpy(base + m.o_tp, m.pe->tiles.data(), sizeof(TilePass) * (size_t)m.npass,
+                           cudaMemcpyHostToDevice));
+    for (int k = 0; k < 2 * max_pass; ++k) {
+        if (steps[k].empty()) continue;
+        const bool rev = k >= max_pass;
+        size_t j = 0;
+        for (const MultiProblem &m : mp) {
+            const int pi = rev ? m.npass - 1 - (k - max_pass) : k;
+            if (pi < 0 || pi >= m.npass) continue;
+            MultiItem &it = steps[k][j++];
+            it.P = (const TilePass *)(base + m.o_tp) + pi;
+            it.mats = base + m.o_mats;
+            it.psi = base + m.o_psi;
+            it.lam = base + m.o_lam;
+            it.rho = (double *)(base + m.o_rho);
+            it.pad = 0;
+        }
+        SV_CUDA(cudaMemcpy(base + o_items[k], steps[k].data(), sizeof(MultiItem) * steps[k].size(),
+                           cudaMemcpyHostToDevice));
+    }
+    // this call runs eagerly; the graph serves the later ones
+    sv_status s = multi_sequence(ctx, mp, dt, cfg.R, base, o_items, n_items, blocks, smem, theta,
+                                 E_out, L_out, G_out, st);
+    if (s != SV_OK) return s;
+    if (!ctx->capture_stream)
+        SV_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+    SV_CUDA(cudaStreamSynchronize(st));
+    cudaStream_t cap = ctx->capture_stream;
+    SV_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    set_capturing(true);
+    s = multi_sequence(ctx, mp, dt, cfg.R, base, o_items, n_items, blocks, smem, theta, E_out,
+                       L_out, G_out, cap);
+    set_capturing(false);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cap, &graph);
+    if (s != SV_OK || ec != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        g = std::move(ng);  // keep the buffer: later calls run eagerly
+        return s != SV_OK ? s : cuda_fail(ec, "uneven batch: graph capture");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&ng->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        ng->exec = nullptr;
+        return cuda_fail(ei, "uneven batch: graph instantiation");
+    }
+    g = std::move(ng);
+    return SV_OK;
+}
+
 }  // namespace
 
 struct sv_state_s {
@@ -1175,6 +1429,25 @@ sv_status sv_grad_adjoint(const sv_problem *p, const double *theta, const double
     e = launch_adjoint_combine(G, E, I, P, cs, energy_out, loss_out, grad_out, st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint combine launch");
     return SV_OK;
+}
+
+sv_status sv_grad_adjoint_multi(const sv_problem *problems, int32_t n_problems,
+                                const double *const *theta, double *const *energy_out,
+                                double *const *loss_out, double *const *grad_out,
+                                sv_stream_t stream) {
+    if (!problems || n_problems < 1 || !theta || !grad_out)
+        return fail(SV_ERR_ARG, "problems/theta/grad_out is NULL or n_problems < 1");
+    for (int j = 0; j < n_problems; ++j) {
+        sv_status s = check_problem(&problems[j], true);
+        if (s != SV_OK) return s;
+        if (problems[j].circuit->n_params > 0 && (!theta[j] || !grad_out[j]))
+            return fail(SV_ERR_ARG, "theta[j]/grad_out[j] is NULL");
+    }
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return multi_adjoint(ctx, problems, n_problems, theta, energy_out, loss_out, grad_out,
+                         (cudaStream_t)stream);
 }
 
 // -------------------------------------------------------------- plain form

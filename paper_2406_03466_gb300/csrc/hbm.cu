@@ -15,7 +15,10 @@
 // states, and the per-slot gradient assembly.
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "engine.cuh"
 #include "hbm.h"
@@ -198,13 +201,13 @@ __host__ __device__ inline bool pass_all_real(const TilePass &P) {
 
 // One forward pass over every tile of every slot.  mats: [slots][G][4].
 template <typename Real, int R, bool kReal>
-__global__ void __launch_bounds__(256, R >= 4 ? 2 : 3)
-k_tile_fwd(const __grid_constant__ TilePass P, int n, int n_slots,
-           const typename CT<Real>::T *mats, int G, typename CT<Real>::T *states) {
+__device__ __forceinline__ void tile_fwd_body(const TilePass &P, int n, int n_slots,
+                                              const typename CT<Real>::T *mats, int G,
+                                              typename CT<Real>::T *states, int nblk, int blk,
+                                              unsigned char *smem) {
     using C = typename CT<Real>::T;
     constexpr int NA = 1 << R;
     constexpr uint32_t kBufs = 2u;
-    extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, T = blockDim.x, t = P.t, S = P.n_stages;
     const uint32_t tbytes = (uint32_t)sizeof(C) << t;
     uint2 *tb = reinterpret_cast<uint2 *>(smem + kBufs * tbytes);
@@ -227,8 +230,8 @@ k_tile_fwd(const __grid_constant__ TilePass P, int n, int n_slots,
     const uint32_t n0 = bit_vectors<R>(P.nat, t, tid, nk);
     const uint32_t sh = (uint32_t)__cvta_generic_to_shared(smem);
     const int64_t tiles = (int64_t)n_slots << P.n_tile_bits;
-    const int64_t per = (tiles + gridDim.x - 1) / gridDim.x;
-    const int64_t t0 = per * blockIdx.x, t_end = min(tiles, t0 + per);
+    const int64_t per = (tiles + nblk - 1) / nblk;
+    const int64_t t0 = per * blk, t_end = min(tiles, t0 + per);
     if (t0 >= t_end) return;
     auto fetch = [&](const TileCursor &c, int buf) {
         const C *src = states + ((int64_t)c.slot << n) + c.base;
@@ -272,6 +275,14 @@ k_tile_fwd(const __grid_constant__ TilePass P, int n, int n_slots,
         cur = nxt;
         nxt = tile_next(P, nxt);
     }
+}
+
+template <typename Real, int R, bool kReal>
+__global__ void __launch_bounds__(256, R >= 4 ? 2 : 3)
+k_tile_fwd(const __grid_constant__ TilePass P, int n, int n_slots,
+           const typename CT<Real>::T *mats, int G, typename CT<Real>::T *states) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    tile_fwd_body<Real, R, kReal>(P, n, n_slots, mats, G, states, gridDim.x, blockIdx.x, smem);
 }
 
 // The derivative of a rotation exp(-i theta P / 2) inside a fused group is
@@ -419,14 +430,13 @@ __device__ void flush_acc(const TilePass &P, Real *acc, int wps, double *rho_g, 
 // rho_g[slot][group][8].  The sums run in the state's precision over one
 // warp and at most 64 tiles, then in FP64.
 template <typename Real, int R, bool kSingle, bool kReal>
-__global__ void __launch_bounds__(256, R >= 4 ? 1 : 2)
-k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
-           const typename CT<Real>::T *mats, int G, typename CT<Real>::T *psi,
-           typename CT<Real>::T *lam, double *rho_g) {
+__device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_slots,
+                                              const typename CT<Real>::T *mats, int G,
+                                              typename CT<Real>::T *psi, typename CT<Real>::T *lam,
+                                              double *rho_g, int nblk, int blk, unsigned char *smem) {
     using C = typename CT<Real>::T;
     constexpr int NA = 1 << R;
     constexpr int kFlushTiles = 64;
-    extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, T = blockDim.x, t = P.t, S = P.n_stages;
     const int lane = tid & 31, wps = T >> 5;
     const uint32_t tbytes = (uint32_t)sizeof(C) << t;
@@ -453,8 +463,8 @@ k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
     const uint32_t n0 = bit_vectors<R>(P.nat, t, tid, nk);
     const uint32_t sh = (uint32_t)__cvta_generic_to_shared(smem);
     const int64_t tiles = (int64_t)n_slots << P.n_tile_bits;
-    const int64_t per = (tiles + gridDim.x - 1) / gridDim.x;
-    const int64_t t0 = per * blockIdx.x, t_end = min(tiles, t0 + per);
+    const int64_t per = (tiles + nblk - 1) / nblk;
+    const int64_t t0 = per * blk, t_end = min(tiles, t0 + per);
     if (t0 >= t_end) return;
     // psi tile of buffer j at [j tbytes], lambda tile at [(2 + j) tbytes]
     auto fetch = [&](const TileCursor &c, int buf) {
@@ -548,6 +558,16 @@ k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
     flush_acc<Real, kSingle>(P, acc, wps, rho_g, mslot, G);
 }
 
+template <typename Real, int R, bool kSingle, bool kReal>
+__global__ void __launch_bounds__(256, R >= 4 ? 1 : 2)
+k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
+           const typename CT<Real>::T *mats, int G, typename CT<Real>::T *psi,
+           typename CT<Real>::T *lam, double *rho_g) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    tile_rev_body<Real, R, kSingle, kReal>(P, n, n_slots, mats, G, psi, lam, rho_g, gridDim.x,
+                                           blockIdx.x, smem);
+}
+
 // Sum of v over the block (every thread gets it); red: one double per warp.
 __device__ __forceinline__ double block_sum(double v, double *red) {
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -558,6 +578,57 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
     if (threadIdx.x == 0)
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
     return s;
+}
+
+// ------------------------------------------ several problems per launch
+
+// The item of this block (items sorted by block_begin) and its descriptor,
+// copied into the front of shared memory; returns the shared memory after it.
+__device__ __forceinline__ unsigned char *multi_item(const MultiItem *items, int n_items,
+                                                     MultiItem &it, unsigned char *smem) {
+    __shared__ int s_item;
+    if (threadIdx.x == 0) {
+        int j = 0;
+        while (j + 1 < n_items && items[j + 1].block_begin <= (int)blockIdx.x) ++j;
+        s_item = j;
+    }
+    __syncthreads();
+    it = items[s_item];
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(it.P);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(smem);
+    for (int i = threadIdx.x; i < (int)(sizeof(TilePass) / 4); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    return smem + ((sizeof(TilePass) + 255) & ~size_t(255));
+}
+
+// Forward passes of several problems (same tile shape, any qubit count and
+// depth) in one launch.
+template <typename Real, int R>
+__global__ void __launch_bounds__(256, R >= 4 ? 2 : 3)
+k_tile_fwd_multi(const MultiItem *items, int n_items) {
+    using C = typename CT<Real>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    MultiItem it;
+    unsigned char *rest = multi_item(items, n_items, it, smem);
+    const TilePass &P = *reinterpret_cast<const TilePass *>(smem);
+    tile_fwd_body<Real, R, false>(P, it.n, it.n_slots, (const C *)it.mats, it.G, (C *)it.psi,
+                                  it.block_end - it.block_begin, (int)blockIdx.x - it.block_begin,
+                                  rest);
+}
+
+// Reverse passes of several problems in one launch.
+template <typename Real, int R>
+__global__ void __launch_bounds__(256, R >= 4 ? 1 : 2)
+k_tile_rev_multi(const MultiItem *items, int n_items) {
+    using C = typename CT<Real>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    MultiItem it;
+    unsigned char *rest = multi_item(items, n_items, it, smem);
+    const TilePass &P = *reinterpret_cast<const TilePass *>(smem);
+    tile_rev_body<Real, R, false, false>(P, it.n, it.n_slots, (const C *)it.mats, it.G,
+                                         (C *)it.psi, (C *)it.lam, it.rho,
+                                         it.block_end - it.block_begin,
+                                         (int)blockIdx.x - it.block_begin, rest);
 }
 
 // ------------------------------------------------------ H over tile passes
@@ -868,8 +939,25 @@ __global__ void k_group_grads(Program p, SlotSource src, const double *rho_g, Co
     }
 }
 
+// A kernel's dynamic shared-memory limit only ever grows (per device and
+// kernel), so a launch sequence that ran once has every limit it needs.
+// While a sequence is captured into a CUDA graph no attribute is changed: a
+// launch that would need a larger limit fails instead.
+thread_local bool t_capturing = false;
+std::mutex g_smem_mu;
+std::map<std::pair<int, const void *>, uint32_t> g_smem_limit;
+
 template <typename K> cudaError_t allow_smem(K kernel, uint32_t bytes) {
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    uint32_t &have = g_smem_limit[{dev, (const void *)kernel}];
+    if (bytes <= have) return cudaSuccess;
+    if (t_capturing) return cudaErrorInvalidValue;
+    const cudaError_t e =
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
 }
 
 // Resident blocks of kernel k on the whole GPU, at most max_blocks.
@@ -1013,6 +1101,51 @@ cudaError_t launch_tile_h(int c128, const HPass &P, int n, int n_slots, const vo
     if (R == 4) return pick(std::integral_constant<int, 4>());
     if (R == 3) return pick(std::integral_constant<int, 3>());
     return pick(std::integral_constant<int, 2>());
+}
+
+void set_capturing(bool on) { t_capturing = on; }
+
+uint32_t tile_multi_smem(int c128, bool rev, const TilePass &P) {
+    return (uint32_t)((sizeof(TilePass) + 255) & ~size_t(255)) +
+           (rev ? tile_rev_smem(c128, P) : tile_fwd_smem(c128, P));
+}
+
+int tile_multi_blocks_per_sm(int c128, int R, bool rev, uint32_t smem, int threads) {
+    int per = 0;
+    HBM_DISPATCH_R(c128, R, {
+        cudaError_t e;
+        if (rev) {
+            auto k = k_tile_rev_multi<Real, RR>;
+            e = allow_smem(k, smem);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, smem);
+        } else {
+            auto k = k_tile_fwd_multi<Real, RR>;
+            e = allow_smem(k, smem);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, smem);
+        }
+        if (e != cudaSuccess) return 0;
+    });
+    return per;
+}
+
+cudaError_t launch_tile_multi(int c128, int R, bool rev, const MultiItem *items, int n_items,
+                              int blocks, int threads, uint32_t smem, cudaStream_t st) {
+    cudaError_t prior = cudaGetLastError();  // not this launch's
+    (void)prior;
+    HBM_DISPATCH_R(c128, R, {
+        if (rev) {
+            auto k = k_tile_rev_multi<Real, RR>;
+            cudaError_t e = allow_smem(k, smem);
+            if (e != cudaSuccess) return e;
+            k<<<blocks, threads, smem, st>>>(items, n_items);
+        } else {
+            auto k = k_tile_fwd_multi<Real, RR>;
+            cudaError_t e = allow_smem(k, smem);
+            if (e != cudaSuccess) return e;
+            k<<<blocks, threads, smem, st>>>(items, n_items);
+        }
+    });
+    return cudaGetLastError();
 }
 
 static dim3 whole_state_grid(int n, int rows) {

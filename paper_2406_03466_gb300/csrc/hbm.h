@@ -25,6 +25,16 @@ cudaError_t launch_tile_fwd(int c128, const TilePass &P, int n, int n_slots, con
 cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, const void *mats,
                             int G, void *psi, void *lam, double *rho_g, int64_t max_blocks,
                             cudaStream_t st);
+// Tile passes of several problems in one launch (forward, or reverse with
+// rev): items sorted by block_begin, device memory; every item uses the same
+// tile shape (threads = 2^(t - R)).  smem: the largest over the items of
+// tile_multi_smem.
+// Launchers skip kernel attribute calls while a graph capture runs.
+void set_capturing(bool on);
+uint32_t tile_multi_smem(int c128, bool rev, const TilePass &P);
+int tile_multi_blocks_per_sm(int c128, int R, bool rev, uint32_t smem, int threads);
+cudaError_t launch_tile_multi(int c128, int R, bool rev, const MultiItem *items, int n_items,
+                              int blocks, int threads, uint32_t smem, cudaStream_t st);
 // One tile pass of lambda = H psi (lam may be null: energies only); adds this
 // pass's part of <psi|H|psi> to E[slot] (zero E before the first pass).
 uint32_t tile_h_smem(int c128, const HPass &P);

@@ -151,6 +151,17 @@ struct Observable {
     const Term *terms;
 };
 
+// One problem's part of a multi-problem tile-pass launch: the launch's
+// blocks [block_begin, block_end) run pass *P of this problem's states.
+struct MultiItem {
+    const TilePass *P;  // device descriptor
+    int32_t n, n_slots, G, pad;
+    const void *mats;   // [slots][G][4]
+    void *psi, *lam;    // forward: psi = the states
+    double *rho;        // reverse: [slots][G][8]
+    int32_t block_begin, block_end;
+};
+
 // lambda = H psi (and <H>) over tiles of 2^t amplitudes.  A pass covers the
 // X-mask groups whose flip mask lies inside its local qubits; inside a
 // group, terms with the same Z mask on the local qubits form a class whose

@@ -146,3 +146,27 @@ def test_autotuned_tile_shape(sv, dtype):
     close(g_.cpu().numpy(), g, TOL[dtype]["G"])
     l_, e_ = sv.sv_energies(prob, theta_of(w))
     close(e_.cpu().numpy(), E, TOL[dtype]["E"])
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_uneven_batch_adjoint(sv, dtype):
+    """Circuits of different qubit counts, depths and observables in one
+    pass-major sequence; the second call replays the captured graph."""
+    ws = [wl.qcl(14, 2, 3), wl.mcvqe(15, 3, "nn+nnn", n_refs=2), wl.qcl(16, 1, 2),
+          wl.random_workload(14, 80, 6, 2, seed=51, with_encoding=True)]
+    probs = [sv.Problem.from_spec(w, dtype) for w in ws]
+    thetas = [theta_of(w) for w in ws]
+    outs = sv.sv_grad_adjoint_multi(probs, thetas)
+    for rep in range(2):
+        for w, pr, th, (l_, e_, g_) in zip(ws, probs, thetas, outs):
+            ls, es, gs = sv.sv_grad_adjoint(pr, th, checkpoint_every=1000)
+            close(e_.cpu().numpy(), es.cpu().numpy(), TOL[dtype]["E"])
+            close(g_.cpu().numpy(), gs.cpu().numpy(), TOL[dtype]["G"])
+            close(l_.cpu().numpy(), ls.cpu().numpy(), TOL[dtype]["E"])
+        for o in outs:  # the replay must rewrite every output
+            for x in o:
+                x.fill_(float("nan"))
+        outs = sv.sv_grad_adjoint_multi(probs, thetas, outputs=outs)
+    L, E, g = oracle.grad_param_shift(ws[1])
+    close(outs[1][1].cpu().numpy(), E, TOL[dtype]["E"])
+    close(outs[1][2].cpu().numpy()[: ws[1].n_params], g, TOL[dtype]["G"])

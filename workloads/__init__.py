@@ -238,6 +238,21 @@ def qcl(n: int = 12, layers: int = 6, n_samples: int = 256, seed: int = 0,
                     targets=y, cost="mse", meta={"layers": layers})
 
 
+def qcl_uneven(n_circuits: int = 8, n_samples: int = 16, n_range=(20, 24), depth_range=(4, 12),
+               seed: int = 0) -> List[Workload]:
+    """The uneven-batch variant of the 20-qubit circuit-learning configuration:
+    circuits with n ~ U{n_range} qubits and depth ~ U{depth_range} layers
+    (drawn in that order per circuit from default_rng(seed)), each a `qcl`
+    workload with its own theta, inputs and targets (seed + 1 + i)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_circuits):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        layers = int(rng.integers(depth_range[0], depth_range[1] + 1))
+        out.append(qcl(n, layers, n_samples, seed=seed + 1 + i))
+    return out
+
+
 def config(idx: int) -> Workload:
     """The five workload configurations at full size (0-based index)."""
     if idx == 0:
