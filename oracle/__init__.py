@@ -231,5 +231,63 @@ def grad_finite_difference(w, theta=None, h: float = 1e-5, n_threads: int = 0):
     return g
 
 
+# ---------------------------------------------- data-driven circuit learning
+
+def js_divergence(P, Q):
+    """Jensen-Shannon divergence of Sec. 4.2 Eq. 3 with natural logarithms:
+    JS = 1/2 sum_b (P log(P/M) + Q log(Q/M)), M = (P + Q)/2, 0 log 0 = 0."""
+    P = np.asarray(P, dtype=np.float64)
+    Q = np.asarray(Q, dtype=np.float64)
+    M = 0.5 * (P + Q)
+    total = 0.0
+    for X in (P, Q):
+        nz = X > 0
+        total += float(np.sum(X[nz] * np.log(X[nz] / M[nz])))
+    return 0.5 * total
+
+
+def output_distribution(w, theta=None, shift_param: int = -1, shift: float = 0.0):
+    """P_theta(b) = |<b|psi>|^2: all qubits measured in the Z basis (Sec. 4.2)."""
+    psi = state(w, theta, 0, shift_param, shift)
+    return (psi.real ** 2 + psi.imag ** 2)
+
+
+def ddcl_cost(w, theta=None):
+    """JS(P | P_theta) of the workload's target distribution P."""
+    return js_divergence(w.target_dist, output_distribution(w, theta))
+
+
+def ddcl_grad_param_shift(w, theta=None, params=None):
+    """(JS, gradient): each P_theta(b) is the expectation of the projector on
+    |b>, so its derivative is the parameter-shift difference of the shifted
+    distributions; the chain rule weights it with dJS/dP_theta(b) =
+    1/2 log(P_theta(b) / M(b)) (0 where P_theta(b) = 0)."""
+    P = np.asarray(w.target_dist, dtype=np.float64)
+    Q = output_distribution(w, theta)
+    M = 0.5 * (P + Q)
+    wb = np.zeros_like(Q)
+    nz = Q > 0
+    wb[nz] = 0.5 * np.log(Q[nz] / M[nz])
+    ks = np.arange(w.n_params) if params is None else np.asarray(params)
+    g = np.zeros(len(ks))
+    for i, k in enumerate(ks):
+        Qp = output_distribution(w, theta, int(k), np.pi / 2)
+        Qm = output_distribution(w, theta, int(k), -np.pi / 2)
+        g[i] = float(np.dot(wb, 0.5 * (Qp - Qm)))
+    return js_divergence(P, Q), g
+
+
+def ddcl_grad_finite_difference(w, theta=None, params=None, h: float = 1e-5):
+    """Central differences of JS(P | P_theta)."""
+    th = _theta(w, theta)
+    ks = np.arange(w.n_params) if params is None else np.asarray(params)
+    g = np.zeros(len(ks))
+    for i, k in enumerate(ks):
+        tp = th.copy(); tp[k] += h
+        tm = th.copy(); tm[k] -= h
+        g[i] = (ddcl_cost(w, tp) - ddcl_cost(w, tm)) / (2 * h)
+    return g
+
+
 def max_threads() -> int:
     return int(_load().orc_max_threads())

@@ -65,6 +65,9 @@ class Workload:
     weights: Optional[np.ndarray] = None  # (I,) float64 instance weights (cost "linear")
     cost: str = "linear"               # "linear": sum_i w_i E_i ; "mse": mean_i (E_i - y_i)^2
     meta: dict = field(default_factory=dict)
+    # cost "js": target distribution over the 2^n bitstrings (data-driven
+    # circuit learning, Sec. 4.2 Eq. 3); the observable is unused
+    target_dist: Optional[np.ndarray] = None
 
     @property
     def n_instances(self) -> int:
@@ -251,6 +254,53 @@ def qcl_uneven(n_circuits: int = 8, n_samples: int = 16, n_range=(20, 24), depth
         layers = int(rng.integers(depth_range[0], depth_range[1] + 1))
         out.append(qcl(n, layers, n_samples, seed=seed + 1 + i))
     return out
+
+
+def bell_pairs(n: int) -> List[Gate]:
+    """Neighbouring qubits (0,1), (2,3), ... entangled as Bell pairs: H then CNOT
+    (Sec. 4.2: the DDCL circuit starts with each pair of neighbouring qubits
+    entangled as a Bell pair; an odd last qubit stays |0>)."""
+    out: List[Gate] = []
+    for q in range(0, n - 1, 2):
+        out.append(Gate("H", target=q))
+        out.append(Gate("CNOT", target=q + 1, control=q))
+    return out
+
+
+def ddcl_target(n: int) -> np.ndarray:
+    """Synthetic target distribution over the 2^n bitstrings b (read as
+    integers): two discretised Gaussians at 2^n/4 and 3*2^n/4 with width
+    2^n/16, normalised; it stands in for the paper's unpublished target."""
+    b = np.arange(1 << n, dtype=np.float64)
+    N = float(1 << n)
+    sig = N / 16.0
+    p = np.exp(-0.5 * ((b - N / 4) / sig) ** 2) + np.exp(-0.5 * ((b - 3 * N / 4) / sig) ** 2)
+    return p / p.sum()
+
+
+def ddcl(n: int = 20, layers: int = 10, seed: int = 0, target: Optional[np.ndarray] = None) -> Workload:
+    """Data-driven circuit learning (Sec. 4.2, Eq. 3, Table 2): Bell pairs, then
+    `layers` layers of Rz-Ry-Rz on every qubit, CNOT ladder, Rz-Ry-Rz on every
+    qubit (6 parameters per qubit per layer, N_theta = 60 N_q at 10 layers;
+    the paper's layer figure is lost, this layout is a reading); cost: the JS
+    divergence of the output distribution from `target` (default ddcl_target)."""
+    rng = np.random.default_rng(seed)
+    gates = bell_pairs(n)
+    p = 0
+    for _ in range(layers):
+        for half in range(2):
+            for q in range(n):
+                for op in ("RZ", "RY", "RZ"):
+                    gates.append(Gate(op, target=q, param=p))
+                    p += 1
+            if half == 0:
+                gates.extend(cnot_ladder(n))
+    theta = rng.uniform(-np.pi, np.pi, p)
+    letters = letters_from_terms(n, [[(0, "Z")]])
+    return Workload(name=f"ddcl{n}", n_qubits=n, gates=gates, n_params=p, theta=theta,
+                    pauli_letters=letters, pauli_coeffs=np.ones(1), refs=np.zeros(1, dtype=np.int64),
+                    cost="js", meta={"layers": layers},
+                    target_dist=ddcl_target(n) if target is None else np.asarray(target, np.float64))
 
 
 def config(idx: int) -> Workload:
