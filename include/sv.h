@@ -262,6 +262,19 @@ sv_status sv_grad_param_shift_noalloc(const sv_problem *problem, const double *t
                                       double *energy_out, double *loss_out, double *grad_out,
                                       sv_stream_t stream);
 
+/* Data-driven circuit learning (Sec. 4.2, Eq. 3): the Jensen-Shannon
+ * divergence JS(P | P_theta) of the circuit's output distribution
+ * P_theta(b) = |<b|psi>|^2 (all qubits measured in the Z basis) from the
+ * target P, and its gradient by the adjoint sweep: dJS/dP_theta(b) =
+ * 1/2 log(P_theta(b)/M(b)), M = (P + P_theta)/2, so dJS/dtheta is the
+ * gradient of <psi| diag(dJS/dP_theta) |psi> with the diagonal held fixed.
+ * The problem's circuit, dtype, refs (one instance), inputs and opts are
+ * used; its observable and cost are ignored.  Runs as tile passes at every
+ * size (n >= 7).  target: device [2^n] doubles (normalised); js_out: device
+ * [1]; grad_out: device [P]; theta: device [P]. */
+sv_status sv_grad_ddcl(const sv_problem *problem, const double *theta, const double *target,
+                       double *js_out, double *grad_out, sv_stream_t stream);
+
 /* Adjoint gradients of several problems at once: circuits of different qubit
  * counts and depths whose states take the tile path (14..30 qubits; all
  * problems share the dtype and the tile shape), each with its own

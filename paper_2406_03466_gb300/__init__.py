@@ -81,7 +81,7 @@ EXPORTED = ("sv_alloc", "sv_free", "sv_state_info", "sv_apply_circuit_batch",
             "sv_expect_pauli_sum", "sv_energies", "sv_param_shift_energies", "sv_grad_param_shift", "sv_grad_adjoint",
             "sv_grad_param_shift_plain", "sv_grad_param_shift_noalloc", "sv_autotune",
             "sv_tuned_shape", "sv_plan_info", "sv_h_plan_info", "sv_phase_timing",
-            "sv_grad_adjoint_multi",
+            "sv_grad_adjoint_multi", "sv_grad_ddcl",
             "sv_last_phase_ms", "sv_status_string",
             "sv_last_error",
             "sv_sync_status", "sv_shutdown", "sv_version")
@@ -104,6 +104,7 @@ def _load():
     lib.sv_grad_param_shift.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_grad_adjoint.argtypes = [P(sv_problem), V, V, V, V, V, I32, V]
     lib.sv_grad_adjoint_multi.argtypes = [P(sv_problem), I32, P(V), P(V), P(V), P(V), V]
+    lib.sv_grad_ddcl.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_grad_param_shift_plain.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_grad_param_shift_noalloc.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_autotune.argtypes = [P(sv_problem), V, I32, V]
@@ -380,6 +381,19 @@ def sv_grad_adjoint_multi(problems, thetas, outputs=None, stream=None):
                                       ptrs([o[0] for o in outputs]), ptrs([o[2] for o in outputs]),
                                       _stream(stream)), "sv_grad_adjoint_multi")
     return outputs
+
+
+def sv_grad_ddcl(problem: Problem, theta, target, js_out=None, grad_out=None, stream=None):
+    """(JS[1], grad[P]) of data-driven circuit learning: the Jensen-Shannon
+    divergence of the circuit's Z-basis output distribution from ``target``
+    (float64 CUDA tensor [2^n]) and its adjoint gradient."""
+    import torch
+    f = dict(dtype=torch.float64, device=theta.device)
+    js_out = torch.empty(1, **f) if js_out is None else js_out
+    grad_out = torch.empty(max(1, problem.n_params), **f) if grad_out is None else grad_out
+    _check(_lib.sv_grad_ddcl(ctypes.byref(problem.struct), _ptr(theta), _ptr(target),
+                             _ptr(js_out), _ptr(grad_out), _stream(stream)), "sv_grad_ddcl")
+    return js_out, grad_out
 
 
 def sv_grad_param_shift_plain(problem: Problem, theta, energy_out=None, loss_out=None,

@@ -691,22 +691,28 @@ sv_status tiles_energies(DeviceCtx *ctx, const sv_problem *p, const double *thet
 // Adjoint gradient of states in device memory: forward passes with stored
 // states every `every` passes, lambda = H psi, reverse passes accumulating the
 // reduced matrices, per-slot gradients, then the sum over instances.
+// ddcl_target (device [2^n]) replaces lambda = H psi by the JS divergence's
+// lambda (data-driven circuit learning); the slot energies are then JS.
 sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta,
                         const double *weights, double *energy_out, double *loss_out,
-                        double *grad_out, int every, cudaStream_t st) {
+                        double *grad_out, int every, cudaStream_t st,
+                        const double *ddcl_target = nullptr, const TileCfg *forced = nullptr) {
     ctx->phase_used = 0;
     const sv_dtype dt = p->dtype;
     const int c128 = dt == SV_C128, n = p->circuit->n_qubits, I = p->n_instances;
     const int P = p->circuit->n_params, Pp = P > 0 ? P : 1;
     TileCfg cfg{};
-    sv_status s = tile_cfg(n, dt, p->opts, &cfg, find_tuned(ctx, p, kTileAdjointKey, I));
+    sv_status s = forced ? SV_OK : tile_cfg(n, dt, p->opts, &cfg, find_tuned(ctx, p, kTileAdjointKey, I));
     if (s != SV_OK) return s;
+    if (forced) cfg = *forced;
     PlanEntry *pe = nullptr;
     s = get_plan(ctx, *p->circuit, cfg.R, use_fusion(p->opts), dt, &pe, cfg.t);
     if (s != SV_OK) return s;
     ObsEntry *obs = nullptr;
-    s = get_obs(ctx, *p->observable, n, dt, &obs, st);
-    if (s != SV_OK) return s;
+    if (!ddcl_target) {
+        s = get_obs(ctx, *p->observable, n, dt, &obs, st);
+        if (s != SV_OK) return s;
+    }
     const void *drefs = nullptr;
     s = get_array(ctx, p->refs, sizeof(int64_t) * I, &drefs);
     if (s != SV_OK) return s;
@@ -753,10 +759,15 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
         s = tiles_forward(ctx, pe, cfg.R, dt, src, psi, mats, true, ncp ? ck : nullptr, every, st);
         if (s != SV_OK) return s;
         phase_mark(ctx, st);
-        s = h_tiles(ctx, obs, n, dt, src.n_slots, psi, lam, Es + c0, st);
-        if (s != SV_OK) return s;
-        phase_mark(ctx, st);
         cudaError_t e = cudaSuccess;
+        if (ddcl_target) {
+            e = launch_ddcl_lambda(c128, n, src.n_slots, psi, ddcl_target, lam, Es + c0, st);
+            if (e != cudaSuccess) return cuda_fail(e, "JS divergence and its lambda");
+        } else {
+            s = h_tiles(ctx, obs, n, dt, src.n_slots, psi, lam, Es + c0, st);
+            if (s != SV_OK) return s;
+        }
+        phase_mark(ctx, st);
         SV_CUDA(cudaMemsetAsync(rho, 0, (size_t)src.n_slots * G * 64, st));
         for (int i = npass - 1; i >= 0; --i) {
             if ((i + 1) % every == 0 && i + 1 < npass) {
@@ -1429,6 +1440,40 @@ sv_status sv_grad_adjoint(const sv_problem *p, const double *theta, const double
     e = launch_adjoint_combine(G, E, I, P, cs, energy_out, loss_out, grad_out, st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint combine launch");
     return SV_OK;
+}
+
+sv_status sv_grad_ddcl(const sv_problem *p, const double *theta, const double *target,
+                       double *js_out, double *grad_out, sv_stream_t stream) {
+    if (!p || !p->circuit) return fail(SV_ERR_ARG, "problem or circuit is NULL");
+    if (!target || !js_out) return fail(SV_ERR_ARG, "target/js_out is NULL");
+    sv_status s = check_circuit(p->circuit, p->dtype == SV_C128 ? 29 : 30);
+    if (s != SV_OK) return s;
+    const int n = p->circuit->n_qubits, P = p->circuit->n_params;
+    if (p->n_instances != 1 || !p->refs) return fail(SV_ERR_ARG, "data-driven circuit learning takes one instance");
+    if (P > 0 && (!theta || !grad_out)) return fail(SV_ERR_ARG, "theta/grad_out is NULL");
+    if (p->circuit->input_dim > 0 && !p->inputs) return fail(SV_ERR_ARG, "inputs are NULL");
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    // the tile path at every size (a whole small state is one tile)
+    TileCfg cfg{};
+    sv_plan_opts o{};
+    if (p->opts) o = *p->opts;
+    if (o.tile_bits <= 0 && !wants_tiles(n, p->dtype, p->opts)) {
+        o.tile_bits = std::min(n, p->dtype == SV_C128 ? 10 : 11);
+        if (o.reg_bits <= 0) o.reg_bits = std::max(2, std::min(p->dtype == SV_C128 ? 2 : 4, o.tile_bits - 5));
+    }
+    s = tile_cfg(n, p->dtype, &o, &cfg);
+    if (s != SV_OK) return s;
+    const double one = 1.0;
+    const void *w1 = nullptr;
+    s = get_array(ctx, &one, sizeof(double), &w1);
+    if (s != SV_OK) return s;
+    sv_problem q = *p;
+    q.opts = &o;
+    q.cost = SV_COST_LINEAR;
+    return tiles_adjoint(ctx, &q, theta, (const double *)w1, js_out, nullptr, grad_out, 0,
+                         (cudaStream_t)stream, target, &cfg);
 }
 
 sv_status sv_grad_adjoint_multi(const sv_problem *problems, int32_t n_problems,

@@ -920,6 +920,43 @@ __global__ void k_apply_h_big(Observable o, int n, const typename CT<Real>::T *p
     if (threadIdx.x == 0) atomicAdd(&E[b], s);
 }
 
+// Data-driven circuit learning (Sec. 4.2, Eq. 3): with Q(b) = |psi_b|^2 and
+// the target P, M = (P + Q)/2, adds JS = 1/2 sum_b (P log(P/M) + Q log(Q/M))
+// to js[slot] and writes lambda_b = w_b psi_b with w_b = dJS/dQ(b) =
+// 1/2 log(Q(b)/M(b)) (0 where Q(b) = 0), so that the reverse sweep with
+// lambda gives dJS/dtheta.  FP64 throughout (Q from the state's components,
+// logarithms, sums); grid.y = slot.
+template <typename Real>
+__global__ void k_ddcl_lambda(int n, const typename CT<Real>::T *psi, const double *target,
+                              typename CT<Real>::T *lam, double *js) {
+    using C = typename CT<Real>::T;
+    __shared__ double red[32];
+    const int b = blockIdx.y;
+    const C *S = psi + ((int64_t)b << n);
+    C *Lm = lam + ((int64_t)b << n);
+    const int64_t dim = int64_t(1) << n;
+    double acc = 0.0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < dim;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const C a = S[j];
+        const double q = (double)a.x * a.x + (double)a.y * a.y, p = target[j];
+        const double m = 0.5 * (p + q);
+        double w = 0.0;
+        if (p > 0.0) acc += p * log(p / m);
+        if (q > 0.0) {
+            const double l = log(q / m);
+            acc += q * l;
+            w = 0.5 * l;
+        }
+        C out;
+        out.x = (Real)(w * a.x);
+        out.y = (Real)(w * a.y);
+        Lm[j] = out;
+    }
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) atomicAdd(&js[b], 0.5 * s);
+}
+
 // Per-slot gradients from the summed reduced matrices: one thread per
 // (slot, group); slot_grads[b][param] += weight_b * dE_b/dtheta.
 template <typename Real>
@@ -1145,6 +1182,19 @@ cudaError_t launch_tile_multi(int c128, int R, bool rev, const MultiItem *items,
             k<<<blocks, threads, smem, st>>>(items, n_items);
         }
     });
+    return cudaGetLastError();
+}
+
+static dim3 whole_state_grid(int n, int rows);
+
+cudaError_t launch_ddcl_lambda(int c128, int n, int n_rows, const void *psi, const double *target,
+                               void *lam, double *js, cudaStream_t st) {
+    if (n_rows <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(js, 0, sizeof(double) * n_rows, st);
+    if (e != cudaSuccess) return e;
+    const dim3 g = whole_state_grid(n, n_rows);
+    if (c128) k_ddcl_lambda<double><<<g, 256, 0, st>>>(n, (const double2 *)psi, target, (double2 *)lam, js);
+    else k_ddcl_lambda<float><<<g, 256, 0, st>>>(n, (const float2 *)psi, target, (float2 *)lam, js);
     return cudaGetLastError();
 }
 

@@ -40,6 +40,10 @@ cudaError_t launch_tile_multi(int c128, int R, bool rev, const MultiItem *items,
 uint32_t tile_h_smem(int c128, const HPass &P);
 cudaError_t launch_tile_h(int c128, const HPass &P, int n, int n_slots, const void *psi, void *lam,
                           double *E, int64_t max_blocks, cudaStream_t st);
+// Data-driven circuit learning: js[r] = JS(target | |psi_r|^2) (zeroed here
+// first) and lam_r = dJS/d|psi_r|^2 * psi_r elementwise.
+cudaError_t launch_ddcl_lambda(int c128, int n, int n_rows, const void *psi, const double *target,
+                               void *lam, double *js, cudaStream_t st);
 // out[r] = <psi_r|H|psi_r> (zeroed here first).
 cudaError_t launch_expect_big(int c128, const Observable &o, int n, int n_rows,
                               const void *states, double *out, cudaStream_t st);
