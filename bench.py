@@ -47,12 +47,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=None)
     ap.add_argument("--workload", default="mcvqe8",
-                    choices=["mcvqe8", "qcl20", "mcvqe28", "qcl-uneven"],
+                    choices=["mcvqe8", "qcl20", "mcvqe28", "qcl-uneven", "ddcl"],
                     help="mcvqe8 (default): batched parameter-shift gradient of the 8-qubit "
                          "MC-VQE; qcl20 / mcvqe28: adjoint gradient of the 20-qubit circuit "
                          "learning / 28-qubit MC-VQE workload (states in device memory); "
                          "qcl-uneven: adjoint gradients of 8 circuit-learning circuits of "
-                         "20-24 qubits and depth 4-12 in one graph launch")
+                         "20-24 qubits and depth 4-12 in one graph launch; ddcl: data-driven "
+                         "circuit learning (Sec. 4.2) at 26 qubits (--qubits for 20-24)")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true", help="skip adjoint/plain/c128 side runs")
@@ -223,7 +224,7 @@ def forward_passes_roofline(sv, w, dev, flush, stream, reps=5, opts=None):
             "forward_ms": t * 1e3, "bytes_per_forward": nbytes, "peak_source": src}
 
 
-def adjoint_phases(sv, w, prob, theta, out, info, flush, stream, reps):
+def adjoint_phases(sv, w, prob, theta, out, info, flush, stream, reps, step=None):
     """Per-phase CUDA-event times of the device-memory adjoint (the library's
     phase timer records events on the call's stream), each step after an L2
     flush; the reverse tile passes are the dominant kernel: per pass they
@@ -233,7 +234,10 @@ def adjoint_phases(sv, w, prob, theta, out, info, flush, stream, reps):
     ph = {"forward_ms": 0.0, "h_ms": 0.0, "reverse_ms": 0.0}
     for _ in range(reps):
         flush.fill_(1.0)
-        sv.sv_grad_adjoint(prob, theta, None, *out)
+        if step is None:
+            sv.sv_grad_adjoint(prob, theta, None, *out)
+        else:
+            step()
         got = sv.sv_last_phase_ms()
         for k in ph:
             ph[k] += got[k] / reps
@@ -376,6 +380,109 @@ def run_device_memory(args, sv, dev, stream, dist, world, rank):
         dist.destroy_process_group()
 
 
+# Table 3 of the paper (DDCL gradient, 10 layers, one V100 per virtual QPU,
+# Aer + cuStateVec): runtime at one GPU from the printed fits, 10^intercept s.
+PAPER_DDCL_1GPU_S = {20: 418.8, 22: 532.1, 24: 907.8, 26: 2500.0}
+
+
+def cpu_baseline_ddcl(w, seconds):
+    """The oracle on whole DDCL circuits at 20 qubits for about `seconds`,
+    scaled by 2^n x gates to the workload and to the 2P + 1 circuits of one
+    parameter-shift gradient (extrapolated)."""
+    import oracle
+    ws = wl.ddcl(min(20, w.n_qubits), w.meta.get("layers", 10))
+    t0 = time.perf_counter()
+    n_done = 0
+    while True:
+        oracle.output_distribution(ws)
+        n_done += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    scale = ((1 << w.n_qubits) * len(w.gates)) / ((1 << ws.n_qubits) * len(ws.gates))
+    per_grad = dt / n_done * scale * (2 * w.n_params + 1)
+    return {"value": 1.0 / per_grad, "unit": "gradients/s", "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": f"{n_done} whole circuits of {ws.name} in {dt:.1f} s (one circuit at a "
+                      f"time), scaled x{scale:.0f} by 2^n x gates to {w.name} and to "
+                      f"{2 * w.n_params + 1} circuits per parameter-shift gradient (extrapolated)"}
+
+
+def run_ddcl(args, sv, dev, stream, dist, world, rank):
+    """Adjoint gradient of the JS divergence of data-driven circuit learning."""
+    import torch
+    n = args.qubits or 26
+    w = wl.ddcl(n, 10)
+    prob = sv.Problem.from_spec(w, "c64", device=dev)
+    theta = torch.as_tensor(w.theta, dtype=torch.float64, device=dev)
+    target = torch.as_tensor(w.target_dist, dtype=torch.float64, device=dev)
+    js = torch.empty(1, dtype=torch.float64, device=dev)
+    grad = torch.empty(w.n_params, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        sv.sv_grad_ddcl(prob, theta, target, js, grad)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    t_dev = timed_loop(step, args.steps, flush, stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    gps, t_dev = job_throughput(t_dev, args.steps, dist, dev)
+    opts = sv.plan_opts(reg_bits=4, tile_bits=11)
+    info = sv.sv_plan_info(sv.Circuit(n, w.gates, w.n_params, 0), "c64", opts)
+    paper_s = PAPER_DDCL_1GPU_S.get(n)
+    result = {"metric": METRIC, "value": gps, "unit": "gradients/s", "n_gpus": world,
+              "steps": args.steps, "warmup": args.warmup,
+              "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+              "config": {"workload": ddcl_workload_name(w), "tile_passes": info["n_passes"],
+                         "l2": f"one {8 << n >> 20} MiB state; 256 MiB flush before each step",
+                         "parallelism": f"replicas x{world}"},
+              "gpu_launches": args.steps * (2 * info["n_passes"] + 5),
+              "clocks": clk, "wall_s_timed_region": t_wall,
+              "paper_context": None if paper_s is None else {
+                  "gradients_per_s": 1.0 / paper_s,
+                  "source": "Table 3 fit intercept at one GPU: NVIDIA V100, Aer + cuStateVec, "
+                            f"parameter shift over {2 * w.n_params} circuits, {n} qubits, "
+                            "10 layers (another machine, another layer layout and target)"}}
+    if rank == 0:
+        result["roofline"] = adjoint_phases(sv, w, prob, theta, None, info, flush, stream,
+                                            reps=3, step=step)
+        th_host = torch.as_tensor(w.theta, dtype=torch.float64).pin_memory()
+        g_host = torch.empty(w.n_params, dtype=torch.float64).pin_memory()
+        th_dev = torch.empty_like(theta)
+        t0 = time.perf_counter()
+        reps = max(1, args.steps // 2)
+        for _ in range(reps):
+            th_dev.copy_(th_host, non_blocking=True)
+            sv.sv_grad_ddcl(prob, th_dev, target, js, grad)
+            g_host.copy_(grad, non_blocking=True)
+            stream.synchronize()
+        result["e2e"] = {"value": reps / (time.perf_counter() - t0), "unit": "gradients/s",
+                         "h2d_bytes_per_step": 8 * w.n_params, "d2h_bytes_per_step": 8 * w.n_params}
+        result["cpu_baseline"] = cpu_baseline_ddcl(w, min(args.cpu_seconds, 10.0))
+        print(json.dumps(result))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def ddcl_workload_name(w):
+    return (f"{w.name}: data-driven circuit learning gradient (JS divergence, Eq. 3), "
+            f"{w.n_qubits} qubits, {w.meta['layers']} layers, {w.n_params} params, adjoint")
+
+
 def uneven_workload_name(ws):
     return (f"qcl-uneven: adjoint gradients of {len(ws)} circuit-learning circuits (n, layers) = "
             + ", ".join(f"({w.n_qubits},{w.meta['layers']})" for w in ws)
@@ -492,15 +599,18 @@ def main():
     args = parse()
     rank, world, local = rank_info()
     if args.steps is None:
-        args.steps = {"mcvqe8": 4000, "qcl20": 20, "mcvqe28": 2, "qcl-uneven": 5}[args.workload]
+        args.steps = {"mcvqe8": 4000, "qcl20": 20, "mcvqe28": 2, "qcl-uneven": 5, "ddcl": 5}[args.workload]
     if args.warmup is None:
-        args.warmup = {"mcvqe8": 50, "qcl20": 3, "mcvqe28": 1, "qcl-uneven": 3}[args.workload]
+        args.warmup = {"mcvqe8": 50, "qcl20": 3, "mcvqe28": 1, "qcl-uneven": 3, "ddcl": 3}[args.workload]
 
     if args.impl == "reference":
         if rank != 0:
             return
         if args.workload == "mcvqe8":
             cb, workload = cpu_baseline(args.cpu_seconds), WORKLOAD
+        elif args.workload == "ddcl":
+            w = wl.ddcl(args.qubits or 26, 10)
+            cb, workload = cpu_baseline_ddcl(w, min(args.cpu_seconds, 10.0)), ddcl_workload_name(w)
         elif args.workload == "qcl-uneven":
             ws = wl.qcl_uneven()
             cb = cpu_baseline_uneven(ws, min(args.cpu_seconds, 10.0))
@@ -534,6 +644,8 @@ def main():
     stream = torch.cuda.current_stream()
     if args.workload == "qcl-uneven":
         return run_uneven(args, sv, dev, stream, dist, world, rank)
+    if args.workload == "ddcl":
+        return run_ddcl(args, sv, dev, stream, dist, world, rank)
     if args.workload != "mcvqe8":
         return run_device_memory(args, sv, dev, stream, dist, world, rank)
 

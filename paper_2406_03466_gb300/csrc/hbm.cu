@@ -924,8 +924,9 @@ __global__ void k_apply_h_big(Observable o, int n, const typename CT<Real>::T *p
 // the target P, M = (P + Q)/2, adds JS = 1/2 sum_b (P log(P/M) + Q log(Q/M))
 // to js[slot] and writes lambda_b = w_b psi_b with w_b = dJS/dQ(b) =
 // 1/2 log(Q(b)/M(b)) (0 where Q(b) = 0), so that the reverse sweep with
-// lambda gives dJS/dtheta.  FP64 throughout (Q from the state's components,
-// logarithms, sums); grid.y = slot.
+// lambda gives dJS/dtheta.  Per amplitude the arithmetic is in the state's
+// precision (FP32 for complex64, whose states carry FP32 rounding anyway;
+// FP64 for complex128); the sums over amplitudes are FP64.  grid.y = slot.
 template <typename Real>
 __global__ void k_ddcl_lambda(int n, const typename CT<Real>::T *psi, const double *target,
                               typename CT<Real>::T *lam, double *js) {
@@ -939,18 +940,19 @@ __global__ void k_ddcl_lambda(int n, const typename CT<Real>::T *psi, const doub
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < dim;
          j += (int64_t)gridDim.x * blockDim.x) {
         const C a = S[j];
-        const double q = (double)a.x * a.x + (double)a.y * a.y, p = target[j];
-        const double m = 0.5 * (p + q);
-        double w = 0.0;
-        if (p > 0.0) acc += p * log(p / m);
-        if (q > 0.0) {
-            const double l = log(q / m);
-            acc += q * l;
-            w = 0.5 * l;
+        const Real q = fmaR(a.x, a.x, a.y * a.y), p = (Real)target[j];
+        const Real m = (Real)0.5 * (p + q);
+        Real w = 0, term = 0;
+        if (p > (Real)0) term = p * log(p / m);
+        if (q > (Real)0) {
+            const Real l = log(q / m);
+            term = fmaR(q, l, term);
+            w = (Real)0.5 * l;
         }
+        acc += (double)term;
         C out;
-        out.x = (Real)(w * a.x);
-        out.y = (Real)(w * a.y);
+        out.x = w * a.x;
+        out.y = w * a.y;
         Lm[j] = out;
     }
     const double s = block_sum(acc, red);
