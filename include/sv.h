@@ -262,6 +262,23 @@ sv_status sv_grad_param_shift_noalloc(const sv_problem *problem, const double *t
                                       double *energy_out, double *loss_out, double *grad_out,
                                       sv_stream_t stream);
 
+/* A contiguous segment of the parameter-shift batch: the energies of slots
+ * [slot_begin, slot_begin + n_slots) in the order sv_param_shift_energies
+ * uses (every instance unshifted, then per parameter k: +pi/2 for every
+ * instance, -pi/2 for every instance).  This is the paper's split of the
+ * vector of circuits into one segment per virtual QPU (Sec. 4.1): each
+ * rank computes its segment, an allgather assembles the batch, and
+ * sv_param_shift_combine finishes the gradient.  out: device [n_slots]. */
+sv_status sv_param_shift_energies_range(const sv_problem *problem, const double *theta,
+                                        int32_t slot_begin, int32_t n_slots, double *out,
+                                        sv_stream_t stream);
+/* The parameter-shift combination of a whole batch of energies (device
+ * [(2P+1) I], the order above): instance energies, cost and gradient, as
+ * sv_grad_param_shift returns them.  Any output but grad_out may be NULL. */
+sv_status sv_param_shift_combine(const sv_problem *problem, const double *energies,
+                                 double *energy_out, double *loss_out, double *grad_out,
+                                 sv_stream_t stream);
+
 /* Data-driven circuit learning (Sec. 4.2, Eq. 3): the Jensen-Shannon
  * divergence JS(P | P_theta) of the circuit's output distribution
  * P_theta(b) = |<b|psi>|^2 (all qubits measured in the Z basis) from the

@@ -81,7 +81,8 @@ EXPORTED = ("sv_alloc", "sv_free", "sv_state_info", "sv_apply_circuit_batch",
             "sv_expect_pauli_sum", "sv_energies", "sv_param_shift_energies", "sv_grad_param_shift", "sv_grad_adjoint",
             "sv_grad_param_shift_plain", "sv_grad_param_shift_noalloc", "sv_autotune",
             "sv_tuned_shape", "sv_plan_info", "sv_h_plan_info", "sv_phase_timing",
-            "sv_grad_adjoint_multi", "sv_grad_ddcl",
+            "sv_grad_adjoint_multi", "sv_grad_ddcl", "sv_param_shift_energies_range",
+            "sv_param_shift_combine",
             "sv_last_phase_ms", "sv_status_string",
             "sv_last_error",
             "sv_sync_status", "sv_shutdown", "sv_version")
@@ -105,6 +106,8 @@ def _load():
     lib.sv_grad_adjoint.argtypes = [P(sv_problem), V, V, V, V, V, I32, V]
     lib.sv_grad_adjoint_multi.argtypes = [P(sv_problem), I32, P(V), P(V), P(V), P(V), V]
     lib.sv_grad_ddcl.argtypes = [P(sv_problem), V, V, V, V, V]
+    lib.sv_param_shift_energies_range.argtypes = [P(sv_problem), V, I32, I32, V, V]
+    lib.sv_param_shift_combine.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_grad_param_shift_plain.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_grad_param_shift_noalloc.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_autotune.argtypes = [P(sv_problem), V, I32, V]
@@ -381,6 +384,27 @@ def sv_grad_adjoint_multi(problems, thetas, outputs=None, stream=None):
                                       ptrs([o[0] for o in outputs]), ptrs([o[2] for o in outputs]),
                                       _stream(stream)), "sv_grad_adjoint_multi")
     return outputs
+
+
+def sv_param_shift_energies_range(problem: Problem, theta, slot_begin: int, n_slots: int,
+                                  out=None, stream=None):
+    """Energies of parameter-shift slots [slot_begin, slot_begin + n_slots)."""
+    import torch
+    if out is None:
+        out = torch.empty(max(1, n_slots), dtype=torch.float64, device=theta.device)
+    _check(_lib.sv_param_shift_energies_range(ctypes.byref(problem.struct), _ptr(theta),
+                                              int(slot_begin), int(n_slots), _ptr(out),
+                                              _stream(stream)), "sv_param_shift_energies_range")
+    return out[:n_slots]
+
+
+def sv_param_shift_combine(problem: Problem, energies, energy_out=None, loss_out=None,
+                           grad_out=None, stream=None):
+    """(loss[1], energies[I], grad[P]) from a whole parameter-shift batch of energies."""
+    e, l, g = _outputs(problem, energies.device, energy_out, loss_out, grad_out)
+    _check(_lib.sv_param_shift_combine(ctypes.byref(problem.struct), _ptr(energies), _ptr(e),
+                                       _ptr(l), _ptr(g), _stream(stream)), "sv_param_shift_combine")
+    return l, e, g
 
 
 def sv_grad_ddcl(problem: Problem, theta, target, js_out=None, grad_out=None, stream=None):

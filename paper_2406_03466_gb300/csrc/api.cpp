@@ -644,7 +644,7 @@ sv_status tiles_forward(DeviceCtx *ctx, const PlanEntry *pe, int R, sv_dtype dt,
 // Energies of n_slots slots (parameter-shift or instance slots) of states in
 // device memory, in groups of slots that fit the memory budget.
 sv_status tiles_energies(DeviceCtx *ctx, const sv_problem *p, const double *theta, int mode,
-                         int n_slots, double *E, cudaStream_t st) {
+                         int n_slots, double *E, cudaStream_t st, int slot_begin = 0) {
     const sv_dtype dt = p->dtype;
     const int c128 = dt == SV_C128, n = p->circuit->n_qubits, I = p->n_instances;
     TileCfg cfg{};
@@ -679,7 +679,7 @@ sv_status tiles_energies(DeviceCtx *ctx, const sv_problem *p, const double *thet
         src.theta = theta;
         src.inputs = p->inputs;
         src.input_stride = p->input_stride;
-        src.slot_base = (int)c0;
+        src.slot_base = slot_begin + (int)c0;
         s = tiles_forward(ctx, pe, cfg.R, dt, src, big, (char *)big + mats_off, true, nullptr, 0, st);
         if (s != SV_OK) return s;
         s = h_tiles(ctx, obs, n, dt, src.n_slots, big, nullptr, E + c0, st);
@@ -1241,11 +1241,13 @@ namespace {
 
 // Launches the batched energies of every parameter-shift slot into E[B]
 // (and, with `fc`, the gradient assembly in the same launch).
+// Energies of parameter-shift slots [slot_begin, slot_begin + B) into E[B].
 sv_status ps_energies_locked(DeviceCtx *ctx, const sv_problem *p, const double *theta, double *E,
-                             int B, cudaStream_t st, const FusedCombine *fc = nullptr) {
+                             int B, cudaStream_t st, const FusedCombine *fc = nullptr,
+                             int slot_begin = 0) {
     const int I = p->n_instances;
     if (wants_tiles(p->circuit->n_qubits, p->dtype, p->opts)) {
-        sv_status s = tiles_energies(ctx, p, theta, SLOTS_PARAM_SHIFT, B, E, st);
+        sv_status s = tiles_energies(ctx, p, theta, SLOTS_PARAM_SHIFT, B, E, st, slot_begin);
         if (s != SV_OK || !fc) return s;
         cudaError_t e = launch_ps_combine(E, fc->I, fc->P, fc->cost, fc->lp, fc->energy_out,
                                           fc->loss_out, fc->grad_out, st);
@@ -1273,6 +1275,7 @@ sv_status ps_energies_locked(DeviceCtx *ctx, const sv_problem *p, const double *
     src.theta = theta;
     src.inputs = p->inputs;
     src.input_stride = p->input_stride;
+    src.slot_base = slot_begin;
     cudaError_t e = launch_onchip_energy(p->dtype == SV_C128, sh, plan->dev, obs->dev, src, E, st,
                                          dtab, fc, &bc);
     if (e != cudaSuccess) return cuda_fail(e, "param-shift energy launch");
@@ -1301,6 +1304,45 @@ sv_status sv_param_shift_energies(const sv_problem *p, const double *theta, doub
     if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
     std::lock_guard<std::mutex> lk(ctx->mu);
     return ps_energies_locked(ctx, p, theta, out, B, (cudaStream_t)stream);
+}
+
+sv_status sv_param_shift_energies_range(const sv_problem *p, const double *theta,
+                                        int32_t slot_begin, int32_t n_slots, double *out,
+                                        sv_stream_t stream) {
+    sv_status s = check_problem(p, false);
+    if (s != SV_OK) return s;
+    if (!out && n_slots > 0) return fail(SV_ERR_ARG, "out is NULL");
+    if (p->circuit->n_params > 0 && !theta) return fail(SV_ERR_ARG, "theta is NULL");
+    int B = 0;
+    s = ps_batch_size(p, &B);
+    if (s != SV_OK) return s;
+    if (slot_begin < 0 || n_slots < 0 || (int64_t)slot_begin + n_slots > B)
+        return fail(SV_ERR_ARG, "slot range outside the parameter-shift batch of " +
+                                    std::to_string(B) + " circuits");
+    if (n_slots == 0) return SV_OK;
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return ps_energies_locked(ctx, p, theta, out, n_slots, (cudaStream_t)stream, nullptr, slot_begin);
+}
+
+sv_status sv_param_shift_combine(const sv_problem *p, const double *energies, double *energy_out,
+                                 double *loss_out, double *grad_out, sv_stream_t stream) {
+    sv_status s = check_problem(p, true);
+    if (s != SV_OK) return s;
+    if (!energies) return fail(SV_ERR_ARG, "energies is NULL");
+    const int P = p->circuit->n_params;
+    if (P > 0 && !grad_out) return fail(SV_ERR_ARG, "grad_out is NULL");
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    void *scr = nullptr;
+    s = get_scratch(ctx, st, sizeof(double) * (size_t)p->n_instances, &scr);
+    if (s != SV_OK) return s;
+    cudaError_t e = launch_ps_combine(energies, p->n_instances, P, cost_of(p, nullptr), (double *)scr,
+                                      energy_out, loss_out, grad_out, st);
+    return e == cudaSuccess ? SV_OK : cuda_fail(e, "param-shift combine launch");
 }
 
 sv_status sv_grad_param_shift(const sv_problem *p, const double *theta, double *energy_out,

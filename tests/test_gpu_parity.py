@@ -240,3 +240,27 @@ def test_repeatable(sv):
     prob = sv.Problem.from_spec(w, "c64")
     a = [sv.sv_grad_param_shift(prob, theta_of(w))[2].cpu().numpy() for _ in range(3)]
     assert all(np.array_equal(a[0], x) for x in a[1:])
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("cfg", [1, 3])
+def test_param_shift_segments_and_combine(sv, dtype, cfg):
+    """Segments of the parameter-shift batch (one per virtual QPU) assembled
+    and combined give sv_grad_param_shift's result."""
+    import torch
+    from paper_2406_03466_gb300 import vqpu
+    w = wl.config(cfg) if cfg != 3 else wl.mcvqe(14, 1, "nn+nnn", n_refs=2)
+    prob = sv.Problem.from_spec(w, dtype)
+    th = torch.as_tensor(w.theta, dtype=torch.float64, device="cuda")
+    B = (2 * w.n_params + 1) * w.n_instances
+    parts = [sv.sv_param_shift_energies_range(prob, th, *(lambda lo, hi: (lo, hi - lo))(
+        *vqpu.segment(B, 3, r))) for r in range(3)]
+    E = torch.cat(parts).contiguous()
+    l1, e1, g1 = sv.sv_param_shift_combine(prob, E)
+    l2, e2, g2 = sv.sv_grad_param_shift(prob, th)
+    tol = 1e-12 if dtype == "c128" else 1e-5
+    np.testing.assert_allclose(g1.cpu().numpy(), g2.cpu().numpy(), atol=tol * 10)
+    np.testing.assert_allclose(e1.cpu().numpy(), e2.cpu().numpy(), atol=tol)
+    np.testing.assert_allclose(l1.cpu().numpy(), l2.cpu().numpy(), atol=tol)
+    l3, e3, g3 = vqpu.param_shift_gradient(prob, th)  # single process: the whole batch
+    np.testing.assert_allclose(g3.cpu().numpy(), g2.cpu().numpy(), atol=tol * 10)
