@@ -161,6 +161,17 @@ sv_status sv_apply_circuit_batch(sv_state state, const sv_circuit *circuits, int
 sv_status sv_expect_pauli_sum(sv_state state, const sv_pauli_sum *h, int32_t n_rows,
                               double *out, sv_stream_t stream);
 
+/* Shots of row `row` of a state: every qubit measured in the Z basis (the
+ * bitstring counts a quantum backend returns, Sec. 3 and Sec. 4.2).  Shot s
+ * is the first basis index b whose cumulative probability
+ * sum_{b' <= b} |psi_b'|^2 (FP64) exceeds uniforms[s] times the total, so
+ * the draw is fixed by the caller's uniforms (device [n_shots] in [0, 1)).
+ * samples_out: device [n_shots] int64 basis indices (bit q = qubit q);
+ * counts_out: device [2^n] int64 histogram of the samples, or NULL.  Uses
+ * library scratch of 2^n / 1024 + 1 doubles. */
+sv_status sv_sample(sv_state state, int32_t row, const double *uniforms, int64_t n_shots,
+                    int64_t *samples_out, int64_t *counts_out, sv_stream_t stream);
+
 /* ------------------------------------------------------------ gradients */
 
 typedef enum {

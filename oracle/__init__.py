@@ -289,5 +289,18 @@ def ddcl_grad_finite_difference(w, theta=None, params=None, h: float = 1e-5):
     return g
 
 
+# ------------------------------------------------------------ shot sampling
+
+def sample_shots(psi, uniforms):
+    """Shots of a state measured in the Z basis with the caller's uniforms:
+    shot s is the first basis index whose cumulative probability exceeds
+    u_s times the total (FP64 probabilities |psi_b|^2)."""
+    psi = np.asarray(psi)
+    P = psi.real.astype(np.float64) ** 2 + psi.imag.astype(np.float64) ** 2
+    cdf = np.cumsum(P)
+    x = np.asarray(uniforms, dtype=np.float64) * cdf[-1]
+    return np.minimum(np.searchsorted(cdf, x, side="right"), P.size - 1), cdf
+
+
 def max_threads() -> int:
     return int(_load().orc_max_threads())

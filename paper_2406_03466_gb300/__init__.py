@@ -81,7 +81,7 @@ EXPORTED = ("sv_alloc", "sv_free", "sv_state_info", "sv_apply_circuit_batch",
             "sv_expect_pauli_sum", "sv_energies", "sv_param_shift_energies", "sv_grad_param_shift", "sv_grad_adjoint",
             "sv_grad_param_shift_plain", "sv_grad_param_shift_noalloc", "sv_autotune",
             "sv_tuned_shape", "sv_plan_info", "sv_h_plan_info", "sv_phase_timing",
-            "sv_grad_adjoint_multi", "sv_grad_ddcl", "sv_param_shift_energies_range",
+            "sv_grad_adjoint_multi", "sv_grad_ddcl", "sv_param_shift_energies_range", "sv_sample",
             "sv_param_shift_combine",
             "sv_last_phase_ms", "sv_status_string",
             "sv_last_error",
@@ -106,6 +106,7 @@ def _load():
     lib.sv_grad_adjoint.argtypes = [P(sv_problem), V, V, V, V, V, I32, V]
     lib.sv_grad_adjoint_multi.argtypes = [P(sv_problem), I32, P(V), P(V), P(V), P(V), V]
     lib.sv_grad_ddcl.argtypes = [P(sv_problem), V, V, V, V, V]
+    lib.sv_sample.argtypes = [V, I32, V, ctypes.c_int64, V, V, V]
     lib.sv_param_shift_energies_range.argtypes = [P(sv_problem), V, I32, I32, V, V]
     lib.sv_param_shift_combine.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_grad_param_shift_plain.argtypes = [P(sv_problem), V, V, V, V, V]
@@ -384,6 +385,25 @@ def sv_grad_adjoint_multi(problems, thetas, outputs=None, stream=None):
                                       ptrs([o[0] for o in outputs]), ptrs([o[2] for o in outputs]),
                                       _stream(stream)), "sv_grad_adjoint_multi")
     return outputs
+
+
+def sv_sample(state, row: int, uniforms, counts: bool = False, stream=None):
+    """Shots of one state row (Z basis): (samples int64 [S], counts int64 [2^n] or
+    None) for the caller's uniforms (float64 CUDA tensor [S] in [0, 1))."""
+    import torch
+    n = state.n_qubits
+    samples = torch.empty(max(1, uniforms.numel()), dtype=torch.int64, device=uniforms.device)
+    cnt = torch.empty(1 << n, dtype=torch.int64, device=uniforms.device) if counts else None
+    _check(_lib.sv_sample(state.handle, int(row), _ptr(uniforms), int(uniforms.numel()),
+                          _ptr(samples), _ptr(cnt), _stream(stream)), "sv_sample")
+    return samples[: uniforms.numel()], cnt
+
+
+def bitstring_counts(samples):
+    """The counts map of a shot list, flattened to arrays on the device:
+    (distinct basis indices, their counts), indices ascending."""
+    import torch
+    return torch.unique(samples, sorted=True, return_counts=True)
 
 
 def sv_param_shift_energies_range(problem: Problem, theta, slot_begin: int, n_slots: int,

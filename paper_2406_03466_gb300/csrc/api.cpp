@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "hbm.h"
+#include "sample.h"
 #include "kernels.h"
 #include "planner.h"
 #include "sv.h"
@@ -1209,6 +1210,26 @@ sv_status sv_apply_circuit_batch(sv_state state, const sv_circuit *circuits, int
         if (e != cudaSuccess) return cuda_fail(e, "apply_circuit_batch launch");
     }
     return SV_OK;
+}
+
+sv_status sv_sample(sv_state state, int32_t row, const double *uniforms, int64_t n_shots,
+                    int64_t *samples_out, int64_t *counts_out, sv_stream_t stream) {
+    if (!state) return fail(SV_ERR_ARG, "state is NULL");
+    if (row < 0 || row >= state->batch) return fail(SV_ERR_ARG, "row out of range");
+    if (n_shots < 0) return fail(SV_ERR_ARG, "n_shots < 0");
+    if (n_shots > 0 && (!uniforms || !samples_out)) return fail(SV_ERR_ARG, "uniforms/samples_out is NULL");
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    void *scr = nullptr;
+    sv_status s = get_scratch(ctx, st, sample_scratch_bytes(state->n), &scr);
+    if (s != SV_OK) return s;
+    const size_t csz = state->dtype == SV_C128 ? 16 : 8;
+    const void *psi = (const char *)state->ptr + ((size_t)row << state->n) * csz;
+    cudaError_t e = launch_sample(state->dtype == SV_C128, state->n, psi, uniforms, n_shots,
+                                  samples_out, counts_out, (double *)scr, st);
+    return e == cudaSuccess ? SV_OK : cuda_fail(e, "sampling launch");
 }
 
 sv_status sv_expect_pauli_sum(sv_state state, const sv_pauli_sum *h, int32_t n_rows, double *out,

@@ -242,3 +242,18 @@ def test_config_shapes():
         assert (w.n_qubits, len(w.gates), w.n_params, w.n_terms, w.n_instances) == (n, ng, P, T, I)
     assert wl.config(1).n_slots_param_shift == 585
     assert counts.batched_param_shift_slots(216, 256) == 110848
+
+
+def test_sample_shots_pins():
+    """The shot sampler against fixed cases: a two-outcome distribution at
+    known uniforms, a basis state, and frequencies of a Bell state."""
+    psi = np.array([0.5, np.sqrt(0.75)], dtype=complex)  # P = (0.25, 0.75)
+    s, _ = oracle.sample_shots(psi, [0.0, 0.1, 0.2499, 0.2501, 0.9, 0.999999])
+    assert list(s) == [0, 0, 0, 1, 1, 1]
+    e5 = np.zeros(16, dtype=complex); e5[5] = 1.0
+    s, _ = oracle.sample_shots(e5, np.random.default_rng(0).random(100))
+    assert np.all(s == 5)
+    bell = np.zeros(4, dtype=complex); bell[0] = bell[3] = 2 ** -0.5
+    s, _ = oracle.sample_shots(bell, np.random.default_rng(1).random(20000))
+    assert set(np.unique(s)) == {0, 3}
+    assert abs(np.mean(s == 0) - 0.5) < 0.02
