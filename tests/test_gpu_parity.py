@@ -264,3 +264,31 @@ def test_param_shift_segments_and_combine(sv, dtype, cfg):
     np.testing.assert_allclose(l1.cpu().numpy(), l2.cpu().numpy(), atol=tol)
     l3, e3, g3 = vqpu.param_shift_gradient(prob, th)  # single process: the whole batch
     np.testing.assert_allclose(g3.cpu().numpy(), g2.cpu().numpy(), atol=tol * 10)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_paper_mcvqe_circuit(sv, dtype):
+    """The paper's MC-VQE circuit (CIS references as per-instance inputs,
+    merged entanglers): parameter shift and adjoint against the oracle."""
+    import torch
+    w = wl.mcvqe_paper(8, n_refs=3, seed=2)
+    L, E, g = oracle.grad_param_shift(w)
+    prob = sv.Problem.from_spec(w, dtype)
+    th = torch.as_tensor(w.theta, dtype=torch.float64, device="cuda")
+    tol = {"c128": (1e-12, 1e-12), "c64": (1e-5, 1e-4)}[dtype]
+    for fn in (sv.sv_grad_param_shift, sv.sv_grad_adjoint):
+        l_, e_, g_ = fn(prob, th)
+        close(e_.cpu().numpy(), E, tol[0])
+        close(g_.cpu().numpy()[: w.n_params], g, tol[1])
+
+
+def test_paper_mcvqe_circuit_tiles(sv):
+    import torch
+    w = wl.mcvqe_paper(16, n_refs=2, seed=4)
+    prob = sv.Problem.from_spec(w, "c64")
+    th = torch.as_tensor(w.theta, dtype=torch.float64, device="cuda")
+    l_, e_, g_ = sv.sv_grad_adjoint(prob, th)
+    ks = [0, 11, 40, 75]
+    _, E, gs = oracle.grad_param_shift(w, params=ks)
+    close(e_.cpu().numpy(), E, 1e-5)
+    close(g_.cpu().numpy()[ks], gs, 1e-4)

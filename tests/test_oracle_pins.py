@@ -7,6 +7,7 @@ the variational bound of Eq. 1, parameter shift against finite differences,
 the closed-form energy of the MC-VQE ansatz at theta = 0, and the circuit
 counts printed in Tables 1 and 2.
 """
+import dataclasses
 import os
 
 import numpy as np
@@ -257,3 +258,34 @@ def test_sample_shots_pins():
     s, _ = oracle.sample_shots(bell, np.random.default_rng(1).random(20000))
     assert set(np.unique(s)) == {0, 3}
     assert abs(np.mean(s == 0) - 0.5) < 0.02
+
+
+def test_paper_mcvqe_circuit_reproduces_table1():
+    """The paper-exact MC-VQE circuit (CIS references, 6-Ry/2-CNOT entanglers
+    with merged rotations) has Table 1's N_H and N_theta; each parameter sits
+    in exactly one gate."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "mcvqe_table1_counts.txt"), dtype=np.int64)
+    for nq, nh, nth, circ in rows:
+        w = wl.mcvqe_paper(int(nq))
+        assert (w.n_terms, w.n_params, 2 * w.n_terms * w.n_params) == (nh, nth, circ)
+        params = [g.param for g in w.gates if g.op in ("RX", "RY", "RZ")]
+        assert sorted(params) == list(range(w.n_params))
+
+
+def test_cis_preparation_closed_form():
+    """The CIS preparation alone gives sum_i c_i |e_i> with the closed-form c."""
+    n = 6
+    w = wl.mcvqe_paper(n, n_refs=3, seed=7)
+    prep = dataclasses.replace(w, gates=wl.cis_prep_gates(n), n_params=0, theta=np.zeros(0))
+    for r in range(3):
+        psi = oracle.state(prep, instance=r)
+        c = wl.cis_coefficients(w.meta["beta"][r])
+        want = np.zeros(1 << n); want[[1 << i for i in range(n)]] = c
+        np.testing.assert_allclose(psi, want, atol=1e-14)
+        assert abs(np.sum(c ** 2) - 1) < 1e-14
+
+
+def test_paper_mcvqe_gradient_finite_differences():
+    w = wl.mcvqe_paper(5, n_refs=2, seed=3)
+    L, E, g = oracle.grad_param_shift(w)
+    np.testing.assert_allclose(g, oracle.grad_finite_difference(w, h=1e-5), atol=1e-8)

@@ -220,6 +220,89 @@ def mcvqe(n: int = 8, layers: int = 4, pairs: str = "all", n_refs: Optional[int]
                     meta={"pairs": pairs, "layers": layers})
 
 
+def cis_prep_gates(n: int) -> List[Gate]:
+    """Preparation of a CIS-like state sum_i c_i |e_i> (a generalised W
+    state, Sec. 4.1) from |e_0>: for i = 0..n-2 a controlled Ry(beta_i) from
+    qubit i to qubit i+1, written as Ry(beta_i/2) CNOT Ry(-beta_i/2) CNOT on
+    the target, then CNOT(i+1 -> i), which moves the excitation on.  The
+    angles are per instance: Ry(arcsin x) gates read x = +-sin(beta_i/2) from
+    input columns 2i and 2i+1, so beta_i is in [-pi, pi] and
+    c_i = prod_{j<i} sin(beta_j/2) cos(beta_i/2), c_{n-1} = prod_j sin(beta_j/2)."""
+    out: List[Gate] = []
+    for i in range(n - 1):
+        out.append(Gate("ENC_RY_ASIN", target=i + 1, param=2 * i))
+        out.append(Gate("CNOT", target=i + 1, control=i))
+        out.append(Gate("ENC_RY_ASIN", target=i + 1, param=2 * i + 1))
+        out.append(Gate("CNOT", target=i + 1, control=i))
+        out.append(Gate("CNOT", target=i, control=i + 1))
+    return out
+
+
+def cis_coefficients(beta: np.ndarray) -> np.ndarray:
+    """The c_i that cis_prep_gates prepares from angles beta (closed form)."""
+    n = len(beta) + 1
+    c = np.zeros(n)
+    run = 1.0
+    for i in range(n - 1):
+        c[i] = run * np.cos(beta[i] / 2)
+        run *= np.sin(beta[i] / 2)
+    c[n - 1] = run
+    return c
+
+
+def mcvqe_entanglers(n: int) -> List[Gate]:
+    """Entanglers U_AB of Sec. 4.1 on adjacent monomers (A, A+1), in order:
+    Ry Ry, CNOT(A -> B), Ry Ry, CNOT(A -> B), Ry Ry (6 Ry, 2 CNOT; the
+    layout figure is lost, this is a reading).  The last Ry of qubit B in
+    U_(A,B) and the first of B in U_(B,C) act back to back, so they merge
+    (Ry(a)Ry(b) = Ry(a+b), Sec. 4.1) into one parameter: N_theta = 5N - 4
+    (Table 1)."""
+    out: List[Gate] = []
+    p = 0
+    last_on = {}
+    for a in range(n - 1):
+        b = a + 1
+        # first pair of rotations: qubit a's merges into the previous
+        # entangler's last rotation of a (already in place), so it is omitted
+        if a not in last_on:
+            out.append(Gate("RY", target=a, param=p)); p += 1
+        out.append(Gate("RY", target=b, param=p)); p += 1
+        out.append(Gate("CNOT", target=b, control=a))
+        out.append(Gate("RY", target=a, param=p)); p += 1
+        out.append(Gate("RY", target=b, param=p)); p += 1
+        out.append(Gate("CNOT", target=b, control=a))
+        out.append(Gate("RY", target=a, param=p)); p += 1
+        last_on[b] = True
+        out.append(Gate("RY", target=b, param=p)); p += 1
+    return out
+
+
+def mcvqe_paper(n: int = 16, n_refs: int = 4, seed: int = 0) -> Workload:
+    """The paper's MC-VQE circuit (Sec. 4.1, Table 1): per reference a CIS
+    state prepared from |e_0> (angles beta ~ U(-pi, pi) per reference, as
+    inputs), then the shared entanglers over adjacent monomers; the Eq. 2
+    Hamiltonian over nearest neighbours (N_H = 6N - 4); cost: the average of
+    the reference energies.  The CIS coefficients of the paper come from
+    quantum-chemistry runs and are not published: these stand in for them."""
+    rng = np.random.default_rng(seed)
+    pairs = [(a, a + 1) for a in range(n - 1)]
+    terms = spin_hamiltonian_terms(n, pairs)
+    coeffs = spin_hamiltonian_coeffs(rng, n, len(pairs))
+    letters = letters_from_terms(n, terms)
+    ent = mcvqe_entanglers(n)
+    P = 1 + max(g.param for g in ent if g.param >= 0)
+    theta = rng.uniform(-np.pi, np.pi, P)
+    beta = rng.uniform(-np.pi, np.pi, (n_refs, n - 1))
+    x = np.zeros((n_refs, 2 * (n - 1)))
+    x[:, 0::2] = np.sin(beta / 2)
+    x[:, 1::2] = -np.sin(beta / 2)
+    return Workload(name=f"mcvqe_paper{n}", n_qubits=n, gates=cis_prep_gates(n) + ent, n_params=P,
+                    theta=theta, pauli_letters=letters, pauli_coeffs=coeffs,
+                    refs=np.full(n_refs, 1, dtype=np.int64), inputs=x,
+                    weights=np.full(n_refs, 1.0 / n_refs), cost="linear",
+                    meta={"beta": beta, "pairs": "nn"})
+
+
 def qcl(n: int = 12, layers: int = 6, n_samples: int = 256, seed: int = 0,
         noise_sd: float = 0.05) -> Workload:
     """Quantum circuit learning regression (paper Sec. 4.2 use-case family).
