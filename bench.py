@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true", help="skip adjoint/plain/c128 side runs")
+    ap.add_argument("--energy-shape", default="",
+                    help="mcvqe8 only: 'R,T' pins the energy kernel to R register bits and T "
+                         "threads per block instead of autotuning (for profiler captures)")
     ap.add_argument("--qubits", type=int, default=0,
                     help="qcl20 / mcvqe28 only: the same workload family at this qubit count "
                          "(a smaller case for profiler captures; not a bench line)")
@@ -651,15 +654,22 @@ def main():
 
     w = wl.config(1)
     B = w.n_slots_param_shift
-    prob = sv.Problem.from_spec(w, "c64", device=dev)
+    shape_opts = None
+    if args.energy_shape:
+        R_, T_ = (int(x) for x in args.energy_shape.split(","))
+        shape_opts = sv.plan_opts(reg_bits=R_, threads_per_block=T_)
+    prob = sv.Problem.from_spec(w, "c64", device=dev, opts=shape_opts)
     theta = torch.as_tensor(w.theta, dtype=torch.float64, device=dev)
     out = sv._outputs(prob, dev, None, None, None)
     e_buf = torch.empty(B, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     # launch shapes (register bits, threads per block) picked by timing
-    sv.sv_autotune(prob, theta)
-    tuned = {"energy": sv.sv_tuned_shape(prob, 1)[:2], "adjoint": sv.sv_tuned_shape(prob, 2)[:2]}
+    if shape_opts is None:
+        sv.sv_autotune(prob, theta)
+        tuned = {"energy": sv.sv_tuned_shape(prob, 1)[:2], "adjoint": sv.sv_tuned_shape(prob, 2)[:2]}
+    else:
+        tuned = {"energy": (R_, T_), "adjoint": (R_, T_)}
 
     def step():
         sv.sv_grad_param_shift(prob, theta, *out)

@@ -564,6 +564,16 @@ __device__ void ps_combine_block(const double *E, int I, int P, const CostSource
 // independent 16-byte loads from every thread and points the program and
 // observable views at the copies.  The pointers are derived from the shared
 // array unconditionally, so every later read compiles to a shared load.
+__device__ __forceinline__ void bc_cp16(void *sdst, const void *gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void bc_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// The copies are asynchronous (cp.async, all in flight at once): the
+// program, observable and thread bases form the first group and are waited
+// for here; the diagonal tables (piece 6) form a second group, which
+// finish_block_const waits for before the epilogue reads them.
 template <int kMode>
 __device__ __forceinline__ void stage_block_const(const BlockConst &bc, unsigned char *smem,
                                                   Program &p, Observable &o) {
@@ -571,10 +581,19 @@ __device__ __forceinline__ void stage_block_const(const BlockConst &bc, unsigned
     unsigned char *base = smem + bc.base;
 #pragma unroll
     for (int k = 0; k < kBlockConst; ++k) {
+        if (k == 6) continue;
         uint4 *dst = reinterpret_cast<uint4 *>(base + bc.off[k]);
         const uint4 *src = bc.src[k];
-        for (uint32_t i = threadIdx.x; i < bc.n16[k]; i += blockDim.x) dst[i] = __ldg(src + i);
+        for (uint32_t i = threadIdx.x; i < bc.n16[k]; i += blockDim.x) bc_cp16(dst + i, src + i);
     }
+    bc_commit();
+    {
+        uint4 *dst = reinterpret_cast<uint4 *>(base + bc.off[6]);
+        const uint4 *src = bc.src[6];
+        for (uint32_t i = threadIdx.x; i < bc.n16[6]; i += blockDim.x) bc_cp16(dst + i, src + i);
+    }
+    bc_commit();
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
     __syncthreads();
     p.stages = reinterpret_cast<const Stage *>(base + bc.off[0]);
     p.ops = reinterpret_cast<const Op *>(base + bc.off[1]);
@@ -583,6 +602,13 @@ __device__ __forceinline__ void stage_block_const(const BlockConst &bc, unsigned
     o.tgroups = reinterpret_cast<const TermGroup *>(base + bc.off[4]);
     o.terms = reinterpret_cast<const Term *>(base + bc.off[5]);
     if constexpr (kMode == 2) p.tbase = reinterpret_cast<const ThreadBase *>(base + bc.off[7]);
+}
+
+// Waits for the diagonal tables staged by stage_block_const (all threads).
+template <int kMode> __device__ __forceinline__ void finish_block_const() {
+    if constexpr (kMode == 0) return;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
 }
 
 __device__ double cost_weight(const CostSource &c, int inst, double E) {

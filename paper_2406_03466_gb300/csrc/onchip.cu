@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(512) k_energy(Program p, Observable o, SlotSou
     for (int g = tid; g < p.n_groups; g += Ts) group_matrix<Real, C>(p, g, si, mats + 4 * g);
     __syncthreads();
     forward_stages<Real, R, kMode>(p, st, mats, tid, si.ref);
+    finish_block_const<kMode>();  // the diagonal tables, copied during the stages
     double e;
     if (kMode > 0 && bc.n16[6]) {  // diagonal tables staged in shared memory
         const C *tab = reinterpret_cast<const C *>(smem + bc.base + bc.off[6]);
@@ -125,6 +126,7 @@ __global__ void __launch_bounds__(512) k_adjoint(Program p, Observable o, SlotSo
     constexpr int NA = 1 << R;
     extern __shared__ __align__(16) unsigned char smem[];
     stage_block_const<kMode>(bc, smem, p, o);
+    finish_block_const<kMode>();
     const int n = p.n, shb = n - R, Ts = 1 << shb;
     const int ls = threadIdx.x >> shb, tid = threadIdx.x & (Ts - 1);
     const int b = blockIdx.x * sh.S + ls;
