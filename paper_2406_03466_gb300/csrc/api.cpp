@@ -1480,6 +1480,13 @@ sv_status sv_grad_adjoint(const sv_problem *p, const double *theta, const double
     BlockConst bc{};
     s = plan_and_shape(ctx, ONCHIP_ADJOINT, *p->circuit, p->dtype, I, p->opts, &plan, &sh,
                        find_tuned(ctx, p, ONCHIP_ADJOINT, I), obs, nullptr, &bc);
+    // A deep circuit whose per-group reduced-matrix buffers leave no room for
+    // one slot in shared memory runs as tile passes instead (a state of
+    // n >= 7 qubits has at least two tiles' worth of amplitudes to split).
+    if (s == SV_ERR_UNSUPPORTED && p->circuit->n_qubits >= 7 &&
+        !(p->opts && (p->opts->reg_bits > 0 || p->opts->threads_per_block > 0)))
+        return tiles_adjoint(ctx, p, theta, weights, energy_out, loss_out, grad_out,
+                             checkpoint_every, st);
     if (s != SV_OK) return s;
     const void *drefs = nullptr;
     s = get_array(ctx, p->refs, sizeof(int64_t) * I, &drefs);

@@ -416,7 +416,9 @@ __device__ double expect_partial(const Observable &o, const typename CT<Real>::T
     constexpr int NA = 1 << R;
     uint32_t v[R];
     const uint32_t s0 = natural_vectors<R>(tid, sh, w, v);
+    constexpr int kRun = 8;  // groups per FP32 run, as in expect_table
     double e = 0.0;
+    Real run = 0;
     for (int g = 0; g < o.n_tgroups; ++g) {
         const TermGroup tg = o.tgroups[g];
         C wv[NA];
@@ -444,9 +446,13 @@ __device__ double expect_partial(const Observable &o, const typename CT<Real>::T
             const Real c = (Real)((tm.phase == 1 || tm.phase == 2) ? -tm.coeff : tm.coeff);
             gacc = fmaR(c, acc, gacc);
         }
-        e += (double)gacc;
+        run += gacc;
+        if ((g + 1) % kRun == 0) {
+            e += (double)run;
+            run = 0;
+        }
     }
-    return e;
+    return e + (double)run;
 }
 
 // Same sum from precomputed diagonals: for each X-mask group g,
@@ -463,22 +469,28 @@ __device__ double expect_table(const Observable &o, const typename CT<Real>::T *
     C pj[NA];
 #pragma unroll
     for (int k = 0; k < NA; ++k) pj[k] = st[s0 ^ xsel<R>(k, v)];
+    // runs of kRun groups are summed in the state's precision (at most
+    // kRun * NA products), the runs in FP64: FP64 adds are scarce on this GPU
+    constexpr int kRun = 8;
     double e = 0.0;
+    Real run = 0;
     for (int g = 0; g < o.n_tgroups; ++g) {
         const uint32_t sx = o.tgroups[g].sx;
         const C *D = dtab + (size_t)g * dim + tid;
-        Real acc = 0;
 #pragma unroll
         for (int k = 0; k < NA; ++k) {
             const C px = st[s0 ^ xsel<R>(k, v) ^ sx];
             const C d = D[(size_t)k << sh];  // shared memory when staged, else global
             const Real wr = fmaR(px.x, pj[k].x, px.y * pj[k].y);
             const Real wi = fmaR(px.x, pj[k].y, -px.y * pj[k].x);
-            acc = fmaR(wr, d.x, fmaR(-wi, d.y, acc));
+            run = fmaR(wr, d.x, fmaR(-wi, d.y, run));
         }
-        e += (double)acc;
+        if ((g + 1) % kRun == 0) {
+            e += (double)run;
+            run = 0;
+        }
     }
-    return e;
+    return e + (double)run;
 }
 
 // lambda = H psi for this thread's amplitudes; returns sum Re(conj(psi_j) lambda_j).
@@ -662,17 +674,16 @@ __device__ void group_gradients(const Program &p, int g, const double *rho8, con
 }
 
 // Reverse of bit_ops_fwd for bits I, I-1, ..., 0: per op, the partial reduced
-// matrix of bit I (reduced over the warp, written to rw[u]) then the inverse
-// gate on psi and lambda.  u counts the stage's ops downwards.
+// matrix of bit I (reduced over the warp, written to rw[group][warp]) then
+// the inverse gate on psi and lambda.
 template <typename C, typename Real, int R, int I>
 __device__ __forceinline__ void bit_ops_rev(const Program &p, const Stage *sg, const C *mats,
-                                            C (&a)[1 << R], C (&al)[1 << R], int &u, int width,
+                                            C (&a)[1 << R], C (&al)[1 << R], int width,
                                             int tid, int wps, Real *rw) {
     if constexpr (I >= 0) {
         const int b0 = sg->op_begin + sg->bit_begin[I];
         for (int o = sg->op_begin + sg->bit_begin[I + 1] - 1; o >= b0; --o) {
             const Op op = p.ops[o];
-            --u;
             const Group grp = p.groups[op.group];
             if (grp.has_param) {
                 Real rh[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -682,7 +693,7 @@ __device__ __forceinline__ void bit_ops_rev(const Program &p, const Stage *sg, c
                     for (int off = width >> 1; off > 0; off >>= 1)
                         rh[v] += __shfl_xor_sync(0xffffffffu, rh[v], off);
                 if ((tid & 31) == 0) {
-                    Real *dst = rw + (u * wps + (tid >> 5)) * 8;
+                    Real *dst = rw + (op.group * wps + (tid >> 5)) * 8;
 #pragma unroll
                     for (int v = 0; v < 8; ++v) dst[v] = rh[v];
                 }
@@ -697,20 +708,20 @@ __device__ __forceinline__ void bit_ops_rev(const Program &p, const Stage *sg, c
                 u1_bit<C, R, I>(al, d0, d1, d2, d3);
             }
         }
-        bit_ops_rev<C, Real, R, I - 1>(p, sg, mats, a, al, u, width, tid, wps, rw);
+        bit_ops_rev<C, Real, R, I - 1>(p, sg, mats, a, al, width, tid, wps, rw);
     }
 }
 
 // Reverse sweep over every stage of `p` on psi and lambda (both in shared
 // memory, natural order, swizzled): un-applies each stage, and for every
-// fused group with parameters adds the reduced matrix
-// rho_ab = sum psi_a conj(lambda_b) at the point after the group into
-// rho[group][8] (FP64).  `rhow`: two buffers of kMaxGroupOpsPerStage x
-// (warps per slot) x 8 partials.  Called by all threads of the slot.
+// fused group with parameters writes the warp sums of its reduced matrix
+// rho_ab = sum psi_a conj(lambda_b) at the point after the group to
+// rw[group][warp][8] (each group occurs once); fold_rho then sums the warps
+// in FP64.  Called by all threads of the slot.
 template <typename Real, int R, int kMode>
 __device__ void reverse_stages(const Program &p, typename CT<Real>::T *psi,
                                typename CT<Real>::T *lam, const typename CT<Real>::T *mats,
-                               int tid, int Ts, Real *rhow, double *rho) {
+                               int tid, int Ts, Real *rw) {
     using C = typename CT<Real>::T;
     constexpr int NA = 1 << R;
     const int wps = Ts >= 32 ? (Ts >> 5) : 1;
@@ -735,15 +746,12 @@ __device__ void reverse_stages(const Program &p, typename CT<Real>::T *psi,
             a[r] = psi[ad];
             al[r] = lam[ad];
         }
-        Real *rw = rhow + (s & 1) * (kMaxGroupOpsPerStage * wps * 8);
-        int u = sg->n_u1;
         if (sg->sorted)
-            bit_ops_rev<C, Real, R, R - 1>(p, sg, mats, a, al, u, width, tid, wps, rw);
+            bit_ops_rev<C, Real, R, R - 1>(p, sg, mats, a, al, width, tid, wps, rw);
         else
         for (int oi = sg->op_end - 1; oi >= sg->op_begin; --oi) {
             const Op op = p.ops[oi];
             if (op.kind == OP_U1) {
-                --u;
                 if (p.groups[op.group].has_param) {
                     Real rh[8] = {0, 0, 0, 0, 0, 0, 0, 0};
                     rho_reg<C, Real, R>(a, al, op.a, rh);
@@ -752,7 +760,7 @@ __device__ void reverse_stages(const Program &p, typename CT<Real>::T *psi,
                         for (int off = width >> 1; off > 0; off >>= 1)
                             rh[v] += __shfl_xor_sync(0xffffffffu, rh[v], off);
                     if ((tid & 31) == 0) {
-                        Real *dst = rw + (u * wps + (tid >> 5)) * 8;
+                        Real *dst = rw + (op.group * wps + (tid >> 5)) * 8;
 #pragma unroll
                         for (int v = 0; v < 8; ++v) dst[v] = rh[v];
                     }
@@ -774,28 +782,20 @@ __device__ void reverse_stages(const Program &p, typename CT<Real>::T *psi,
             lam[ad] = al[r];
         }
         __syncthreads();
-        // Fold the per-warp partials of every group op of this stage (a slot
-        // may have fewer threads than the stage has group ops).
-        for (int uu = tid; uu < sg->n_u1; uu += Ts) {
-            int cnt = 0, gi = -1;
-            for (int oi = sg->op_begin; oi < sg->op_end; ++oi) {
-                const Op op = p.ops[oi];
-                if (op.kind != OP_U1) continue;
-                if (cnt == uu) {
-                    gi = op.group;
-                    break;
-                }
-                ++cnt;
-            }
-            if (gi >= 0 && p.groups[gi].has_param) {
-#pragma unroll
-                for (int v = 0; v < 8; ++v) {
-                    double acc = 0.0;
-                    for (int wi = 0; wi < wps; ++wi) acc += (double)rw[(uu * wps + wi) * 8 + v];
-                    rho[gi * 8 + v] += acc;
-                }
-            }
-        }
+    }
+}
+
+// rho[g][v] = sum over the warps of rw[g][warp][v] in FP64, for the groups
+// with parameters.  Called by all threads of the slot after reverse_stages.
+template <typename Real>
+__device__ void fold_rho(const Program &p, const Real *rw, int tid, int Ts, double *rho) {
+    const int wps = Ts >= 32 ? (Ts >> 5) : 1;
+    for (int q = tid; q < 8 * p.n_groups; q += Ts) {
+        const int g = q >> 3, v = q & 7;
+        double acc = 0.0;
+        if (p.groups[g].has_param)
+            for (int w = 0; w < wps; ++w) acc += (double)rw[(g * wps + w) * 8 + v];
+        rho[q] = acc;
     }
 }
 

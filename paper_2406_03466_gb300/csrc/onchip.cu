@@ -144,14 +144,14 @@ __global__ void __launch_bounds__(512) k_adjoint(Program p, Observable o, SlotSo
     const SlotInfo si = resolve(src, live ? b : 0);
     for (int g = tid; g < G; g += Ts) group_matrix<Real, C>(p, g, si, mats + 4 * g);
     for (int q = tid; q < P; q += Ts) grad[q] = 0.0;
-    for (int q = tid; q < 8 * G; q += Ts) rho[q] = 0.0;
     __syncthreads();
     forward_stages<Real, R, kMode>(p, psi, mats, tid, si.ref);
     double e = apply_h<Real, R>(o, psi, lam, tid, shb, p.swz_bits);
     e = slot_sum(e, Ts, red);
     __syncthreads();
 
-    reverse_stages<Real, R, kMode>(p, psi, lam, mats, tid, Ts, rhow, rho);
+    reverse_stages<Real, R, kMode>(p, psi, lam, mats, tid, Ts, rhow);
+    fold_rho<Real>(p, rhow, tid, Ts, rho);
     __syncthreads();
     for (int g = tid; g < G; g += Ts)
         if (p.groups[g].has_param) group_gradients<Real>(p, g, rho + 8 * g, si, grad);
@@ -271,7 +271,7 @@ const char *onchip_shape(int kind, int n, int n_groups, int n_params, int c128, 
         if (kind == ONCHIP_ADJOINT) {
             s.st_rho = up16((size_t)n_groups * 8 * 8);
             s.st_grad = up16((size_t)n_params * 8);
-            s.st_rhow = up16((size_t)2 * kMaxGroupOpsPerStage * wps * 8 * rsz);
+            s.st_rhow = up16((size_t)n_groups * wps * 8 * rsz);  // [group][warp][8]
             s.off_rho = (uint32_t)off;
             off += (size_t)S * s.st_rho;
             s.off_grad = (uint32_t)off;
