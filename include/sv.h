@@ -220,6 +220,17 @@ sv_status sv_grad_param_shift(const sv_problem *problem, const double *theta,
                               double *energy_out, double *loss_out, double *grad_out,
                               sv_stream_t stream);
 
+/* sv_grad_param_shift with host buffers, synchronous: copies theta (host
+ * [P], any host memory) through library-owned pinned staging to the device,
+ * runs the same fused launch, copies loss, gradient and instance energies
+ * back in one transfer and waits for `stream` before returning.
+ * energy_host: [n_instances] or NULL; loss_host: [1] or NULL; grad_host: [P].
+ * Uses (2P + 1 + I) doubles of pinned host and device staging per stream
+ * besides the scratch of sv_grad_param_shift. */
+sv_status sv_grad_param_shift_host(const sv_problem *problem, const double *theta_host,
+                                   double *energy_host, double *loss_host, double *grad_host,
+                                   sv_stream_t stream);
+
 /* Adjoint (reverse-sweep) gradient, same result as sv_grad_param_shift:
  * lambda = H psi, then for each gate in reverse order the derivative
  * Im <lambda| G psi> of its generator G, psi <- U^dag psi, lambda <- U^dag lambda.

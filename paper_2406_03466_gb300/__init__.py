@@ -103,6 +103,7 @@ def _load():
     lib.sv_energies.argtypes = [P(sv_problem), V, V, V, V]
     lib.sv_param_shift_energies.argtypes = [P(sv_problem), V, V, V]
     lib.sv_grad_param_shift.argtypes = [P(sv_problem), V, V, V, V, V]
+    lib.sv_grad_param_shift_host.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_grad_adjoint.argtypes = [P(sv_problem), V, V, V, V, V, I32, V]
     lib.sv_grad_adjoint_multi.argtypes = [P(sv_problem), I32, P(V), P(V), P(V), P(V), V]
     lib.sv_grad_ddcl.argtypes = [P(sv_problem), V, V, V, V, V]
@@ -356,6 +357,22 @@ def sv_grad_param_shift(problem: Problem, theta, energy_out=None, loss_out=None,
     e, l, g = _outputs(problem, theta.device, energy_out, loss_out, grad_out)
     _check(_lib.sv_grad_param_shift(ctypes.byref(problem.struct), _ptr(theta), _ptr(e), _ptr(l),
                                     _ptr(g), _stream(stream)), "sv_grad_param_shift")
+    return l, e, g
+
+
+def sv_grad_param_shift_host(problem: Problem, theta, energy_out=None, loss_out=None,
+                             grad_out=None, stream=None):
+    """sv_grad_param_shift with host (CPU) float64 tensors in and out; returns
+    once the results are in host memory.  (loss[1], energies[I], grad[P])."""
+    import torch
+    for t in (theta, energy_out, loss_out, grad_out):
+        if t is not None and (t.device.type != "cpu" or t.dtype != torch.float64
+                              or not t.is_contiguous()):
+            raise ValueError("sv_grad_param_shift_host takes contiguous float64 CPU tensors")
+    e, l, g = _outputs(problem, torch.device("cpu"), energy_out, loss_out, grad_out)
+    _check(_lib.sv_grad_param_shift_host(ctypes.byref(problem.struct), _ptr(theta), _ptr(e),
+                                         _ptr(l), _ptr(g), _stream(stream)),
+           "sv_grad_param_shift_host")
     return l, e, g
 
 

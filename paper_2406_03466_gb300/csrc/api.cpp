@@ -118,6 +118,18 @@ struct DeviceCtx {
     // stream the captures run on.
     std::unordered_map<uint64_t, std::unique_ptr<struct MultiGraph>> graphs;
     cudaStream_t capture_stream = nullptr;
+    // Host-buffer entry points: pinned host and device staging per stream.
+    std::unordered_map<cudaStream_t, std::unique_ptr<struct HostIO>> hostio;
+};
+
+struct HostIO {
+    void *host = nullptr;  // pinned
+    void *dev = nullptr;
+    size_t bytes = 0;
+    ~HostIO() {
+        if (host) cudaFreeHost(host);
+        if (dev) cudaFree(dev);
+    }
 };
 
 struct MultiGraph {
@@ -337,6 +349,26 @@ sv_status get_scratch(DeviceCtx *ctx, cudaStream_t st, size_t bytes, void **out)
         s->bytes = want;
     }
     *out = s->ptr;
+    return SV_OK;
+}
+
+// Pinned host + device staging of `bytes` for one stream, grown on demand
+// (growth synchronizes the stream).
+sv_status get_hostio(DeviceCtx *ctx, cudaStream_t st, size_t bytes, HostIO **out) {
+    auto &h = ctx->hostio[st];
+    if (!h) h.reset(new HostIO());
+    if (h->bytes < bytes) {
+        SV_CUDA(cudaStreamSynchronize(st));
+        if (h->host) cudaFreeHost(h->host);
+        if (h->dev) cudaFree(h->dev);
+        h->host = h->dev = nullptr;
+        h->bytes = 0;
+        const size_t want = bytes < 4096 ? 4096 : bytes;
+        SV_CUDA(cudaMallocHost(&h->host, want));
+        SV_CUDA(cudaMalloc(&h->dev, want));
+        h->bytes = want;
+    }
+    *out = h.get();
     return SV_OK;
 }
 
@@ -1396,6 +1428,56 @@ sv_status sv_grad_param_shift(const sv_problem *p, const double *theta, double *
     fc.loss_out = loss_out;
     fc.grad_out = grad_out;
     return ps_energies_locked(ctx, p, theta, E, B, st, &fc);
+}
+
+sv_status sv_grad_param_shift_host(const sv_problem *p, const double *theta_host,
+                                   double *energy_host, double *loss_host, double *grad_host,
+                                   sv_stream_t stream) {
+    sv_status s = check_problem(p, true);
+    if (s != SV_OK) return s;
+    const int P = p->circuit->n_params, I = p->n_instances;
+    if (P > 0 && (!theta_host || !grad_host)) return fail(SV_ERR_ARG, "theta/grad is NULL");
+    int B = 0;
+    s = ps_batch_size(p, &B);
+    if (s != SV_OK) return s;
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    // staging, in doubles: [theta P][loss 1][grad P][energies I]
+    const size_t nP = (size_t)(P > 0 ? P : 1), n_out = 1 + nP + (size_t)I;
+    HostIO *io = nullptr;
+    s = get_hostio(ctx, st, sizeof(double) * (nP + n_out), &io);
+    if (s != SV_OK) return s;
+    void *scr = nullptr;
+    s = get_scratch(ctx, st, sizeof(double) * ((size_t)B + I), &scr);
+    if (s != SV_OK) return s;
+    unsigned *counter = nullptr;
+    s = get_counter(ctx, st, &counter);
+    if (s != SV_OK) return s;
+    double *h = (double *)io->host, *d = (double *)io->dev;
+    if (P > 0) {
+        std::memcpy(h, theta_host, sizeof(double) * P);
+        SV_CUDA(cudaMemcpyAsync(d, h, sizeof(double) * P, cudaMemcpyHostToDevice, st));
+    }
+    double *E = (double *)scr;
+    FusedCombine fc{};
+    fc.counter = counter;
+    fc.I = I;
+    fc.P = P;
+    fc.cost = cost_of(p, nullptr);
+    fc.lp = E + B;
+    fc.loss_out = d + nP;
+    fc.grad_out = d + nP + 1;
+    fc.energy_out = d + 2 * nP + 1;
+    s = ps_energies_locked(ctx, p, d, E, B, st, &fc);
+    if (s != SV_OK) return s;
+    SV_CUDA(cudaMemcpyAsync(h + nP, d + nP, sizeof(double) * n_out, cudaMemcpyDeviceToHost, st));
+    SV_CUDA(cudaStreamSynchronize(st));
+    if (loss_host) *loss_host = h[nP];
+    if (P > 0) std::memcpy(grad_host, h + nP + 1, sizeof(double) * P);
+    if (energy_host) std::memcpy(energy_host, h + 2 * nP + 1, sizeof(double) * I);
+    return SV_OK;
 }
 
 sv_status sv_energies(const sv_problem *p, const double *theta, double *energy_out,

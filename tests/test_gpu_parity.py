@@ -5,6 +5,7 @@ complex64 paths <= 1e-5 on energies and losses, <= 1e-4 on gradients,
 2e-5 on amplitudes (products in FP32, reductions in FP64).
 """
 import ctypes
+import dataclasses
 
 import numpy as np
 import pytest
@@ -232,6 +233,38 @@ def test_energies_entry(sv):
     B = sv.sv_param_shift_energies(prob, theta_of(w)).cpu().numpy()
     inst, sp, sh = oracle.param_shift_slots(w)
     close(B, oracle.energies(w, None, inst, sp, sh), 1e-5)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("n", [8, 14])
+def test_param_shift_host_buffers(sv, dtype, n):
+    """The host-buffer entry point against the oracle, on chip (8 qubits) and
+    as tile passes (14 qubits); bitwise equal to the device-buffer call on
+    chip (the tile passes sum energies with FP64 atomics, in any order)."""
+    import torch
+    w = wl.mcvqe(n, 2) if n == 8 else wl.mcvqe(n, 2, "nn+nnn", n_refs=2)
+    L, E, g = oracle.grad_param_shift(w)
+    prob = sv.Problem.from_spec(w, dtype)
+    th = torch.as_tensor(w.theta, dtype=torch.float64)
+    l_, e_, g_ = sv.sv_grad_param_shift_host(prob, th)
+    assert l_.device.type == "cpu" and g_.device.type == "cpu"
+    close(e_.numpy(), E, TOL[dtype]["E"])
+    close(l_.numpy()[0], L, TOL[dtype]["E"])
+    close(g_.numpy()[: w.n_params], g, TOL[dtype]["G"])
+    ld, ed, gd = sv.sv_grad_param_shift(prob, theta_of(w))
+    if n == 8:
+        assert np.array_equal(gd.cpu().numpy(), g_.numpy())
+        assert np.array_equal(ed.cpu().numpy(), e_.numpy())
+    else:
+        close(gd.cpu().numpy(), g_.numpy(), 1e-12 if dtype == "c128" else 1e-6)
+    # outputs may be left out, and the call repeats with new theta
+    th2 = th + 0.25
+    g2 = torch.empty(w.n_params, dtype=torch.float64)
+    sv.sv_grad_param_shift_host(prob, th2, None, None, g2)
+    w2 = dataclasses.replace(w, theta=th2.numpy())
+    close(g2.numpy(), oracle.grad_param_shift(w2)[2], TOL[dtype]["G"])
+    with pytest.raises(ValueError):
+        sv.sv_grad_param_shift_host(prob, theta_of(w))
 
 
 def test_repeatable(sv):
