@@ -112,7 +112,11 @@ typedef struct {
                                 stay on chip, larger ones run as tile passes over device
                                 memory with the default tile; > 0 forces tile passes of
                                 2^tile_bits amplitudes (6..12) */
-    int32_t reserved[3];
+    int32_t coalesce_bits;   /* tile passes: the lowest qubits kept in every tile, so that
+                                tiles are read and written in contiguous runs of
+                                2^coalesce_bits amplitudes (1..tile_bits - 2); 0 = default
+                                (4 complex64 / 3 complex128: 128-byte runs) */
+    int32_t reserved[2];
 } sv_plan_opts;
 
 /* ---------------------------------------------------------------- states */

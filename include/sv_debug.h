@@ -33,10 +33,13 @@ sv_status sv_debug_passes(const sv_circuit *circuit, int32_t tile_bits, int32_t 
 
 /* The kernel descriptors of the tile passes exactly as the GPU entry points
  * build them for `dtype` (SV_C64 / SV_C128): counts[0..2] = groups, members,
- * passes; `tile_passes` gets counts[2] descriptors of sizes[7] bytes. */
+ * passes; `tile_passes` gets counts[2] descriptors of sizes[7] bytes.
+ * relabel: plan as the gradient and energy paths do (passes move qubits
+ * into the low index bits); `layout` (int32 [n_qubits] or NULL) gets the bit
+ * of the amplitude index that holds each qubit after the last pass. */
 sv_status sv_debug_tile_passes(const sv_circuit *circuit, int32_t tile_bits, int32_t reg_bits,
-                               int32_t fuse, int32_t dtype, int32_t *counts, void *groups,
-                               void *members, void *tile_passes);
+                               int32_t fuse, int32_t dtype, int32_t relabel, int32_t *counts,
+                               void *groups, void *members, void *tile_passes, int32_t *layout);
 
 /* The tile passes of lambda = H psi: counts[0..3] = passes, groups, classes,
  * terms.  In the exported pass records the three array pointers hold the

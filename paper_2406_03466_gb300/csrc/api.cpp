@@ -85,7 +85,8 @@ struct ObsEntry {
     DeviceBuf buf;
     Observable dev{};
     DeviceBuf dtab;  // diagonal tables D_g(j) for on-chip sizes, or empty
-    std::map<int, std::unique_ptr<HPlanEntry>> hplans;  // by tile bits
+    // by tile bits and the qubits' bit layout of the states they run on
+    std::map<std::pair<int, std::vector<int>>, std::unique_ptr<HPlanEntry>> hplans;
 };
 
 struct ArrayEntry {
@@ -187,12 +188,16 @@ int swz_bits(sv_dtype d) { return d == SV_C128 ? 3 : 4; }
 // tile_bits > 0: the circuit cut into tile passes of 2^tile_bits amplitudes
 // (states in device memory) instead of one on-chip program.
 sv_status get_plan(DeviceCtx *ctx, const sv_circuit &c, int R, bool fuse, sv_dtype dt,
-                   PlanEntry **out, int tile_bits = 0) {
+                   PlanEntry **out, int tile_bits = 0, int coalesce = 0, bool relabel = false) {
+    if (coalesce <= 0) coalesce = dt == SV_C128 ? 3 : 4;
+    if (tile_bits <= 0) relabel = false;
     uint64_t key = hash_circuit(c);
     key = mix64(key, (uint64_t)R);
     key = mix64(key, fuse ? 1 : 0);
     key = mix64(key, (uint64_t)swz_bits(dt));
     key = mix64(key, (uint64_t)(1000 + tile_bits));
+    key = mix64(key, (uint64_t)(2000 + coalesce));
+    key = mix64(key, relabel ? 0x7e1abe1ull : 0ull);
     auto it = ctx->plans.find(key);
     if (it != ctx->plans.end()) {
         PlanEntry *e = it->second.get();
@@ -206,7 +211,7 @@ sv_status get_plan(DeviceCtx *ctx, const sv_circuit &c, int R, bool fuse, sv_dty
     std::unique_ptr<PlanEntry> e(new PlanEntry());
     std::string err;
     if (tile_bits > 0) {
-        err = plan_passes(c, tile_bits, dt == SV_C128 ? 3 : 4, R, fuse, swz_bits(dt), &e->host);
+        err = plan_passes(c, tile_bits, coalesce, R, fuse, swz_bits(dt), &e->host, relabel);
         if (err.empty()) err = build_tile_passes(e->host, dt == SV_C128 ? 16 : 8, &e->tiles);
     } else {
         err = plan_circuit(c, R, fuse, swz_bits(dt), &e->host);
@@ -545,12 +550,47 @@ int h_tile_bits(int n, sv_dtype dt) {
     return n < t ? n : t;
 }
 
-sv_status get_hplan(ObsEntry *obs, int n, sv_dtype dt, HPlanEntry **out) {
+// layout: qubit q in bit layout[q] of the amplitude index (states left
+// relabeled by tile passes), or null / empty for the identity; the terms'
+// masks are moved to those bits.
+sv_status get_hplan(ObsEntry *obs, int n, sv_dtype dt, HPlanEntry **out,
+                    const std::vector<int> *layout = nullptr) {
     const int t = h_tile_bits(n, dt);
-    std::unique_ptr<HPlanEntry> &slot = obs->hplans[t];
+    std::vector<int> lay;
+    if (layout)
+        for (int q = 0; q < (int)layout->size(); ++q)
+            if ((*layout)[q] != q) {
+                lay = *layout;
+                break;
+            }
+    std::unique_ptr<HPlanEntry> &slot = obs->hplans[{t, lay}];
     if (!slot) {
         std::unique_ptr<HPlanEntry> e(new HPlanEntry());
-        std::string err = plan_h_passes(obs->host, t, dt == SV_C128 ? 3 : 4, &e->host);
+        const HostObservable *ho = &obs->host;
+        HostObservable moved;
+        if (!lay.empty()) {
+            auto move = [&](uint64_t m) {
+                uint64_t r = 0;
+                for (int q = 0; q < n; ++q)
+                    if ((m >> q) & 1ull) r |= 1ull << lay[q];
+                return r;
+            };
+            std::vector<uint64_t> xm(obs->xm.size()), zm(obs->zm.size());
+            for (size_t i = 0; i < xm.size(); ++i) {
+                xm[i] = move(obs->xm[i]);
+                zm[i] = move(obs->zm[i]);
+            }
+            sv_pauli_sum h{};
+            h.n_qubits = n;
+            h.n_terms = (int32_t)xm.size();
+            h.x_mask = xm.data();
+            h.z_mask = zm.data();
+            h.coeff = obs->c.data();
+            std::string err = plan_observable(h, n, swz_bits(dt), &moved);
+            if (!err.empty()) return fail(SV_ERR_ARG, "observable: " + err);
+            ho = &moved;
+        }
+        std::string err = plan_h_passes(*ho, t, dt == SV_C128 ? 3 : 4, &e->host);
         if (!err.empty()) return fail(SV_ERR_ARG, "observable: " + err);
         const HostHPlan &h = e->host;
         Packer pk;
@@ -580,9 +620,9 @@ int64_t tile_blocks(const DeviceCtx *ctx, int64_t tiles);
 // E[r] = <psi_r|H|psi_r> for n_rows states (and lam = H psi unless lam is
 // null) by tile passes.
 sv_status h_tiles(DeviceCtx *ctx, ObsEntry *obs, int n, sv_dtype dt, int n_rows, const void *psi,
-                  void *lam, double *E, cudaStream_t st) {
+                  void *lam, double *E, cudaStream_t st, const std::vector<int> *layout = nullptr) {
     HPlanEntry *hp = nullptr;
-    sv_status s = get_hplan(obs, n, dt, &hp);
+    sv_status s = get_hplan(obs, n, dt, &hp, layout);
     if (s != SV_OK) return s;
     SV_CUDA(cudaMemsetAsync(E, 0, sizeof(double) * (size_t)n_rows, st));
     for (const HPass &P : hp->passes) {
@@ -600,7 +640,7 @@ bool wants_tiles(int n, sv_dtype dt, const sv_plan_opts *o) {
 }
 
 struct TileCfg {
-    int t, R;
+    int t, R, c;  // tile bits, register bits, coalesced low qubits
 };
 
 // Tuning keys of the tile tier (by instance count), beside the on-chip kinds.
@@ -617,7 +657,8 @@ sv_status tile_cfg(int n, sv_dtype dt, const sv_plan_opts *o, TileCfg *cfg,
         t.tile_bits = tn->R + __builtin_ctz((unsigned)tn->tpb);
         return tile_cfg(n, dt, &t, cfg, nullptr);
     }
-    const int c = dt == SV_C128 ? 3 : 4, rmax = dt == SV_C128 ? 3 : 4;
+    const int c = (o && o->coalesce_bits > 0) ? o->coalesce_bits : (dt == SV_C128 ? 3 : 4);
+    const int rmax = dt == SV_C128 ? 3 : 4;
     // Default: 2^11 (complex64) / 2^10 (complex128) amplitudes per tile with
     // 4 / 2 register bits: 128 / 256 threads per block.
     int t = (o && o->tile_bits > 0) ? o->tile_bits : (dt == SV_C128 ? 10 : 11);
@@ -631,8 +672,10 @@ sv_status tile_cfg(int n, sv_dtype dt, const sv_plan_opts *o, TileCfg *cfg,
     if (R > rmax) return fail(SV_ERR_UNSUPPORTED, "tile too large for the register width");
     if (t - R < 5)
         return fail(SV_ERR_UNSUPPORTED, "tile passes need tile_bits - reg_bits >= 5 (a warp of threads)");
+    if (c + 2 > t) return fail(SV_ERR_ARG, "coalesce_bits must be at most tile_bits - 2");
     cfg->t = t;
     cfg->R = R;
+    cfg->c = c;
     return SV_OK;
 }
 
@@ -684,7 +727,7 @@ sv_status tiles_energies(DeviceCtx *ctx, const sv_problem *p, const double *thet
     sv_status s = tile_cfg(n, dt, p->opts, &cfg, find_tuned(ctx, p, kTileEnergyKey, p->n_instances));
     if (s != SV_OK) return s;
     PlanEntry *pe = nullptr;
-    s = get_plan(ctx, *p->circuit, cfg.R, use_fusion(p->opts), dt, &pe, cfg.t);
+    s = get_plan(ctx, *p->circuit, cfg.R, use_fusion(p->opts), dt, &pe, cfg.t, cfg.c, true);
     if (s != SV_OK) return s;
     ObsEntry *obs = nullptr;
     s = get_obs(ctx, *p->observable, n, dt, &obs, st);
@@ -715,7 +758,7 @@ sv_status tiles_energies(DeviceCtx *ctx, const sv_problem *p, const double *thet
         src.slot_base = slot_begin + (int)c0;
         s = tiles_forward(ctx, pe, cfg.R, dt, src, big, (char *)big + mats_off, true, nullptr, 0, st);
         if (s != SV_OK) return s;
-        s = h_tiles(ctx, obs, n, dt, src.n_slots, big, nullptr, E + c0, st);
+        s = h_tiles(ctx, obs, n, dt, src.n_slots, big, nullptr, E + c0, st, &pe->host.layout);
         if (s != SV_OK) return s;
     }
     return SV_OK;
@@ -739,7 +782,10 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
     if (s != SV_OK) return s;
     if (forced) cfg = *forced;
     PlanEntry *pe = nullptr;
-    s = get_plan(ctx, *p->circuit, cfg.R, use_fusion(p->opts), dt, &pe, cfg.t);
+    // relabeled passes unless the JS divergence reads the states in the
+    // target distribution's index order
+    s = get_plan(ctx, *p->circuit, cfg.R, use_fusion(p->opts), dt, &pe, cfg.t, cfg.c,
+                 ddcl_target == nullptr);
     if (s != SV_OK) return s;
     ObsEntry *obs = nullptr;
     if (!ddcl_target) {
@@ -797,7 +843,7 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
             e = launch_ddcl_lambda(c128, n, src.n_slots, psi, ddcl_target, lam, Es + c0, st);
             if (e != cudaSuccess) return cuda_fail(e, "JS divergence and its lambda");
         } else {
-            s = h_tiles(ctx, obs, n, dt, src.n_slots, psi, lam, Es + c0, st);
+            s = h_tiles(ctx, obs, n, dt, src.n_slots, psi, lam, Es + c0, st, &pe->host.layout);
             if (s != SV_OK) return s;
         }
         phase_mark(ctx, st);
@@ -858,7 +904,7 @@ sv_status multi_sequence(DeviceCtx *ctx, std::vector<MultiProblem> &mp, sv_dtype
         if (k == nsteps) {  // between the sweeps: lambda = H psi, cleared sums
             for (MultiProblem &m : mp) {
                 sv_status s = h_tiles(ctx, m.obs, m.n, dt, m.I, base + m.o_psi, base + m.o_lam,
-                                      (double *)(base + m.o_E), st);
+                                      (double *)(base + m.o_E), st, &m.pe->host.layout);
                 if (s != SV_OK) return s;
                 SV_CUDA(cudaMemsetAsync(base + m.o_rho, 0, (size_t)m.I * m.G * 64, st));
                 SV_CUDA(cudaMemsetAsync(base + m.o_G, 0, sizeof(double) * (size_t)m.I * (m.P > 0 ? m.P : 1), st));
@@ -906,7 +952,7 @@ sv_status multi_adjoint(DeviceCtx *ctx, const sv_problem *problems, int np,
         sv_status s = tile_cfg(p->circuit->n_qubits, dt, p->opts, &c);
         if (s != SV_OK) return s;
         if (j == 0) cfg = c;
-        else if (c.t != cfg.t || c.R != cfg.R)
+        else if (c.t != cfg.t || c.R != cfg.R || c.c != cfg.c)
             return fail(SV_ERR_UNSUPPORTED, "uneven batch: problems need one tile shape");
         key = mix64(key, mix64(hash_circuit(*p->circuit), hash_observable(*p->observable)));
         key = mix64(key, (uint64_t)p->n_instances);
@@ -940,11 +986,12 @@ sv_status multi_adjoint(DeviceCtx *ctx, const sv_problem *problems, int np,
         m.n = m.p->circuit->n_qubits;
         m.I = m.p->n_instances;
         m.P = m.p->circuit->n_params;
-        sv_status s = get_plan(ctx, *m.p->circuit, cfg.R, use_fusion(m.p->opts), dt, &m.pe, cfg.t);
+        sv_status s = get_plan(ctx, *m.p->circuit, cfg.R, use_fusion(m.p->opts), dt, &m.pe, cfg.t,
+                               cfg.c, true);
         if (s == SV_OK) s = get_obs(ctx, *m.p->observable, m.n, dt, &m.obs, st);
         if (s == SV_OK) s = get_array(ctx, m.p->refs, sizeof(int64_t) * m.I, &m.drefs);
         HPlanEntry *hp = nullptr;
-        if (s == SV_OK) s = get_hplan(m.obs, m.n, dt, &hp);
+        if (s == SV_OK) s = get_hplan(m.obs, m.n, dt, &hp, &m.pe->host.layout);
         if (s != SV_OK) return s;
         m.G = m.pe->dev.n_groups;
         m.npass = (int)m.pe->tiles.size();
@@ -1196,7 +1243,7 @@ sv_status sv_apply_circuit_batch(sv_state state, const sv_circuit *circuits, int
             sv_status s = tile_cfg(state->n, state->dtype, opts, &cfg);
             if (s != SV_OK) return s;
             PlanEntry *pe = nullptr;
-            s = get_plan(ctx, circuits[c], cfg.R, use_fusion(opts), state->dtype, &pe, cfg.t);
+            s = get_plan(ctx, circuits[c], cfg.R, use_fusion(opts), state->dtype, &pe, cfg.t, cfg.c);
             if (s != SV_OK) return s;
             const void *dslots = nullptr;
             s = get_array(ctx, sub.data(), sub.size() * sizeof(sv_slot), &dslots);
@@ -1941,7 +1988,7 @@ sv_status sv_plan_info(const sv_circuit *c, sv_dtype dt, const sv_plan_opts *o, 
         s = tile_cfg(c->n_qubits, dt, o, &cfg);
         if (s != SV_OK) return s;
         t = cfg.t;
-        err = plan_passes(*c, cfg.t, dt == SV_C128 ? 3 : 4, cfg.R, use_fusion(o), swz_bits(dt), &h);
+        err = plan_passes(*c, cfg.t, cfg.c, cfg.R, use_fusion(o), swz_bits(dt), &h, true);
     } else {
         err = plan_circuit(*c, (o && o->reg_bits > 0) ? o->reg_bits : (dt == SV_C128 ? 3 : 4),
                            use_fusion(o), swz_bits(dt), &h);

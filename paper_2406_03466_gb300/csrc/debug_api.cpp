@@ -61,12 +61,13 @@ sv_status sv_debug_passes(const sv_circuit *c, int32_t tile_bits, int32_t coales
 }
 
 sv_status sv_debug_tile_passes(const sv_circuit *c, int32_t tile_bits, int32_t reg_bits,
-                               int32_t fuse, int32_t dtype, int32_t *counts, void *groups,
-                               void *members, void *tile_passes) {
+                               int32_t fuse, int32_t dtype, int32_t relabel, int32_t *counts,
+                               void *groups, void *members, void *tile_passes, int32_t *layout) {
     if (!c || !counts) return SV_ERR_ARG;
     const bool c128 = dtype == SV_C128;
     HostProgram h;
-    std::string err = plan_passes(*c, tile_bits, c128 ? 3 : 4, reg_bits, fuse != 0, c128 ? 3 : 4, &h);
+    std::string err = plan_passes(*c, tile_bits, c128 ? 3 : 4, reg_bits, fuse != 0, c128 ? 3 : 4, &h,
+                                  relabel != 0);
     std::vector<TilePass> tp;
     if (err.empty()) err = build_tile_passes(h, c128 ? 16 : 8, &tp);
     if (!err.empty()) return SV_ERR_ARG;
@@ -76,6 +77,8 @@ sv_status sv_debug_tile_passes(const sv_circuit *c, int32_t tile_bits, int32_t r
     if (groups) std::memcpy(groups, h.groups.data(), h.groups.size() * sizeof(Group));
     if (members) std::memcpy(members, h.members.data(), h.members.size() * sizeof(Member));
     if (tile_passes) std::memcpy(tile_passes, tp.data(), tp.size() * sizeof(TilePass));
+    if (layout)
+        for (size_t q = 0; q < h.layout.size(); ++q) layout[q] = h.layout[q];
     return SV_OK;
 }
 

@@ -254,7 +254,7 @@ std::string plan_circuit(const sv_circuit &c, int reg_bits, bool fuse, int swz_b
 }
 
 std::string plan_passes(const sv_circuit &c0, int tile_bits, int coalesce_bits, int reg_bits,
-                        bool fuse, int swz_bits, HostProgram *P) {
+                        bool fuse, int swz_bits, HostProgram *P, bool relabel) {
     // CZ(a, b) = H_b CNOT(a -> b) H_b: tile passes run fused single-qubit
     // groups and CNOT permutations only.
     std::vector<sv_gate> gates;
@@ -298,10 +298,15 @@ std::string plan_passes(const sv_circuit &c0, int tile_bits, int coalesce_bits, 
     P->swz_bits = swz_bits;
     P->members = F.members;
     P->groups = F.groups;
-    const uint32_t forced = (1u << coalesce_bits) - 1u;
+    // phys[q]: the bit of the amplitude index that holds qubit q; who[b]: the
+    // qubit held by bit b.
+    std::vector<int> phys(n), who(n);
+    for (int q = 0; q < n; ++q) phys[q] = who[q] = q;
     std::vector<int> pending(F.lops.size());
     for (size_t i = 0; i < pending.size(); ++i) pending[i] = (int)i;
     while (!pending.empty()) {
+        uint32_t forced = 0;
+        for (int b = 0; b < coalesce_bits; ++b) forced |= 1u << who[b];
         uint32_t L = forced, blocked = 0;
         std::vector<int> taken, rest;
         for (int idx : pending) {
@@ -320,16 +325,27 @@ std::string plan_passes(const sv_circuit &c0, int tile_bits, int coalesce_bits, 
             }
         }
         if (taken.empty()) return "internal: pass planner made no progress";
-        for (int p = 0; __builtin_popcount(L) < t && p < n; ++p) L |= 1u << p;
+        // Spare local qubits: with relabeling, the qubits that the ops left
+        // for later passes need first (they can then move to the low bits);
+        // otherwise (and then) the lowest qubits.
+        if (relabel)
+            for (size_t i = 0; i < rest.size() && __builtin_popcount(L) < t; ++i) {
+                const uint32_t q = lop_qubits(F.lops[rest[i]]);
+                if (__builtin_popcount(L | q) <= t) L |= q;
+            }
+        for (int p = 0; __builtin_popcount(L) < t && p < n; ++p) L |= 1u << who[p];
+        // Tile-local positions in the order of the bits that hold them, so
+        // that positions 0..coalesce_bits-1 are the low (contiguous) bits.
         PassDesc pd{};
         std::vector<int> pos(n, -1);
         int b = 0, k = 0;
-        for (int q = 0; q < n; ++q) {
+        for (int pb = 0; pb < n; ++pb) {
+            const int q = who[pb];
             if ((L >> q) & 1u) {
                 pos[q] = b;
-                pd.gl[b++] = 1u << q;
+                pd.gl[b++] = 1u << pb;
             } else {
-                pd.gt[k++] = 1u << q;
+                pd.gt[k++] = 1u << pb;
             }
         }
         pd.t = t;
@@ -371,9 +387,48 @@ std::string plan_passes(const sv_circuit &c0, int tile_bits, int coalesce_bits, 
             return "internal: a tile pass exceeds the stage or op limit";
         for (size_t i = keep; i < taken.size(); ++i) rest.push_back(taken[i]);
         std::sort(rest.begin(), rest.end());
+        // Relabel on the way out: the local qubits that the remaining ops
+        // need first take the low bits; the qubits they displace take the
+        // bits these leave (all within the tile, so the stored tile covers
+        // the same addresses).
+        std::vector<uint32_t> stp(t);
+        for (int bb = 0; bb < t; ++bb) stp[bb] = swizzle(1u << bb, swz_bits);
+        if (relabel && !rest.empty()) {
+            std::vector<int> want;
+            for (size_t i = 0; i < rest.size() && (int)want.size() < coalesce_bits; ++i) {
+                const LOp &o = F.lops[rest[i]];
+                const int qs[2] = {o.a, o.kind == 0 ? -1 : o.b};
+                for (int q : qs)
+                    if (q >= 0 && ((L >> q) & 1u) && (int)want.size() < coalesce_bits &&
+                        std::find(want.begin(), want.end(), q) == want.end())
+                        want.push_back(q);
+            }
+            std::vector<int> nwho = who;
+            for (int q : want) {
+                if (phys[q] < coalesce_bits) continue;
+                int lb = -1;  // a low bit whose qubit is not wanted there
+                for (int x = 0; x < coalesce_bits && lb < 0; ++x)
+                    if (std::find(want.begin(), want.end(), nwho[x]) == want.end()) lb = x;
+                if (lb < 0) break;
+                const int hb = phys[q], out = nwho[lb];
+                nwho[lb] = q;
+                nwho[hb] = out;
+                phys[q] = lb;
+                phys[out] = hb;
+            }
+            // The store writes to global tile bit bb the tile-local bit of
+            // the qubit that now lives there.
+            for (int bb = 0; bb < t; ++bb) {
+                const int pb = __builtin_ctz(pd.gl[bb]);
+                stp[bb] = swizzle(1u << pos[nwho[pb]], swz_bits);
+            }
+            who.swap(nwho);
+        }
+        P->stperm.push_back(stp);
         P->passes.push_back(pd);
         pending.swap(rest);
     }
+    P->layout = phys;
     return "";
 }
 
@@ -392,7 +447,8 @@ std::string build_tile_passes(const HostProgram &P, int csz, std::vector<TilePas
         for (int b = 0; b < pd.t; ++b) {
             tp.gl[b] = pd.gl[b];
             tp.ldperm[b] = pd.ldperm[b] * (uint32_t)csz;
-            tp.nat[b] = swizzle(1u << b, w) * (uint32_t)csz;
+            tp.nat[b] = (P.stperm.empty() ? swizzle(1u << b, w) : P.stperm[&pd - P.passes.data()][b]) *
+                        (uint32_t)csz;
         }
         uint32_t acc = 0;
         for (int k = 0; k < pd.n_tile_bits; ++k) {

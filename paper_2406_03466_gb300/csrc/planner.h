@@ -17,6 +17,13 @@ struct HostProgram {
     std::vector<Stage> stages;
     std::vector<std::vector<uint32_t>> perm_cols;  // per stage: f(e_b), b < n
     std::vector<PassDesc> passes;                  // tile passes (device-memory states)
+    // Per tile pass: shared-memory address vector (swizzled, in amplitudes)
+    // of the tile-local bit stored at global tile bit b; differs from
+    // swizzle(e_b) where the pass relabels qubits on its way out.
+    std::vector<std::vector<uint32_t>> stperm;
+    // Layout after the last tile pass: qubit q lives in bit layout[q] of the
+    // amplitude index (the identity unless the passes relabel).
+    std::vector<int> layout;
     std::vector<ThreadBase> tbase;                 // [stages][2^(t-R)] thread bases
 };
 
@@ -41,9 +48,13 @@ std::string fuse_circuit(const sv_circuit &c, bool fuse, FusedCircuit *out);
 void stage_lops(const std::vector<LOp> &lops, const std::vector<int> &pos, int t, int R, int w,
                 HostProgram *P, bool one_per_bit);
 // Cuts a circuit into tile passes of 2^tile_bits amplitudes whose local
-// qubits always include the lowest coalesce_bits qubits.
+// qubits always include the qubits in the lowest coalesce_bits bits of the
+// amplitude index (so that tiles move in contiguous runs).  relabel: a pass
+// may store its tile with its qubits in other bits of the same tile, moving
+// into the low bits qubits that the next pass needs (P->layout gives the
+// final bit of every qubit); otherwise every qubit keeps its own bit.
 std::string plan_passes(const sv_circuit &c, int tile_bits, int coalesce_bits, int reg_bits,
-                        bool fuse, int swz_bits, HostProgram *P);
+                        bool fuse, int swz_bits, HostProgram *P, bool relabel = false);
 
 // Kernel descriptors of every pass of a tile plan (amplitudes of csz bytes).
 std::string build_tile_passes(const HostProgram &P, int csz, std::vector<TilePass> *out);

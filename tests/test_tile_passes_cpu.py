@@ -44,20 +44,29 @@ class TilePass(ctypes.Structure):
                 ("st", TileStage * 16), ("fmode", ctypes.c_int8 * 48)]
 
 
-def export(circ, t, R, fuse=True, dtype=0):
+def _debug_tile_passes():
     L = sv.library()
-    L.sv_debug_tile_passes.argtypes = [ctypes.c_void_p, I32, I32, I32, I32, ctypes.POINTER(I32),
-                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.sv_debug_tile_passes.argtypes = [ctypes.c_void_p, I32, I32, I32, I32, I32,
+                                       ctypes.POINTER(I32), ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]
     L.sv_debug_tile_passes.restype = I32
+    return L.sv_debug_tile_passes
+
+
+def export(circ, t, R, fuse=True, dtype=0, relabel=False):
+    """(groups, members, tile passes, layout): layout[q] = the index bit that
+    holds qubit q after the last pass."""
+    f = _debug_tile_passes()
     counts = (I32 * 3)()
-    st = L.sv_debug_tile_passes(ctypes.byref(circ.struct), t, R, int(fuse), dtype, counts,
-                                None, None, None)
+    st = f(ctypes.byref(circ.struct), t, R, int(fuse), dtype, int(relabel), counts,
+           None, None, None, None)
     assert st == 0, sv.sv_status_string(st)
     arrs = [(Group * max(1, counts[0]))(), (Member * max(1, counts[1]))(),
             (TilePass * max(1, counts[2]))()]
-    assert L.sv_debug_tile_passes(ctypes.byref(circ.struct), t, R, int(fuse), dtype, counts,
-                                  *arrs) == 0
-    return [a[:k] for a, k in zip(arrs, counts)]
+    lay = (I32 * circ.n_qubits)()
+    assert f(ctypes.byref(circ.struct), t, R, int(fuse), dtype, int(relabel), counts,
+             *arrs, lay) == 0
+    return [a[:k] for a, k in zip(arrs, counts)] + [list(lay)]
 
 
 def test_descriptor_size_matches():
@@ -296,7 +305,7 @@ def circuit_of(w):
 def test_forward_passes_match_oracle(name, t, R, dtype):
     w = CASES[name]()
     circ = circuit_of(w)
-    groups, members, passes = export(circ, t, R, dtype=dtype)
+    groups, members, passes, _ = export(circ, t, R, dtype=dtype)
     csz = 16 if dtype else 8
     I = min(2, w.n_instances)
     xs = [None if w.inputs is None else w.inputs[i] for i in range(I)]
@@ -311,7 +320,7 @@ def test_forward_passes_match_oracle(name, t, R, dtype):
 
 def test_tile_walk_covers_every_tile_once():
     w = wl.qcl(12, 1, 1)
-    groups, members, passes = export(circuit_of(w), 8, 3)
+    groups, members, passes, _ = export(circuit_of(w), 8, 3)
     for P in passes[:4]:
         for nb in (1, 3, 7, 40):
             seen = tile_walk(P, 3, nb)
@@ -324,7 +333,7 @@ def test_tile_walk_covers_every_tile_once():
 def test_reverse_passes_give_oracle_gradient(name, t, R, dtype):
     w = CASES[name]()
     circ = circuit_of(w)
-    groups, members, passes = export(circ, t, R, dtype=dtype)
+    groups, members, passes, _ = export(circ, t, R, dtype=dtype)
     csz = 16 if dtype else 8
     I = w.n_instances
     xs = [None if w.inputs is None else w.inputs[i] for i in range(I)]
@@ -349,21 +358,86 @@ def test_reverse_passes_give_oracle_gradient(name, t, R, dtype):
     np.testing.assert_allclose(grad, g_o, atol=1e-11)
 
 
+def to_layout(vec, layout):
+    """A state in qubit order, rearranged so that qubit q sits in index bit
+    layout[q]."""
+    n = len(layout)
+    j = np.arange(1 << n)
+    jp = np.zeros_like(j)
+    for q in range(n):
+        jp |= ((j >> q) & 1) << layout[q]
+    out = np.empty_like(vec)
+    out[jp] = vec
+    return out
+
+
+def moved_letters(letters, layout):
+    out = np.zeros_like(letters)  # identity letters (code 0)
+    for q in range(letters.shape[1]):
+        out[:, layout[q]] = letters[:, q]
+    return out
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("t,R,dtype", [(7, 2, 0), (6, 1, 0), (7, 2, 1)])
+def test_relabeling_passes_forward_and_reverse(name, t, R, dtype):
+    """Passes that move qubits into the low index bits: the forward sweep
+    leaves the oracle's state in the exported layout, and the reverse sweep
+    with lambda = H psi in that layout gives the oracle's gradient and
+    returns psi to |ref>."""
+    w = CASES[name]()
+    circ = circuit_of(w)
+    groups, members, passes, lay = export(circ, t, R, dtype=dtype, relabel=True)
+    assert sorted(lay) == list(range(w.n_qubits))
+    csz = 16 if dtype else 8
+    I = w.n_instances
+    xs = [None if w.inputs is None else w.inputs[i] for i in range(I)]
+    mats = [group_mats(groups, members, w.theta, xs[i]) for i in range(I)]
+    psi = init_states(w, I)
+    for P in passes:
+        run_fwd(P, psi, mats, csz)
+    for i in range(I):
+        np.testing.assert_allclose(psi[i], to_layout(oracle.state(w, instance=i), lay), atol=1e-12)
+    H = dense.hamiltonian(w.n_qubits, moved_letters(np.asarray(w.pauli_letters), lay),
+                          w.pauli_coeffs)
+    lam = np.stack([H @ psi[i] for i in range(I)])
+    E = np.array([np.vdot(psi[i], lam[i]).real for i in range(I)])
+    rho = [[np.zeros((2, 2), complex) for _ in groups] for _ in range(I)]
+    for P in reversed(passes):
+        run_rev(P, psi, lam, mats, rho, csz)
+    for i in range(I):
+        np.testing.assert_allclose(psi[i], init_states(w, I)[i], atol=1e-12)
+    wts = oracle.cost_weights(w, E)
+    grad = np.zeros(w.n_params)
+    for i in range(I):
+        group_gradients(groups, members, rho[i], w.theta, xs[i], grad, wts[i])
+    L, E_o, g_o = oracle.grad_param_shift(w)
+    np.testing.assert_allclose(E, E_o, atol=1e-12)
+    np.testing.assert_allclose(grad, g_o, atol=1e-11)
+
+
+def test_relabeling_saves_passes():
+    """On a wide layered circuit the low (contiguous) index bits carry qubits
+    that the next pass needs, instead of the same four qubits in every pass."""
+    w = wl.mcvqe(16, 4, "nn+nnn", n_refs=1)
+    plain = export(circuit_of(w), 10, 3)[2]
+    moved, lay = export(circuit_of(w), 10, 3, relabel=True)[2:]
+    assert len(moved) < len(plain)
+    assert lay != list(range(16))
+
+
 def test_cz_is_planned_as_h_cnot_h():
     w = wl.random_workload(8, 70, 5, 2, seed=41, with_encoding=True)
     assert any(g.op == "CZ" for g in w.gates)
-    groups, members, passes = export(circuit_of(w), 7, 2)
+    groups, members, passes, _ = export(circuit_of(w), 7, 2)
     assert any(m.kind == 4 for m in members)  # H members absorbed into groups
 
 
 def test_rejects_tiles_narrower_than_a_warp():
     w = wl.qcl(8, 1, 1)
-    L = sv.library()
     counts = (I32 * 3)()
-    L.sv_debug_tile_passes.argtypes = [ctypes.c_void_p, I32, I32, I32, I32, ctypes.POINTER(I32),
-                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
-    assert L.sv_debug_tile_passes(ctypes.byref(circuit_of(w).struct), 7, 3, 1, 0, counts,
-                                  None, None, None) != 0
+    assert _debug_tile_passes()(ctypes.byref(circuit_of(w).struct), 7, 3, 1, 0, 0, counts,
+                                None, None, None, None) != 0
 
 
 # ------------------------------------------------------------ lambda = H psi
@@ -468,9 +542,9 @@ def test_h_passes_match_dense(n, t, c, kind):
 
 def test_single_sum_mode_chosen_for_one_rotation_groups():
     w = wl.mcvqe(8, 2, "nn+nnn", n_refs=2)  # one Ry per group
-    groups, members, passes = export(circuit_of(w), 8, 3)
+    groups, members, passes, _ = export(circuit_of(w), 8, 3)
     assert all(P.all_single for P in passes)
     assert all(P.fmode[u] == 1 for P in passes for u in range(P.n_ops) if P.param_mask >> u & 1)
     w = wl.qcl(8, 2, 2)  # Rx Rz Rx groups
-    groups, members, passes = export(circuit_of(w), 8, 3)
+    groups, members, passes, _ = export(circuit_of(w), 8, 3)
     assert not any(P.all_single for P in passes)
