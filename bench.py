@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--energy-shape", default="",
                     help="mcvqe8 only: 'R,T' pins the energy kernel to R register bits and T "
                          "threads per block instead of autotuning (for profiler captures)")
+    ap.add_argument("--tile-shape", default="",
+                    help="qcl20 / mcvqe28 only: 't,R' pins the tile passes to 2^t amplitudes and "
+                         "R register bits instead of autotuning (for profiler captures)")
     ap.add_argument("--qubits", type=int, default=0,
                     help="qcl20 / mcvqe28 only: the same workload family at this qubit count "
                          "(a smaller case for profiler captures; not a bench line)")
@@ -312,14 +315,19 @@ def run_device_memory(args, sv, dev, stream, dist, world, rank):
     """Adjoint gradient of a workload whose states live in device memory."""
     import torch
     w = device_workload(args)
-    prob = sv.Problem.from_spec(w, "c64", device=dev)
+    pinned = None
+    if args.tile_shape:
+        tile_bits, R = (int(x) for x in args.tile_shape.split(","))
+        pinned = sv.plan_opts(reg_bits=R, tile_bits=tile_bits)
+    prob = sv.Problem.from_spec(w, "c64", device=dev, opts=pinned)
     theta = torch.as_tensor(w.theta, dtype=torch.float64, device=dev)
     out = sv._outputs(prob, dev, None, None, None)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    # tile shape (tile bits, register bits) picked by timing
-    sv.sv_autotune(prob, theta, 2)
-    R, tpb, _ = sv.sv_tuned_shape(prob, 2)
-    tile_bits = R + tpb.bit_length() - 1
+    if pinned is None:
+        # tile shape (tile bits, register bits) picked by timing
+        sv.sv_autotune(prob, theta, 2)
+        R, tpb, _ = sv.sv_tuned_shape(prob, 2)
+        tile_bits = R + tpb.bit_length() - 1
     opts = sv.plan_opts(reg_bits=R, tile_bits=tile_bits)
 
     def step():

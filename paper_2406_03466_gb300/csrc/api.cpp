@@ -119,6 +119,8 @@ struct DeviceCtx {
     // stream the captures run on.
     std::unordered_map<uint64_t, std::unique_ptr<struct MultiGraph>> graphs;
     cudaStream_t capture_stream = nullptr;
+    // Target distributions rewritten for relabeled states, per stream.
+    std::unordered_map<cudaStream_t, std::unique_ptr<DeviceBuf>> relayout;
     // Host-buffer entry points: pinned host and device staging per stream.
     std::unordered_map<cudaStream_t, std::unique_ptr<struct HostIO>> hostio;
 };
@@ -782,11 +784,33 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
     if (s != SV_OK) return s;
     if (forced) cfg = *forced;
     PlanEntry *pe = nullptr;
-    // relabeled passes unless the JS divergence reads the states in the
-    // target distribution's index order
-    s = get_plan(ctx, *p->circuit, cfg.R, use_fusion(p->opts), dt, &pe, cfg.t, cfg.c,
-                 ddcl_target == nullptr);
+    s = get_plan(ctx, *p->circuit, cfg.R, use_fusion(p->opts), dt, &pe, cfg.t, cfg.c, true);
     if (s != SV_OK) return s;
+    if (ddcl_target) {
+        // The passes leave qubit q in index bit layout[q]: rewrite the target
+        // distribution in that bit order for the JS divergence.
+        const std::vector<int> &lay = pe->host.layout;
+        bool moved = false;
+        for (int q = 0; q < (int)lay.size(); ++q) moved |= lay[q] != q;
+        if (moved) {
+            std::vector<int32_t> who(n);
+            for (int q = 0; q < n; ++q) who[lay[q]] = q;
+            auto &buf = ctx->relayout[st];
+            if (!buf) buf.reset(new DeviceBuf());
+            const size_t bytes = sizeof(double) << n;
+            if (buf->bytes < bytes) {
+                SV_CUDA(cudaStreamSynchronize(st));
+                if (buf->ptr) cudaFree(buf->ptr);
+                buf->ptr = nullptr;
+                buf->bytes = 0;
+                SV_CUDA(cudaMalloc(&buf->ptr, bytes));
+                buf->bytes = bytes;
+            }
+            cudaError_t e = launch_relayout(n, who.data(), ddcl_target, (double *)buf->ptr, st);
+            if (e != cudaSuccess) return cuda_fail(e, "target relayout");
+            ddcl_target = (const double *)buf->ptr;
+        }
+    }
     ObsEntry *obs = nullptr;
     if (!ddcl_target) {
         s = get_obs(ctx, *p->observable, n, dt, &obs, st);

@@ -15,6 +15,7 @@
 // states, and the per-slot gradient assembly.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <type_traits>
@@ -1188,6 +1189,33 @@ cudaError_t launch_tile_multi(int c128, int R, bool rev, const MultiItem *items,
 }
 
 static dim3 whole_state_grid(int n, int rows);
+
+// out[j] = in[j'] where j' moves bit b of j to bit who.q[b]: a table indexed
+// by qubit values rewritten in a relabeled bit layout (who.q[b] = the qubit
+// held by bit b).  Grid-stride, one entry per thread step.
+struct QubitOfBit {
+    int32_t q[30];
+};
+__global__ void k_relayout(int n, QubitOfBit who, const double *in, double *out) {
+    const int64_t dim = int64_t(1) << n;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < dim;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int64_t src = 0;
+        for (int b = 0; b < n; ++b) src |= ((j >> b) & 1) << who.q[b];
+        out[j] = in[src];
+    }
+}
+
+cudaError_t launch_relayout(int n, const int32_t *qubit_of_bit, const double *in, double *out,
+                            cudaStream_t st) {
+    if (n < 1 || n > 30) return cudaErrorInvalidValue;
+    QubitOfBit w{};
+    for (int b = 0; b < n; ++b) w.q[b] = qubit_of_bit[b];
+    const int64_t dim = int64_t(1) << n;
+    const int64_t blocks = std::min<int64_t>((dim + 255) / 256, 152 * 16);
+    k_relayout<<<(unsigned)blocks, 256, 0, st>>>(n, w, in, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_ddcl_lambda(int c128, int n, int n_rows, const void *psi, const double *target,
                                void *lam, double *js, cudaStream_t st) {

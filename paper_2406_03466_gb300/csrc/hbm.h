@@ -44,6 +44,10 @@ cudaError_t launch_tile_h(int c128, const HPass &P, int n, int n_slots, const vo
 // first) and lam_r = dJS/d|psi_r|^2 * psi_r elementwise.
 cudaError_t launch_ddcl_lambda(int c128, int n, int n_rows, const void *psi, const double *target,
                                void *lam, double *js, cudaStream_t st);
+// out[j] = in[j with bit b moved to bit qubit_of_bit[b]]: a 2^n table indexed
+// by qubit values, rewritten for states whose bit b holds qubit qubit_of_bit[b].
+cudaError_t launch_relayout(int n, const int32_t *qubit_of_bit, const double *in, double *out,
+                            cudaStream_t st);
 // out[r] = <psi_r|H|psi_r> (zeroed here first).
 cudaError_t launch_expect_big(int c128, const Observable &o, int n, int n_rows,
                               const void *states, double *out, cudaStream_t st);
