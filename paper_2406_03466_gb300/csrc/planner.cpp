@@ -148,17 +148,57 @@ void stage_lops(const std::vector<LOp> &lops, const std::vector<int> &pos, int t
         st.op_end = (int)P->ops.size();
         st.n_thr = t - R;
         st.n_u1 = n_u1;
-        // Thread bit order: first one position of every residue mod w (so the
-        // lanes of a wavefront land in distinct banks), then the rest.
+        // Thread bit order: the first w thread bits (the lanes of one
+        // wavefront) take positions whose swizzled load vectors and store
+        // vectors both have independent low w bits, so that those lanes hit
+        // distinct banks on the load and on the store; then the rest.
         std::vector<int> rest, order;
         for (int p = 0; p < t; ++p)
             if (find_pos(Q, p) < 0) rest.push_back(p);
-        for (int r = 0; r < w; ++r)
-            for (int p : rest)
-                if (p % w == r && find_pos(order, p) < 0) {
-                    order.push_back(p);
-                    break;
+        {
+            // every subset of min(w, |rest|) positions (at most C(12, 4)):
+            // the largest load rank + store rank of the low w bits
+            const uint32_t lowm = (1u << w) - 1u;
+            auto rank = [&](const uint32_t *v, int m) {
+                uint32_t bas[32] = {};
+                int r = 0;
+                for (int i = 0; i < m; ++i) {
+                    uint32_t x = v[i];
+                    for (int h = w - 1; h >= 0 && x; --h)
+                        if ((x >> h) & 1u) {
+                            if (bas[h]) {
+                                x ^= bas[h];
+                            } else {
+                                bas[h] = x;
+                                ++r;
+                                break;
+                            }
+                        }
                 }
+                return r;
+            };
+            const int m = std::min<int>(w, (int)rest.size()), nr = (int)rest.size();
+            uint32_t best_mask = 0;
+            int best = -1;
+            for (uint32_t sel = 0; sel < (1u << nr); ++sel) {
+                if (__builtin_popcount(sel) != m) continue;
+                uint32_t vl[32], vs[32];
+                int k = 0;
+                for (int i = 0; i < nr; ++i)
+                    if ((sel >> i) & 1u) {
+                        vl[k] = swizzle(1u << rest[i], w) & lowm;
+                        vs[k] = swizzle(col[rest[i]], w) & lowm;
+                        ++k;
+                    }
+                const int sc = rank(vl, m) + rank(vs, m);
+                if (sc > best) {
+                    best = sc;
+                    best_mask = sel;
+                }
+            }
+            for (int i = 0; i < nr; ++i)
+                if ((best_mask >> i) & 1u) order.push_back(rest[i]);
+        }
         for (int p : rest)
             if (find_pos(order, p) < 0) order.push_back(p);
         for (int i = 0; i < kRMax; ++i) {
@@ -334,16 +374,18 @@ std::string plan_passes(const sv_circuit &c0, int tile_bits, int coalesce_bits, 
                 if (__builtin_popcount(L | q) <= t) L |= q;
             }
         for (int p = 0; __builtin_popcount(L) < t && p < n; ++p) L |= 1u << who[p];
-        // Tile-local positions in the order of the bits that hold them, so
-        // that positions 0..coalesce_bits-1 are the low (contiguous) bits.
+        // Tile bit b: the b-th lowest index bit among the local qubits (tile
+        // bits 0..coalesce_bits-1 are the contiguous low bits); qb[b] is its
+        // qubit.  Shared-memory positions pos[q] start in the same order.
         PassDesc pd{};
-        std::vector<int> pos(n, -1);
-        int b = 0, k = 0;
+        std::vector<int> qb, pos(n, -1);
+        int k = 0;
         for (int pb = 0; pb < n; ++pb) {
             const int q = who[pb];
             if ((L >> q) & 1u) {
-                pos[q] = b;
-                pd.gl[b++] = 1u << pb;
+                pos[q] = (int)qb.size();
+                pd.gl[qb.size()] = 1u << pb;
+                qb.push_back(q);
             } else {
                 pd.gt[k++] = 1u << pb;
             }
@@ -351,25 +393,25 @@ std::string plan_passes(const sv_circuit &c0, int tile_bits, int coalesce_bits, 
         pd.t = t;
         pd.n_tile_bits = n - t;
         pd.local_mask = L;
-        // Stage the taken ops; a pass holds at most kPassStages stages and
-        // kPassOps group ops, so an over-long pass keeps a prefix of them (a
-        // prefix of the taken ops in circuit order is closed under
-        // dependencies) and returns the rest to the pending list.
-        size_t keep = taken.size();
+        // Stages the first `keep` taken ops at positions `ps` (a pass holds at
+        // most kPassStages stages and kPassOps group ops); a leading stage
+        // without ops is only a permutation and is folded into the tile load
+        // (and the reverse pass's tile store).  Returns whether it fits.
         const size_t st0 = P->stages.size(), op0 = P->ops.size();
-        for (;;) {
+        auto stage_with = [&](const std::vector<int> &ps, size_t keep) {
+            P->stages.resize(st0);
+            P->perm_cols.resize(st0);
+            P->ops.resize(op0);
             pd.stage_begin = (int)st0;
             std::vector<LOp> sub;
             for (size_t i = 0; i < keep; ++i) sub.push_back(F.lops[taken[i]]);
-            stage_lops(sub, pos, t, reg_bits, swz_bits, P, true);
+            stage_lops(sub, ps, t, reg_bits, swz_bits, P, true);
             pd.stage_end = (int)P->stages.size();
-            // A leading stage without ops is only a permutation: fold it into
-            // the tile load (and the reverse pass's tile store).
-            for (int bb = 0; bb < t; ++bb) pd.ldperm[bb] = swizzle(1u << bb, swz_bits);
+            for (int bb = 0; bb < t; ++bb) pd.ldperm[bb] = swizzle(1u << ps[qb[bb]], swz_bits);
             const Stage &s0 = P->stages[pd.stage_begin];
             if (s0.op_begin == s0.op_end && pd.stage_end - pd.stage_begin > 1) {
                 const std::vector<uint32_t> &col = P->perm_cols[pd.stage_begin];
-                for (int bb = 0; bb < t; ++bb) pd.ldperm[bb] = swizzle(col[bb], swz_bits);
+                for (int bb = 0; bb < t; ++bb) pd.ldperm[bb] = swizzle(col[ps[qb[bb]]], swz_bits);
                 P->stages.erase(P->stages.begin() + pd.stage_begin);
                 P->perm_cols.erase(P->perm_cols.begin() + pd.stage_begin);
                 --pd.stage_end;
@@ -377,12 +419,13 @@ std::string plan_passes(const sv_circuit &c0, int tile_bits, int coalesce_bits, 
             int nu = 0;
             for (int si = pd.stage_begin; si < pd.stage_end; ++si) nu += P->stages[si].n_u1;
             pd.n_u1 = nu;
-            if ((pd.stage_end - pd.stage_begin <= kPassStages && nu <= kPassOps) || keep <= 1) break;
-            P->stages.resize(st0);
-            P->perm_cols.resize(st0);
-            P->ops.resize(op0);
-            keep = keep * 3 / 4;
-        }
+            return pd.stage_end - pd.stage_begin <= kPassStages && nu <= kPassOps;
+        };
+        // An over-long pass keeps a prefix of the taken ops (a prefix in
+        // circuit order is closed under dependencies); the rest go back to
+        // the pending list.
+        size_t keep = taken.size();
+        while (!stage_with(pos, keep) && keep > 1) keep = keep * 3 / 4;
         if (pd.stage_end - pd.stage_begin > kPassStages || pd.n_u1 > kPassOps)
             return "internal: a tile pass exceeds the stage or op limit";
         for (size_t i = keep; i < taken.size(); ++i) rest.push_back(taken[i]);
@@ -391,8 +434,7 @@ std::string plan_passes(const sv_circuit &c0, int tile_bits, int coalesce_bits, 
         // need first take the low bits; the qubits they displace take the
         // bits these leave (all within the tile, so the stored tile covers
         // the same addresses).
-        std::vector<uint32_t> stp(t);
-        for (int bb = 0; bb < t; ++bb) stp[bb] = swizzle(1u << bb, swz_bits);
+        std::vector<int> nwho = who;
         if (relabel && !rest.empty()) {
             std::vector<int> want;
             for (size_t i = 0; i < rest.size() && (int)want.size() < coalesce_bits; ++i) {
@@ -403,7 +445,6 @@ std::string plan_passes(const sv_circuit &c0, int tile_bits, int coalesce_bits, 
                         std::find(want.begin(), want.end(), q) == want.end())
                         want.push_back(q);
             }
-            std::vector<int> nwho = who;
             for (int q : want) {
                 if (phys[q] < coalesce_bits) continue;
                 int lb = -1;  // a low bit whose qubit is not wanted there
@@ -413,17 +454,79 @@ std::string plan_passes(const sv_circuit &c0, int tile_bits, int coalesce_bits, 
                 const int hb = phys[q], out = nwho[lb];
                 nwho[lb] = q;
                 nwho[hb] = out;
-                phys[q] = lb;
-                phys[out] = hb;
             }
-            // The store writes to global tile bit bb the tile-local bit of
-            // the qubit that now lives there.
-            for (int bb = 0; bb < t; ++bb) {
-                const int pb = __builtin_ctz(pd.gl[bb]);
-                stp[bb] = swizzle(1u << pos[nwho[pb]], swz_bits);
+            // Shared-memory positions whose residues mod swz_bits differ
+            // across the qubits of the low bits before the pass (the lanes
+            // of the tile load) and across those after it (the lanes of the
+            // tile store), so both hit distinct banks; re-staged with them
+            // when the pass still fits.
+            if (swz_bits == coalesce_bits) {
+                const int w = swz_bits;
+                std::vector<int> res(n, -1), lowin, lowout;
+                for (int x = 0; x < w; ++x) {
+                    lowin.push_back(who[x]);
+                    lowout.push_back(nwho[x]);
+                }
+                std::vector<bool> used_in(w, false), used_out(w, false);
+                for (int q : lowin)
+                    if (std::find(lowout.begin(), lowout.end(), q) != lowout.end())
+                        for (int r = 0; r < w; ++r)
+                            if (!used_in[r] && !used_out[r]) {
+                                res[q] = r;
+                                used_in[r] = used_out[r] = true;
+                                break;
+                            }
+                for (int q : lowin)
+                    if (res[q] < 0)
+                        for (int r = 0; r < w; ++r)
+                            if (!used_in[r]) {
+                                res[q] = r;
+                                used_in[r] = true;
+                                break;
+                            }
+                for (int q : lowout)
+                    if (res[q] < 0)
+                        for (int r = 0; r < w; ++r)
+                            if (!used_out[r]) {
+                                res[q] = r;
+                                used_out[r] = true;
+                                break;
+                            }
+                std::vector<int> pos2(n, -1);
+                std::vector<bool> taken_pos(t, false);
+                bool ok = true;
+                for (int q : qb)
+                    if (res[q] >= 0) {
+                        int pp = -1;
+                        for (int c2 = res[q]; c2 < t && pp < 0; c2 += w)
+                            if (!taken_pos[c2]) pp = c2;
+                        if (pp < 0) ok = false;
+                        else {
+                            pos2[q] = pp;
+                            taken_pos[pp] = true;
+                        }
+                    }
+                for (int q : qb)
+                    if (pos2[q] < 0)
+                        for (int pp = 0; pp < t; ++pp)
+                            if (!taken_pos[pp]) {
+                                pos2[q] = pp;
+                                taken_pos[pp] = true;
+                                break;
+                            }
+                if (ok && pos2 != pos) {
+                    if (stage_with(pos2, keep)) pos = pos2;
+                    else stage_with(pos, keep);
+                }
             }
-            who.swap(nwho);
+            for (int q = 0; q < n; ++q) phys[nwho[q]] = q;
         }
+        // The store writes to tile bit bb the shared-memory position of the
+        // qubit that now lives in its index bit.
+        std::vector<uint32_t> stp(t);
+        for (int bb = 0; bb < t; ++bb)
+            stp[bb] = swizzle(1u << pos[nwho[__builtin_ctz(pd.gl[bb])]], swz_bits);
+        who.swap(nwho);
         P->stperm.push_back(stp);
         P->passes.push_back(pd);
         pending.swap(rest);
