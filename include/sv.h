@@ -104,7 +104,8 @@ typedef struct {
 /* Planning knobs; all-zero (or a NULL pointer) selects the defaults. */
 typedef struct {
     int32_t reg_bits;        /* amplitudes held per thread = 2^reg_bits (1..5); 0 = default */
-    int32_t threads_per_block; /* 0 = default */
+    int32_t threads_per_block; /* 0 = default; else a multiple of 32 (whole warps) and of
+                                  the threads per circuit, at most 512 */
     int32_t no_fusion;       /* 1 = apply every gate on its own (no 1-qubit gate fusion) */
     int32_t epilogue;        /* <H> epilogue: 0 = default, 1 = per Pauli term, 2 = per-X-group
                                 diagonal tables (states of at most 13 qubits) */

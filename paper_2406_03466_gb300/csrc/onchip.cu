@@ -13,6 +13,8 @@
 // reduction across amplitudes, threads or terms is accumulated in FP64.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "engine.cuh"
 #include "kernels.h"
 
@@ -243,6 +245,7 @@ const char *onchip_shape(int kind, int n, int n_groups, int n_params, int c128, 
         S = threads_per_block / Ts;
         if (threads_per_block % Ts != 0 || S < 1)
             return "threads_per_block must be a multiple of the threads per slot";
+        if (threads_per_block % 32 != 0) return "threads_per_block must be a multiple of 32";
     } else {
         // Enough blocks for two per SM where the batch allows, at least one
         // warp and at most 256 threads per block.
@@ -250,7 +253,9 @@ const char *onchip_shape(int kind, int n, int n_groups, int n_params, int c128, 
         if (S * Ts > 256) S = 256 / Ts;
         if (S < 1) S = 1;
     }
-    if (S * Ts < 32) S = 32 / Ts;
+    // whole warps: the reductions shuffle over full warps
+    const int sm = Ts < 32 ? 32 / Ts : 1;
+    S = (S + sm - 1) / sm * sm;
     const size_t dim = size_t(1) << n;
     const int wps = Ts >= 32 ? Ts / 32 : 1;
     const uint32_t kLimit = 200 * 1024;
@@ -291,8 +296,8 @@ const char *onchip_shape(int kind, int n, int n_groups, int n_params, int c128, 
             s.smem = (uint32_t)off;
             break;
         }
-        if (S == 1) return "state too large for the on-chip engine";
-        S = S / 2;
+        if (S <= sm) return "state too large for the on-chip engine";
+        S = std::max(sm, S / 2 / sm * sm);
     }
     s.R = R;
     s.Ts = Ts;

@@ -267,6 +267,22 @@ def test_param_shift_host_buffers(sv, dtype, n):
         sv.sv_grad_param_shift_host(prob, theta_of(w))
 
 
+def test_whole_warp_blocks(sv):
+    """A batch whose default launch would put 3 circuits of 16 threads in a
+    block (48 threads) runs in whole warps and matches the oracle; a
+    threads_per_block that is not a multiple of 32 is rejected."""
+    w = wl.random_workload(6, 200, 6, 5, seed=7)
+    assert 609 <= w.n_slots_param_shift <= 912  # ceil(B / 304) == 3
+    L, E, g = oracle.grad_param_shift(w)
+    prob = sv.Problem.from_spec(w, "c64")
+    l_, e_, g_ = sv.sv_grad_param_shift(prob, theta_of(w))
+    close(e_.cpu().numpy(), E, TOL["c64"]["E"])
+    close(g_.cpu().numpy()[: w.n_params], g, TOL["c64"]["G"])
+    bad = sv.Problem.from_spec(w, "c64", opts=sv.plan_opts(reg_bits=2, threads_per_block=48))
+    with pytest.raises(sv.SvError):
+        sv.sv_grad_param_shift(bad, theta_of(w))
+
+
 def test_repeatable(sv):
     """A fixed plan gives bitwise identical results run to run."""
     w = wl.mcvqe(8, 4)
