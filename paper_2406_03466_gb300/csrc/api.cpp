@@ -104,7 +104,6 @@ struct DeviceCtx {
     std::mutex mu;
     int sms = 152;
     std::unordered_map<uint64_t, Tuned> tuned;
-    std::unordered_map<cudaStream_t, std::unique_ptr<DeviceBuf>> counters;
     std::unordered_map<uint64_t, std::unique_ptr<PlanEntry>> plans;
     std::unordered_map<uint64_t, std::unique_ptr<ObsEntry>> obs;
     std::unordered_map<uint64_t, std::unique_ptr<ArrayEntry>> arrays;
@@ -323,20 +322,6 @@ sv_status get_array(DeviceCtx *ctx, const void *host, size_t bytes, const void *
     if (bytes) SV_CUDA(cudaMemcpy(e->buf.ptr, host, bytes, cudaMemcpyHostToDevice));
     *dev = e->buf.ptr;
     ctx->arrays[key] = std::move(e);
-    return SV_OK;
-}
-
-// A zeroed counter for the energy kernel's last-block gradient assembly (the
-// kernel resets it to zero when it finishes).
-sv_status get_counter(DeviceCtx *ctx, cudaStream_t st, unsigned **out) {
-    auto &c = ctx->counters[st];
-    if (!c) {
-        c.reset(new DeviceBuf());
-        SV_CUDA(cudaMalloc(&c->ptr, 256));
-        c->bytes = 256;
-        SV_CUDA(cudaMemsetAsync(c->ptr, 0, 256, st));
-    }
-    *out = (unsigned *)c->ptr;
     return SV_OK;
 }
 
@@ -1486,11 +1471,7 @@ sv_status sv_grad_param_shift(const sv_problem *p, const double *theta, double *
     s = get_scratch(ctx, st, sizeof(double) * ((size_t)B + I), &scr);
     if (s != SV_OK) return s;
     double *E = (double *)scr, *lp = E + B;
-    unsigned *counter = nullptr;
-    s = get_counter(ctx, st, &counter);
-    if (s != SV_OK) return s;
     FusedCombine fc{};
-    fc.counter = counter;
     fc.I = I;
     fc.P = P;
     fc.cost = cost_of(p, nullptr);
@@ -1523,9 +1504,6 @@ sv_status sv_grad_param_shift_host(const sv_problem *p, const double *theta_host
     void *scr = nullptr;
     s = get_scratch(ctx, st, sizeof(double) * ((size_t)B + I), &scr);
     if (s != SV_OK) return s;
-    unsigned *counter = nullptr;
-    s = get_counter(ctx, st, &counter);
-    if (s != SV_OK) return s;
     double *h = (double *)io->host, *d = (double *)io->dev;
     if (P > 0) {
         std::memcpy(h, theta_host, sizeof(double) * P);
@@ -1533,7 +1511,6 @@ sv_status sv_grad_param_shift_host(const sv_problem *p, const double *theta_host
     }
     double *E = (double *)scr;
     FusedCombine fc{};
-    fc.counter = counter;
     fc.I = I;
     fc.P = P;
     fc.cost = cost_of(p, nullptr);

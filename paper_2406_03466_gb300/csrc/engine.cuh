@@ -581,10 +581,22 @@ __device__ double apply_h(const Observable &o, const typename CT<Real>::T *psi,
 // (E_{k+,i} - E_{k-,i}) / 2, the energies and the cost.  `red`: 32 doubles.
 __device__ void ps_combine_block(const double *E, int I, int P, const CostSource &c, double *lp,
                                  double *energy_out, double *loss_out, double *grad_out,
-                                 double *red) {
+                                 double *red, double *stage = nullptr, int stage_cap = 0) {
+    // With room in `stage` (shared memory the block no longer needs), every
+    // thread first copies a share of the (2P + 1) I energies, so the sums
+    // below wait for one round of device-memory loads instead of one per
+    // unrolled batch; the arithmetic and its order are the same.
+    const int64_t B = (int64_t)(2 * P + 1) * I;
+    const bool staged = stage && B + I <= (int64_t)stage_cap;
+    if (staged) {
+        for (int64_t i = threadIdx.x; i < B; i += blockDim.x) stage[i] = __ldcg(E + i);
+        __syncthreads();
+        lp = stage + B;
+    }
+    auto ld = [&](int64_t i) { return staged ? stage[i] : __ldcg(E + i); };
     double part = 0.0;
     for (int i = threadIdx.x; i < I; i += blockDim.x) {
-        const double e = __ldcg(E + i);
+        const double e = ld(i);
         if (energy_out) energy_out[i] = e;
         if (c.cost == SV_COST_MSE) {
             const double d = e - c.targets[i];
@@ -604,10 +616,10 @@ __device__ void ps_combine_block(const double *E, int I, int P, const CostSource
         loss_out[0] = s;
     }
     for (int k = threadIdx.x; k < P; k += blockDim.x) {
-        const double *ep = E + I + (int64_t)2 * k * I, *em = ep + I;
+        const int64_t ep = I + (int64_t)2 * k * I, em = ep + I;
         double g = 0.0;
 #pragma unroll 8
-        for (int i = 0; i < I; ++i) g += lp[i] * 0.5 * (__ldcg(ep + i) - __ldcg(em + i));
+        for (int i = 0; i < I; ++i) g += lp[i] * 0.5 * (ld(ep + i) - ld(em + i));
         grad_out[k] = g;
     }
 }

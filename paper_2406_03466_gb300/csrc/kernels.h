@@ -73,9 +73,9 @@ const char *onchip_shape(int kind, int n, int n_groups, int n_params, int c128, 
                          int num_sms = 152, uint32_t const_bytes = 0);
 enum OnchipKind { ONCHIP_ENERGY = 0, ONCHIP_STORE = 1, ONCHIP_EXPECT = 2, ONCHIP_ADJOINT = 3 };
 
-// Gradient assembly done by the last block of the energy kernel.
+// Gradient assembly launched behind the energy kernel (a programmatic
+// dependent launch that waits for the energies).
 struct FusedCombine {
-    unsigned *counter;  // zero before the launch; the last block resets it
     int32_t I, P;
     CostSource cost;
     double *lp;         // [I] scratch
@@ -84,7 +84,7 @@ struct FusedCombine {
 
 // dtab: diagonal tables of the observable ([groups][2^n] complex of the
 // state's precision) or NULL for the per-term epilogue; fc: NULL or the
-// fused gradient assembly.
+// gradient assembly that follows the energies.
 cudaError_t launch_onchip_energy(int c128, const OnchipShape &sh, const Program &p,
                                  const Observable &o, const SlotSource &s, double *energies,
                                  cudaStream_t st, const void *dtab = nullptr,

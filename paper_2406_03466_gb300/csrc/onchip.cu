@@ -27,9 +27,12 @@ template <typename Real, int R, int kMode>
 __global__ void __launch_bounds__(512) k_energy(Program p, Observable o, SlotSource src,
                                                 OnchipShape sh, double *energies,
                                                 const typename CT<Real>::T *dtab,
-                                                FusedCombine fc, BlockConst bc) {
+                                                BlockConst bc) {
     using C = typename CT<Real>::T;
     extern __shared__ __align__(16) unsigned char smem[];
+    // a combination kernel launched behind this one may be scheduled now (it
+    // waits for this grid's completion before reading the energies)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     stage_block_const<kMode>(bc, smem, p, o);
     const int n = p.n, shb = n - R, Ts = 1 << shb;
     const int ls = threadIdx.x >> shb, tid = threadIdx.x & (Ts - 1);
@@ -55,19 +58,6 @@ __global__ void __launch_bounds__(512) k_energy(Program p, Observable o, SlotSou
     }
     e = slot_sum(e, Ts, red);
     if (live && tid == 0) energies[b] = e;
-    if (!fc.counter) return;
-    // The last block to finish assembles the gradient (no second launch).
-    __shared__ unsigned last;
-    __shared__ double cred[32];
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(fc.counter, 1u) == gridDim.x - 1) ? 1u : 0u;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    ps_combine_block(energies, fc.I, fc.P, fc.cost, fc.lp, fc.energy_out, fc.loss_out,
-                     fc.grad_out, cred);
-    if (threadIdx.x == 0) *fc.counter = 0u;
 }
 
 template <typename Real, int R>
@@ -171,6 +161,20 @@ __global__ void k_ps_combine(const double *E, int I, int P, CostSource c, double
                              double *energy_out, double *loss_out, double *grad_out) {
     __shared__ double red[32];
     ps_combine_block(E, I, P, c, lp, energy_out, loss_out, grad_out, red);
+}
+
+// The same, launched as a programmatic dependent of the energy kernel: it
+// is scheduled while the energies are computed and waits for that grid to
+// complete (its writes visible) before it reads them.  `stage`: dynamic
+// shared memory of stage_cap doubles for the energies.
+__global__ void k_ps_combine_dep(const double *E, int I, int P, CostSource c, double *lp,
+                                 double *energy_out, double *loss_out, double *grad_out,
+                                 int stage_cap) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ double red[32];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    ps_combine_block(E, I, P, c, lp, energy_out, loss_out, grad_out, red,
+                     reinterpret_cast<double *>(dsm), stage_cap);
 }
 
 // Adjoint combination: dL/dtheta = sum_i (weighted per-instance gradients).
@@ -327,13 +331,13 @@ const char *onchip_shape(int kind, int n, int n_groups, int n_params, int c128, 
 template <typename Real, int R>
 static cudaError_t run_energy(const OnchipShape &sh, const Program &p, const Observable &o,
                               const SlotSource &s, double *E, const void *dtab,
-                              const FusedCombine &fc, const BlockConst &bc, cudaStream_t st) {
+                              const BlockConst &bc, cudaStream_t st) {
     auto k = !bc.bytes ? k_energy<Real, R, 0> : (bc.n16[7] ? k_energy<Real, R, 2>
                                                            : k_energy<Real, R, 1>);
     cudaError_t e = prep(k, sh.smem);
     if (e != cudaSuccess) return e;
     k<<<sh.blocks, sh.S * sh.Ts, sh.smem, st>>>(
-        p, o, s, sh, E, reinterpret_cast<const typename CT<Real>::T *>(dtab), fc, bc);
+        p, o, s, sh, E, reinterpret_cast<const typename CT<Real>::T *>(dtab), bc);
     return cudaGetLastError();
 }
 
@@ -348,20 +352,44 @@ static BlockConst fit_const(const OnchipShape &sh, const BlockConst *bc) {
     return b;
 }
 
+static cudaError_t energy_kernel(int c128, const OnchipShape &sh, const Program &p,
+                                 const Observable &o, const SlotSource &s, double *E,
+                                 cudaStream_t st, const void *dtab, const BlockConst &b) {
+    if (c128) {
+        SVK_DISPATCH_R_C128(sh.R, return (run_energy<double, RR>(sh, p, o, s, E, dtab, b, st)));
+    }
+    SVK_DISPATCH_R(sh.R, return (run_energy<float, RR>(sh, p, o, s, E, dtab, b, st)));
+    return cudaSuccess;
+}
+
 cudaError_t launch_onchip_energy(int c128, const OnchipShape &sh, const Program &p,
                                  const Observable &o, const SlotSource &s, double *E,
                                  cudaStream_t st, const void *dtab, const FusedCombine *fc,
                                  const BlockConst *bc) {
     if (sh.blocks == 0) return cudaSuccess;
-    FusedCombine none{};
-    const FusedCombine &f = fc ? *fc : none;
     BlockConst b = fit_const(sh, bc);
     if (!dtab) b.n16[6] = 0;
-    if (c128) {
-        SVK_DISPATCH_R_C128(sh.R, return (run_energy<double, RR>(sh, p, o, s, E, dtab, f, b, st)));
-    }
-    SVK_DISPATCH_R(sh.R, return (run_energy<float, RR>(sh, p, o, s, E, dtab, f, b, st)));
-    return cudaSuccess;
+    if (!fc) return energy_kernel(c128, sh, p, o, s, E, st, dtab, b);
+    // The gradient combination follows as a programmatic dependent launch:
+    // its launch overlaps the energy kernel, no block of which waits for the
+    // others (a last-block tail in the energy kernel measured slower).
+    cudaError_t e = energy_kernel(c128, sh, p, o, s, E, st, dtab, b);
+    if (e != cudaSuccess) return e;
+    const int64_t B = (int64_t)(2 * fc->P + 1) * fc->I;
+    const int cap = B + fc->I <= 6144 ? (int)(B + fc->I) : 0;  // <= 48 KiB of staging
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = sizeof(double) * (size_t)cap;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_ps_combine_dep, (const double *)E, fc->I, fc->P, fc->cost,
+                           fc->lp, fc->energy_out, fc->loss_out, fc->grad_out, cap);
+    return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 // Diagonal tables D_g(j) of an observable, [groups][2^n] complex (Real).
