@@ -319,6 +319,18 @@ sv_status sv_param_shift_combine(const sv_problem *problem, const double *energi
 sv_status sv_grad_ddcl(const sv_problem *problem, const double *theta, const double *target,
                        double *js_out, double *grad_out, sv_stream_t stream);
 
+/* The same gradient by the paper's parameter-shift rule (Sec. 4.2: 2 N_theta
+ * circuits per update): P_theta(b) is the expectation of the projector
+ * |b><b|, so dP_theta(b)/dtheta_k = 1/2 [P_{theta+pi/2 e_k}(b) -
+ * P_{theta-pi/2 e_k}(b)] and dJS/dtheta_k = 1/2 [<D>_{k+} - <D>_{k-}] with
+ * D = diag(dJS/dP_theta) taken from the unshifted circuit.  Runs the 2P + 1
+ * circuits as tile passes over device memory in chunks that fit; arguments
+ * and outputs as for sv_grad_ddcl.  Uses library scratch of (2P + 2 + 2^n)
+ * doubles. */
+sv_status sv_grad_ddcl_param_shift(const sv_problem *problem, const double *theta,
+                                   const double *target, double *js_out, double *grad_out,
+                                   sv_stream_t stream);
+
 /* Adjoint gradients of several problems at once: circuits of different qubit
  * counts and depths whose states take the tile path (14..30 qubits; all
  * problems share the dtype and the tile shape), each with its own

@@ -108,6 +108,7 @@ def _load():
     lib.sv_grad_adjoint.argtypes = [P(sv_problem), V, V, V, V, V, I32, V]
     lib.sv_grad_adjoint_multi.argtypes = [P(sv_problem), I32, P(V), P(V), P(V), P(V), V]
     lib.sv_grad_ddcl.argtypes = [P(sv_problem), V, V, V, V, V]
+    lib.sv_grad_ddcl_param_shift.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_sample.argtypes = [V, I32, V, ctypes.c_int64, V, V, V]
     lib.sv_param_shift_energies_range.argtypes = [P(sv_problem), V, I32, I32, V, V]
     lib.sv_param_shift_combine.argtypes = [P(sv_problem), V, V, V, V, V]
@@ -456,6 +457,20 @@ def sv_grad_ddcl(problem: Problem, theta, target, js_out=None, grad_out=None, st
     grad_out = torch.empty(max(1, problem.n_params), **f) if grad_out is None else grad_out
     _check(_lib.sv_grad_ddcl(ctypes.byref(problem.struct), _ptr(theta), _ptr(target),
                              _ptr(js_out), _ptr(grad_out), _stream(stream)), "sv_grad_ddcl")
+    return js_out, grad_out
+
+
+def sv_grad_ddcl_param_shift(problem: Problem, theta, target, js_out=None, grad_out=None,
+                             stream=None):
+    """(JS[1], grad[P]) as sv_grad_ddcl, by the parameter-shift rule over the
+    2P + 1 circuits (the paper's form of the gradient)."""
+    import torch
+    f = dict(dtype=torch.float64, device=theta.device)
+    js_out = torch.empty(1, **f) if js_out is None else js_out
+    grad_out = torch.empty(max(1, problem.n_params), **f) if grad_out is None else grad_out
+    _check(_lib.sv_grad_ddcl_param_shift(ctypes.byref(problem.struct), _ptr(theta), _ptr(target),
+                                         _ptr(js_out), _ptr(grad_out), _stream(stream)),
+           "sv_grad_ddcl_param_shift")
     return js_out, grad_out
 
 

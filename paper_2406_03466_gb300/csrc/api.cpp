@@ -1676,6 +1676,91 @@ sv_status sv_grad_ddcl(const sv_problem *p, const double *theta, const double *t
                          (cudaStream_t)stream, target, &cfg);
 }
 
+sv_status sv_grad_ddcl_param_shift(const sv_problem *p, const double *theta,
+                                   const double *target, double *js_out, double *grad_out,
+                                   sv_stream_t stream) {
+    if (!p || !p->circuit) return fail(SV_ERR_ARG, "problem or circuit is NULL");
+    if (!target || !js_out) return fail(SV_ERR_ARG, "target/js_out is NULL");
+    sv_status s = check_circuit(p->circuit, p->dtype == SV_C128 ? 29 : 30);
+    if (s != SV_OK) return s;
+    const int n = p->circuit->n_qubits, P = p->circuit->n_params;
+    if (p->n_instances != 1 || !p->refs) return fail(SV_ERR_ARG, "data-driven circuit learning takes one instance");
+    if (P > 0 && (!theta || !grad_out)) return fail(SV_ERR_ARG, "theta/grad_out is NULL");
+    if (p->circuit->input_dim > 0 && !p->inputs) return fail(SV_ERR_ARG, "inputs are NULL");
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    const sv_dtype dt = p->dtype;
+    const int c128 = dt == SV_C128;
+    // tile passes at every size, as for the adjoint form (identity layout:
+    // the derivative table is indexed like the target)
+    sv_plan_opts o{};
+    if (p->opts) o = *p->opts;
+    if (o.tile_bits <= 0 && !wants_tiles(n, dt, p->opts)) {
+        o.tile_bits = std::min(n, c128 ? 10 : 11);
+        if (o.reg_bits <= 0) o.reg_bits = std::max(2, std::min(c128 ? 2 : 4, o.tile_bits - 5));
+    }
+    TileCfg cfg{};
+    s = tile_cfg(n, dt, &o, &cfg);
+    if (s != SV_OK) return s;
+    PlanEntry *pe = nullptr;
+    s = get_plan(ctx, *p->circuit, cfg.R, use_fusion(&o), dt, &pe, cfg.t, cfg.c, false);
+    if (s != SV_OK) return s;
+    const void *drefs = nullptr;
+    s = get_array(ctx, p->refs, sizeof(int64_t), &drefs);
+    if (s != SV_OK) return s;
+    const double one = 1.0;
+    const void *w1 = nullptr;
+    s = get_array(ctx, &one, sizeof(double), &w1);
+    if (s != SV_OK) return s;
+    const int B = 2 * P + 1;
+    const size_t dim = size_t(1) << n;
+    void *scr = nullptr;
+    s = get_scratch(ctx, st, sizeof(double) * ((size_t)B + 1 + dim), &scr);
+    if (s != SV_OK) return s;
+    double *E = (double *)scr, *lp = E + B, *D = lp + 1;
+    const size_t csz = c128 ? 16 : 8, sb = csz << n;
+    const size_t mb = (size_t)pe->dev.n_groups * 4 * csz;
+    int64_t chunk = (int64_t)(big_budget(ctx, st) / (sb + mb + 512));
+    if (chunk < 1) return fail(SV_ERR_OOM, "one state does not fit in free device memory");
+    if (chunk > B) chunk = B;
+    if (chunk > 65535) chunk = 65535;
+    void *big = nullptr;
+    const size_t mats_off = ((size_t)chunk * sb + 255) & ~size_t(255);
+    s = get_big_scratch(ctx, st, mats_off + (size_t)chunk * mb + 256, &big);
+    if (s != SV_OK) return s;
+    SlotSource src{};
+    src.mode = SLOTS_PARAM_SHIFT;
+    src.n_instances = 1;
+    src.refs = (const int64_t *)drefs;
+    src.theta = theta;
+    src.inputs = p->inputs;
+    src.input_stride = p->input_stride;
+    // the unshifted circuit (slot 0): JS and the table dJS/dP_theta
+    src.n_slots = 1;
+    src.slot_base = 0;
+    s = tiles_forward(ctx, pe, cfg.R, dt, src, big, (char *)big + mats_off, true, nullptr, 0, st);
+    if (s != SV_OK) return s;
+    cudaError_t e = launch_ddcl_diag(c128, n, big, target, D, js_out, st);
+    if (e != cudaSuccess) return cuda_fail(e, "JS divergence and its derivative table");
+    // every circuit of the batch: <psi_s| diag(dJS/dP_theta) |psi_s>
+    for (int64_t c0 = 0; c0 < B; c0 += chunk) {
+        src.n_slots = (int)std::min<int64_t>(chunk, B - c0);
+        src.slot_base = (int)c0;
+        s = tiles_forward(ctx, pe, cfg.R, dt, src, big, (char *)big + mats_off, true, nullptr, 0, st);
+        if (s != SV_OK) return s;
+        e = launch_diag_expect(c128, n, src.n_slots, big, D, E + c0, st);
+        if (e != cudaSuccess) return cuda_fail(e, "shifted-circuit table expectations");
+    }
+    CostSource cs{};
+    cs.cost = SV_COST_LINEAR;
+    cs.n_instances = 1;
+    cs.weights = (const double *)w1;
+    e = launch_ps_combine(E, 1, P, cs, lp, nullptr, nullptr, P > 0 ? grad_out : nullptr, st);
+    return e == cudaSuccess ? SV_OK : cuda_fail(e, "parameter-shift combine launch");
+}
+
 sv_status sv_grad_adjoint_multi(const sv_problem *problems, int32_t n_problems,
                                 const double *const *theta, double *const *energy_out,
                                 double *const *loss_out, double *const *grad_out,

@@ -1190,6 +1190,56 @@ cudaError_t launch_tile_multi(int c128, int R, bool rev, const MultiItem *items,
 
 static dim3 whole_state_grid(int n, int rows);
 
+// The JS divergence of one state's output distribution from the target and
+// its derivative table D[j] = dJS/dP_theta(j) = 1/2 log(P_theta(j) / M(j)),
+// M = (P + P_theta) / 2 (0 where P_theta(j) = 0); per-amplitude arithmetic
+// in Real, the sum in FP64 (js zeroed by the launcher).
+template <typename Real>
+__global__ void k_ddcl_diag(int n, const typename CT<Real>::T *psi, const double *target,
+                            double *D, double *js) {
+    using C = typename CT<Real>::T;
+    __shared__ double red[32];
+    const int64_t dim = int64_t(1) << n;
+    double acc = 0.0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < dim;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const C a = psi[j];
+        const Real q = fmaR(a.x, a.x, a.y * a.y), p = (Real)target[j];
+        const Real m = (Real)0.5 * (p + q);
+        Real w = 0, term = 0;
+        if (p > (Real)0) term = p * log(p / m);
+        if (q > (Real)0) {
+            const Real l = log(q / m);
+            term = fmaR(q, l, term);
+            w = (Real)0.5 * l;
+        }
+        acc += (double)term;
+        D[j] = (double)w;
+    }
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) atomicAdd(js, 0.5 * s);
+}
+
+// out[r] = sum_j D[j] |psi_r(j)|^2 for n_rows states (grid.y = row; out
+// zeroed by the launcher); products in Real, sums in FP64.
+template <typename Real>
+__global__ void k_diag_expect(int n, const typename CT<Real>::T *states, const double *D,
+                              double *out) {
+    using C = typename CT<Real>::T;
+    __shared__ double red[32];
+    const int r = blockIdx.y;
+    const C *S = states + ((int64_t)r << n);
+    const int64_t dim = int64_t(1) << n;
+    double acc = 0.0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < dim;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const C a = S[j];
+        acc += (double)((Real)D[j] * fmaR(a.x, a.x, a.y * a.y));
+    }
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) atomicAdd(&out[r], s);
+}
+
 // out[j] = in[j'] where j' moves bit b of j to bit who.q[b]: a table indexed
 // by qubit values rewritten in a relabeled bit layout (who.q[b] = the qubit
 // held by bit b).  Grid-stride, one entry per thread step.
@@ -1214,6 +1264,27 @@ cudaError_t launch_relayout(int n, const int32_t *qubit_of_bit, const double *in
     const int64_t dim = int64_t(1) << n;
     const int64_t blocks = std::min<int64_t>((dim + 255) / 256, 152 * 16);
     k_relayout<<<(unsigned)blocks, 256, 0, st>>>(n, w, in, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ddcl_diag(int c128, int n, const void *psi, const double *target, double *D,
+                             double *js, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(js, 0, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const dim3 g = whole_state_grid(n, 1);
+    if (c128) k_ddcl_diag<double><<<g, 256, 0, st>>>(n, (const double2 *)psi, target, D, js);
+    else k_ddcl_diag<float><<<g, 256, 0, st>>>(n, (const float2 *)psi, target, D, js);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag_expect(int c128, int n, int n_rows, const void *states, const double *D,
+                               double *out, cudaStream_t st) {
+    if (n_rows <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * n_rows, st);
+    if (e != cudaSuccess) return e;
+    const dim3 g = whole_state_grid(n, n_rows);
+    if (c128) k_diag_expect<double><<<g, 256, 0, st>>>(n, (const double2 *)states, D, out);
+    else k_diag_expect<float><<<g, 256, 0, st>>>(n, (const float2 *)states, D, out);
     return cudaGetLastError();
 }
 

@@ -44,6 +44,13 @@ cudaError_t launch_tile_h(int c128, const HPass &P, int n, int n_slots, const vo
 // first) and lam_r = dJS/d|psi_r|^2 * psi_r elementwise.
 cudaError_t launch_ddcl_lambda(int c128, int n, int n_rows, const void *psi, const double *target,
                                void *lam, double *js, cudaStream_t st);
+// js[0] = JS divergence of one state's output distribution from `target`;
+// D[j] = dJS/dP_theta(j) (device [2^n] doubles).
+cudaError_t launch_ddcl_diag(int c128, int n, const void *psi, const double *target, double *D,
+                             double *js, cudaStream_t st);
+// out[r] = sum_j D[j] |psi_r(j)|^2 for n_rows states of 2^n amplitudes.
+cudaError_t launch_diag_expect(int c128, int n, int n_rows, const void *states, const double *D,
+                               double *out, cudaStream_t st);
 // out[j] = in[j with bit b moved to bit qubit_of_bit[b]]: a 2^n table indexed
 // by qubit values, rewritten for states whose bit b holds qubit qubit_of_bit[b].
 cudaError_t launch_relayout(int n, const int32_t *qubit_of_bit, const double *in, double *out,

@@ -68,3 +68,28 @@ def test_ddcl_zero_gradient_at_its_own_output(sv):
     w = wl.ddcl(9, 2, seed=6, target=oracle.output_distribution(w0))
     js, g = run(sv, w, "c128")
     assert abs(js) < 1e-12 and np.max(np.abs(g)) < 1e-10
+
+
+def run_ps(sv, w, dtype, opts=None):
+    import torch
+    prob = sv.Problem.from_spec(w, dtype, opts=opts)
+    th = torch.as_tensor(w.theta, dtype=torch.float64, device="cuda")
+    tg = torch.as_tensor(w.target_dist, dtype=torch.float64, device="cuda")
+    js, g = sv.sv_grad_ddcl_param_shift(prob, th, tg)
+    return float(js.cpu()[0]), g.cpu().numpy()[: w.n_params]
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("n,layers,opts", [(8, 2, None), (10, 2, (8, 2)), (9, 1, None)])
+def test_ddcl_param_shift_form(sv, dtype, n, layers, opts):
+    """The paper's form of the gradient (2 N_theta shifted circuits and the
+    derivative table of the unshifted one) against the oracle's parameter
+    shift, and against the adjoint form on the device."""
+    w = wl.ddcl(n, layers, seed=n)
+    o = None if opts is None else sv.plan_opts(tile_bits=opts[0], reg_bits=opts[1])
+    js_o, g_o = oracle.ddcl_grad_param_shift(w)
+    js, g = run_ps(sv, w, dtype, o)
+    close(js, js_o, TOL[dtype]["E"])
+    close(g, g_o, TOL[dtype]["G"])
+    js_a, g_a = run(sv, w, dtype, o)
+    close(g, g_a, TOL[dtype]["G"])
