@@ -513,9 +513,23 @@ __device__ double expect_table(const Observable &o, const typename CT<Real>::T *
     for (int k = 0; k < NA; ++k) pj[k] = st[s0 ^ xsel<R>(k, v)];
     // runs of kRun groups are summed in the state's precision (at most
     // kRun * NA products), the runs in FP64: FP64 adds are scarce on this GPU
+    // One accumulator per amplitude slot k: NA independent FMA chains
+    // instead of one chain through every group (the epilogue runs with few
+    // warps per SM, so the chain's latency is exposed).
     constexpr int kRun = 8;
     double e = 0.0;
-    Real run = 0;
+    Real run[NA];
+#pragma unroll
+    for (int k = 0; k < NA; ++k) run[k] = 0;
+    auto fold = [&]() {
+        Real r = 0;
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+            r += run[k];
+            run[k] = 0;
+        }
+        e += (double)r;
+    };
     for (int g = 0; g < o.n_tgroups; ++g) {
         const uint32_t sx = o.tgroups[g].sx;
         const C *D = dtab + (size_t)g * dim + tid;
@@ -525,14 +539,12 @@ __device__ double expect_table(const Observable &o, const typename CT<Real>::T *
             const C d = D[(size_t)k << sh];  // shared memory when staged, else global
             const Real wr = fmaR(px.x, pj[k].x, px.y * pj[k].y);
             const Real wi = fmaR(px.x, pj[k].y, -px.y * pj[k].x);
-            run = fmaR(wr, d.x, fmaR(-wi, d.y, run));
+            run[k] = fmaR(wr, d.x, fmaR(-wi, d.y, run[k]));
         }
-        if ((g + 1) % kRun == 0) {
-            e += (double)run;
-            run = 0;
-        }
+        if ((g + 1) % kRun == 0) fold();
     }
-    return e + (double)run;
+    fold();
+    return e;
 }
 
 // lambda = H psi for this thread's amplitudes; returns sum Re(conj(psi_j) lambda_j).

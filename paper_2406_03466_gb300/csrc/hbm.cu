@@ -675,7 +675,7 @@ template <typename Real> struct HCoef {
 // the thread's amplitudes are j = tid + k 2^(t-R), handled 8 at a time.
 // Products in the state's precision, sums over the block's amplitudes in
 // FP64.  kLam = false: energies only.
-template <typename Real, int R, bool kLam>
+template <typename Real, int R, bool kLam, bool kRealH>
 __global__ void __launch_bounds__(256)
 k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<Real>::T *psi,
          typename CT<Real>::T *lam, double *E) {
@@ -702,7 +702,7 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
     const int64_t per = (tiles + gridDim.x - 1) / gridDim.x;
     const int64_t t0 = per * blockIdx.x, t_end = min(tiles, t0 + per);
     if (t0 >= t_end) return;
-    const bool real = P.real != 0;
+    constexpr bool real = kRealH;  // every term's coefficient times i^phase is real
     auto fetch = [&](const TileCursor &c, int buf) {
         const C *src = psi + ((int64_t)c.slot << n) + c.base;
         const uint32_t d = sh + (uint32_t)buf * tbytes;
@@ -799,8 +799,13 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
                 }
 #pragma unroll
                 for (int k = 0; k < KC; ++k) {
-                    lr[k] = fmaR(dr[k], p[k].x, fmaR(-di[k], p[k].y, lr[k]));
-                    li[k] = fmaR(dr[k], p[k].y, fmaR(di[k], p[k].x, li[k]));
+                    if constexpr (kRealH) {
+                        lr[k] = fmaR(dr[k], p[k].x, lr[k]);
+                        li[k] = fmaR(dr[k], p[k].y, li[k]);
+                    } else {
+                        lr[k] = fmaR(dr[k], p[k].x, fmaR(-di[k], p[k].y, lr[k]));
+                        li[k] = fmaR(dr[k], p[k].y, fmaR(di[k], p[k].x, li[k]));
+                    }
                 }
             }
             if (add && !lam_ready) {
@@ -1129,14 +1134,19 @@ cudaError_t launch_tile_h(int c128, const HPass &P, int n, int n_slots, const vo
         k<<<blocks, threads, smem, st>>>(P, n, n_slots, psi_t, lam_t, E);
         return cudaGetLastError();
     };
-    auto pick = [&](auto rr) -> cudaError_t {
+    auto pick2 = [&](auto rr, auto re) -> cudaError_t {
         constexpr int RR = decltype(rr)::value;
+        constexpr bool RE = decltype(re)::value;
         if (c128) {
-            if (lam) return go(k_tile_h<double, RR, true>, (const double2 *)psi, (double2 *)lam);
-            return go(k_tile_h<double, RR, false>, (const double2 *)psi, (double2 *)nullptr);
+            if (lam) return go(k_tile_h<double, RR, true, RE>, (const double2 *)psi, (double2 *)lam);
+            return go(k_tile_h<double, RR, false, RE>, (const double2 *)psi, (double2 *)nullptr);
         }
-        if (lam) return go(k_tile_h<float, RR, true>, (const float2 *)psi, (float2 *)lam);
-        return go(k_tile_h<float, RR, false>, (const float2 *)psi, (float2 *)nullptr);
+        if (lam) return go(k_tile_h<float, RR, true, RE>, (const float2 *)psi, (float2 *)lam);
+        return go(k_tile_h<float, RR, false, RE>, (const float2 *)psi, (float2 *)nullptr);
+    };
+    auto pick = [&](auto rr) -> cudaError_t {
+        if (P.real) return pick2(rr, std::true_type());
+        return pick2(rr, std::false_type());
     };
     if (R == 4) return pick(std::integral_constant<int, 4>());
     if (R == 3) return pick(std::integral_constant<int, 3>());
