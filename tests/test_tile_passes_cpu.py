@@ -548,3 +548,42 @@ def test_single_sum_mode_chosen_for_one_rotation_groups():
     w = wl.qcl(8, 2, 2)  # Rx Rz Rx groups
     groups, members, passes, _ = export(circuit_of(w), 8, 3)
     assert not any(P.all_single for P in passes)
+
+
+def _low_rank(vecs, w):
+    """GF(2) rank of the low w bits of the given address vectors."""
+    basis = [0] * w
+    r = 0
+    for v in vecs:
+        x = int(v) & ((1 << w) - 1)
+        for h in range(w - 1, -1, -1):
+            if not (x >> h) & 1:
+                continue
+            if basis[h]:
+                x ^= basis[h]
+            else:
+                basis[h] = x
+                r += 1
+                break
+    return r
+
+
+@pytest.mark.parametrize("name,t,R", [("mcvqe", 10, 4), ("mcvqe", 11, 4), ("qcl", 12, 4)])
+def test_relabeled_lanes_hit_distinct_banks(name, t, R):
+    """The planner's shared-memory positions: in every relabeling pass the
+    lanes of one wavefront (tile bits 0-3) store from four distinct banks
+    pairs, and in every stage the lane bits' load and store vectors stay as
+    independent as the stage's positions allow (here: full rank for at
+    least 90 % of the stages)."""
+    w = wl.mcvqe(22, 8, "nn+nnn", n_refs=2) if name == "mcvqe" else wl.qcl(19, 10, 2)
+    passes = export(circuit_of(w), t, R, relabel=True)[2]
+    csz, sw = 8, 4
+    full = total = 0
+    for P in passes:
+        assert _low_rank([P.nat[b] // csz for b in range(sw)], sw) == sw
+        for s in range(P.n_stages):
+            sg = P.st[s]
+            total += 2
+            full += _low_rank([sg.ldt[k] // csz for k in range(sw)], sw) == sw
+            full += _low_rank([sg.stt[k] // csz for k in range(sw)], sw) == sw
+    assert full >= 0.9 * total
