@@ -334,11 +334,25 @@ __device__ __forceinline__ Real single_sum(const C (&a)[1 << R], const C (&l)[1 
                                            uint32_t md) {
     Real v = 0;
     if (md == 1) {
+        if constexpr (std::is_same<C, float2>::value) {
+            // k3 = sum x0 . y1 - x1 . y0 (as real 2-vectors): two packed FMA
+            // chains, their halves added at the end
+            uint64_t pa = 0, pb = 0;
 #pragma unroll
-        for (int r = 0; r < (1 << R); ++r) {
-            if (r & (1 << I)) continue;
-            const C x0 = a[r], x1 = a[r | (1 << I)], y0 = l[r], y1 = l[r | (1 << I)];
-            v = fmaR(x0.x, y1.x, fmaR(x0.y, y1.y, fmaR(-x1.x, y0.x, fmaR(-x1.y, y0.y, v))));
+            for (int r = 0; r < (1 << R); ++r) {
+                if (r & (1 << I)) continue;
+                pa = f2fma(f2of(a[r]), f2of(l[r | (1 << I)]), pa);
+                pb = f2fma(f2of(a[r | (1 << I)]), f2of(l[r]), pb);
+            }
+            const float2 A = f2unpack(pa), B = f2unpack(pb);
+            v = (A.x + A.y) - (B.x + B.y);
+        } else {
+#pragma unroll
+            for (int r = 0; r < (1 << R); ++r) {
+                if (r & (1 << I)) continue;
+                const C x0 = a[r], x1 = a[r | (1 << I)], y0 = l[r], y1 = l[r | (1 << I)];
+                v = fmaR(x0.x, y1.x, fmaR(x0.y, y1.y, fmaR(-x1.x, y0.x, fmaR(-x1.y, y0.y, v))));
+            }
         }
     } else if (md == 2) {
 #pragma unroll
