@@ -210,7 +210,11 @@ def forward_passes_roofline(sv, w, dev, flush, stream, reps=5, opts=None):
     import torch
     d = 0 if w.inputs is None else 1
     circ = sv.Circuit(w.n_qubits, w.gates, w.n_params, d)
-    info = sv.sv_plan_info(circ, "c64", opts)
+    # the states come back in qubit order: identity-layout passes
+    o = sv.plan_opts() if opts is None else opts
+    ident = sv.plan_opts(o.reg_bits, o.threads_per_block, bool(o.no_fusion), o.epilogue,
+                         o.tile_bits, o.coalesce_bits, no_relabel=True)
+    info = sv.sv_plan_info(circ, "c64", ident)
     n, I = w.n_qubits, w.n_instances
     st = sv.sv_alloc(n, I, "c64", device=dev)
     theta = torch.as_tensor(w.theta, dtype=torch.float64, device=dev).reshape(1, -1)
@@ -225,8 +229,8 @@ def forward_passes_roofline(sv, w, dev, flush, stream, reps=5, opts=None):
     st.free()
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": None,
-            "kernel": f"k_tile_fwd x {info['n_passes']} tile passes of 2^{info['tile_bits']} "
-                      f"amplitudes ({w.name}: {I} states of {n} qubits)",
+            "kernel": f"k_tile_fwd x {info['n_passes']} identity-layout tile passes of "
+                      f"2^{info['tile_bits']} amplitudes ({w.name}: {I} states of {n} qubits)",
             "forward_ms": t * 1e3, "bytes_per_forward": nbytes, "peak_source": src}
 
 
@@ -254,13 +258,18 @@ def adjoint_phases(sv, w, prob, theta, out, info, flush, stream, reps, step=None
     nbytes = 4 * info["n_passes"] * state
     peak, src = measured_hbm_gbs()
     achieved = nbytes / (ph["reverse_ms"] * 1e-3) / 1e9
+    # the gradient's own forward passes (the same relabeling plan), 16 B per
+    # amplitude per pass; the phase also holds |ref>, the group matrices and
+    # the stored checkpoint copies
+    fwd_bytes = 2 * info["n_passes"] * state
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": None,
             "kernel": f"k_tile_rev x {info['n_passes']} reverse tile passes of "
                       f"2^{info['tile_bits']} amplitudes ({w.name}: {I} states of {n} qubits; "
                       "psi and lambda read and written per pass)",
             "reverse_ms": ph["reverse_ms"], "bytes_per_reverse": nbytes, "peak_source": src,
-            "phases_ms": ph}
+            "phases_ms": ph,
+            "forward_phase_frac": fwd_bytes / (ph["forward_ms"] * 1e-3) / 1e9 / peak}
 
 
 def cpu_baseline_device_memory(w, seconds):

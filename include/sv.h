@@ -117,7 +117,11 @@ typedef struct {
                                 tiles are read and written in contiguous runs of
                                 2^coalesce_bits amplitudes (1..tile_bits - 2); 0 = default
                                 (4 complex64 / 3 complex128: 128-byte runs) */
-    int32_t reserved[2];
+    int32_t no_relabel;      /* tile passes of energies and gradients: 1 = every qubit keeps
+                                its own index bit (by default a pass may move the qubits the
+                                next pass needs into the low bits); states returned to the
+                                caller always keep qubit order */
+    int32_t reserved[1];
 } sv_plan_opts;
 
 /* ---------------------------------------------------------------- states */
@@ -352,7 +356,9 @@ sv_status sv_grad_adjoint_multi(const sv_problem *problems, int32_t n_problems,
 
 /* How a circuit will run for a state precision and options: on_chip = 1 when
  * the whole state stays in one block's shared memory, else the number of tile
- * passes over device memory and their tile size (2^tile_bits amplitudes);
+ * passes over device memory and their tile size (2^tile_bits amplitudes), as
+ * the energy and gradient entry points plan them (relabeling passes unless
+ * opts->no_relabel; sv_apply_circuit_batch plans with no_relabel set);
  * n_stages: register stages of the program; n_groups: fused single-qubit
  * groups.  Host-only (plans the circuit, launches nothing).  Any out-pointer
  * may be NULL. */

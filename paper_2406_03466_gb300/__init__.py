@@ -60,7 +60,7 @@ class sv_plan_opts(ctypes.Structure):
     _fields_ = [("reg_bits", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
                 ("no_fusion", ctypes.c_int32), ("epilogue", ctypes.c_int32),
                 ("tile_bits", ctypes.c_int32), ("coalesce_bits", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("no_relabel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class sv_slot(ctypes.Structure):
@@ -202,11 +202,11 @@ class PauliSum:
 
 
 def plan_opts(reg_bits=0, threads_per_block=0, no_fusion=False, epilogue=0,
-              tile_bits=0, coalesce_bits=0) -> sv_plan_opts:
+              tile_bits=0, coalesce_bits=0, no_relabel=False) -> sv_plan_opts:
     o = sv_plan_opts()
     o.reg_bits, o.threads_per_block = int(reg_bits), int(threads_per_block)
     o.no_fusion, o.epilogue, o.tile_bits = int(bool(no_fusion)), int(epilogue), int(tile_bits)
-    o.coalesce_bits = int(coalesce_bits)
+    o.coalesce_bits, o.no_relabel = int(coalesce_bits), int(bool(no_relabel))
     return o
 
 

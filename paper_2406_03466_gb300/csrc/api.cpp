@@ -377,6 +377,7 @@ sv_status check_circuit(const sv_circuit *c, int n_limit) {
 int default_regbits(const sv_plan_opts *o) { return (o && o->reg_bits > 0) ? o->reg_bits : 0; }
 int default_tpb(const sv_plan_opts *o) { return (o && o->threads_per_block > 0) ? o->threads_per_block : 0; }
 bool use_fusion(const sv_plan_opts *o) { return !(o && o->no_fusion); }
+bool use_relabel(const sv_plan_opts *o) { return !(o && o->no_relabel); }
 
 // Planner register bits for a kernel kind: the launch shape decides R first.
 sv_status shape_for(int kind, const sv_circuit &c, int n_groups_hint, sv_dtype dt, int n_slots,
@@ -687,19 +688,23 @@ sv_status tiles_forward(DeviceCtx *ctx, const PlanEntry *pe, int R, sv_dtype dt,
         e = launch_init_states(c128, states, n, src, st);
         if (e != cudaSuccess) return cuda_fail(e, "state init");
     }
+    // A pass that ends at a stored forward state writes its output there
+    // (out of place) and the next pass reads it from there: no copies.  The
+    // last pass always writes `states`.
     const auto &passes = pe->tiles;
+    const void *in = states;
     for (size_t i = 0; i < passes.size(); ++i) {
         const TilePass &tp = passes[i];
         const int64_t tiles = (int64_t)src.n_slots << tp.n_tile_bits;
         const uint32_t smem = tile_fwd_smem(c128, tp);
         if (smem > 220u * 1024u) return fail(SV_ERR_UNSUPPORTED, "tile pass needs too much shared memory");
-        e = launch_tile_fwd(c128, tp, n, src.n_slots, mats, G, states, tile_blocks(ctx, tiles), st);
+        void *out = states;
+        if (ck && every > 0 && (i + 1) % every == 0 && i + 1 < passes.size())
+            out = (char *)ck + ((i + 1) / every - 1) * sbytes;
+        e = launch_tile_fwd(c128, tp, n, src.n_slots, mats, G, out, tile_blocks(ctx, tiles), st,
+                            in);
         if (e != cudaSuccess) return cuda_fail(e, "forward tile pass");
-        if (ck && every > 0 && (i + 1) % every == 0 && i + 1 < passes.size()) {
-            e = cudaMemcpyAsync((char *)ck + ((i + 1) / every - 1) * sbytes, states, sbytes,
-                                cudaMemcpyDeviceToDevice, st);
-            if (e != cudaSuccess) return cuda_fail(e, "checkpoint copy");
-        }
+        in = out;
     }
     return SV_OK;
 }
@@ -714,7 +719,8 @@ sv_status tiles_energies(DeviceCtx *ctx, const sv_problem *p, const double *thet
     sv_status s = tile_cfg(n, dt, p->opts, &cfg, find_tuned(ctx, p, kTileEnergyKey, p->n_instances));
     if (s != SV_OK) return s;
     PlanEntry *pe = nullptr;
-    s = get_plan(ctx, *p->circuit, cfg.R, use_fusion(p->opts), dt, &pe, cfg.t, cfg.c, true);
+    s = get_plan(ctx, *p->circuit, cfg.R, use_fusion(p->opts), dt, &pe, cfg.t, cfg.c,
+                 use_relabel(p->opts));
     if (s != SV_OK) return s;
     ObsEntry *obs = nullptr;
     s = get_obs(ctx, *p->observable, n, dt, &obs, st);
@@ -769,7 +775,8 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
     if (s != SV_OK) return s;
     if (forced) cfg = *forced;
     PlanEntry *pe = nullptr;
-    s = get_plan(ctx, *p->circuit, cfg.R, use_fusion(p->opts), dt, &pe, cfg.t, cfg.c, true);
+    s = get_plan(ctx, *p->circuit, cfg.R, use_fusion(p->opts), dt, &pe, cfg.t, cfg.c,
+                 use_relabel(p->opts));
     if (s != SV_OK) return s;
     if (ddcl_target) {
         // The passes leave qubit q in index bit layout[q]: rewrite the target
@@ -858,17 +865,17 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
         phase_mark(ctx, st);
         SV_CUDA(cudaMemsetAsync(rho, 0, (size_t)src.n_slots * G * 64, st));
         for (int i = npass - 1; i >= 0; --i) {
-            if ((i + 1) % every == 0 && i + 1 < npass) {
-                // restart psi from the stored forward state after pass i
-                SV_CUDA(cudaMemcpyAsync(psi, (char *)ck + (size_t)((i + 1) / every - 1) * cb, cb,
-                                        cudaMemcpyDeviceToDevice, st));
-            }
+            // restart psi from the stored forward state after pass i: the
+            // reverse pass reads it there and writes psi (no copy)
+            const void *psi_in = nullptr;
+            if ((i + 1) % every == 0 && i + 1 < npass)
+                psi_in = (const char *)ck + (size_t)((i + 1) / every - 1) * cb;
             const TilePass &tp = passes[i];
             const int64_t tiles = (int64_t)src.n_slots << tp.n_tile_bits;
             const uint32_t smem = tile_rev_smem(c128, tp);
             if (smem > 220u * 1024u) return fail(SV_ERR_UNSUPPORTED, "reverse pass needs too much shared memory");
             e = launch_tile_rev(c128, tp, n, src.n_slots, mats, G, psi, lam, rho,
-                                tile_blocks(ctx, tiles), st);
+                                tile_blocks(ctx, tiles), st, psi_in);
             if (e != cudaSuccess) return cuda_fail(e, "reverse tile pass");
         }
         phase_mark(ctx, st);
@@ -996,7 +1003,7 @@ sv_status multi_adjoint(DeviceCtx *ctx, const sv_problem *problems, int np,
         m.I = m.p->n_instances;
         m.P = m.p->circuit->n_params;
         sv_status s = get_plan(ctx, *m.p->circuit, cfg.R, use_fusion(m.p->opts), dt, &m.pe, cfg.t,
-                               cfg.c, true);
+                               cfg.c, use_relabel(m.p->opts));
         if (s == SV_OK) s = get_obs(ctx, *m.p->observable, m.n, dt, &m.obs, st);
         if (s == SV_OK) s = get_array(ctx, m.p->refs, sizeof(int64_t) * m.I, &m.drefs);
         HPlanEntry *hp = nullptr;
@@ -2074,7 +2081,7 @@ sv_status sv_plan_info(const sv_circuit *c, sv_dtype dt, const sv_plan_opts *o, 
         s = tile_cfg(c->n_qubits, dt, o, &cfg);
         if (s != SV_OK) return s;
         t = cfg.t;
-        err = plan_passes(*c, cfg.t, cfg.c, cfg.R, use_fusion(o), swz_bits(dt), &h, true);
+        err = plan_passes(*c, cfg.t, cfg.c, cfg.R, use_fusion(o), swz_bits(dt), &h, use_relabel(o));
     } else {
         err = plan_circuit(*c, (o && o->reg_bits > 0) ? o->reg_bits : (dt == SV_C128 ? 3 : 4),
                            use_fusion(o), swz_bits(dt), &h);

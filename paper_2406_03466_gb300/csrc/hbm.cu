@@ -204,6 +204,7 @@ __host__ __device__ inline bool pass_all_real(const TilePass &P) {
 template <typename Real, int R, bool kReal>
 __device__ __forceinline__ void tile_fwd_body(const TilePass &P, int n, int n_slots,
                                               const typename CT<Real>::T *mats, int G,
+                                              const typename CT<Real>::T *src_states,
                                               typename CT<Real>::T *states, int nblk, int blk,
                                               unsigned char *smem) {
     using C = typename CT<Real>::T;
@@ -235,7 +236,7 @@ __device__ __forceinline__ void tile_fwd_body(const TilePass &P, int n, int n_sl
     const int64_t t0 = per * blk, t_end = min(tiles, t0 + per);
     if (t0 >= t_end) return;
     auto fetch = [&](const TileCursor &c, int buf) {
-        const C *src = states + ((int64_t)c.slot << n) + c.base;
+        const C *src = src_states + ((int64_t)c.slot << n) + c.base;
         const uint32_t d = sh + (uint32_t)buf * tbytes;
 #pragma unroll
         for (int k = 0; k < NA; ++k) cp_async_amp(d + (p0 ^ xsel<R>(k, pk)), src + (g0 ^ xsel<R>(k, gk)));
@@ -278,12 +279,17 @@ __device__ __forceinline__ void tile_fwd_body(const TilePass &P, int n, int n_sl
     }
 }
 
+// src: the states the pass reads; states: where it writes them (the same
+// buffer, or another one when the pass's output is also kept as a stored
+// forward state).
 template <typename Real, int R, bool kReal>
 __global__ void __launch_bounds__(256, R >= 4 ? 2 : 3)
 k_tile_fwd(const __grid_constant__ TilePass P, int n, int n_slots,
-           const typename CT<Real>::T *mats, int G, typename CT<Real>::T *states) {
+           const typename CT<Real>::T *mats, int G, const typename CT<Real>::T *src,
+           typename CT<Real>::T *states) {
     extern __shared__ __align__(16) unsigned char smem[];
-    tile_fwd_body<Real, R, kReal>(P, n, n_slots, mats, G, states, gridDim.x, blockIdx.x, smem);
+    tile_fwd_body<Real, R, kReal>(P, n, n_slots, mats, G, src, states, gridDim.x, blockIdx.x,
+                                  smem);
 }
 
 // The derivative of a rotation exp(-i theta P / 2) inside a fused group is
@@ -447,6 +453,7 @@ __device__ void flush_acc(const TilePass &P, Real *acc, int wps, double *rho_g, 
 template <typename Real, int R, bool kSingle, bool kReal>
 __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_slots,
                                               const typename CT<Real>::T *mats, int G,
+                                              const typename CT<Real>::T *psi_src,
                                               typename CT<Real>::T *psi, typename CT<Real>::T *lam,
                                               double *rho_g, int nblk, int blk, unsigned char *smem) {
     using C = typename CT<Real>::T;
@@ -484,7 +491,7 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
     // psi tile of buffer j at [j tbytes], lambda tile at [(2 + j) tbytes]
     auto fetch = [&](const TileCursor &c, int buf) {
         const int64_t off = ((int64_t)c.slot << n) + c.base;
-        const C *sp = psi + off, *sl = lam + off;
+        const C *sp = psi_src + off, *sl = lam + off;
         const uint32_t dp = sh + (uint32_t)buf * tbytes, dl = dp + 2 * tbytes;
 #pragma unroll
         for (int k = 0; k < NA; ++k) {
@@ -576,11 +583,11 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
 template <typename Real, int R, bool kSingle, bool kReal>
 __global__ void __launch_bounds__(256, R >= 4 ? 1 : 2)
 k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
-           const typename CT<Real>::T *mats, int G, typename CT<Real>::T *psi,
-           typename CT<Real>::T *lam, double *rho_g) {
+           const typename CT<Real>::T *mats, int G, const typename CT<Real>::T *psi_src,
+           typename CT<Real>::T *psi, typename CT<Real>::T *lam, double *rho_g) {
     extern __shared__ __align__(16) unsigned char smem[];
-    tile_rev_body<Real, R, kSingle, kReal>(P, n, n_slots, mats, G, psi, lam, rho_g, gridDim.x,
-                                           blockIdx.x, smem);
+    tile_rev_body<Real, R, kSingle, kReal>(P, n, n_slots, mats, G, psi_src, psi, lam, rho_g,
+                                           gridDim.x, blockIdx.x, smem);
 }
 
 // Sum of v over the block (every thread gets it); red: one double per warp.
@@ -626,7 +633,8 @@ k_tile_fwd_multi(const MultiItem *items, int n_items) {
     MultiItem it;
     unsigned char *rest = multi_item(items, n_items, it, smem);
     const TilePass &P = *reinterpret_cast<const TilePass *>(smem);
-    tile_fwd_body<Real, R, false>(P, it.n, it.n_slots, (const C *)it.mats, it.G, (C *)it.psi,
+    tile_fwd_body<Real, R, false>(P, it.n, it.n_slots, (const C *)it.mats, it.G, (const C *)it.psi,
+                                  (C *)it.psi,
                                   it.block_end - it.block_begin, (int)blockIdx.x - it.block_begin,
                                   rest);
 }
@@ -641,7 +649,7 @@ k_tile_rev_multi(const MultiItem *items, int n_items) {
     unsigned char *rest = multi_item(items, n_items, it, smem);
     const TilePass &P = *reinterpret_cast<const TilePass *>(smem);
     tile_rev_body<Real, R, false, false>(P, it.n, it.n_slots, (const C *)it.mats, it.G,
-                                         (C *)it.psi, (C *)it.lam, it.rho,
+                                         (const C *)it.psi, (C *)it.psi, (C *)it.lam, it.rho,
                                          it.block_end - it.block_begin,
                                          (int)blockIdx.x - it.block_begin, rest);
 }
@@ -1093,23 +1101,26 @@ uint32_t tile_rev_smem(int c128, const TilePass &P) {
 }
 
 cudaError_t launch_tile_fwd(int c128, const TilePass &P, int n, int n_slots, const void *mats,
-                            int G, void *states, int64_t max_blocks, cudaStream_t st) {
+                            int G, void *states, int64_t max_blocks, cudaStream_t st,
+                            const void *src) {
     const uint32_t smem = tile_fwd_smem(c128, P);
     const int threads = 1 << (P.t - P.R);
+    if (!src) src = states;
     HBM_DISPATCH_R(c128, P.R, {
         using C = typename CT<Real>::T;
         auto k = pass_all_real(P) ? k_tile_fwd<Real, RR, true> : k_tile_fwd<Real, RR, false>;
         cudaError_t e = allow_smem(k, smem);
         if (e != cudaSuccess) return e;
         const int blocks = fill_blocks(k, threads, smem, max_blocks);
-        k<<<blocks, threads, smem, st>>>(P, n, n_slots, (const C *)mats, G, (C *)states);
+        k<<<blocks, threads, smem, st>>>(P, n, n_slots, (const C *)mats, G, (const C *)src,
+                                         (C *)states);
     });
     return cudaGetLastError();
 }
 
 cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, const void *mats,
                             int G, void *psi, void *lam, double *rho_g, int64_t max_blocks,
-                            cudaStream_t st) {
+                            cudaStream_t st, const void *psi_src) {
     const uint32_t smem = tile_rev_smem(c128, P);
     const int threads = 1 << (P.t - P.R);
     HBM_DISPATCH_R(c128, P.R, {
@@ -1121,7 +1132,8 @@ cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, con
         cudaError_t e = allow_smem(k, smem);
         if (e != cudaSuccess) return e;
         const int blocks = fill_blocks(k, threads, smem, max_blocks);
-        k<<<blocks, threads, smem, st>>>(P, n, n_slots, (const C *)mats, G, (C *)psi, (C *)lam,
+        k<<<blocks, threads, smem, st>>>(P, n, n_slots, (const C *)mats, G,
+                                         (const C *)(psi_src ? psi_src : psi), (C *)psi, (C *)lam,
                                          rho_g);
     });
     return cudaGetLastError();

@@ -18,13 +18,16 @@ cudaError_t launch_init_states(int c128, void *states, int n, const SlotSource &
 uint32_t tile_fwd_smem(int c128, const TilePass &P);
 uint32_t tile_rev_smem(int c128, const TilePass &P);
 // Forward pass P over n_slots states of n qubits (mats: [slots][G][4]).
+// src (null: states) holds the pass's input; the output goes to states.
 cudaError_t launch_tile_fwd(int c128, const TilePass &P, int n, int n_slots, const void *mats,
-                            int G, void *states, int64_t max_blocks, cudaStream_t st);
+                            int G, void *states, int64_t max_blocks, cudaStream_t st,
+                            const void *src = nullptr);
 // Reverse pass P on psi and lambda; adds the reduced matrices of its
-// parametrised groups to rho_g[slot][G][8].
+// parametrised groups to rho_g[slot][G][8].  psi_src (null: psi) holds the
+// psi the pass reads (a stored forward state); its output psi goes to psi.
 cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, const void *mats,
                             int G, void *psi, void *lam, double *rho_g, int64_t max_blocks,
-                            cudaStream_t st);
+                            cudaStream_t st, const void *psi_src = nullptr);
 // Tile passes of several problems in one launch (forward, or reverse with
 // rev): items sorted by block_begin, device memory; every item uses the same
 // tile shape (threads = 2^(t - R)).  smem: the largest over the items of
