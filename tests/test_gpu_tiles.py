@@ -4,7 +4,10 @@ Small states are forced through tile passes with `tile_bits` so that every
 tile size, register width and checkpoint interval is compared with the CPU
 oracle; 14-qubit states take the path on their own; reduced circuit-learning
 and multi-contracted VQE workloads at 16-20 qubits check sampled gradient
-entries.  Tolerances as in test_gpu_parity.
+entries; the benchmark's 28-qubit workload itself is checked at full size
+through properties that hold at any size (the closed form at theta = 0, and
+the complex64 adjoint against complex128 parameter shift on a subsample).
+Tolerances as in test_gpu_parity.
 """
 import numpy as np
 import pytest
@@ -170,3 +173,69 @@ def test_uneven_batch_adjoint(sv, dtype):
     L, E, g = oracle.grad_param_shift(ws[1])
     close(outs[1][1].cpu().numpy(), E, TOL[dtype]["E"])
     close(outs[1][2].cpu().numpy()[: ws[1].n_params], g, TOL[dtype]["G"])
+
+
+# ------------------------------------------------ the 28-qubit workload itself
+
+def _basis_state_at_zero_angles(w, ref):
+    """The index of the basis state the circuit maps |ref> to when every
+    rotation angle is 0 (rotations are then identities, CNOTs permute)."""
+    b = [(int(ref) >> q) & 1 for q in range(w.n_qubits)]
+    for g in w.gates:
+        if g.op in ("RX", "RY", "RZ"):
+            continue
+        assert g.op == "CNOT", g.op
+        b[g.target] ^= b[g.control]
+    return sum(bit << q for q, bit in enumerate(b))
+
+
+def _closed_form_energy(w, j):
+    """<j|H|j> for a basis state: only terms without X or Y letters count,
+    each with sign (-1)^(number of its Z letters on 1-bits of j)."""
+    letters = np.asarray(w.pauli_letters)
+    e = 0.0
+    for row, c in zip(letters, w.pauli_coeffs):
+        if np.any((row == 1) | (row == 2)):
+            continue
+        zs = [q for q in range(w.n_qubits) if row[q] == 3]
+        e += c * (-1) ** sum((j >> q) & 1 for q in zs)
+    return e
+
+
+def test_mcvqe28_full_size_closed_form(sv):
+    """The benchmark's 28-qubit multi-contracted VQE (8 states of 2 GiB), in
+    the launch configuration the benchmark uses (autotuned tile passes): at
+    theta = 0 every instance energy equals the closed form of its basis
+    state."""
+    import torch
+    w = wl.config(4)
+    prob = sv.Problem.from_spec(w, "c64")
+    th = torch.zeros(w.n_params, dtype=torch.float64, device="cuda")
+    l_, e_ = sv.sv_energies(prob, th)
+    want = [_closed_form_energy(w, _basis_state_at_zero_angles(w, r)) for r in w.refs]
+    close(e_.cpu().numpy(), want, TOL["c64"]["E"])
+
+
+def test_mcvqe28_full_size_adjoint_vs_param_shift_c128(sv):
+    """The 28-qubit adjoint gradient (complex64, relabeling passes, stored
+    forward states) on a 16-parameter subsample against parameter shift in
+    complex128 on the GPU (segments of the parameter-shift batch).  Two of
+    the eight reference states keep the complex128 side (FP64 arithmetic,
+    scarce on this GPU) to about 40 s; every state is a full 2^28 one."""
+    import dataclasses
+    import torch
+    w8 = wl.config(4)
+    w = dataclasses.replace(w8, refs=w8.refs[:2], weights=w8.weights[:2])
+    th = theta_of(w)
+    prob64 = sv.Problem.from_spec(w, "c64")
+    g64 = sv.sv_grad_adjoint(prob64, th)[2].cpu().numpy()
+    prob128 = sv.Problem.from_spec(w, "c128")
+    I = w.n_instances
+    wts = np.asarray(w.weights)
+    ks = list(range(0, w.n_params, w.n_params // 16))[:16]
+    for k in ks:
+        seg = torch.empty(2 * I, dtype=torch.float64, device="cuda")
+        sv.sv_param_shift_energies_range(prob128, th, I + 2 * k * I, 2 * I, seg)
+        e = seg.cpu().numpy()
+        g128 = float(np.dot(wts, 0.5 * (e[:I] - e[I:])))
+        assert abs(g64[k] - g128) <= TOL["c64"]["G"] * max(1.0, abs(g128)), (k, g64[k], g128)
