@@ -587,3 +587,15 @@ def test_relabeled_lanes_hit_distinct_banks(name, t, R):
             full += _low_rank([sg.ldt[k] // csz for k in range(sw)], sw) == sw
             full += _low_rank([sg.stt[k] // csz for k in range(sw)], sw) == sw
     assert full >= 0.9 * total
+
+
+def test_plan_info_reports_the_relabeling_plan_and_no_relabel():
+    """sv_plan_info gives the pass count of the plan the energy and gradient
+    paths run (relabeling), and of the identity layout with no_relabel."""
+    w = wl.mcvqe(22, 8, "nn+nnn", n_refs=2)
+    c = circuit_of(w)
+    moved = sv.sv_plan_info(c, "c64", sv.plan_opts(reg_bits=4, tile_bits=10))
+    ident = sv.sv_plan_info(c, "c64", sv.plan_opts(reg_bits=4, tile_bits=10, no_relabel=True))
+    assert moved["n_passes"] == len(export(c, 10, 4, relabel=True)[2])
+    assert ident["n_passes"] == len(export(c, 10, 4)[2])
+    assert moved["n_passes"] < ident["n_passes"]
