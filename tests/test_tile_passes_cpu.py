@@ -599,3 +599,26 @@ def test_plan_info_reports_the_relabeling_plan_and_no_relabel():
     assert moved["n_passes"] == len(export(c, 10, 4, relabel=True)[2])
     assert ident["n_passes"] == len(export(c, 10, 4)[2])
     assert moved["n_passes"] < ident["n_passes"]
+
+
+@pytest.mark.parametrize("seed", [3, 4, 5, 6])
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_relabeling_random_circuits(seed, dtype):
+    """Random circuits with CZ, encodings and long-range CNOTs at 10-11
+    qubits through narrow tiles (many passes, many relabelings), both
+    amplitude sizes: the forward model leaves the oracle's state in the
+    exported layout."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(10, 12))
+    t, R = [(7, 2), (8, 3), (7, 1)][seed % 3]
+    if dtype == 1 and R > 3:
+        R = 3
+    w = wl.random_workload(n, 90, 4, 1, seed=100 + seed, with_encoding=bool(seed % 2))
+    groups, members, passes, lay = export(circuit_of(w), t, R, dtype=dtype, relabel=True)
+    assert sorted(lay) == list(range(n))
+    xs = [None if w.inputs is None else w.inputs[0]]
+    mats = [group_mats(groups, members, w.theta, xs[0])]
+    psi = init_states(w, 1)
+    for P in passes:
+        run_fwd(P, psi, mats, 16 if dtype else 8)
+    np.testing.assert_allclose(psi[0], to_layout(oracle.state(w, instance=0), lay), atol=1e-12)
