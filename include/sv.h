@@ -221,7 +221,8 @@ sv_status sv_param_shift_energies(const sv_problem *problem, const double *theta
 
 /* Parameter-shift gradient (Sec. 4.1: O(2 N_H N_theta) shifted circuits per
  * update; here the whole <H> per circuit, so (2P + 1) circuits per instance,
- * all in one batched launch): dE_i/dtheta_k = 1/2 [E_i(theta + pi/2 e_k)
+ * all in one batched launch for states on chip, followed by the assembly as a
+ * programmatic dependent launch): dE_i/dtheta_k = 1/2 [E_i(theta + pi/2 e_k)
  * - E_i(theta - pi/2 e_k)], chained through the cost.  theta: device [P].
  * energy_out: device [n_instances] or NULL; loss_out: device [1] or NULL;
  * grad_out: device [P].  Uses library scratch of (2P+1) I doubles. */
