@@ -82,7 +82,8 @@ EXPORTED = ("sv_alloc", "sv_free", "sv_state_info", "sv_apply_circuit_batch",
             "sv_expect_pauli_sum", "sv_energies", "sv_param_shift_energies", "sv_grad_param_shift", "sv_grad_adjoint",
             "sv_grad_param_shift_plain", "sv_grad_param_shift_noalloc", "sv_autotune",
             "sv_tuned_shape", "sv_plan_info", "sv_h_plan_info", "sv_phase_timing",
-            "sv_grad_adjoint_multi", "sv_grad_ddcl", "sv_param_shift_energies_range", "sv_sample",
+            "sv_grad_adjoint_multi", "sv_grad_ddcl", "sv_grad_ddcl_param_shift",
+            "sv_grad_param_shift_host", "sv_param_shift_energies_range", "sv_sample",
             "sv_param_shift_combine",
             "sv_last_phase_ms", "sv_status_string",
             "sv_last_error",
