@@ -622,3 +622,36 @@ def test_relabeling_random_circuits(seed, dtype):
     for P in passes:
         run_fwd(P, psi, mats, 16 if dtype else 8)
     np.testing.assert_allclose(psi[0], to_layout(oracle.state(w, instance=0), lay), atol=1e-12)
+
+
+@pytest.mark.parametrize("name", ["mcvqe8", "rand8_cz"])
+def test_relabeled_sweep_with_moved_hamiltonian(name):
+    """A full relabeled sweep: forward passes, then lambda = H psi by the H
+    passes of the Hamiltonian moved to the final layout (the same plan the
+    library builds), then the reverse passes: energies and gradient equal the
+    oracle's."""
+    w = CASES[name]()
+    n = w.n_qubits
+    groups, members, passes, lay = export(circuit_of(w), 7, 2, relabel=True)
+    I = w.n_instances
+    xs = [None if w.inputs is None else w.inputs[i] for i in range(I)]
+    mats = [group_mats(groups, members, w.theta, xs[i]) for i in range(I)]
+    psi = init_states(w, I)
+    for P in passes:
+        run_fwd(P, psi, mats, 8)
+    obs = sv.PauliSum(n, moved_letters(np.asarray(w.pauli_letters), lay), w.pauli_coeffs)
+    plan = export_h(obs, 7, 4)
+    lam = np.zeros_like(psi)
+    E = np.zeros(I)
+    for i in range(I):
+        lam[i], E[i] = run_h(plan, psi[i], n)
+    rho = [[np.zeros((2, 2), complex) for _ in groups] for _ in range(I)]
+    for P in reversed(passes):
+        run_rev(P, psi, lam, mats, rho, 8)
+    wts = oracle.cost_weights(w, E)
+    grad = np.zeros(w.n_params)
+    for i in range(I):
+        group_gradients(groups, members, rho[i], w.theta, xs[i], grad, wts[i])
+    L, E_o, g_o = oracle.grad_param_shift(w)
+    np.testing.assert_allclose(E, E_o, atol=1e-12)
+    np.testing.assert_allclose(grad, g_o, atol=1e-11)
