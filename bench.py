@@ -1,31 +1,40 @@
-"""Benchmark: batched parameter-shift gradients of a multi-contracted VQE.
+"""Benchmark: batched gradients of the paper's circuit workloads on one GB300.
 
-Workload (one step = one full gradient): 8 qubits (monomers), 4 layers of Ry
-on every qubit + CNOT ladder (32 parameters), the Eq. 2 exciton Hamiltonian
-with all 28 pairs (128 Pauli terms, synthetic coefficients), 9 reference
-states; the parameter-shift batch is 2 x 32 x 9 + 9 = 585 circuits, each with
-its full <H>, run by one batched kernel launch, then the gradient assembly
-as a dependent launch that overlaps it.
+Default workload (one step = one full gradient): the 28-qubit multi-contracted
+VQE -- 8 layers of Ry on every qubit + CNOT ladder (224 parameters), the Eq. 2
+exciton Hamiltonian over nearest and next-nearest pairs (268 Pauli terms,
+synthetic coefficients), 8 reference states of 2^28 complex64 amplitudes
+(2 GiB each) in device memory -- by the adjoint sweep of tile passes.
 Inputs are seeded and synthetic.
 
-Printed (one JSON line on rank 0): gradients/s of the batched complex64
-path (value), shifted circuits/s, the adjoint gradient, the plain
-one-circuit-per-launch complex128 form and the batched complex128 form, the
-roofline of the dominant kernel, the CPU oracle timed on the host cores, and
-an end-to-end number through the C ABI with host buffers.
+Printed (one JSON line on rank 0): gradients/s (value), the HBM roofline of
+the dominant kernel (the reverse tile passes) and of gate application (the
+identity-layout forward passes), the CPU oracle timed on the host cores
+(extrapolated from a bounded sample), an end-to-end number through the C ABI
+with host buffers, and under ``forms`` the 8-qubit MC-VQE (585 shifted
+circuits in one batched launch; adjoint; complex128; the plain
+one-circuit-per-launch complex128 form) and the 20-qubit circuit-learning
+gate application.
 
-``--impl reference`` times the CPU oracle (the reference arm: there is no
-runnable reference implementation, only the paper) on the same workload.
-Multi-GPU (torchrun): every rank runs its own replica of the workload; the
-value is the gradients of all ranks over the slowest rank's time.
+``--workload`` selects another configuration (mcvqe8, qcl20, qcl-uneven,
+ddcl).  ``--impl reference`` times the CPU oracle (the reference arm: there
+is no runnable reference implementation, only the paper) on the same
+workload.  Multi-GPU: ``--gpus N`` without a torchrun environment starts N
+ranks itself under ``torch.distributed.run``; every rank runs its own replica
+of the workload and the value is the gradients of all ranks over the slowest
+rank's time.  ``--workload mcvqe8 --split vqpu`` instead splits one
+parameter-shift batch into one contiguous segment per rank with one
+allgather of the energies (the paper's virtual-QPU split, Sec. 4.1).
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import socket
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -36,7 +45,7 @@ sys.path.insert(0, ROOT)
 import workloads as wl  # noqa: E402
 
 METRIC = "gradients/sec & shifted circuits/sec, batched/adjoint vs plain; % HBM roofline"
-WORKLOAD = ("mcvqe8: multi-contracted VQE gradient, 8 qubits, 4 layers Ry + CNOT ladder "
+WORKLOAD_MCVQE8 = ("mcvqe8: multi-contracted VQE gradient, 8 qubits, 4 layers Ry + CNOT ladder "
             "(32 params), 128-term Eq. 2 Hamiltonian, 9 references, 585 shifted circuits")
 L2_FLUSH_BYTES = 256 << 20   # larger than the 126.5 MiB L2
 
@@ -46,15 +55,20 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=None)
-    ap.add_argument("--workload", default="mcvqe8",
+    ap.add_argument("--workload", default="mcvqe28",
                     choices=["mcvqe8", "qcl20", "mcvqe28", "qcl-uneven", "ddcl"],
-                    help="mcvqe8 (default): batched parameter-shift gradient of the 8-qubit "
-                         "MC-VQE; qcl20 / mcvqe28: adjoint gradient of the 20-qubit circuit "
-                         "learning / 28-qubit MC-VQE workload (states in device memory); "
+                    help="mcvqe28 (default): adjoint gradient of the 28-qubit MC-VQE (8 states "
+                         "of 2 GiB in device memory); qcl20: the same for the 20-qubit circuit "
+                         "learning; mcvqe8: batched parameter-shift gradient of the 8-qubit "
+                         "MC-VQE (on chip); "
                          "qcl-uneven: adjoint gradients of 8 circuit-learning circuits of "
                          "20-24 qubits and depth 4-12 in one graph launch; ddcl: data-driven "
                          "circuit learning (Sec. 4.2) at 26 qubits (--qubits for 20-24)")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--split", default="replicas", choices=["replicas", "vqpu"],
+                    help="multi-GPU mode: replicas (default; every rank its own gradients) or "
+                         "vqpu (mcvqe8 only: one parameter-shift batch split into one segment "
+                         "per rank, one allgather of energies, Sec. 4.1)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true", help="skip adjoint/plain/c128 side runs")
     ap.add_argument("--energy-shape", default="",
@@ -119,7 +133,8 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.idx = device_index
         self.proc = None
-        self.path = os.path.join("/tmp", f"svclocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="svclocks_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
@@ -380,20 +395,35 @@ def run_device_memory(args, sv, dev, stream, dist, world, rank):
         result["roofline_forward"] = forward_passes_roofline(sv, w, dev, flush, stream,
                                                              reps=3 if w.n_qubits > 24 else 5,
                                                              opts=opts)
-        th_host = torch.as_tensor(w.theta, dtype=torch.float64).pin_memory()
-        g_host = torch.empty(w.n_params, dtype=torch.float64).pin_memory()
-        th_dev = torch.empty_like(theta)
+        # end to end through the C ABI with host buffers: theta from host
+        # memory in, loss + gradient + instance energies back to host memory
+        # (sv_grad_adjoint_host returns once they are there)
+        th_host = torch.as_tensor(w.theta, dtype=torch.float64)
+        g_host = torch.empty(w.n_params, dtype=torch.float64)
+        l_host = torch.empty(1, dtype=torch.float64)
+        e_host = torch.empty(w.n_instances, dtype=torch.float64)
+        sv.sv_grad_adjoint_host(prob, th_host, e_host, l_host, g_host, stream=stream)
+        reps = max(2, args.steps // 2)
         t0 = time.perf_counter()
-        reps = max(1, args.steps // 2)
         for _ in range(reps):
-            th_dev.copy_(th_host, non_blocking=True)
-            l_, e_, g_ = sv.sv_grad_adjoint(prob, th_dev, None, *out)
-            g_host.copy_(g_[: w.n_params], non_blocking=True)
-            stream.synchronize()
+            sv.sv_grad_adjoint_host(prob, th_host, e_host, l_host, g_host, stream=stream)
         result["e2e"] = {"value": reps / (time.perf_counter() - t0), "unit": "gradients/s",
                          "h2d_bytes_per_step": 8 * w.n_params,
-                         "d2h_bytes_per_step": 8 * w.n_params}
+                         "d2h_bytes_per_step": 8 * (w.n_params + 1 + w.n_instances),
+                         "timing": "host wall clock per step; sv_grad_adjoint_host returns once "
+                                   "the results are in host memory"}
         result["cpu_baseline"] = cpu_baseline_device_memory(w, min(args.cpu_seconds, 10.0))
+        if not args.no_extras and not args.qubits:
+            forms = {}
+            if args.workload == "mcvqe28":
+                # gate application with complex Rx.Rz.Rx groups: the 20-qubit
+                # circuit-learning batch (64 states, 512 MiB)
+                forms["qcl20_gate_application"] = forward_passes_roofline(
+                    sv, wl.config(3), dev, flush, stream)
+            _, _, _, side = mcvqe8_side(sv, dev, stream, flush, 2000)
+            side["cpu_baseline"] = cpu_baseline(min(args.cpu_seconds, 3.0))
+            forms["mcvqe8"] = side
+            result["forms"] = forms
         print(json.dumps(result))
     if dist:
         dist.barrier()
@@ -615,19 +645,214 @@ def run_uneven(args, sv, dev, stream, dist, world, rank):
         dist.destroy_process_group()
 
 
+def mcvqe8_side(sv, dev, stream, flush, steps, extras=True):
+    """The 8-qubit MC-VQE batched parameter-shift gradient (585 circuits in one
+    energy launch + the dependent assembly) and its side forms: the energy
+    kernel alone against the FP32 ALU roof, the host-buffer entry point, the
+    adjoint, both complex128 forms and the plain one-circuit-per-launch
+    complex128 form.  Returns (problem, outputs, dict)."""
+    import torch
+    w = wl.config(1)
+    B = w.n_slots_param_shift
+    prob = sv.Problem.from_spec(w, "c64", device=dev)
+    theta = torch.as_tensor(w.theta, dtype=torch.float64, device=dev)
+    out = sv._outputs(prob, dev, None, None, None)
+    e_buf = torch.empty(B, dtype=torch.float64, device=dev)
+    sv.sv_autotune(prob, theta)
+    tuned = {"energy": sv.sv_tuned_shape(prob, 1)[:2], "adjoint": sv.sv_tuned_shape(prob, 2)[:2]}
+    fn = lambda: sv.sv_grad_param_shift(prob, theta, *out)  # noqa: E731
+    for _ in range(20):
+        fn()
+    res = {"workload": WORKLOAD_MCVQE8, "circuits_per_gradient": B,
+           "tuned_shape_c64": {k: {"reg_bits": v[0], "threads_per_block": v[1]}
+                               for k, v in tuned.items()}}
+    t = timed_loop(fn, steps, flush, stream)
+    res["gradients_per_s"] = steps / t
+    res["shifted_circuits_per_s"] = steps / t * B
+    # dominant kernel alone: the batched energies of all 585 circuits
+    k_steps = max(200, steps // 4)
+    fn = lambda: sv.sv_param_shift_energies(prob, theta, e_buf)  # noqa: E731
+    for _ in range(20):
+        fn()
+    t_k = timed_loop(fn, k_steps, flush, stream) / k_steps
+    flops = algorithmic_flops(w, B)
+    peak = fp32_peak_tflops()
+    achieved = flops / t_k / 1e12
+    res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                       "frac": achieved / peak, "traffic": None,
+                       "kernel": f"k_energy<float,{tuned['energy'][0]}> (batched shifted-circuit "
+                                 "energies; the gradient assembly follows as a dependent launch)",
+                       "kernel_us": t_k * 1e6,
+                       "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    # end to end through the C ABI: theta from host memory in, loss +
+    # gradient + energies back to host memory, every step
+    th_host = torch.as_tensor(w.theta, dtype=torch.float64).pin_memory()
+    g_host = torch.empty(w.n_params, dtype=torch.float64).pin_memory()
+    l_host = torch.empty(1, dtype=torch.float64).pin_memory()
+    e_host = torch.empty(w.n_instances, dtype=torch.float64).pin_memory()
+    e2e_steps = max(200, steps // 4)
+
+    def e2e_step():
+        sv.sv_grad_param_shift_host(prob, th_host, e_host, l_host, g_host, stream=stream)
+
+    for _ in range(10):
+        e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    t_e2e = time.perf_counter() - t0
+    res["e2e"] = {"value": e2e_steps / t_e2e, "unit": "gradients/s",
+                  "h2d_bytes_per_step": 8 * w.n_params,
+                  "d2h_bytes_per_step": 8 * (w.n_params + 1 + w.n_instances),
+                  "timing": "host wall clock per step; sv_grad_param_shift_host returns once "
+                            "the results are in host memory"}
+    if extras:
+        n = max(200, steps // 4)
+        fn = lambda: sv.sv_grad_adjoint(prob, theta, None, *out)  # noqa: E731
+        for _ in range(20):
+            fn()
+        res["adjoint_c64_gradients_per_s"] = n / timed_loop(fn, n, flush, stream)
+        prob128 = sv.Problem.from_spec(w, "c128", device=dev)
+        out128 = sv._outputs(prob128, dev, None, None, None)
+        sv.sv_autotune(prob128, theta)
+        fn = lambda: sv.sv_grad_param_shift(prob128, theta, *out128)  # noqa: E731
+        for _ in range(20):
+            fn()
+        res["batched_c128_gradients_per_s"] = n / timed_loop(fn, n, flush, stream)
+        fn = lambda: sv.sv_grad_adjoint(prob128, theta, None, *out128)  # noqa: E731
+        for _ in range(20):
+            fn()
+        res["adjoint_c128_gradients_per_s"] = n / timed_loop(fn, n, flush, stream)
+        # the plain form is host-driven (one launch per gate and term): wall clock
+        sv.sv_grad_param_shift_plain(prob128, theta, *out128)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 2
+        for _ in range(reps):
+            sv.sv_grad_param_shift_plain(prob128, theta, *out128)
+        torch.cuda.synchronize()
+        res["plain_c128_gradients_per_s"] = reps / (time.perf_counter() - t0)
+        res["plain_c128_launches_per_gradient"] = B * (1 + len(w.gates) + w.n_terms) + 1
+    return prob, theta, out, res
+
+
+def run_mcvqe8(args, sv, dev, stream, dist, world, rank):
+    """The 8-qubit batched parameter-shift gradient as the bench line
+    (replicas, or --split vqpu: one batch split over the ranks)."""
+    import torch
+    w = wl.config(1)
+    B = w.n_slots_param_shift
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    shape_opts = None
+    if args.energy_shape:
+        R_, T_ = (int(x) for x in args.energy_shape.split(","))
+        shape_opts = sv.plan_opts(reg_bits=R_, threads_per_block=T_)
+    prob = sv.Problem.from_spec(w, "c64", device=dev, opts=shape_opts)
+    theta = torch.as_tensor(w.theta, dtype=torch.float64, device=dev)
+    out = sv._outputs(prob, dev, None, None, None)
+    if shape_opts is None:
+        sv.sv_autotune(prob, theta)
+    vqpu_split = args.split == "vqpu" and dist is not None
+    if vqpu_split:
+        from paper_2406_03466_gb300 import vqpu
+
+        def step():
+            vqpu.param_shift_gradient(prob, theta, dist, stream=stream)
+    else:
+        def step():
+            sv.sv_grad_param_shift(prob, theta, *out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    t_dev = timed_loop(step, args.steps, flush, stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    if vqpu_split:
+        # one gradient per step for the whole job: strong scaling
+        t = torch.tensor([t_dev], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev = float(t.item())
+        grads_per_s = args.steps / t_dev
+    else:
+        grads_per_s, t_dev = job_throughput(t_dev, args.steps, dist, dev)
+    lo, hi = (0, B)
+    if vqpu_split:
+        from paper_2406_03466_gb300 import vqpu
+        lo, hi = vqpu.segment(B, world, rank)
+    result = {"metric": METRIC, "value": grads_per_s, "unit": "gradients/s", "n_gpus": world,
+              "steps": args.steps, "warmup": args.warmup,
+              "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+              "scaling": "strong" if vqpu_split else "weak", "vs_baseline": None, "dtype": "c64",
+              "data": "synthetic",
+              "config": {"workload": WORKLOAD_MCVQE8, "circuits_per_gradient": B,
+                         "l2": "flushed before every timed step (256 MiB write, untimed)",
+                         "parallelism": (f"vqpu x{world}: one segment of the batch per rank "
+                                         f"(rank 0: slots [{lo}, {hi})) + NCCL allgather of "
+                                         "energies" if vqpu_split else f"replicas x{world}")},
+              "shifted_circuits_per_s": grads_per_s * B,
+              # k_energy + k_ps_combine_dep, or per rank its segment's k_energy + the combine
+              "gpu_launches": 2 * args.steps,
+              "clocks": clk, "wall_s_timed_region": t_wall}
+    if rank == 0:
+        _, _, _, side = mcvqe8_side(sv, dev, stream, flush, max(200, args.steps // 4),
+                                    extras=not args.no_extras)
+        result["config"]["tuned_shape_c64"] = side.pop("tuned_shape_c64")
+        result["roofline"] = side.pop("roofline")
+        result["e2e"] = side.pop("e2e")
+        for k in ("workload", "circuits_per_gradient", "gradients_per_s", "shifted_circuits_per_s"):
+            side.pop(k, None)
+        if not args.no_extras:
+            # the metric's "% HBM roofline": gate application on the 20-qubit
+            # circuit-learning batch (64 states, 512 MiB)
+            result["hbm_gate_passes"] = forward_passes_roofline(sv, wl.config(3), dev, flush, stream)
+            result["forms"] = side
+        result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(result))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _free_port():
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        return so.getsockname()[1]
+
+
+def relaunch_cmd(argv, gpus, port):
+    """The torch.distributed.run command that starts `gpus` ranks of this
+    script with the same arguments (one node, rendezvous on 127.0.0.1)."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+            f"--nproc-per-node={gpus}", "--master-addr", "127.0.0.1", "--master-port", str(port),
+            os.path.abspath(__file__)] + list(argv)
+
+
 def main():
     args = parse()
     rank, world, local = rank_info()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # --gpus N outside torchrun: start the N ranks here
+        sys.exit(subprocess.call(relaunch_cmd(sys.argv[1:], args.gpus, _free_port())))
     if args.steps is None:
-        args.steps = {"mcvqe8": 4000, "qcl20": 20, "mcvqe28": 2, "qcl-uneven": 5, "ddcl": 5}[args.workload]
+        args.steps = {"mcvqe8": 4000, "qcl20": 20, "mcvqe28": 5, "qcl-uneven": 5, "ddcl": 5}[args.workload]
     if args.warmup is None:
-        args.warmup = {"mcvqe8": 50, "qcl20": 3, "mcvqe28": 1, "qcl-uneven": 3, "ddcl": 3}[args.workload]
+        args.warmup = {"mcvqe8": 50, "qcl20": 3, "mcvqe28": 3, "qcl-uneven": 3, "ddcl": 3}[args.workload]
 
     if args.impl == "reference":
         if rank != 0:
             return
         if args.workload == "mcvqe8":
-            cb, workload = cpu_baseline(args.cpu_seconds), WORKLOAD
+            cb, workload = cpu_baseline(args.cpu_seconds), WORKLOAD_MCVQE8
         elif args.workload == "ddcl":
             w = wl.ddcl(args.qubits or 26, 10)
             cb, workload = cpu_baseline_ddcl(w, min(args.cpu_seconds, 10.0)), ddcl_workload_name(w)
@@ -641,7 +866,7 @@ def main():
             workload = device_workload_name(w)
         v = cb["value"]
         line = {"metric": METRIC, "value": v, "unit": "gradients/s", "impl": "reference",
-                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "c128", "data": "synthetic",
                 "config": {"workload": workload}, "cpu_baseline": cb,
@@ -666,142 +891,9 @@ def main():
         return run_uneven(args, sv, dev, stream, dist, world, rank)
     if args.workload == "ddcl":
         return run_ddcl(args, sv, dev, stream, dist, world, rank)
-    if args.workload != "mcvqe8":
-        return run_device_memory(args, sv, dev, stream, dist, world, rank)
-
-    w = wl.config(1)
-    B = w.n_slots_param_shift
-    shape_opts = None
-    if args.energy_shape:
-        R_, T_ = (int(x) for x in args.energy_shape.split(","))
-        shape_opts = sv.plan_opts(reg_bits=R_, threads_per_block=T_)
-    prob = sv.Problem.from_spec(w, "c64", device=dev, opts=shape_opts)
-    theta = torch.as_tensor(w.theta, dtype=torch.float64, device=dev)
-    out = sv._outputs(prob, dev, None, None, None)
-    e_buf = torch.empty(B, dtype=torch.float64, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-
-    # launch shapes (register bits, threads per block) picked by timing
-    if shape_opts is None:
-        sv.sv_autotune(prob, theta)
-        tuned = {"energy": sv.sv_tuned_shape(prob, 1)[:2], "adjoint": sv.sv_tuned_shape(prob, 2)[:2]}
-    else:
-        tuned = {"energy": (R_, T_), "adjoint": (R_, T_)}
-
-    def step():
-        sv.sv_grad_param_shift(prob, theta, *out)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t_wall = time.perf_counter()
-    t_dev = timed_loop(step, args.steps, flush, stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    t_wall = time.perf_counter() - t_wall
-    clk = clocks.stop()
-    grads_per_s, t_dev = job_throughput(t_dev, args.steps, dist, dev)
-
-    result = {"metric": METRIC, "value": grads_per_s, "unit": "gradients/s", "n_gpus": world,
-              "steps": args.steps, "warmup": args.warmup,
-              "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
-              "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-              "config": {"workload": WORKLOAD, "circuits_per_gradient": B,
-                         "l2": "flushed before every timed step (256 MiB write, untimed)",
-                         "tuned_shape_c64": {k: {"reg_bits": v[0], "threads_per_block": v[1]}
-                                             for k, v in tuned.items()},
-                         "parallelism": f"replicas x{world}"},
-              "shifted_circuits_per_s": grads_per_s * B,
-              "gpu_launches": 2 * args.steps,  # k_energy + k_ps_combine_dep
-              "clocks": clk, "wall_s_timed_region": t_wall}
-
-    if rank == 0:
-        # dominant kernel alone: the batched energies of all 585 circuits
-        k_steps = max(200, args.steps // 4)
-        fn = lambda: sv.sv_param_shift_energies(prob, theta, e_buf)  # noqa: E731
-        for _ in range(20):
-            fn()
-        t_k = timed_loop(fn, k_steps, flush, stream) / k_steps
-        flops = algorithmic_flops(w, B)
-        peak = fp32_peak_tflops()
-        achieved = flops / t_k / 1e12
-        result["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak,
-                              "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                              "kernel": f"k_energy<float,{tuned['energy'][0]}> (batched "
-                                        "shifted-circuit energies; the gradient assembly follows as a dependent launch)",
-                              "kernel_us": t_k * 1e6,
-                              "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
-
-        # end to end through the C ABI: theta from pinned host memory in,
-        # loss + gradient back to pinned host memory, every step.
-        # (sv_grad_param_shift_host: theta in through pinned staging, one
-        # device-to-host transfer of loss + gradient + energies, synchronous)
-        th_host = torch.as_tensor(w.theta, dtype=torch.float64).pin_memory()
-        g_host = torch.empty(w.n_params, dtype=torch.float64).pin_memory()
-        l_host = torch.empty(1, dtype=torch.float64).pin_memory()
-        e_host = torch.empty(w.n_instances, dtype=torch.float64).pin_memory()
-        e2e_steps = max(200, args.steps // 4)
-
-        def e2e_step():
-            sv.sv_grad_param_shift_host(prob, th_host, e_host, l_host, g_host, stream=stream)
-
-        for _ in range(10):
-            e2e_step()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            e2e_step()
-        t_e2e = time.perf_counter() - t0
-        result["e2e"] = {"value": e2e_steps / t_e2e, "unit": "gradients/s",
-                         "h2d_bytes_per_step": 8 * w.n_params,
-                         "d2h_bytes_per_step": 8 * (w.n_params + 1 + w.n_instances),
-                         "timing": "host wall clock per step; sv_grad_param_shift_host "
-                                   "returns once the results are in host memory"}
-
-        if not args.no_extras:
-            # the metric's "% HBM roofline": forward tile passes of the
-            # 20-qubit circuit-learning batch (64 states, 512 MiB)
-            result["hbm_gate_passes"] = forward_passes_roofline(sv, wl.config(3), dev, flush, stream)
-            extras = {}
-            fn = lambda: sv.sv_grad_adjoint(prob, theta, None, *out)  # noqa: E731
-            for _ in range(20):
-                fn()
-            n = max(200, args.steps // 4)
-            extras["adjoint_c64_gradients_per_s"] = n / timed_loop(fn, n, flush, stream)
-            prob128 = sv.Problem.from_spec(w, "c128", device=dev)
-            out128 = sv._outputs(prob128, dev, None, None, None)
-            sv.sv_autotune(prob128, theta)
-            fn = lambda: sv.sv_grad_param_shift(prob128, theta, *out128)  # noqa: E731
-            for _ in range(20):
-                fn()
-            extras["batched_c128_gradients_per_s"] = n / timed_loop(fn, n, flush, stream)
-            fn = lambda: sv.sv_grad_adjoint(prob128, theta, None, *out128)  # noqa: E731
-            for _ in range(20):
-                fn()
-            extras["adjoint_c128_gradients_per_s"] = n / timed_loop(fn, n, flush, stream)
-            # the plain form is host-driven (one launch per gate and term): wall clock
-            sv.sv_grad_param_shift_plain(prob128, theta, *out128)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            reps = 2
-            for _ in range(reps):
-                sv.sv_grad_param_shift_plain(prob128, theta, *out128)
-            torch.cuda.synchronize()
-            extras["plain_c128_gradients_per_s"] = reps / (time.perf_counter() - t0)
-            extras["plain_c128_launches_per_gradient"] = B * (1 + len(w.gates) + w.n_terms) + 1
-            result["forms"] = extras
-
-        result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
-        print(json.dumps(result))
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
+    if args.workload == "mcvqe8":
+        return run_mcvqe8(args, sv, dev, stream, dist, world, rank)
+    return run_device_memory(args, sv, dev, stream, dist, world, rank)
 
 
 if __name__ == "__main__":

@@ -256,6 +256,19 @@ sv_status sv_grad_adjoint(const sv_problem *problem, const double *theta, const 
                           double *energy_out, double *loss_out, double *grad_out,
                           int32_t checkpoint_every, sv_stream_t stream);
 
+/* sv_grad_adjoint with host buffers, synchronous (the adjoint counterpart of
+ * sv_grad_param_shift_host): copies theta (host [P], any host memory)
+ * through library-owned pinned staging to the device, runs the adjoint
+ * gradient with the problem's cost (no external weights), copies loss,
+ * gradient and instance energies back in one transfer and waits for
+ * `stream` before returning.  energy_host: [n_instances] or NULL;
+ * loss_host: [1] or NULL; grad_host: [P].  checkpoint_every as for
+ * sv_grad_adjoint.  Uses (2P + 1 + I) doubles of pinned host and device
+ * staging per stream besides the scratch of sv_grad_adjoint. */
+sv_status sv_grad_adjoint_host(const sv_problem *problem, const double *theta_host,
+                               double *energy_host, double *loss_host, double *grad_host,
+                               int32_t checkpoint_every, sv_stream_t stream);
+
 /* The plain form, for comparison only: one circuit at a time, one kernel
  * launch per gate and per Pauli term, complex128 state in device memory,
  * parameter shift as above.  Host-synchronous per circuit batch. */
@@ -280,10 +293,15 @@ sv_status sv_grad_param_shift_plain(const sv_problem *problem, const double *the
  * or allocating library routine.
  *
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call re-plans on the host and copies the
- * plan from pageable host memory into the array, so the call waits for work
- * already queued on `stream`.  All calls share the one array and it keeps
+ * (cudaGetSymbolAddress, with that device current) and keeps it; make that
+ * first call before any stream capture.  After cudaDeviceReset, call
+ * sv_shutdown() before the next call, which then looks the address up again
+ * in the new context.  Every call re-plans on the host and copies the plan
+ * from pageable host memory into the array, so the call waits for work
+ * already queued on `stream`, and it cannot be captured into a CUDA graph:
+ * on a capturing stream it returns SV_ERR_UNSUPPORTED and enqueues nothing.
+ * It runs the on-chip engine only: at most 13 qubits for SV_C64 and 12 for
+ * SV_C128 (larger problems return SV_ERR_UNSUPPORTED naming this limit).  All calls share the one array and it keeps
  * the last call's contents; nothing in it needs to start at zero (every
  * value is written before it is read).  Calls that overlap on the GPU
  * (different streams, or other threads) race on the array: serialise them.
@@ -410,7 +428,8 @@ const char *sv_status_string(sv_status status);
 const char *sv_last_error(void);
 /* Synchronize `stream` and report any pending CUDA error as a status. */
 sv_status sv_sync_status(sv_stream_t stream);
-/* Release plan caches and scratch on every device. */
+/* Release plan caches and scratch on every device, and forget the device
+ * addresses that sv_grad_param_shift_noalloc looked up. */
 sv_status sv_shutdown(void);
 int32_t sv_version(void);
 

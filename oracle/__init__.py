@@ -211,15 +211,6 @@ def grad_param_shift(w, theta=None, params=None, n_threads: int = 0):
     return cost_from_energies(w, E0), E0, g
 
 
-def instance_grads_param_shift(w, theta=None, n_threads: int = 0):
-    """Per-instance dE_i/dtheta (I, P) by the parameter-shift rule."""
-    inst, sp, sh = param_shift_slots(w)
-    E = energies(w, theta, inst, sp, sh, n_threads=n_threads)
-    I = w.n_instances
-    Es = E[I:].reshape(-1, 2, I)
-    return (0.5 * (Es[:, 0, :] - Es[:, 1, :])).T
-
-
 def grad_finite_difference(w, theta=None, h: float = 1e-5, n_threads: int = 0):
     """Central differences of the cost, [L(theta+h e_k) - L(theta-h e_k)] / 2h."""
     th = _theta(w, theta)

@@ -83,7 +83,7 @@ EXPORTED = ("sv_alloc", "sv_free", "sv_state_info", "sv_apply_circuit_batch",
             "sv_grad_param_shift_plain", "sv_grad_param_shift_noalloc", "sv_autotune",
             "sv_tuned_shape", "sv_plan_info", "sv_h_plan_info", "sv_phase_timing",
             "sv_grad_adjoint_multi", "sv_grad_ddcl", "sv_grad_ddcl_param_shift",
-            "sv_grad_param_shift_host", "sv_param_shift_energies_range", "sv_sample",
+            "sv_grad_param_shift_host", "sv_grad_adjoint_host", "sv_param_shift_energies_range", "sv_sample",
             "sv_param_shift_combine",
             "sv_last_phase_ms", "sv_status_string",
             "sv_last_error",
@@ -107,6 +107,7 @@ def _load():
     lib.sv_grad_param_shift.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_grad_param_shift_host.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_grad_adjoint.argtypes = [P(sv_problem), V, V, V, V, V, I32, V]
+    lib.sv_grad_adjoint_host.argtypes = [P(sv_problem), V, V, V, V, I32, V]
     lib.sv_grad_adjoint_multi.argtypes = [P(sv_problem), I32, P(V), P(V), P(V), P(V), V]
     lib.sv_grad_ddcl.argtypes = [P(sv_problem), V, V, V, V, V]
     lib.sv_grad_ddcl_param_shift.argtypes = [P(sv_problem), V, V, V, V, V]
@@ -388,6 +389,23 @@ def sv_grad_adjoint(problem: Problem, theta, weights=None, energy_out=None, loss
     _check(_lib.sv_grad_adjoint(ctypes.byref(problem.struct), _ptr(theta), _ptr(weights),
                                 _ptr(e), _ptr(l), _ptr(g), int(checkpoint_every),
                                 _stream(stream)), "sv_grad_adjoint")
+    return l, e, g
+
+
+def sv_grad_adjoint_host(problem: Problem, theta, energy_out=None, loss_out=None,
+                         grad_out=None, checkpoint_every: int = 0, stream=None):
+    """sv_grad_adjoint with host (CPU) float64 tensors in and out and the
+    problem's own cost; returns once the results are in host memory.
+    (loss[1], energies[I], grad[P])."""
+    import torch
+    for t in (theta, energy_out, loss_out, grad_out):
+        if t is not None and (t.device.type != "cpu" or t.dtype != torch.float64
+                              or not t.is_contiguous()):
+            raise ValueError("sv_grad_adjoint_host takes contiguous float64 CPU tensors")
+    e, l, g = _outputs(problem, torch.device("cpu"), energy_out, loss_out, grad_out)
+    _check(_lib.sv_grad_adjoint_host(ctypes.byref(problem.struct), _ptr(theta), _ptr(e), _ptr(l),
+                                     _ptr(g), int(checkpoint_every), _stream(stream)),
+           "sv_grad_adjoint_host")
     return l, e, g
 
 

@@ -20,6 +20,10 @@
 
 using namespace svk;
 
+namespace svk {
+void noalloc_forget();  // noalloc.cu: drops the cached array addresses
+}  // namespace svk
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -1594,18 +1598,14 @@ sv_status sv_energies(const sv_problem *p, const double *theta, double *energy_o
     return SV_OK;
 }
 
-sv_status sv_grad_adjoint(const sv_problem *p, const double *theta, const double *weights,
-                          double *energy_out, double *loss_out, double *grad_out,
-                          int32_t checkpoint_every, sv_stream_t stream) {
-    sv_status s = check_problem(p, weights == nullptr);
-    if (s != SV_OK) return s;
-    if (checkpoint_every < 0) return fail(SV_ERR_ARG, "checkpoint_every must be >= 0");
+namespace {
+
+// The adjoint gradient with ctx->mu held (arguments checked by the caller).
+sv_status adjoint_locked(DeviceCtx *ctx, const sv_problem *p, const double *theta,
+                         const double *weights, double *energy_out, double *loss_out,
+                         double *grad_out, int checkpoint_every, cudaStream_t st) {
+    sv_status s = SV_OK;
     const int P = p->circuit->n_params, I = p->n_instances;
-    if (P > 0 && (!theta || !grad_out)) return fail(SV_ERR_ARG, "theta/grad_out is NULL");
-    DeviceCtx *ctx = context();
-    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    cudaStream_t st = (cudaStream_t)stream;
     if (wants_tiles(p->circuit->n_qubits, p->dtype, p->opts))
         return tiles_adjoint(ctx, p, theta, weights, energy_out, loss_out, grad_out,
                              checkpoint_every, st);
@@ -1646,6 +1646,56 @@ sv_status sv_grad_adjoint(const sv_problem *p, const double *theta, const double
     if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
     e = launch_adjoint_combine(G, E, I, P, cs, energy_out, loss_out, grad_out, st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint combine launch");
+    return SV_OK;
+}
+
+}  // namespace
+
+sv_status sv_grad_adjoint(const sv_problem *p, const double *theta, const double *weights,
+                          double *energy_out, double *loss_out, double *grad_out,
+                          int32_t checkpoint_every, sv_stream_t stream) {
+    sv_status s = check_problem(p, weights == nullptr);
+    if (s != SV_OK) return s;
+    if (checkpoint_every < 0) return fail(SV_ERR_ARG, "checkpoint_every must be >= 0");
+    const int P = p->circuit->n_params;
+    if (P > 0 && (!theta || !grad_out)) return fail(SV_ERR_ARG, "theta/grad_out is NULL");
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return adjoint_locked(ctx, p, theta, weights, energy_out, loss_out, grad_out,
+                          checkpoint_every, (cudaStream_t)stream);
+}
+
+sv_status sv_grad_adjoint_host(const sv_problem *p, const double *theta_host,
+                               double *energy_host, double *loss_host, double *grad_host,
+                               int32_t checkpoint_every, sv_stream_t stream) {
+    sv_status s = check_problem(p, true);
+    if (s != SV_OK) return s;
+    if (checkpoint_every < 0) return fail(SV_ERR_ARG, "checkpoint_every must be >= 0");
+    const int P = p->circuit->n_params, I = p->n_instances;
+    if (P > 0 && (!theta_host || !grad_host)) return fail(SV_ERR_ARG, "theta/grad is NULL");
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    // staging, in doubles: [theta P][loss 1][grad P][energies I]
+    const size_t nP = (size_t)(P > 0 ? P : 1), n_out = 1 + nP + (size_t)I;
+    HostIO *io = nullptr;
+    s = get_hostio(ctx, st, sizeof(double) * (nP + n_out), &io);
+    if (s != SV_OK) return s;
+    double *h = (double *)io->host, *d = (double *)io->dev;
+    if (P > 0) {
+        std::memcpy(h, theta_host, sizeof(double) * P);
+        SV_CUDA(cudaMemcpyAsync(d, h, sizeof(double) * P, cudaMemcpyHostToDevice, st));
+    }
+    s = adjoint_locked(ctx, p, d, nullptr, d + 2 * nP + 1, d + nP, d + nP + 1, checkpoint_every,
+                       st);
+    if (s != SV_OK) return s;
+    SV_CUDA(cudaMemcpyAsync(h + nP, d + nP, sizeof(double) * n_out, cudaMemcpyDeviceToHost, st));
+    SV_CUDA(cudaStreamSynchronize(st));
+    if (loss_host) *loss_host = h[nP];
+    if (P > 0) std::memcpy(grad_host, h + nP + 1, sizeof(double) * P);
+    if (energy_host) std::memcpy(energy_host, h + 2 * nP + 1, sizeof(double) * I);
     return SV_OK;
 }
 
@@ -2169,6 +2219,7 @@ sv_status sv_sync_status(sv_stream_t stream) {
 }
 
 sv_status sv_shutdown(void) {
+    svk::noalloc_forget();
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto &kv : g_ctx) {
         int cur = 0;

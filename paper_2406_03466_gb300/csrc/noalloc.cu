@@ -38,7 +38,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 unsigned char *g_noalloc_ptr[kMaxDevices];  // device address of the array, per device
 
-// Once per device, with that device current.
+// Once per device, with that device current.  sv_shutdown() forgets the
+// addresses (svk::noalloc_forget), so that a caller who reset a device and
+// then shut the library down gets the address in the new context.
 sv_status noalloc_setup(int dev, unsigned char **out) {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
@@ -57,6 +59,13 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
+namespace svk {
+void noalloc_forget() {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    for (auto &p : g_noalloc_ptr) p = nullptr;
+}
+}  // namespace svk
+
 extern "C" sv_status sv_grad_param_shift_noalloc(const sv_problem *p, const double *theta,
                                                  double *energy_out, double *loss_out,
                                                  double *grad_out, sv_stream_t stream) {
@@ -67,6 +76,31 @@ extern "C" sv_status sv_grad_param_shift_noalloc(const sv_problem *p, const doub
     const int64_t B64 = (int64_t)(2 * (int64_t)P + 1) * I;
     const int swz = p->dtype == SV_C128 ? 3 : 4;
     const int c128 = p->dtype == SV_C128;
+    cudaStream_t st = (cudaStream_t)stream;
+    // The plan is copied from a host vector released on return: a captured
+    // copy would read freed memory on every replay, so capture is refused.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(st, &cap);
+    if (ce != cudaSuccess)
+        return record_error(SV_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(ce));
+    if (cap != cudaStreamCaptureStatusNone)
+        return record_error(SV_ERR_UNSUPPORTED,
+                            "sv_grad_param_shift_noalloc cannot be captured into a CUDA graph "
+                            "(it uploads a host-side plan on every call)");
+    const int onchip_max = c128 ? 12 : 13;
+    if (p->circuit->n_qubits > onchip_max)
+        return record_error(SV_ERR_UNSUPPORTED,
+                            "sv_grad_param_shift_noalloc runs the on-chip engine only: at most " +
+                                std::to_string(onchip_max) + " qubits for " +
+                                (c128 ? "complex128" : "complex64") + ", got " +
+                                std::to_string(p->circuit->n_qubits));
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return record_error(SV_ERR_CUDA, "no usable current CUDA device");
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return record_error(SV_ERR_CUDA, "cannot read the device's SM count");
     const sv_plan_opts *o = p->opts;
     const int reg = (o && o->reg_bits > 0) ? o->reg_bits : 0;
     const int tpb = (o && o->threads_per_block > 0) ? o->threads_per_block : 0;
@@ -75,7 +109,7 @@ extern "C" sv_status sv_grad_param_shift_noalloc(const sv_problem *p, const doub
     // Plan on the host only.
     OnchipShape pre{}, sh{};
     const char *err = onchip_shape(ONCHIP_ENERGY, p->circuit->n_qubits, 0, P, c128,
-                                   (int)(B64 > (1 << 30) ? 1 : B64), reg, tpb, &pre);
+                                   (int)(B64 > (1 << 30) ? 1 : B64), reg, tpb, &pre, sms);
     if (err) return record_error(SV_ERR_UNSUPPORTED, err);
     HostProgram hp;
     std::string perr = plan_circuit(*p->circuit, pre.R, fuse, swz, &hp);
@@ -108,17 +142,12 @@ extern "C" sv_status sv_grad_param_shift_noalloc(const sv_problem *p, const doub
                                 std::to_string((size_t)SV_NOALLOC_SCRATCH_BYTES));
     const int B = (int)B64;
     err = onchip_shape(ONCHIP_ENERGY, p->circuit->n_qubits, (int)hp.groups.size(), P, c128, B,
-                       reg, tpb, &sh);
+                       reg, tpb, &sh, sms);
     if (err) return record_error(SV_ERR_UNSUPPORTED, err);
 
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return record_error(SV_ERR_CUDA, "no usable current CUDA device");
     unsigned char *base = nullptr;
     s = noalloc_setup(dev, &base);
     if (s != SV_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
     // From pageable host memory: the copy is staged before this returns, so
     // `blob` may be released afterwards.
     e = cudaMemcpyAsync(base, blob.data(), blob.size(), cudaMemcpyHostToDevice, st);

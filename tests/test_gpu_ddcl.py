@@ -9,7 +9,7 @@ import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"c128": dict(E=1e-12, G=1e-11), "c64": dict(E=1e-5, G=1e-4)}
+TOL = {"c128": dict(E=1e-12, G=1e-12), "c64": dict(E=1e-5, G=1e-4)}
 
 
 @pytest.fixture(scope="module")

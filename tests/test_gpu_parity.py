@@ -267,6 +267,33 @@ def test_param_shift_host_buffers(sv, dtype, n):
         sv.sv_grad_param_shift_host(prob, theta_of(w))
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("n", [8, 15])
+def test_adjoint_host_buffers(sv, dtype, n):
+    """The host-buffer adjoint entry point against the oracle, on chip (8
+    qubits) and as tile passes (15 qubits), and against the device-buffer
+    call; outputs may be left out and the call repeats with a new theta."""
+    import torch
+    w = wl.mcvqe(n, 2) if n == 8 else wl.mcvqe(n, 2, "nn+nnn", n_refs=2)
+    L, E, g = oracle.grad_param_shift(w)
+    prob = sv.Problem.from_spec(w, dtype)
+    th = torch.as_tensor(w.theta, dtype=torch.float64)
+    l_, e_, g_ = sv.sv_grad_adjoint_host(prob, th)
+    assert l_.device.type == "cpu" and g_.device.type == "cpu"
+    close(e_.numpy(), E, TOL[dtype]["E"])
+    close(l_.numpy()[0], L, TOL[dtype]["E"])
+    close(g_.numpy()[: w.n_params], g, TOL[dtype]["G"])
+    ld, ed, gd = sv.sv_grad_adjoint(prob, theta_of(w))
+    close(gd.cpu().numpy(), g_.numpy(), 1e-12 if dtype == "c128" else 1e-6)
+    th2 = th - 0.4
+    g2 = torch.empty(w.n_params, dtype=torch.float64)
+    sv.sv_grad_adjoint_host(prob, th2, None, None, g2)
+    w2 = dataclasses.replace(w, theta=th2.numpy())
+    close(g2.numpy(), oracle.grad_param_shift(w2)[2], TOL[dtype]["G"])
+    with pytest.raises(ValueError):
+        sv.sv_grad_adjoint_host(prob, theta_of(w))
+
+
 def test_whole_warp_blocks(sv):
     """A batch whose default launch would put 3 circuits of 16 threads in a
     block (48 threads) runs in whole warps and matches the oracle; a

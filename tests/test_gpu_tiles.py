@@ -6,7 +6,10 @@ oracle; 14-qubit states take the path on their own; reduced circuit-learning
 and multi-contracted VQE workloads at 16-20 qubits check sampled gradient
 entries; the benchmark's 28-qubit workload itself is checked at full size
 through properties that hold at any size (the closed form at theta = 0, and
-the complex64 adjoint against complex128 parameter shift on a subsample).
+the complex64 adjoint against complex128 parameter shift on a subsample) and
+against the sparse-state oracle at angles where few qubits rotate; the
+20-qubit circuit-learning workload at full depth against the dense oracle on
+sampled instances and parameters.
 Tolerances as in test_gpu_parity.
 """
 import numpy as np
@@ -170,9 +173,14 @@ def test_uneven_batch_adjoint(sv, dtype):
             for x in o:
                 x.fill_(float("nan"))
         outs = sv.sv_grad_adjoint_multi(probs, thetas, outputs=outs)
-    L, E, g = oracle.grad_param_shift(ws[1])
-    close(outs[1][1].cpu().numpy(), E, TOL[dtype]["E"])
-    close(outs[1][2].cpu().numpy()[: ws[1].n_params], g, TOL[dtype]["G"])
+    # every problem of the batch against the oracle: all instance energies,
+    # the cost and sampled gradient entries (parameter shift on the CPU)
+    for w, (l_, e_, g_) in zip(ws, outs):
+        ks = sorted({0, w.n_params // 3, w.n_params // 2, w.n_params - 1})
+        L, E, g = oracle.grad_param_shift(w, params=ks)
+        close(e_.cpu().numpy(), E, TOL[dtype]["E"])
+        close(l_.cpu().numpy()[0], L, TOL[dtype]["E"])
+        close(g_.cpu().numpy()[ks], g, TOL[dtype]["G"])
 
 
 # ------------------------------------------------ the 28-qubit workload itself
@@ -239,3 +247,80 @@ def test_mcvqe28_full_size_adjoint_vs_param_shift_c128(sv):
         e = seg.cpu().numpy()
         g128 = float(np.dot(wts, 0.5 * (e[:I] - e[I:])))
         assert abs(g64[k] - g128) <= TOL["c64"]["G"] * max(1.0, abs(g128)), (k, g64[k], g128)
+
+
+# Angles of the 28-qubit workload at which the sparse-state oracle is exact:
+# qubit 0 rotates in every layer, qubit 17 in layers 2 and 5, qubit 27 in
+# layer 3, every other angle is 0.  Sampled parameters: those rotations, and
+# others on the same and neighbouring qubits (their derivatives at angle 0).
+MCVQE28_ROTATING = [l * 28 for l in range(8)] + [2 * 28 + 17, 5 * 28 + 17, 3 * 28 + 27]
+MCVQE28_SAMPLED = [0, 5, 10, 21, 27, 28, 33, 45, 50, 56, 73, 84, 87, 101, 111, 117, 140, 144, 157,
+                   168, 172, 196, 222]
+
+
+def test_mcvqe28_full_size_gradient_against_sparse_oracle(sv):
+    """The benchmark's 28-qubit multi-contracted VQE at full size (8 states of
+    2^28, 8 layers, 224 parameters, 268 terms) in the launch configuration
+    the benchmark times (autotuned tile passes, relabeling plan, stored
+    forward states): its complex64 adjoint energies, cost and sampled
+    gradient entries against the sparse-state oracle's exact values."""
+    import torch
+    from oracle import sparse
+    w = wl.config(4)
+    th = np.zeros(w.n_params)
+    th[MCVQE28_ROTATING] = w.theta[MCVQE28_ROTATING]
+    th_dev = torch.as_tensor(th, dtype=torch.float64, device="cuda")
+    prob = sv.Problem.from_spec(w, "c64")
+    sv.sv_autotune(prob, th_dev, 2)
+    l_, e_, g_ = sv.sv_grad_adjoint(prob, th_dev)
+    L, E, g = sparse.grad_param_shift(w, th, params=MCVQE28_SAMPLED, workers=16)
+    close(e_.cpu().numpy(), E, TOL["c64"]["E"])
+    close(l_.cpu().numpy()[0], L, TOL["c64"]["E"])
+    close(g_.cpu().numpy()[MCVQE28_SAMPLED], g, TOL["c64"]["G"])
+
+
+def test_qcl20_full_depth_against_oracle(sv):
+    """The benchmark's 20-qubit circuit learning at full depth (10 layers of
+    Rx-Rz-Rx + ring, 600 parameters, 64 inputs) in the launch configuration
+    the benchmark times: with dL/dE weights on two of the 64 inputs, the
+    adjoint gradient is a weighted sum of those inputs' derivatives, which
+    the dense oracle computes by parameter shift on sampled parameters; every
+    instance energy of a sample of inputs is checked too."""
+    import torch
+    w = wl.config(3)
+    th = theta_of(w)
+    prob = sv.Problem.from_spec(w, "c64")
+    sv.sv_autotune(prob, th, 2)
+    wts = np.zeros(w.n_instances)
+    wts[0], wts[37] = 1.0, -0.5
+    l_, e_, g_ = sv.sv_grad_adjoint(prob, th, weights=torch.as_tensor(wts, device="cuda"))
+    ks = [0, 1, 2, 151, 305, 598, 599]
+    inst, sp, sh = [], [], []
+    for k in ks:
+        for sign in (1.0, -1.0):
+            for i in (0, 37):
+                inst.append(i)
+                sp.append(k)
+                sh.append(sign * np.pi / 2)
+    checked = [0, 11, 37, 63]
+    E = oracle.energies(w, None, np.array(checked + inst), np.array([-1] * 4 + sp),
+                        np.array([0.0] * 4 + sh))
+    close(e_.cpu().numpy()[checked], E[:4], TOL["c64"]["E"])
+    Es = E[4:].reshape(len(ks), 2, 2)
+    g = 0.5 * (Es[:, 0, :] - Es[:, 1, :]) @ np.array([1.0, -0.5])
+    close(g_.cpu().numpy()[ks], g, TOL["c64"]["G"])
+
+
+def test_mcvqe22_full_depth_against_oracle(sv):
+    """The 28-qubit workload's generator at 22 qubits with all 8 layers and
+    general angles (every rotation non-trivial), 2 references: the adjoint
+    against the dense oracle's energies and sampled parameter-shift
+    gradient entries."""
+    w = wl.mcvqe(22, 8, "nn+nnn", n_refs=2)
+    prob = sv.Problem.from_spec(w, "c64")
+    l_, e_, g_ = sv.sv_grad_adjoint(prob, theta_of(w))
+    ks = [0, 21, 88, 130, 175]
+    L, E, g = oracle.grad_param_shift(w, params=ks)
+    close(e_.cpu().numpy(), E, TOL["c64"]["E"])
+    close(l_.cpu().numpy()[0], L, TOL["c64"]["E"])
+    close(g_.cpu().numpy()[ks], g, TOL["c64"]["G"])

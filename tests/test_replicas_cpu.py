@@ -53,3 +53,33 @@ def test_single_rank_without_process_group():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.job_throughput(2.0, 8, None, torch.device("cpu")) == (4.0, 2.0)
+
+
+def test_bench_starts_its_own_ranks():
+    """`bench.py --gpus 2` outside torchrun starts two ranks itself (under
+    torch.distributed.run on 127.0.0.1); the reference arm runs on rank 0
+    alone, which prints one line reporting the true world size."""
+    import json
+    import subprocess
+    import sys
+    env = {k: v for k, v in os.environ.items()
+           if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--gpus", "2", "--workload", "mcvqe8", "--cpu-seconds", "0.3",
+                        "--steps", "3", "--warmup", "3"],
+                       capture_output=True, text=True, env=env, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stdout + r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_relaunch_command():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    cmd = bench.relaunch_cmd(["--gpus", "4", "--steps", "3"], 4, 29500)
+    assert cmd[1:4] == ["-m", "torch.distributed.run", "--nnodes=1"]
+    assert "--nproc-per-node=4" in cmd and cmd[cmd.index("--master-addr") + 1] == "127.0.0.1"
+    assert cmd[-3:] == ["--gpus", "4", "--steps", "3"][-3:]
