@@ -817,11 +817,26 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
     if (s != SV_OK) return s;
     const int G = pe->dev.n_groups;
     const int npass = (int)pe->tiles.size();
-    if (every <= 0) every = 4;
-    const int ncp = npass > 1 ? (npass - 1) / every : 0;
     const size_t csz = c128 ? 16 : 8, sb = csz << n;
-    const size_t per = (2 + (size_t)ncp) * sb + (size_t)G * 4 * csz + (size_t)G * 64;
-    int64_t chunk = (int64_t)(big_budget(ctx, st) / (per + 2048));
+    const size_t budget = big_budget(ctx, st);
+    auto per_instance = [&](int ev) {
+        const size_t ncp_ = npass > 1 ? (size_t)((npass - 1) / ev) : 0;
+        return (2 + ncp_) * sb + (size_t)G * 4 * csz + (size_t)G * 64;
+    };
+    if (every <= 0) {
+        // The most stored states that still let every instance run at once:
+        // a reverse pass followed by a restart from a stored state skips
+        // writing psi, and un-computation rounding spans fewer passes.
+        every = 4;
+        for (int ev : {1, 2})
+            if (budget / (per_instance(ev) + 2048) >= (size_t)I) {
+                every = ev;
+                break;
+            }
+    }
+    const int ncp = npass > 1 ? (npass - 1) / every : 0;
+    const size_t per = per_instance(every);
+    int64_t chunk = (int64_t)(budget / (per + 2048));
     if (chunk < 1) return fail(SV_ERR_OOM, "psi, lambda and the stored states do not fit");
     if (chunk > I) chunk = I;
     if (chunk > 65535) chunk = 65535;
@@ -878,8 +893,11 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
             const int64_t tiles = (int64_t)src.n_slots << tp.n_tile_bits;
             const uint32_t smem = tile_rev_smem(c128, tp);
             if (smem > 220u * 1024u) return fail(SV_ERR_UNSUPPORTED, "reverse pass needs too much shared memory");
+            // psi after this pass is needed only if the next reverse pass
+            // un-computes from it (it restarts from a stored state otherwise)
+            const bool write_psi = i > 0 && !(i % every == 0 && i < npass);
             e = launch_tile_rev(c128, tp, n, src.n_slots, mats, G, psi, lam, rho,
-                                tile_blocks(ctx, tiles), st, psi_in);
+                                tile_blocks(ctx, tiles), st, psi_in, write_psi);
             if (e != cudaSuccess) return cuda_fail(e, "reverse tile pass");
         }
         phase_mark(ctx, st);

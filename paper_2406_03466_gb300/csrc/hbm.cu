@@ -23,6 +23,7 @@
 
 #include "engine.cuh"
 #include "hbm.h"
+#include "tile_common.cuh"
 
 namespace svk {
 namespace {
@@ -50,154 +51,6 @@ __global__ void k_set_ref(C *states, int n, SlotSource src) {
         one.y = 0;
         states[((int64_t)b << n) + si.ref] = one;
     }
-}
-
-// ------------------------------------------------------------ tile passes
-//
-// A block owns one contiguous range of (slot, tile) pairs.  Tiles arrive by
-// cp.async in one of two buffers, so the next tile is in flight while the
-// current one is computed.  Every register stage loads the thread's 2^R
-// amplitudes from shared memory, applies the fused 2x2 group of each of its
-// register bits (at most one per bit) and stores them back in place.  The
-// pass descriptor is a __grid_constant__ parameter: its stage vectors are
-// read with warp-uniform indices through the constant cache.  Each thread
-// computes its per-stage address bases once per launch.
-
-__device__ __forceinline__ void cp_async_amp(uint32_t sdst, const float2 *g) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sdst), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_amp(uint32_t sdst, const double2 *g) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-// Waits for all but the most recently committed group.
-__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
-// Offsets of this thread's amplitudes (tile-local index tid + k 2^(t-R))
-// through the per-bit vector table v: returns the tid part and fills the
-// parts of the R register bits.
-template <int R>
-__device__ __forceinline__ uint32_t bit_vectors(const uint32_t *v, int t, int tid,
-                                                uint32_t (&k)[R]) {
-    const int tb = t - R;
-    uint32_t g = 0;
-    for (int b = 0; b < tb; ++b)
-        if ((tid >> b) & 1) g ^= v[b];
-#pragma unroll
-    for (int j = 0; j < R; ++j) k[j] = v[tb + j];
-    return g;
-}
-
-// Position of one tile in the walk over (slot, tile): global offset of the
-// tile's first amplitude within its state.
-struct TileCursor {
-    int slot;
-    uint32_t local, base;
-};
-
-__device__ __forceinline__ TileCursor tile_cursor(const TilePass &P, int64_t tix) {
-    TileCursor c;
-    c.slot = (int)(tix >> P.n_tile_bits);
-    c.local = (uint32_t)(tix & ((int64_t(1) << P.n_tile_bits) - 1));
-    c.base = 0;
-    for (int k = 0; k < P.n_tile_bits; ++k)
-        if ((c.local >> k) & 1u) c.base ^= P.gpre[k] ^ (k ? P.gpre[k - 1] : 0u);
-    return c;
-}
-
-// Next tile: counting up flips tile-number bits 0..ctz(local + 1).
-__device__ __forceinline__ TileCursor tile_next(const TilePass &P, TileCursor c) {
-    ++c.local;
-    if ((c.local >> P.n_tile_bits) != 0u) {
-        c.local = 0;
-        c.base = 0;
-        ++c.slot;
-    } else {
-        c.base ^= P.gpre[__ffs((int)c.local) - 1];
-    }
-    return c;
-}
-
-// Shared-memory record of one stage (32 bytes, read with warp-uniform
-// addresses): word 0 holds one op byte per register bit, (u + 1) | real << 6
-// | parametrised << 7 for pass-local op u (0: no op); word 1 + i holds
-// ldq[i] | stq[i] << 16 (byte offsets, < 2^16 for every supported tile);
-// word 5 holds the ops' fmode bytes.
-__device__ __forceinline__ void build_stage_recs(const TilePass &P, uint4 *rec) {
-    for (int s = threadIdx.x; s < P.n_stages; s += blockDim.x) {
-        const TileStage &sg = P.st[s];
-        uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int i = 0; i < P.R && i < 4; ++i) {
-            const int u = sg.op[i];
-            if (u >= 0) {
-                const uint32_t ob = (uint32_t)(u + 1) | (((P.real_mask >> u) & 1ull) ? 64u : 0u) |
-                                    (((P.param_mask >> u) & 1ull) ? 128u : 0u);
-                w[0] |= ob << (8 * i);
-            }
-            w[1 + i] = sg.ldq[i] | (sg.stq[i] << 16);
-            if (u >= 0) w[5] |= (uint32_t)(P.fmode[u] & 3) << (8 * i);
-        }
-        rec[2 * s] = make_uint4(w[0], w[1], w[2], w[3]);
-        rec[2 * s + 1] = make_uint4(w[4], w[5], w[6], w[7]);
-    }
-}
-
-template <int R>
-__device__ __forceinline__ uint32_t read_stage_rec(const uint4 *rec, int s, uint32_t (&lq)[R],
-                                                   uint32_t (&sq)[R]) {
-    static_assert(R <= 4, "stage records hold four register bits");
-    const uint4 a = rec[2 * s];
-    uint32_t w[4] = {a.y, a.z, a.w, 0u};
-    if constexpr (R > 3) w[3] = rec[2 * s + 1].x;
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-        lq[j] = w[j] & 0xffffu;
-        sq[j] = w[j] >> 16;
-    }
-    return a.x;
-}
-
-// The four entries of matrix u (32-byte aligned records) as two 16-byte loads.
-__device__ __forceinline__ void load_mat(const float2 *sm, int u, float2 &m0, float2 &m1,
-                                         float2 &m2, float2 &m3) {
-    const float4 *p = reinterpret_cast<const float4 *>(sm) + 2 * u;
-    const float4 x = p[0], y = p[1];
-    m0 = make_float2(x.x, x.y);
-    m1 = make_float2(x.z, x.w);
-    m2 = make_float2(y.x, y.y);
-    m3 = make_float2(y.z, y.w);
-}
-__device__ __forceinline__ void load_mat(const double2 *sm, int u, double2 &m0, double2 &m1,
-                                         double2 &m2, double2 &m3) {
-    m0 = sm[4 * u];
-    m1 = sm[4 * u + 1];
-    m2 = sm[4 * u + 2];
-    m3 = sm[4 * u + 3];
-}
-
-// The group ops of one stage (op bytes `ops`), register bits I..R-1 in order.
-// kReal: every op of the pass has a real matrix (no complex path compiled).
-template <typename C, int R, int I, bool kReal>
-__device__ __forceinline__ void tile_ops_fwd(uint32_t ops, const C *sm, C (&a)[1 << R]) {
-    if constexpr (I < R) {
-        const uint32_t ob = (ops >> (8 * I)) & 0xffu;
-        if (ob) {
-            C m0, m1, m2, m3;
-            load_mat(sm, (int)(ob & 63u) - 1, m0, m1, m2, m3);
-            if (kReal || (ob & 64u))
-                u1r_bit<C, decltype(m0.x), R, I>(a, m0.x, m1.x, m2.x, m3.x);
-            else
-                u1_bit<C, R, I>(a, m0, m1, m2, m3);
-        }
-        tile_ops_fwd<C, R, I + 1, kReal>(ops, sm, a);
-    }
-}
-
-// Every op of pass P has a real matrix.
-__host__ __device__ inline bool pass_all_real(const TilePass &P) {
-    const uint64_t all = P.n_ops >= 64 ? ~0ull : ((1ull << P.n_ops) - 1ull);
-    return (P.real_mask & all) == all;
 }
 
 // One forward pass over every tile of every slot.  mats: [slots][G][4].
@@ -341,16 +194,29 @@ __device__ __forceinline__ Real single_sum(const C (&a)[1 << R], const C (&l)[1 
     Real v = 0;
     if (md == 1) {
         if constexpr (std::is_same<C, float2>::value) {
-            // k3 = sum x0 . y1 - x1 . y0 (as real 2-vectors): two packed FMA
-            // chains, their halves added at the end
-            uint64_t pa = 0, pb = 0;
+            // k3 = sum x0 . y1 - x1 . y0 (as real 2-vectors): packed FMA
+            // chains (two per product when there are four or more pairs, so
+            // that the chains are half as long), their halves added at the end
+            constexpr int NC = (1 << R) >= 8 ? 2 : 1;
+            uint64_t pa[NC], pb[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) pa[c] = pb[c] = 0;
+            int m = 0;
 #pragma unroll
             for (int r = 0; r < (1 << R); ++r) {
                 if (r & (1 << I)) continue;
-                pa = f2fma(f2of(a[r]), f2of(l[r | (1 << I)]), pa);
-                pb = f2fma(f2of(a[r | (1 << I)]), f2of(l[r]), pb);
+                pa[m % NC] = f2fma(f2of(a[r]), f2of(l[r | (1 << I)]), pa[m % NC]);
+                pb[m % NC] = f2fma(f2of(a[r | (1 << I)]), f2of(l[r]), pb[m % NC]);
+                ++m;
             }
-            const float2 A = f2unpack(pa), B = f2unpack(pb);
+            float2 A = f2unpack(pa[0]), B = f2unpack(pb[0]);
+            if constexpr (NC > 1) {
+                const float2 A1 = f2unpack(pa[1]), B1 = f2unpack(pb[1]);
+                A.x += A1.x;
+                A.y += A1.y;
+                B.x += B1.x;
+                B.y += B1.y;
+            }
             v = (A.x + A.y) - (B.x + B.y);
         } else {
 #pragma unroll
@@ -455,7 +321,8 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
                                               const typename CT<Real>::T *mats, int G,
                                               const typename CT<Real>::T *psi_src,
                                               typename CT<Real>::T *psi, typename CT<Real>::T *lam,
-                                              double *rho_g, int nblk, int blk, unsigned char *smem) {
+                                              double *rho_g, int nblk, int blk, unsigned char *smem,
+                                              bool write_psi = true) {
     using C = typename CT<Real>::T;
     constexpr int NA = 1 << R;
     constexpr int kFlushTiles = 64;
@@ -567,11 +434,19 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
         }
         const int64_t off = ((int64_t)cur.slot << n) + cur.base;
         C *dp = psi + off, *dl = lam + off;
+        if (write_psi) {
 #pragma unroll
-        for (int k = 0; k < NA; ++k) {
-            const uint32_t so = p0 ^ xsel<R>(k, pk), go = g0 ^ xsel<R>(k, gk);
-            dp[go] = *reinterpret_cast<const C *>(tp + so);
-            dl[go] = *reinterpret_cast<const C *>(tl + so);
+            for (int k = 0; k < NA; ++k) {
+                const uint32_t so = p0 ^ xsel<R>(k, pk), go = g0 ^ xsel<R>(k, gk);
+                dp[go] = *reinterpret_cast<const C *>(tp + so);
+                dl[go] = *reinterpret_cast<const C *>(tl + so);
+            }
+        } else {  // the next reverse pass restarts psi from a stored state
+#pragma unroll
+            for (int k = 0; k < NA; ++k) {
+                const uint32_t so = p0 ^ xsel<R>(k, pk), go = g0 ^ xsel<R>(k, gk);
+                dl[go] = *reinterpret_cast<const C *>(tl + so);
+            }
         }
         ++since;
         cur = nxt;
@@ -584,10 +459,10 @@ template <typename Real, int R, bool kSingle, bool kReal>
 __global__ void __launch_bounds__(256, R >= 4 ? 1 : 2)
 k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
            const typename CT<Real>::T *mats, int G, const typename CT<Real>::T *psi_src,
-           typename CT<Real>::T *psi, typename CT<Real>::T *lam, double *rho_g) {
+           typename CT<Real>::T *psi, typename CT<Real>::T *lam, double *rho_g, int write_psi) {
     extern __shared__ __align__(16) unsigned char smem[];
     tile_rev_body<Real, R, kSingle, kReal>(P, n, n_slots, mats, G, psi_src, psi, lam, rho_g,
-                                           gridDim.x, blockIdx.x, smem);
+                                           gridDim.x, blockIdx.x, smem, write_psi != 0);
 }
 
 // Sum of v over the block (every thread gets it); red: one double per warp.
@@ -681,36 +556,55 @@ __device__ __forceinline__ TileCursor h_next(const HPass &P, TileCursor c) {
 
 // Per-tile record of one class of terms: its coefficient sum_t c_t i^phase_t
 // times the term's sign on the tile's non-local bits and the class's sign
-// on the group's flip bits, the Z mask on the thread bits, and the class's
-// sign for each of the thread's amplitude slots k (parity of k & the Z mask
-// on the register bits).
+// on the group's flip bits, and its Z mask on the thread bits.
 template <typename Real> struct HCoef {
-    uint32_t zt, kpat;
+    uint32_t zt, pad;
     Real re, im;
 };
+
+// Walsh-Hadamard transform over the NA = 2^R entries of v (in place):
+// v[k] <- sum_p v[p] (-1)^|k & p|.
+template <typename Real, int NA>
+__device__ __forceinline__ void wht(Real (&v)[NA]) {
+#pragma unroll
+    for (int b = 1; b < NA; b <<= 1)
+#pragma unroll
+        for (int p = 0; p < NA; ++p)
+            if (!(p & b)) {
+                const Real x = v[p], y = v[p | b];
+                v[p] = x + y;
+                v[p | b] = x - y;
+            }
+}
 
 // One H pass: for the pass's X-mask groups g,
 //   lambda_j (+)= sum_g D_g(j ^ x_g) psi_(j ^ x_g),
 //   D_g(k) = sum_(t in g) c_t i^phase_t (-1)^|k & z_t|,
 // and E[slot] += sum_j Re(conj(psi_j) lambda_j) over this pass's part of
 // lambda.  psi tiles arrive by cp.async (double-buffered) in natural order;
-// the thread's amplitudes are j = tid + k 2^(t-R), handled 8 at a time.
-// Products in the state's precision, sums over the block's amplitudes in
-// FP64.  kLam = false: energies only.
+// the thread's amplitudes are j = tid + k 2^(t-R).  Per group, every
+// thread adds its signed class coefficients (the sign of the class's Z mask
+// on the thread bits) into one bucket per register-bit Z mask (the planner
+// sorted the classes that way) and a Walsh-Hadamard transform over the
+// register bits turns the buckets into D_g at the thread's 2^R amplitudes:
+// the work per class is per thread, not per amplitude.  Products in the
+// state's precision, sums over the block's amplitudes in FP64.  kLam =
+// false: energies only.
 template <typename Real, int R, bool kLam, bool kRealH>
 __global__ void __launch_bounds__(256)
 k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<Real>::T *psi,
          typename CT<Real>::T *lam, double *E) {
     using C = typename CT<Real>::T;
-    constexpr int NA = 1 << R, KC = NA < 8 ? NA : 8;
+    constexpr int NA = 1 << R;
+    static_assert(R <= kHRegBitsMax, "H kernel register bits");
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, T = blockDim.x, t = P.t;
     const uint32_t tbytes = (uint32_t)sizeof(C) << t;
     // psi tiles at [0, 2 tbytes), the lambda tile being added to at [2 tbytes, 3 tbytes)
-    HTerm *trm = reinterpret_cast<HTerm *>(smem + 3 * tbytes);
-    HCoef<Real> *coef = reinterpret_cast<HCoef<Real> *>(trm + P.n_terms);
-    HGroup *grp = reinterpret_cast<HGroup *>(coef + P.n_classes);
-    HClass *cls = reinterpret_cast<HClass *>(grp + P.n_groups);
+    HGroup *grp = reinterpret_cast<HGroup *>(smem + 3 * tbytes);
+    HCoef<Real> *coef = reinterpret_cast<HCoef<Real> *>(grp + P.n_groups);
+    HTerm *trm = reinterpret_cast<HTerm *>(coef + P.n_classes);
+    HClass *cls = reinterpret_cast<HClass *>(trm + P.n_terms);
     double *red = reinterpret_cast<double *>(cls + P.n_classes);
     for (int i = tid; i < P.n_terms; i += T) trm[i] = P.terms[i];
     for (int i = tid; i < P.n_groups; i += T) grp[i] = P.groups[i];
@@ -724,7 +618,6 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
     const int64_t per = (tiles + gridDim.x - 1) / gridDim.x;
     const int64_t t0 = per * blockIdx.x, t_end = min(tiles, t0 + per);
     if (t0 >= t_end) return;
-    constexpr bool real = kRealH;  // every term's coefficient times i^phase is real
     auto fetch = [&](const TileCursor &c, int buf) {
         const C *src = psi + ((int64_t)c.slot << n) + c.base;
         const uint32_t d = sh + (uint32_t)buf * tbytes;
@@ -762,12 +655,9 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
                 re = -re;
                 im = -im;
             }
-            const uint32_t zh = cl.zl >> (t - R);
-            uint32_t kp = 0;
-            for (int k = 0; k < NA; ++k) kp |= (uint32_t)(__popc((uint32_t)k & zh) & 1) << k;
             HCoef<Real> h;
             h.zt = cl.zl & (uint32_t)(T - 1);
-            h.kpat = kp;
+            h.pad = 0;
             h.re = re;
             h.im = im;
             coef[c] = h;
@@ -787,69 +677,85 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
         else cp_async_commit();  // keeps "all but the newest group" meaning the lambda tile
         const C *tile = reinterpret_cast<const C *>(smem + (uint32_t)buf * tbytes);
         const C *Sg = psi + ((int64_t)cur.slot << n);
-        Real part = 0;
-        bool lam_ready = false;
+        Real lr[NA], li[NA];
 #pragma unroll
-        for (int k0 = 0; k0 < NA; k0 += KC) {
-            Real lr[KC], li[KC];
-#pragma unroll
-            for (int k = 0; k < KC; ++k) lr[k] = li[k] = 0;
-            for (int g = 0; g < P.n_groups; ++g) {
-                const HGroup gr = grp[g];
-                C p[KC];
-#pragma unroll
-                for (int k = 0; k < KC; ++k) {
-                    const uint32_t j = (uint32_t)(tid + (k0 + k) * T);
-                    p[k] = gr.xfar ? Sg[(cur.base ^ g0 ^ xsel<R>(k0 + k, gk)) ^ gr.xfar]
-                                   : tile[j ^ gr.xl];
-                }
-                Real dr[KC], di[KC];
-#pragma unroll
-                for (int k = 0; k < KC; ++k) dr[k] = di[k] = 0;
+        for (int k = 0; k < NA; ++k) lr[k] = li[k] = 0;
+        for (int g = 0; g < P.n_groups; ++g) {
+            const HGroup &gr = grp[g];
+            const uint32_t xl = gr.xl, xfar = gr.xfar, kact = gr.kact;
+            auto partner = [&](int k) -> C {
+                return xfar ? Sg[(cur.base ^ g0 ^ xsel<R>(k, gk)) ^ xfar]
+                            : tile[(uint32_t)(tid + k * T) ^ xl];
+            };
+            if (kact == 0) {
+                // no class has a Z on a register bit: one value per thread
+                Real vr = 0, vi = 0;
                 for (int c = gr.c_begin; c < gr.c_end; ++c) {
                     const HCoef<Real> h = coef[c];
                     const bool nt = __popc((uint32_t)tid & h.zt) & 1u;
-                    const Real vr = nt ? -h.re : h.re;
-                    const uint32_t kp = h.kpat >> k0;
-#pragma unroll
-                    for (int k = 0; k < KC; ++k) dr[k] += ((kp >> k) & 1u) ? -vr : vr;
-                    if (!real) {
-                        const Real vi = nt ? -h.im : h.im;
-#pragma unroll
-                        for (int k = 0; k < KC; ++k) di[k] += ((kp >> k) & 1u) ? -vi : vi;
-                    }
+                    vr += nt ? -h.re : h.re;
+                    if constexpr (!kRealH) vi += nt ? -h.im : h.im;
                 }
 #pragma unroll
-                for (int k = 0; k < KC; ++k) {
+                for (int k = 0; k < NA; ++k) {
+                    const C pk = partner(k);
                     if constexpr (kRealH) {
-                        lr[k] = fmaR(dr[k], p[k].x, lr[k]);
-                        li[k] = fmaR(dr[k], p[k].y, li[k]);
+                        lr[k] = fmaR(vr, pk.x, lr[k]);
+                        li[k] = fmaR(vr, pk.y, li[k]);
                     } else {
-                        lr[k] = fmaR(dr[k], p[k].x, fmaR(-di[k], p[k].y, lr[k]));
-                        li[k] = fmaR(dr[k], p[k].y, fmaR(di[k], p[k].x, li[k]));
+                        lr[k] = fmaR(vr, pk.x, fmaR(-vi, pk.y, lr[k]));
+                        li[k] = fmaR(vr, pk.y, fmaR(vi, pk.x, li[k]));
                     }
                 }
+                continue;
             }
-            if (add && !lam_ready) {
-                cp_async_wait_prior();  // own copies of the lambda tile have landed
-                lam_ready = true;
-            }
+            // buckets: classes with register-bit Z mask p (a subset of kact)
+            Real vr[NA], vi[NA];
 #pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                const C pj = tile[tid + (k0 + k) * T];
-                part = fmaR(pj.x, lr[k], fmaR(pj.y, li[k], part));
-                if constexpr (kLam) {
-                    const uint32_t go = g0 ^ xsel<R>(k0 + k, gk);
-                    C out;
-                    out.x = lr[k];
-                    out.y = li[k];
-                    if (add) {  // each thread reads back only its own copies
-                        const C old = lt[tid + (k0 + k) * T];
-                        out.x += old.x;
-                        out.y += old.y;
-                    }
-                    L[go] = out;
+            for (int p = 0; p < NA; ++p) vr[p] = vi[p] = 0;
+            int c = gr.c_begin;
+#pragma unroll
+            for (int p = 0; p < NA; ++p) {
+                if (p & ~kact) continue;
+                const int c_end = c + (int)gr.nk[p];
+                for (; c < c_end; ++c) {
+                    const HCoef<Real> h = coef[c];
+                    const bool nt = __popc((uint32_t)tid & h.zt) & 1u;
+                    vr[p] += nt ? -h.re : h.re;
+                    if constexpr (!kRealH) vi[p] += nt ? -h.im : h.im;
                 }
+            }
+            wht<Real, NA>(vr);
+            if constexpr (!kRealH) wht<Real, NA>(vi);
+#pragma unroll
+            for (int k = 0; k < NA; ++k) {
+                const C pk = partner(k);
+                if constexpr (kRealH) {
+                    lr[k] = fmaR(vr[k], pk.x, lr[k]);
+                    li[k] = fmaR(vr[k], pk.y, li[k]);
+                } else {
+                    lr[k] = fmaR(vr[k], pk.x, fmaR(-vi[k], pk.y, lr[k]));
+                    li[k] = fmaR(vr[k], pk.y, fmaR(vi[k], pk.x, li[k]));
+                }
+            }
+        }
+        if (add) cp_async_wait_prior();  // own copies of the lambda tile have landed
+        Real part = 0;
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+            const C pj = tile[tid + k * T];
+            part = fmaR(pj.x, lr[k], fmaR(pj.y, li[k], part));
+            if constexpr (kLam) {
+                const uint32_t go = g0 ^ xsel<R>(k, gk);
+                C out;
+                out.x = lr[k];
+                out.y = li[k];
+                if (add) {  // each thread reads back only its own copies
+                    const C old = lt[tid + k * T];
+                    out.x += old.x;
+                    out.y += old.y;
+                }
+                L[go] = out;
             }
         }
         e_acc += (double)part;
@@ -1120,7 +1026,7 @@ cudaError_t launch_tile_fwd(int c128, const TilePass &P, int n, int n_slots, con
 
 cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, const void *mats,
                             int G, void *psi, void *lam, double *rho_g, int64_t max_blocks,
-                            cudaStream_t st, const void *psi_src) {
+                            cudaStream_t st, const void *psi_src, bool write_psi) {
     const uint32_t smem = tile_rev_smem(c128, P);
     const int threads = 1 << (P.t - P.R);
     HBM_DISPATCH_R(c128, P.R, {
@@ -1134,25 +1040,25 @@ cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, con
         const int blocks = fill_blocks(k, threads, smem, max_blocks);
         k<<<blocks, threads, smem, st>>>(P, n, n_slots, (const C *)mats, G,
                                          (const C *)(psi_src ? psi_src : psi), (C *)psi, (C *)lam,
-                                         rho_g);
+                                         rho_g, write_psi ? 1 : 0);
     });
     return cudaGetLastError();
 }
 
 uint32_t tile_h_smem(int c128, const HPass &P) {
     const uint32_t csz = c128 ? 16u : 8u;
-    return 3u * (csz << P.t) + (uint32_t)P.n_terms * (uint32_t)sizeof(HTerm) +
+    return 3u * (csz << P.t) + (uint32_t)P.n_groups * (uint32_t)sizeof(HGroup) +
            (uint32_t)P.n_classes * (csz + 8u + (uint32_t)sizeof(HClass)) +
-           (uint32_t)P.n_groups * (uint32_t)sizeof(HGroup) + 32u * 8u + 16u;
+           (uint32_t)P.n_terms * (uint32_t)sizeof(HTerm) + 32u * 8u + 16u;
 }
 
 cudaError_t launch_tile_h(int c128, const HPass &P, int n, int n_slots, const void *psi, void *lam,
                           double *E, int64_t max_blocks, cudaStream_t st) {
     const uint32_t smem = tile_h_smem(c128, P);
-    // 2^R amplitudes per thread: 256 threads for t >= 10, at least 32 below
-    const int R = P.t >= 12 ? 4 : (P.t == 11 ? 3 : 2);
+    // 2^R amplitudes per thread (R = h_reg_bits(t), the planner's bucketing)
+    const int R = h_reg_bits(P.t);
     const int threads = 1 << (P.t - R);
-    if (P.t < 7 || P.t > 12) return cudaErrorInvalidValue;
+    if (P.t < 7 || P.t > 12 || P.R != R) return cudaErrorInvalidValue;
     auto go = [&](auto k, auto *psi_t, auto *lam_t) -> cudaError_t {
         cudaError_t e = allow_smem(k, smem);
         if (e != cudaSuccess) return e;

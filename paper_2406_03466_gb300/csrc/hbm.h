@@ -24,10 +24,13 @@ cudaError_t launch_tile_fwd(int c128, const TilePass &P, int n, int n_slots, con
                             const void *src = nullptr);
 // Reverse pass P on psi and lambda; adds the reduced matrices of its
 // parametrised groups to rho_g[slot][G][8].  psi_src (null: psi) holds the
-// psi the pass reads (a stored forward state); its output psi goes to psi.
+// psi the pass reads (a stored forward state); its output psi goes to psi
+// unless write_psi is false (the next reverse pass restarts psi from a
+// stored state, or this is the last one).
 cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, const void *mats,
                             int G, void *psi, void *lam, double *rho_g, int64_t max_blocks,
-                            cudaStream_t st, const void *psi_src = nullptr);
+                            cudaStream_t st, const void *psi_src = nullptr,
+                            bool write_psi = true);
 // Tile passes of several problems in one launch (forward, or reverse with
 // rev): items sorted by block_begin, device memory; every item uses the same
 // tile shape (threads = 2^(t - R)).  smem: the largest over the items of

@@ -638,6 +638,7 @@ std::string plan_h_passes(const HostObservable &h, int tile_bits, int coalesce_b
         P.t = t;
         P.n_tile_bits = n - t;
         P.first = out->passes.empty() ? 1 : 0;
+        P.R = h_reg_bits(t);
         std::vector<int> pos(n, -1);
         int b = 0, k = 0;
         uint32_t acc = 0;
@@ -693,6 +694,13 @@ std::string plan_h_passes(const HostObservable &h, int tile_bits, int coalesce_b
                 out->classes.back().t_end = (int)out->terms.size() - t0;
             }
             G.c_end = (int)out->classes.size() - c0;
+            // classes are in increasing zl order, hence grouped by their
+            // register-bit Z mask kz = zl >> (t - R)
+            for (int c = G.c_begin; c < G.c_end; ++c) {
+                const uint32_t kz = out->classes[(size_t)(c0 + c)].zl >> (t - P.R);
+                G.nk[kz] += 1;
+                G.kact |= kz;
+            }
             out->groups.push_back(G);
         }
         P.real = 1;

@@ -167,11 +167,21 @@ struct MultiItem {
 // group, terms with the same Z mask on the local qubits form a class whose
 // coefficient is summed once per tile (the Z mask's tile-number bits only
 // give each term a sign per tile).
+// The H kernel's threads hold 2^R amplitudes j = tid + k 2^(t - R) (k over
+// the R register bits, the top R tile-local bits).  A group's classes are
+// sorted by their Z mask on the register bits, kz = zl >> (t - R): the
+// kernel sums each thread's signed class coefficients into one bucket per
+// kz and expands the 2^R buckets to the thread's 2^R diagonal values by a
+// Walsh-Hadamard transform over the register bits.
+constexpr int kHRegBitsMax = 4;
 struct HGroup {
     uint32_t xl;              // flip mask on tile-local bits
     int32_t c_begin, c_end;   // its classes
     uint32_t xfar;            // whole flip mask when it leaves the tile (partner read from
                               // global memory), else 0
+    uint32_t kact;            // register bits in some class's Z mask (0: one value per thread)
+    uint32_t pad[3];
+    uint16_t nk[1 << kHRegBitsMax];  // classes with register Z mask kz, in kz order
 };
 
 struct HClass {
@@ -191,13 +201,17 @@ struct HTerm {
 struct HPass {
     int32_t t, n_tile_bits, n_groups, n_classes, n_terms, first;  // first: writes lambda
     int32_t real;               // every coefficient c_t i^phase_t is real
-    int32_t pad;
+    int32_t R;                  // register bits of the kernel's threads (h_reg_bits(t))
     uint32_t gl[kTileBitsMax];  // tile-local bit b -> global offset bit
     uint32_t gpre[kNMax];       // gt[0] ^ ... ^ gt[k] for tile-number bit k
     const HGroup *groups;       // device arrays of this pass
     const HClass *classes;
     const HTerm *terms;
 };
+
+// Register bits of the H-pass kernel for tiles of 2^t amplitudes: 256
+// threads for t >= 12 (R = 4), fewer below (at least 32 threads).
+inline int h_reg_bits(int t) { return t >= 12 ? 4 : (t == 11 ? 3 : 2); }
 
 // GF(2)-linear swizzle of a shared-memory amplitude index: the low `w` bits
 // are XORed with the fold of all higher w-bit chunks.  w = 4 for 8-byte

@@ -1,0 +1,162 @@
+// Device helpers shared by the tile-pass kernels (register stages in
+// hbm.cu, tensor-core blocks in tc.cu): asynchronous tile copies, the walk
+// over (slot, tile) pairs, per-thread address vectors and the packed stage
+// records of a pass descriptor.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "engine.cuh"
+
+namespace svk {
+namespace {
+
+// ------------------------------------------------------------ tile passes
+//
+// A block owns one contiguous range of (slot, tile) pairs.  Tiles arrive by
+// cp.async in one of two buffers, so the next tile is in flight while the
+// current one is computed.  Every register stage loads the thread's 2^R
+// amplitudes from shared memory, applies the fused 2x2 group of each of its
+// register bits (at most one per bit) and stores them back in place.  The
+// pass descriptor is a __grid_constant__ parameter: its stage vectors are
+// read with warp-uniform indices through the constant cache.  Each thread
+// computes its per-stage address bases once per launch.
+
+__device__ __forceinline__ void cp_async_amp(uint32_t sdst, const float2 *g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sdst), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_amp(uint32_t sdst, const double2 *g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// Waits for all but the most recently committed group.
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Offsets of this thread's amplitudes (tile-local index tid + k 2^(t-R))
+// through the per-bit vector table v: returns the tid part and fills the
+// parts of the R register bits.
+template <int R>
+__device__ __forceinline__ uint32_t bit_vectors(const uint32_t *v, int t, int tid,
+                                                uint32_t (&k)[R]) {
+    const int tb = t - R;
+    uint32_t g = 0;
+    for (int b = 0; b < tb; ++b)
+        if ((tid >> b) & 1) g ^= v[b];
+#pragma unroll
+    for (int j = 0; j < R; ++j) k[j] = v[tb + j];
+    return g;
+}
+
+// Position of one tile in the walk over (slot, tile): global offset of the
+// tile's first amplitude within its state.
+struct TileCursor {
+    int slot;
+    uint32_t local, base;
+};
+
+__device__ __forceinline__ TileCursor tile_cursor(const TilePass &P, int64_t tix) {
+    TileCursor c;
+    c.slot = (int)(tix >> P.n_tile_bits);
+    c.local = (uint32_t)(tix & ((int64_t(1) << P.n_tile_bits) - 1));
+    c.base = 0;
+    for (int k = 0; k < P.n_tile_bits; ++k)
+        if ((c.local >> k) & 1u) c.base ^= P.gpre[k] ^ (k ? P.gpre[k - 1] : 0u);
+    return c;
+}
+
+// Next tile: counting up flips tile-number bits 0..ctz(local + 1).
+__device__ __forceinline__ TileCursor tile_next(const TilePass &P, TileCursor c) {
+    ++c.local;
+    if ((c.local >> P.n_tile_bits) != 0u) {
+        c.local = 0;
+        c.base = 0;
+        ++c.slot;
+    } else {
+        c.base ^= P.gpre[__ffs((int)c.local) - 1];
+    }
+    return c;
+}
+
+// Shared-memory record of one stage (32 bytes, read with warp-uniform
+// addresses): word 0 holds one op byte per register bit, (u + 1) | real << 6
+// | parametrised << 7 for pass-local op u (0: no op); word 1 + i holds
+// ldq[i] | stq[i] << 16 (byte offsets, < 2^16 for every supported tile);
+// word 5 holds the ops' fmode bytes.
+__device__ __forceinline__ void build_stage_recs(const TilePass &P, uint4 *rec) {
+    for (int s = threadIdx.x; s < P.n_stages; s += blockDim.x) {
+        const TileStage &sg = P.st[s];
+        uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int i = 0; i < P.R && i < 4; ++i) {
+            const int u = sg.op[i];
+            if (u >= 0) {
+                const uint32_t ob = (uint32_t)(u + 1) | (((P.real_mask >> u) & 1ull) ? 64u : 0u) |
+                                    (((P.param_mask >> u) & 1ull) ? 128u : 0u);
+                w[0] |= ob << (8 * i);
+            }
+            w[1 + i] = sg.ldq[i] | (sg.stq[i] << 16);
+            if (u >= 0) w[5] |= (uint32_t)(P.fmode[u] & 3) << (8 * i);
+        }
+        rec[2 * s] = make_uint4(w[0], w[1], w[2], w[3]);
+        rec[2 * s + 1] = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+}
+
+template <int R>
+__device__ __forceinline__ uint32_t read_stage_rec(const uint4 *rec, int s, uint32_t (&lq)[R],
+                                                   uint32_t (&sq)[R]) {
+    static_assert(R <= 4, "stage records hold four register bits");
+    const uint4 a = rec[2 * s];
+    uint32_t w[4] = {a.y, a.z, a.w, 0u};
+    if constexpr (R > 3) w[3] = rec[2 * s + 1].x;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        lq[j] = w[j] & 0xffffu;
+        sq[j] = w[j] >> 16;
+    }
+    return a.x;
+}
+
+// The four entries of matrix u (32-byte aligned records) as two 16-byte loads.
+__device__ __forceinline__ void load_mat(const float2 *sm, int u, float2 &m0, float2 &m1,
+                                         float2 &m2, float2 &m3) {
+    const float4 *p = reinterpret_cast<const float4 *>(sm) + 2 * u;
+    const float4 x = p[0], y = p[1];
+    m0 = make_float2(x.x, x.y);
+    m1 = make_float2(x.z, x.w);
+    m2 = make_float2(y.x, y.y);
+    m3 = make_float2(y.z, y.w);
+}
+__device__ __forceinline__ void load_mat(const double2 *sm, int u, double2 &m0, double2 &m1,
+                                         double2 &m2, double2 &m3) {
+    m0 = sm[4 * u];
+    m1 = sm[4 * u + 1];
+    m2 = sm[4 * u + 2];
+    m3 = sm[4 * u + 3];
+}
+
+// The group ops of one stage (op bytes `ops`), register bits I..R-1 in order.
+// kReal: every op of the pass has a real matrix (no complex path compiled).
+template <typename C, int R, int I, bool kReal>
+__device__ __forceinline__ void tile_ops_fwd(uint32_t ops, const C *sm, C (&a)[1 << R]) {
+    if constexpr (I < R) {
+        const uint32_t ob = (ops >> (8 * I)) & 0xffu;
+        if (ob) {
+            C m0, m1, m2, m3;
+            load_mat(sm, (int)(ob & 63u) - 1, m0, m1, m2, m3);
+            if (kReal || (ob & 64u))
+                u1r_bit<C, decltype(m0.x), R, I>(a, m0.x, m1.x, m2.x, m3.x);
+            else
+                u1_bit<C, R, I>(a, m0, m1, m2, m3);
+        }
+        tile_ops_fwd<C, R, I + 1, kReal>(ops, sm, a);
+    }
+}
+
+// Every op of pass P has a real matrix.
+__host__ __device__ inline bool pass_all_real(const TilePass &P) {
+    const uint64_t all = P.n_ops >= 64 ? ~0ull : ((1ull << P.n_ops) - 1ull);
+    return (P.real_mask & all) == all;
+}
+
+}  // namespace
+}  // namespace svk

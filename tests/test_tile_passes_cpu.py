@@ -444,14 +444,15 @@ def test_rejects_tiles_narrower_than_a_warp():
 
 class HPassRec(ctypes.Structure):
     _fields_ = [("t", I32), ("n_tile_bits", I32), ("n_groups", I32), ("n_classes", I32),
-                ("n_terms", I32), ("first", I32), ("real", I32), ("pad", I32), ("gl", U32 * KT),
+                ("n_terms", I32), ("first", I32), ("real", I32), ("R", I32), ("gl", U32 * KT),
                 ("gpre", U32 * 30),
                 ("groups", ctypes.c_void_p), ("classes", ctypes.c_void_p),
                 ("terms", ctypes.c_void_p)]
 
 
 class HGroup(ctypes.Structure):
-    _fields_ = [("xl", U32), ("c_begin", I32), ("c_end", I32), ("xfar", U32)]
+    _fields_ = [("xl", U32), ("c_begin", I32), ("c_end", I32), ("xfar", U32), ("kact", U32),
+                ("pad", U32 * 3), ("nk", ctypes.c_uint16 * 16)]
 
 
 class HClass(ctypes.Structure):
@@ -475,8 +476,25 @@ def export_h(obs, t, c):
     return [a[:k] for a, k in zip(arrs, counts)]
 
 
+def _wht(v):
+    """v[k] <- sum_p v[p] (-1)^|k & p| over the last axis (length 2^R)."""
+    v = v.copy()
+    b = 1
+    while b < v.shape[-1]:
+        for p in range(v.shape[-1]):
+            if not p & b:
+                x, y = v[..., p].copy(), v[..., p | b].copy()
+                v[..., p], v[..., p | b] = x + y, x - y
+        b <<= 1
+    return v
+
+
 def run_h(plan, psi, n):
-    """The tile H kernel, tile by tile: returns lambda = H psi and <psi|H|psi>."""
+    """The tile H kernel, tile by tile: returns lambda = H psi and <psi|H|psi>.
+    Like the kernel, thread tid holds amplitudes j = tid + k 2^(t - R); per
+    group it sums its signed class coefficients into one bucket per
+    register-bit Z mask (the classes' planned order and the group's bucket
+    counts) and expands the buckets by a Walsh-Hadamard transform."""
     passes, groups, classes, terms = plan
     lam = np.zeros_like(psi)
     E = 0.0
@@ -499,12 +517,30 @@ def run_h(plan, psi, n):
                     v += sgn * tm.coeff * 1j ** tm.phase
                 coef.append(v)
             part = np.zeros(1 << t, complex)
+            R = P.R
+            T = 1 << (t - R)
+            tid = np.arange(T)
             for gr in groups[g0:g0 + P.n_groups]:
                 jx = j ^ gr.xl
-                D = np.zeros(1 << t, complex)
-                for c in range(gr.c_begin, gr.c_end):
-                    par = np.array([bin(v).count("1") & 1 for v in (jx & classes[c0 + c].zl)])
-                    D += np.where(par == 1, -coef[c], coef[c])
+                # the kernel's buckets: classes in planned order, nk[p] per
+                # register-bit Z mask p; per thread the signed coefficients
+                V = np.zeros((T, 1 << R), complex)
+                c = gr.c_begin
+                for p in range(1 << R):
+                    for _ in range(gr.nk[p]):
+                        zl = classes[c0 + c].zl
+                        assert zl >> (t - R) == p
+                        # the class's sign on the flip bits: D(j ^ xl) = D(j) x that
+                        sx = -1.0 if bin(gr.xl & zl).count("1") & 1 else 1.0
+                        par = np.array([bin(v).count("1") & 1 for v in (tid & zl)])
+                        V[:, p] += sx * np.where(par == 1, -coef[c], coef[c])
+                        c += 1
+                assert c == gr.c_end
+                assert gr.kact == np.bitwise_or.reduce(
+                    [classes[c0 + x].zl >> (t - R) for x in range(gr.c_begin, gr.c_end)] + [0])
+                Dk = _wht(V) if gr.kact else np.repeat(V[:, :1], 1 << R, axis=1)
+                # amplitude j = tid + k T holds D(j ^ xl) at [tid, k]
+                D = Dk.T.reshape(-1)
                 part += D * (psi[(base + loc) ^ gr.xfar] if gr.xfar else tile[jx])
             E += float(np.sum(np.conj(tile) * part).real)
             if P.first:

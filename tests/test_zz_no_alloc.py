@@ -108,42 +108,79 @@ _FRESH = r"""
 import ctypes, sys
 sys.path.insert(0, sys.argv[1])
 import numpy as np
-import torch
 import paper_2406_03466_gb300 as sv
 import workloads as wl
-torch.cuda.set_device(0)
-lib = sv.library()
-stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-cases = []
-for w in (wl.mcvqe(8, 4), wl.qcl(6, 2, 7), wl.vqe_random_pauli(4, 2, 10)):
-    prob = sv.Problem.from_spec(w, "c64")
-    theta = torch.as_tensor(w.theta, dtype=torch.float64, device="cuda")
-    out = [torch.empty(n, dtype=torch.float64, device="cuda") for n in (w.n_instances, 1, w.n_params)]
-    cases.append((prob, theta, out))
-torch.cuda.synchronize()
-def run_all():
-    for prob, theta, (e, l, g) in cases:
-        st = lib.sv_grad_param_shift_noalloc(
-            ctypes.byref(prob.struct), ctypes.c_void_p(theta.data_ptr()),
-            ctypes.c_void_p(e.data_ptr()), ctypes.c_void_p(l.data_ptr()),
-            ctypes.c_void_p(g.data_ptr()), stream)
+rt = ctypes.CDLL("libcudart.so.13")   # the CUDA runtime libsv.so is linked against
+assert rt.cudaSetDevice(0) == 0 and rt.cudaFree(None) == 0
+
+
+class Dev:
+    # a float64 device array made with cudaMalloc (no torch in this process)
+    def __init__(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        self.shape = a.shape
+        self.p = ctypes.c_void_p()
+        assert rt.cudaMalloc(ctypes.byref(self.p), ctypes.c_size_t(max(8, a.nbytes))) == 0
+        if a.size:
+            assert rt.cudaMemcpy(self.p, a.ctypes.data_as(ctypes.c_void_p),
+                                 ctypes.c_size_t(a.nbytes), 1) == 0
+
+    def data_ptr(self):
+        return self.p.value
+
+
+def free_bytes():
+    f, t = ctypes.c_size_t(), ctypes.c_size_t()
+    assert rt.cudaDeviceSynchronize() == 0 and rt.cudaMemGetInfo(ctypes.byref(f), ctypes.byref(t)) == 0
+    return f.value
+
+
+def cases(seed):
+    out = []
+    for w in (wl.mcvqe(8, 4, seed=seed), wl.qcl(6, 2, 7, seed=seed),
+              wl.vqe_random_pauli(4, 2, 10, seed=seed)):
+        d = 0 if w.inputs is None else int(np.asarray(w.inputs).shape[1])
+        circ = sv.Circuit(w.n_qubits, w.gates, w.n_params, d)
+        obs = sv.PauliSum(w.n_qubits, w.pauli_letters, w.pauli_coeffs)
+        dev = lambda a: None if a is None else Dev(a)  # noqa: E731
+        prob = sv.Problem(circ, obs, w.refs, "c64", inputs=dev(w.inputs), cost=w.cost,
+                          weights=dev(w.weights), targets=dev(w.targets))
+        outs = [Dev(np.zeros(k)) for k in (w.n_instances, 1, w.n_params)]
+        out.append((prob, Dev(w.theta), outs, [w, prob.inputs, prob.weights, prob.targets]))
+    return out
+
+
+def run(cs):
+    for prob, th, outs, _ in cs:
+        st = sv.library().sv_grad_param_shift_noalloc(
+            ctypes.byref(prob.struct), th.p, outs[0].p, outs[1].p, outs[2].p, None)
         assert st == sv.SV_OK, sv.sv_last_error()
-    torch.cuda.synchronize()
-run_all()          # the very first library calls of this process
-free0 = torch.cuda.mem_get_info()[0]
+    assert rt.cudaDeviceSynchronize() == 0
+
+
+first, later = cases(0), cases(1)   # the same shapes (same kernels), other values
+run(first)          # the very first library calls of this process
+free0 = free_bytes()
 for _ in range(3):
-    run_all()
-free1 = torch.cuda.mem_get_info()[0]
+    run(later)
+    run(first)
+free1 = free_bytes()
 assert free1 == free0, (free0, free1)
-assert all(np.isfinite(c[2][2].cpu().numpy()).all() for c in cases)
+g = np.zeros(later[0][3][0].n_params)
+assert rt.cudaMemcpy(g.ctypes.data_as(ctypes.c_void_p), later[0][2][2].p,
+                     ctypes.c_size_t(g.nbytes), 2) == 0
+assert np.isfinite(g).all() and np.abs(g).max() > 0
 print("NOALLOC_FRESH_OK", free0, free1)
 """
 
 
 def test_noalloc_allocates_nothing_in_a_fresh_process():
-    """In a new process whose first library calls are allocation-free ones,
-    the device's free memory does not move across repeated calls (modules
-    load eagerly, so kernel loading cannot be mistaken for an allocation)."""
+    """In a new process without torch whose first library calls are
+    allocation-free ones, the device's free memory does not move across
+    repeated calls on problems the library has not seen before (modules
+    load eagerly at context creation, so kernel loading cannot be mistaken
+    for an allocation; a library cache keyed on the problem would have to
+    allocate for the new problems)."""
     import os
     import subprocess
     import sys
