@@ -121,7 +121,11 @@ typedef struct {
                                 its own index bit (by default a pass may move the qubits the
                                 next pass needs into the low bits); states returned to the
                                 caller always keep qubit order */
-    int32_t reserved[1];
+    int32_t tensor_blocks;   /* forward tile passes (complex64, reg_bits 4, tile_bits 11 or
+                                12): 1 = apply every register stage's four fused groups as
+                                one dense 16 x 16 complex block on the tensor cores
+                                (tcgen05, 3xTF32 split, FP32 accumulation); 0 = FP32 FMAs
+                                in registers.  sv_autotune may pick either. */
 } sv_plan_opts;
 
 /* ---------------------------------------------------------------- states */
@@ -247,8 +251,11 @@ sv_status sv_grad_param_shift_host(const sv_problem *problem, const double *thet
  * weights: device [n_instances] dL/dE_i; NULL derives them from the
  * problem's cost.  States that do not fit on chip run as tile passes over
  * device memory; their forward states are stored every `checkpoint_every`
- * passes (0 = every 4) and the reverse sweep restarts psi from each stored
- * state instead of carrying the rounding of the un-computation further.
+ * passes and the reverse sweep restarts psi from each stored state instead
+ * of carrying the rounding of the un-computation further (a reverse pass
+ * followed by such a restart writes only lambda).  0 = every pass, else
+ * every 2nd, if that many stored states still let all instances run at
+ * once in free device memory, else every 4th.
  * Uses library scratch of I * P doubles, plus for device-memory states
  * (2 + checkpoints) states per instance processed at once (instances are
  * processed in groups that fit in free device memory). */
@@ -420,13 +427,24 @@ sv_status sv_autotune(const sv_problem *problem, const double *theta, int32_t ki
  * threads_per_block is 2^(tile_bits - reg_bits). */
 sv_status sv_tuned_shape(const sv_problem *problem, int32_t kind, int32_t *reg_bits,
                          int32_t *threads_per_block, float *microseconds);
+/* The tile shape sv_autotune chose for a problem whose states live in device
+ * memory (kind 1 = energies, 2 = adjoint): tile bits, register bits, whether
+ * the forward passes run as tensor-core blocks (sv_plan_opts.tensor_blocks),
+ * and the time of the best call.  Any out-pointer may be NULL. */
+sv_status sv_tuned_tile(const sv_problem *problem, int32_t kind, int32_t *tile_bits,
+                        int32_t *reg_bits, int32_t *tensor_blocks, float *microseconds);
 
 /* ----------------------------------------------------------------- misc */
 
 const char *sv_status_string(sv_status status);
 /* Thread-local description of the last failed call (empty if none). */
 const char *sv_last_error(void);
-/* Synchronize `stream` and report any pending CUDA error as a status. */
+/* Synchronize `stream` and report any pending CUDA error as a status.  A
+ * kernel whose bounded device-side wait gave up (the tensor-core passes wait
+ * for their MMAs at most about 2^22 times) records that in the library's
+ * device error word; this call reports it as SV_ERR_TIMEOUT (and clears
+ * it): the results of the calls since the last check are then invalid,
+ * while the CUDA context stays usable. */
 sv_status sv_sync_status(sv_stream_t stream);
 /* Release plan caches and scratch on every device, and forget the device
  * addresses that sv_grad_param_shift_noalloc looked up. */

@@ -48,6 +48,13 @@ sv_status sv_debug_h_passes(const sv_pauli_sum *h, int32_t tile_bits, int32_t co
                             int32_t *counts, void *passes, void *groups, void *classes,
                             void *terms);
 
+/* The bounded-wait path end to end: launches one block on `stream` that
+ * waits `limit` times on an mbarrier nothing arrives on and then records the
+ * expiry in the library's device error word, as a tensor-core pass whose
+ * MMAs never completed would (the next sv_sync_status returns
+ * SV_ERR_TIMEOUT).  limit: 1..2^20. */
+sv_status sv_debug_wait_expiry(int32_t limit, sv_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

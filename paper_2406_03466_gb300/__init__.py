@@ -60,7 +60,7 @@ class sv_plan_opts(ctypes.Structure):
     _fields_ = [("reg_bits", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
                 ("no_fusion", ctypes.c_int32), ("epilogue", ctypes.c_int32),
                 ("tile_bits", ctypes.c_int32), ("coalesce_bits", ctypes.c_int32),
-                ("no_relabel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("no_relabel", ctypes.c_int32), ("tensor_blocks", ctypes.c_int32)]
 
 
 class sv_slot(ctypes.Structure):
@@ -81,7 +81,7 @@ class sv_problem(ctypes.Structure):
 EXPORTED = ("sv_alloc", "sv_free", "sv_state_info", "sv_apply_circuit_batch",
             "sv_expect_pauli_sum", "sv_energies", "sv_param_shift_energies", "sv_grad_param_shift", "sv_grad_adjoint",
             "sv_grad_param_shift_plain", "sv_grad_param_shift_noalloc", "sv_autotune",
-            "sv_tuned_shape", "sv_plan_info", "sv_h_plan_info", "sv_phase_timing",
+            "sv_tuned_shape", "sv_tuned_tile", "sv_plan_info", "sv_h_plan_info", "sv_phase_timing",
             "sv_grad_adjoint_multi", "sv_grad_ddcl", "sv_grad_ddcl_param_shift",
             "sv_grad_param_shift_host", "sv_grad_adjoint_host", "sv_param_shift_energies_range", "sv_sample",
             "sv_param_shift_combine",
@@ -119,6 +119,9 @@ def _load():
     lib.sv_autotune.argtypes = [P(sv_problem), V, I32, V]
     lib.sv_plan_info.argtypes = [P(sv_circuit), I32, P(sv_plan_opts)] + [P(I32)] * 5
     lib.sv_tuned_shape.argtypes = [P(sv_problem), I32, P(I32), P(I32), P(ctypes.c_float)]
+    lib.sv_tuned_tile.argtypes = [P(sv_problem), I32, P(I32), P(I32), P(I32), P(ctypes.c_float)]
+    lib.sv_debug_wait_expiry.argtypes = [I32, V]
+    lib.sv_debug_wait_expiry.restype = I32
     lib.sv_h_plan_info.argtypes = [P(sv_pauli_sum), I32, P(I32), P(I32)]
     lib.sv_phase_timing.argtypes = [I32]
     lib.sv_last_phase_ms.argtypes = [P(ctypes.c_float)] * 3
@@ -204,11 +207,13 @@ class PauliSum:
 
 
 def plan_opts(reg_bits=0, threads_per_block=0, no_fusion=False, epilogue=0,
-              tile_bits=0, coalesce_bits=0, no_relabel=False) -> sv_plan_opts:
+              tile_bits=0, coalesce_bits=0, no_relabel=False,
+              tensor_blocks=False) -> sv_plan_opts:
     o = sv_plan_opts()
     o.reg_bits, o.threads_per_block = int(reg_bits), int(threads_per_block)
     o.no_fusion, o.epilogue, o.tile_bits = int(bool(no_fusion)), int(epilogue), int(tile_bits)
     o.coalesce_bits, o.no_relabel = int(coalesce_bits), int(bool(no_relabel))
+    o.tensor_blocks = int(bool(tensor_blocks))
     return o
 
 
@@ -529,6 +534,23 @@ def sv_tuned_shape(problem: Problem, kind: int):
     _check(_lib.sv_tuned_shape(ctypes.byref(problem.struct), int(kind), ctypes.byref(r),
                                ctypes.byref(t), ctypes.byref(us)), "sv_tuned_shape")
     return r.value, t.value, us.value
+
+
+def sv_tuned_tile(problem: Problem, kind: int):
+    """(tile_bits, reg_bits, tensor_blocks, microseconds) chosen by sv_autotune
+    for a problem whose states live in device memory."""
+    t, r, tc, us = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(_lib.sv_tuned_tile(ctypes.byref(problem.struct), int(kind), ctypes.byref(t),
+                              ctypes.byref(r), ctypes.byref(tc), ctypes.byref(us)),
+           "sv_tuned_tile")
+    return t.value, r.value, bool(tc.value), us.value
+
+
+def sv_debug_wait_expiry(limit: int, stream=None) -> None:
+    """Test hook: one block whose bounded wait on an mbarrier nothing arrives
+    on gives up after `limit` tries and records it in the device error word
+    (the next sv_sync_status raises SV_ERR_TIMEOUT)."""
+    _check(_lib.sv_debug_wait_expiry(int(limit), _stream(stream)), "sv_debug_wait_expiry")
 
 
 def sv_plan_info(circuit: Circuit, dtype="c64", opts: Optional[sv_plan_opts] = None) -> dict:

@@ -101,6 +101,7 @@ struct ArrayEntry {
 // Launch shape chosen by sv_autotune for one problem structure and kernel.
 struct Tuned {
     int R = 0, tpb = 0, epi = 0;
+    int tc = 0;  // tile passes: forward stages as tensor-core blocks
     float us = 0.f;
 };
 
@@ -126,6 +127,8 @@ struct DeviceCtx {
     std::unordered_map<cudaStream_t, std::unique_ptr<DeviceBuf>> relayout;
     // Host-buffer entry points: pinned host and device staging per stream.
     std::unordered_map<cudaStream_t, std::unique_ptr<struct HostIO>> hostio;
+    // Device error word of the kernels with bounded waits (0 = none gave up).
+    DeviceBuf err;
 };
 
 struct HostIO {
@@ -633,7 +636,21 @@ bool wants_tiles(int n, sv_dtype dt, const sv_plan_opts *o) {
 
 struct TileCfg {
     int t, R, c;  // tile bits, register bits, coalesced low qubits
+    bool tc;      // forward stages as tensor-core blocks
 };
+
+// The device error word (allocated and zeroed on first use).
+int *device_err(DeviceCtx *ctx) {
+    if (!ctx->err.ptr) {
+        if (cudaMalloc(&ctx->err.ptr, 256) != cudaSuccess) {
+            ctx->err.ptr = nullptr;
+            return nullptr;
+        }
+        ctx->err.bytes = 256;
+        if (cudaMemset(ctx->err.ptr, 0, 256) != cudaSuccess) return nullptr;
+    }
+    return (int *)ctx->err.ptr;
+}
 
 // Tuning keys of the tile tier (by instance count), beside the on-chip kinds.
 constexpr int kTileEnergyKey = 10 + ONCHIP_ENERGY, kTileAdjointKey = 10 + ONCHIP_ADJOINT;
@@ -647,6 +664,7 @@ sv_status tile_cfg(int n, sv_dtype dt, const sv_plan_opts *o, TileCfg *cfg,
         if (o) t = *o;
         t.reg_bits = tn->R;
         t.tile_bits = tn->R + __builtin_ctz((unsigned)tn->tpb);
+        t.tensor_blocks = tn->tc;
         return tile_cfg(n, dt, &t, cfg, nullptr);
     }
     const int c = (o && o->coalesce_bits > 0) ? o->coalesce_bits : (dt == SV_C128 ? 3 : 4);
@@ -665,9 +683,14 @@ sv_status tile_cfg(int n, sv_dtype dt, const sv_plan_opts *o, TileCfg *cfg,
     if (t - R < 5)
         return fail(SV_ERR_UNSUPPORTED, "tile passes need tile_bits - reg_bits >= 5 (a warp of threads)");
     if (c + 2 > t) return fail(SV_ERR_ARG, "coalesce_bits must be at most tile_bits - 2");
+    const bool tc = o && o->tensor_blocks;
+    if (tc && (dt == SV_C128 || R != 4 || (t != 11 && t != 12)))
+        return fail(SV_ERR_UNSUPPORTED, "tensor_blocks: complex64 tile passes with reg_bits 4 and "
+                                        "tile_bits 11 or 12 only");
     cfg->t = t;
     cfg->R = R;
     cfg->c = c;
+    cfg->tc = tc;
     return SV_OK;
 }
 
@@ -683,7 +706,7 @@ int64_t tile_blocks(const DeviceCtx *ctx, int64_t tiles) {
 // are copied to checkpoint (i + 1) / every - 1 of `ck`.
 sv_status tiles_forward(DeviceCtx *ctx, const PlanEntry *pe, int R, sv_dtype dt,
                         const SlotSource &src, void *states, void *mats, bool init, void *ck,
-                        int every, cudaStream_t st) {
+                        int every, cudaStream_t st, bool tc = false) {
     const int c128 = dt == SV_C128, n = pe->n, G = pe->dev.n_groups;
     const size_t sbytes = ((size_t)src.n_slots << n) * (c128 ? 16 : 8);
     cudaError_t e = launch_group_mats(c128, pe->dev, src, mats, st);
@@ -705,9 +728,17 @@ sv_status tiles_forward(DeviceCtx *ctx, const PlanEntry *pe, int R, sv_dtype dt,
         void *out = states;
         if (ck && every > 0 && (i + 1) % every == 0 && i + 1 < passes.size())
             out = (char *)ck + ((i + 1) / every - 1) * sbytes;
-        e = launch_tile_fwd(c128, tp, n, src.n_slots, mats, G, out, tile_blocks(ctx, tiles), st,
-                            in);
-        if (e != cudaSuccess) return cuda_fail(e, "forward tile pass");
+        if (tc && tile_fwd_tc_supported(c128, tp)) {
+            int *err = device_err(ctx);
+            if (!err) return fail(SV_ERR_CUDA, "device error word");
+            e = launch_tile_fwd_tc(tp, n, src.n_slots, mats, G, out, tile_blocks(ctx, tiles), st,
+                                   err, in);
+            if (e != cudaSuccess) return cuda_fail(e, "forward tile pass (tensor cores)");
+        } else {
+            e = launch_tile_fwd(c128, tp, n, src.n_slots, mats, G, out, tile_blocks(ctx, tiles), st,
+                                in);
+            if (e != cudaSuccess) return cuda_fail(e, "forward tile pass");
+        }
         in = out;
     }
     return SV_OK;
@@ -753,7 +784,8 @@ sv_status tiles_energies(DeviceCtx *ctx, const sv_problem *p, const double *thet
         src.inputs = p->inputs;
         src.input_stride = p->input_stride;
         src.slot_base = slot_begin + (int)c0;
-        s = tiles_forward(ctx, pe, cfg.R, dt, src, big, (char *)big + mats_off, true, nullptr, 0, st);
+        s = tiles_forward(ctx, pe, cfg.R, dt, src, big, (char *)big + mats_off, true, nullptr, 0, st,
+                          cfg.tc);
         if (s != SV_OK) return s;
         s = h_tiles(ctx, obs, n, dt, src.n_slots, big, nullptr, E + c0, st, &pe->host.layout);
         if (s != SV_OK) return s;
@@ -870,7 +902,8 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
         void *psi = bb, *lam = bb + o_lam, *ck = bb + o_ck, *mats = bb + o_mats;
         double *rho = (double *)(bb + o_rho);
         phase_mark(ctx, st);
-        s = tiles_forward(ctx, pe, cfg.R, dt, src, psi, mats, true, ncp ? ck : nullptr, every, st);
+        s = tiles_forward(ctx, pe, cfg.R, dt, src, psi, mats, true, ncp ? ck : nullptr, every, st,
+                          cfg.tc);
         if (s != SV_OK) return s;
         phase_mark(ctx, st);
         cudaError_t e = cudaSuccess;
@@ -1299,7 +1332,8 @@ sv_status sv_apply_circuit_batch(sv_state state, const sv_circuit *circuits, int
             src.input_stride = input_stride;
             src.slots = (const sv_slot *)dslots;
             char *rows0 = (char *)state->ptr + (size_t)rows[0] * (csz << state->n);
-            s = tiles_forward(ctx, pe, cfg.R, state->dtype, src, rows0, mats, true, nullptr, 0, st);
+            s = tiles_forward(ctx, pe, cfg.R, state->dtype, src, rows0, mats, true, nullptr, 0, st,
+                              cfg.tc);
             if (s != SV_OK) return s;
             continue;
         }
@@ -1815,7 +1849,8 @@ sv_status sv_grad_ddcl_param_shift(const sv_problem *p, const double *theta,
     // the unshifted circuit (slot 0): JS and the table dJS/dP_theta
     src.n_slots = 1;
     src.slot_base = 0;
-    s = tiles_forward(ctx, pe, cfg.R, dt, src, big, (char *)big + mats_off, true, nullptr, 0, st);
+    s = tiles_forward(ctx, pe, cfg.R, dt, src, big, (char *)big + mats_off, true, nullptr, 0, st,
+                      cfg.tc);
     if (s != SV_OK) return s;
     cudaError_t e = launch_ddcl_diag(c128, n, big, target, D, js_out, st);
     if (e != cudaSuccess) return cuda_fail(e, "JS divergence and its derivative table");
@@ -1823,7 +1858,8 @@ sv_status sv_grad_ddcl_param_shift(const sv_problem *p, const double *theta,
     for (int64_t c0 = 0; c0 < B; c0 += chunk) {
         src.n_slots = (int)std::min<int64_t>(chunk, B - c0);
         src.slot_base = (int)c0;
-        s = tiles_forward(ctx, pe, cfg.R, dt, src, big, (char *)big + mats_off, true, nullptr, 0, st);
+        s = tiles_forward(ctx, pe, cfg.R, dt, src, big, (char *)big + mats_off, true, nullptr, 0, st,
+                          cfg.tc);
         if (s != SV_OK) return s;
         e = launch_diag_expect(c128, n, src.n_slots, big, D, E + c0, st);
         if (e != cudaSuccess) return cuda_fail(e, "shifted-circuit table expectations");
@@ -1985,8 +2021,10 @@ sv_status tune_tiles(const sv_problem *p, const double *theta, int32_t kinds, cu
     if (p->opts && (p->opts->tile_bits > 0 || p->opts->reg_bits > 0)) return SV_OK;  // fixed by the caller
     const int n = p->circuit->n_qubits, I = p->n_instances, Pp = p->circuit->n_params > 0 ? p->circuit->n_params : 1;
     const bool c128 = p->dtype == SV_C128;
-    const int cand_c64[][2] = {{11, 4}, {11, 3}, {12, 4}, {10, 3}, {10, 4}};
-    const int cand_c128[][2] = {{10, 2}, {10, 3}, {11, 3}, {9, 2}};
+    // (tile bits, register bits, tensor-core blocks)
+    const int cand_c64[][3] = {{11, 4, 0}, {11, 3, 0}, {12, 4, 0}, {10, 3, 0}, {10, 4, 0},
+                               {11, 4, 1}, {12, 4, 1}};
+    const int cand_c128[][3] = {{10, 2, 0}, {10, 3, 0}, {11, 3, 0}, {9, 2, 0}};
     void *out = nullptr;
     const size_t need = sizeof(double) * (2 * (size_t)I + Pp + 2);
     if (cudaMalloc(&out, need) != cudaSuccess) return fail(SV_ERR_OOM, "tuning outputs");
@@ -1999,15 +2037,17 @@ sv_status tune_tiles(const sv_problem *p, const double *theta, int32_t kinds, cu
         if (!(kinds & (key == kTileEnergyKey ? 1 : 2))) continue;
         Tuned best;
         best.us = 1e30f;
-        const int nc = c128 ? 4 : 5;
+        const int nc = c128 ? 4 : 7;
         for (int ci = 0; ci < nc; ++ci) {
             const int t = c128 ? cand_c128[ci][0] : cand_c64[ci][0];
             const int R = c128 ? cand_c128[ci][1] : cand_c64[ci][1];
+            const int tc = c128 ? cand_c128[ci][2] : cand_c64[ci][2];
             if (t > n || t - R < 5) continue;
             sv_plan_opts o{};
             if (p->opts) o = *p->opts;
             o.tile_bits = t;
             o.reg_bits = R;
+            o.tensor_blocks = tc;
             sv_problem q = *p;
             q.opts = &o;
             auto run = [&]() {
@@ -2029,6 +2069,7 @@ sv_status tune_tiles(const sv_problem *p, const double *theta, int32_t kinds, cu
                 best.us = tbest * 1e3f;
                 best.R = R;
                 best.tpb = 1 << (t - R);
+                best.tc = tc;
             }
         }
         std::lock_guard<std::mutex> lk(ctx->mu);
@@ -2233,7 +2274,52 @@ sv_status sv_sync_status(sv_stream_t stream) {
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "pending error");
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->err.ptr) {
+        // the word is written only by kernels on any stream: wait for them
+        SV_CUDA(cudaDeviceSynchronize());
+        int code = 0;
+        SV_CUDA(cudaMemcpy(&code, ctx->err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+        if (code != 0) {
+            SV_CUDA(cudaMemset(ctx->err.ptr, 0, sizeof(int)));
+            return fail(SV_ERR_TIMEOUT, "a bounded device-side wait gave up (code " +
+                                            std::to_string(code) +
+                                            "); results since the last check are invalid");
+        }
+    }
     return SV_OK;
+}
+
+sv_status sv_tuned_tile(const sv_problem *p, int32_t kind, int32_t *tile_bits,
+                        int32_t *reg_bits, int32_t *tensor_blocks, float *us) {
+    if (!p || !p->circuit || !p->observable) return fail(SV_ERR_ARG, "problem is NULL");
+    if (kind != 1 && kind != 2) return fail(SV_ERR_ARG, "kind must be 1 or 2");
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!wants_tiles(p->circuit->n_qubits, p->dtype, p->opts))
+        return fail(SV_ERR_ARG, "the problem's states stay on chip: no tile shape");
+    const Tuned *t =
+        find_tuned(ctx, p, kind == 1 ? kTileEnergyKey : kTileAdjointKey, p->n_instances);
+    if (!t) return fail(SV_ERR_ARG, "no tuned tile shape for this problem");
+    if (tile_bits) *tile_bits = t->R + __builtin_ctz((unsigned)t->tpb);
+    if (reg_bits) *reg_bits = t->R;
+    if (tensor_blocks) *tensor_blocks = t->tc;
+    if (us) *us = t->us;
+    return SV_OK;
+}
+
+sv_status sv_debug_wait_expiry(int32_t limit, sv_stream_t stream) {
+    if (limit < 1 || limit > (1 << 20)) return fail(SV_ERR_ARG, "limit must be 1..2^20");
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    int *err = device_err(ctx);
+    if (!err) return fail(SV_ERR_CUDA, "device error word");
+    cudaError_t e = launch_wait_expiry(err, (uint32_t)limit, (cudaStream_t)stream);
+    return e == cudaSuccess ? SV_OK : cuda_fail(e, "wait-expiry launch");
 }
 
 sv_status sv_shutdown(void) {

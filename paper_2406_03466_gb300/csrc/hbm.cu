@@ -920,6 +920,14 @@ thread_local bool t_capturing = false;
 std::mutex g_smem_mu;
 std::map<std::pair<int, const void *>, uint32_t> g_smem_limit;
 
+template <typename K> cudaError_t allow_smem(K kernel, uint32_t bytes);
+
+}  // namespace
+
+cudaError_t allow_smem_attr(const void *kernel, uint32_t bytes) { return allow_smem(kernel, bytes); }
+
+namespace {
+
 template <typename K> cudaError_t allow_smem(K kernel, uint32_t bytes) {
     int dev = 0;
     cudaGetDevice(&dev);

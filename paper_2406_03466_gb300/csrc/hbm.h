@@ -31,6 +31,23 @@ cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, con
                             int G, void *psi, void *lam, double *rho_g, int64_t max_blocks,
                             cudaStream_t st, const void *psi_src = nullptr,
                             bool write_psi = true);
+// Codes a kernel writes to the library's device error word when a bounded
+// device-side wait gives up (reported as SV_ERR_TIMEOUT by sv_sync_status).
+constexpr int SV_DEVERR_MMA_WAIT = 1;
+// Raises kernel's dynamic shared-memory limit to `bytes` (limits only grow;
+// no attribute change while a graph capture runs: fails instead).
+cudaError_t allow_smem_attr(const void *kernel, uint32_t bytes);
+// Forward pass P with every register stage applied as one dense 16 x 16
+// complex block on the tensor cores (tc.cu; complex64, R = 4, t = 11 or 12).
+// err: the device error word (bounded waits), or null.
+uint32_t tile_fwd_tc_smem(const TilePass &P);
+bool tile_fwd_tc_supported(int c128, const TilePass &P);
+cudaError_t launch_tile_fwd_tc(const TilePass &P, int n, int n_slots, const void *mats, int G,
+                               void *states, int64_t max_blocks, cudaStream_t st, int *err,
+                               const void *src = nullptr);
+// One block that waits `limit` times on an mbarrier nothing arrives on and
+// records SV_DEVERR_MMA_WAIT: the bounded-wait path, for tests.
+cudaError_t launch_wait_expiry(int *err, uint32_t limit, cudaStream_t st);
 // Tile passes of several problems in one launch (forward, or reverse with
 // rev): items sorted by block_begin, device memory; every item uses the same
 // tile shape (threads = 2^(t - R)).  smem: the largest over the items of
