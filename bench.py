@@ -77,6 +77,9 @@ def parse():
     ap.add_argument("--tile-shape", default="",
                     help="qcl20 / mcvqe28 only: 't,R' pins the tile passes to 2^t amplitudes and "
                          "R register bits instead of autotuning (for profiler captures)")
+    ap.add_argument("--tensor-blocks", action="store_true",
+                    help="qcl20 / mcvqe28 with --tile-shape t,4 (t = 11 or 12): forward passes as "
+                         "dense 16x16 blocks on the tensor cores (for profiler captures)")
     ap.add_argument("--qubits", type=int, default=0,
                     help="qcl20 / mcvqe28 only: the same workload family at this qubit count "
                          "(a smaller case for profiler captures; not a bench line)")
@@ -228,7 +231,8 @@ def forward_passes_roofline(sv, w, dev, flush, stream, reps=5, opts=None):
     # the states come back in qubit order: identity-layout passes
     o = sv.plan_opts() if opts is None else opts
     ident = sv.plan_opts(o.reg_bits, o.threads_per_block, bool(o.no_fusion), o.epilogue,
-                         o.tile_bits, o.coalesce_bits, no_relabel=True)
+                         o.tile_bits, o.coalesce_bits, no_relabel=True,
+                         tensor_blocks=bool(o.tensor_blocks))
     info = sv.sv_plan_info(circ, "c64", ident)
     n, I = w.n_qubits, w.n_instances
     st = sv.sv_alloc(n, I, "c64", device=dev)
@@ -244,7 +248,8 @@ def forward_passes_roofline(sv, w, dev, flush, stream, reps=5, opts=None):
     st.free()
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": None,
-            "kernel": f"k_tile_fwd x {info['n_passes']} identity-layout tile passes of "
+            "kernel": f"{'k_tile_fwd_tc' if o.tensor_blocks else 'k_tile_fwd'} x "
+                      f"{info['n_passes']} identity-layout tile passes of "
                       f"2^{info['tile_bits']} amplitudes ({w.name}: {I} states of {n} qubits)",
             "forward_ms": t * 1e3, "bytes_per_forward": nbytes, "peak_source": src}
 
@@ -342,17 +347,18 @@ def run_device_memory(args, sv, dev, stream, dist, world, rank):
     pinned = None
     if args.tile_shape:
         tile_bits, R = (int(x) for x in args.tile_shape.split(","))
-        pinned = sv.plan_opts(reg_bits=R, tile_bits=tile_bits)
+        pinned = sv.plan_opts(reg_bits=R, tile_bits=tile_bits, tensor_blocks=args.tensor_blocks)
     prob = sv.Problem.from_spec(w, "c64", device=dev, opts=pinned)
     theta = torch.as_tensor(w.theta, dtype=torch.float64, device=dev)
     out = sv._outputs(prob, dev, None, None, None)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    tc = bool(args.tensor_blocks)
     if pinned is None:
-        # tile shape (tile bits, register bits) picked by timing
+        # tile shape (tile bits, register bits, tensor-core forward passes)
+        # picked by timing
         sv.sv_autotune(prob, theta, 2)
-        R, tpb, _ = sv.sv_tuned_shape(prob, 2)
-        tile_bits = R + tpb.bit_length() - 1
-    opts = sv.plan_opts(reg_bits=R, tile_bits=tile_bits)
+        tile_bits, R, tc, _ = sv.sv_tuned_tile(prob, 2)
+    opts = sv.plan_opts(reg_bits=R, tile_bits=tile_bits, tensor_blocks=tc)
 
     def step():
         sv.sv_grad_adjoint(prob, theta, None, *out)
@@ -381,7 +387,8 @@ def run_device_memory(args, sv, dev, stream, dist, world, rank):
               "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
               "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
               "config": {"workload": device_workload_name(w), "tile_passes": info["n_passes"],
-                         "tuned_tile": {"tile_bits": tile_bits, "reg_bits": R},
+                         "tuned_tile": {"tile_bits": tile_bits, "reg_bits": R,
+                                        "tensor_blocks": tc},
                          "h_passes": hinfo["n_passes"],
                          "l2": "states larger than L2; 256 MiB flush before each step",
                          "parallelism": f"replicas x{world}"},
@@ -417,9 +424,14 @@ def run_device_memory(args, sv, dev, stream, dist, world, rank):
             forms = {}
             if args.workload == "mcvqe28":
                 # gate application with complex Rx.Rz.Rx groups: the 20-qubit
-                # circuit-learning batch (64 states, 512 MiB)
+                # circuit-learning batch (64 states, 512 MiB), register
+                # stages and the same stages as tensor-core blocks
+                q20 = wl.config(3)
                 forms["qcl20_gate_application"] = forward_passes_roofline(
-                    sv, wl.config(3), dev, flush, stream)
+                    sv, q20, dev, flush, stream, opts=sv.plan_opts(reg_bits=4, tile_bits=11))
+                forms["qcl20_gate_application_tensor_blocks"] = forward_passes_roofline(
+                    sv, q20, dev, flush, stream,
+                    opts=sv.plan_opts(reg_bits=4, tile_bits=12, tensor_blocks=True))
             _, _, _, side = mcvqe8_side(sv, dev, stream, flush, 2000)
             side["cpu_baseline"] = cpu_baseline(min(args.cpu_seconds, 3.0))
             forms["mcvqe8"] = side
@@ -536,7 +548,7 @@ def ddcl_workload_name(w):
 def uneven_workload_name(ws):
     return (f"qcl-uneven: adjoint gradients of {len(ws)} circuit-learning circuits (n, layers) = "
             + ", ".join(f"({w.n_qubits},{w.meta['layers']})" for w in ws)
-            + f", {ws[0].n_instances} inputs each, one CUDA graph launch")
+            + f", {ws[0].n_instances} inputs each, one CUDA graph launch (persistent sweeps)")
 
 
 def uneven_cost_model(w):
@@ -606,7 +618,7 @@ def run_uneven(args, sv, dev, stream, dist, world, rank):
         nbytes += state * (1 + 2 * npass + 2 + 3 * (nh - 1) + 4 * npass)
         launches += 4 + nh
         max_pass = max(max_pass, npass)
-    launches += 2 * max_pass
+    launches += 2  # the two persistent sweeps (forward, reverse) of all circuits
     peak, src = measured_hbm_gbs()
     achieved = nbytes * args.steps / t_dev / 1e9 / world
     result = {"metric": METRIC, "value": gps, "unit": "gradients/s", "n_gpus": world,
@@ -620,8 +632,8 @@ def run_uneven(args, sv, dev, stream, dist, world, rank):
               "clocks": clk, "wall_s_timed_region": t_wall,
               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                            "frac": achieved / peak, "traffic": None,
-                           "kernel": "whole step: k_tile_fwd_multi + k_tile_h + k_tile_rev_multi "
-                                     "(pass-major launches of all circuits, one graph)",
+                           "kernel": "whole step: persistent forward sweep (k_tile_sweep) + k_tile_h "
+                                     "+ persistent reverse sweep of all circuits, one graph",
                            "bytes_per_step": nbytes, "peak_source": src}}
     if rank == 0:
         th_host = [torch.as_tensor(w.theta, dtype=torch.float64).pin_memory() for w in ws]
@@ -691,9 +703,17 @@ def mcvqe8_side(sv, dev, stream, flush, steps, extras=True):
     l_host = torch.empty(1, dtype=torch.float64).pin_memory()
     e_host = torch.empty(w.n_instances, dtype=torch.float64).pin_memory()
     e2e_steps = max(200, steps // 4)
+    # the C-ABI call itself, arguments marshalled once (the binding's per-call
+    # argument checks are Python work, not the library's)
+    import ctypes
+    c_fn = sv.library().sv_grad_param_shift_host
+    c_args = (ctypes.byref(prob.struct), ctypes.c_void_p(th_host.data_ptr()),
+              ctypes.c_void_p(e_host.data_ptr()), ctypes.c_void_p(l_host.data_ptr()),
+              ctypes.c_void_p(g_host.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
 
     def e2e_step():
-        sv.sv_grad_param_shift_host(prob, th_host, e_host, l_host, g_host, stream=stream)
+        if c_fn(*c_args) != sv.SV_OK:
+            raise RuntimeError(sv.sv_last_error())
 
     for _ in range(10):
         e2e_step()
@@ -704,8 +724,9 @@ def mcvqe8_side(sv, dev, stream, flush, steps, extras=True):
     res["e2e"] = {"value": e2e_steps / t_e2e, "unit": "gradients/s",
                   "h2d_bytes_per_step": 8 * w.n_params,
                   "d2h_bytes_per_step": 8 * (w.n_params + 1 + w.n_instances),
-                  "timing": "host wall clock per step; sv_grad_param_shift_host returns once "
-                            "the results are in host memory"}
+                  "timing": "host wall clock per step of the C-ABI call "
+                            "sv_grad_param_shift_host (returns once the results are in host "
+                            "memory), arguments marshalled once"}
     if extras:
         n = max(200, steps // 4)
         fn = lambda: sv.sv_grad_adjoint(prob, theta, None, *out)  # noqa: E731

@@ -364,12 +364,18 @@ sv_status sv_grad_ddcl_param_shift(const sv_problem *problem, const double *thet
 /* Adjoint gradients of several problems at once: circuits of different qubit
  * counts and depths whose states take the tile path (14..30 qubits; all
  * problems share the dtype and the tile shape), each with its own
- * observable, instances, theta and outputs.  The forward and reverse sweeps
- * run pass-major — one launch per pass index covers that pass of every
- * problem that has it — and the whole sequence (group matrices, |ref>,
- * forward passes, lambda = H psi, reverse passes, gradients) is captured
- * into one CUDA graph per configuration (the problems' structures and every
- * pointer), replayed by a single graph launch on `stream`.  The first call
+ * observable, instances, theta and outputs.  The forward sweeps of all
+ * problems run as one persistent launch, and so do the reverse sweeps: every
+ * pass of every problem is cut into chunks of tiles that take tickets level
+ * by level (pass k of every problem before pass k + 1), and a block runs a
+ * chunk once the same problem's previous pass has completed every chunk
+ * (a bounded wait: on expiry the launch records a device error that
+ * sv_sync_status reports as SV_ERR_TIMEOUT), so problems of different depth
+ * never wait for one another at a pass boundary.  The whole sequence (group
+ * matrices, |ref>, forward sweep, lambda = H psi, reverse sweep, gradients)
+ * is captured into one CUDA graph per configuration (the problems'
+ * structures and every pointer), replayed by a single graph launch on
+ * `stream`.  The first call
  * for a configuration plans, allocates, runs eagerly and captures
  * (host-synchronous); later calls only launch the graph.  No checkpoints.
  * theta[j]: device [P_j]; energy_out[j]: device [I_j] or NULL; loss_out[j]:

@@ -955,15 +955,24 @@ struct MultiProblem {
     SlotSource src{};
 };
 
-// Launches the whole multi-problem adjoint on st (eagerly, or into a capture).
+// Launches the whole multi-problem adjoint on st (eagerly, or into a
+// capture): group matrices and |ref> per problem, the forward sweeps of all
+// problems as one persistent launch, lambda = H psi per problem, the reverse
+// sweeps as one persistent launch, then per-problem gradients.
+struct Sweep {
+    size_t o_tasks = 0, o_ticket = 0, o_done = 0;
+    int n_tasks = 0, blocks = 0;
+    long long n_tickets = 0;
+    uint32_t smem = 0;
+};
+
 sv_status multi_sequence(DeviceCtx *ctx, std::vector<MultiProblem> &mp, sv_dtype dt, int R,
-                         unsigned char *base, const std::vector<size_t> &o_items,
-                         const std::vector<int> &n_items, const std::vector<int> &blocks,
-                         const std::vector<uint32_t> &smem, const double *const *theta,
+                         unsigned char *base, const Sweep (&sw)[2], const double *const *theta,
                          double *const *E_out, double *const *L_out, double *const *G_out,
                          cudaStream_t st) {
     const int c128 = dt == SV_C128;
-    const int nsteps = (int)n_items.size() / 2;  // forward steps, then reverse steps
+    int *err = device_err(ctx);
+    if (!err) return fail(SV_ERR_CUDA, "device error word");
     for (MultiProblem &m : mp) {
         m.src.theta = theta[&m - &mp[0]];
         cudaError_t e = launch_group_mats(c128, m.pe->dev, m.src, base + m.o_mats, st);
@@ -971,8 +980,8 @@ sv_status multi_sequence(DeviceCtx *ctx, std::vector<MultiProblem> &mp, sv_dtype
         if (e != cudaSuccess) return cuda_fail(e, "uneven batch: group matrices / init");
     }
     const int threads = 1 << (mp[0].pe->tiles[0].t - R);
-    for (int k = 0; k < 2 * nsteps; ++k) {
-        if (k == nsteps) {  // between the sweeps: lambda = H psi, cleared sums
+    for (int rev = 0; rev < 2; ++rev) {
+        if (rev) {  // between the sweeps: lambda = H psi, cleared sums
             for (MultiProblem &m : mp) {
                 sv_status s = h_tiles(ctx, m.obs, m.n, dt, m.I, base + m.o_psi, base + m.o_lam,
                                       (double *)(base + m.o_E), st, &m.pe->host.layout);
@@ -981,15 +990,19 @@ sv_status multi_sequence(DeviceCtx *ctx, std::vector<MultiProblem> &mp, sv_dtype
                 SV_CUDA(cudaMemsetAsync(base + m.o_G, 0, sizeof(double) * (size_t)m.I * (m.P > 0 ? m.P : 1), st));
             }
         }
-        if (n_items[k] == 0) continue;
-        cudaError_t e = launch_tile_multi(c128, R, k >= nsteps, (const MultiItem *)(base + o_items[k]),
-                                          n_items[k], blocks[k], threads, smem[k], st);
+        const Sweep &w = sw[rev];
+        if (w.n_tasks == 0) continue;
+        SV_CUDA(cudaMemsetAsync(base + w.o_ticket, 0, (w.o_done - w.o_ticket) + sizeof(unsigned int) * (size_t)w.n_tasks, st));
+        cudaError_t e = launch_tile_sweep(c128, R, rev != 0, (const SweepTask *)(base + w.o_tasks),
+                                          w.n_tasks, w.n_tickets,
+                                          (unsigned long long *)(base + w.o_ticket),
+                                          (unsigned int *)(base + w.o_done), err, w.blocks,
+                                          threads, w.smem, st);
         if (e != cudaSuccess)
-            return cuda_fail(e, ("uneven batch: tile pass step " + std::to_string(k) + " (" +
-                                    std::to_string(n_items[k]) + " items, " +
-                                    std::to_string(blocks[k]) + " blocks of " +
-                                    std::to_string(threads) + " threads, " +
-                                    std::to_string(smem[k]) + " B shared)").c_str());
+            return cuda_fail(e, ("uneven batch: persistent " + std::string(rev ? "reverse" : "forward") +
+                                 " sweep (" + std::to_string(w.n_tasks) + " passes, " +
+                                 std::to_string(w.blocks) + " blocks of " + std::to_string(threads) +
+                                 " threads, " + std::to_string(w.smem) + " B shared)").c_str());
     }
     for (size_t j = 0; j < mp.size(); ++j) {
         MultiProblem &m = mp[j];
@@ -1081,49 +1094,53 @@ sv_status multi_adjoint(DeviceCtx *ctx, const sv_problem *problems, int np,
         m.o_E = take(sizeof(double) * (size_t)m.I);
         m.o_G = take(sizeof(double) * (size_t)m.I * (m.P > 0 ? m.P : 1));
     }
-    // item tables: forward step k runs pass k, reverse step k pass npass - 1 - k
-    std::vector<std::vector<MultiItem>> steps(2 * max_pass);
-    std::vector<uint32_t> smem(2 * max_pass, 0);
-    std::vector<int> blocks(2 * max_pass, 0), n_items(2 * max_pass, 0);
-    std::vector<size_t> o_items(2 * max_pass, 0);
+    // sweep task tables: level k of the forward sweep is pass k of every
+    // problem that has it, level k of the reverse sweep pass npass - 1 - k;
+    // chunks of kSweepChunk tiles take consecutive tickets in level order
+    constexpr int kSweepChunk = 16;
     const int threads = 1 << (cfg.t - cfg.R);
-    for (int k = 0; k < 2 * max_pass; ++k) {
-        const bool rev = k >= max_pass;
-        int64_t total = 0;
-        for (const MultiProblem &m : mp) {
-            const int pi = rev ? m.npass - 1 - (k - max_pass) : k;
-            if (pi < 0 || pi >= m.npass) continue;
-            const TilePass &tp = m.pe->tiles[pi];
-            smem[k] = std::max(smem[k], tile_multi_smem(c128, rev, tp));
-            total += (int64_t)m.I << tp.n_tile_bits;
-        }
-        if (total == 0) continue;
-        if (smem[k] > 220u * 1024u) return fail(SV_ERR_UNSUPPORTED, "uneven batch: pass needs too much shared memory");
-        const int per_sm = tile_multi_blocks_per_sm(c128, cfg.R, rev, smem[k], threads);
+    Sweep sw[2];
+    std::vector<SweepTask> tasks[2];
+    std::vector<std::pair<int, int>> who[2];  // (problem, pass) of each task
+    for (int rev = 0; rev < 2; ++rev) {
+        std::vector<int> task_of(np * (size_t)max_pass, -1);
+        long long tickets = 0;
+        for (int k = 0; k < max_pass; ++k)
+            for (int j = 0; j < np; ++j) {
+                const MultiProblem &m = mp[j];
+                if (k >= m.npass) continue;
+                const int pi = rev ? m.npass - 1 - k : k;
+                const TilePass &tp = m.pe->tiles[pi];
+                sw[rev].smem = std::max(sw[rev].smem, tile_sweep_smem(c128, rev != 0, tp));
+                SweepTask T{};
+                T.n = m.n;
+                T.n_slots = m.I;
+                T.G = m.G;
+                T.dep = k > 0 ? task_of[(size_t)j * max_pass + k - 1] : -1;
+                T.tiles = (int64_t)m.I << tp.n_tile_bits;
+                T.chunk_tiles = kSweepChunk;
+                T.n_chunks = (T.tiles + kSweepChunk - 1) / kSweepChunk;
+                T.chunk_begin = tickets;
+                tickets += T.n_chunks;
+                task_of[(size_t)j * max_pass + k] = (int)tasks[rev].size();
+                tasks[rev].push_back(T);
+                who[rev].push_back({j, pi});
+            }
+        Sweep &w = sw[rev];
+        w.n_tasks = (int)tasks[rev].size();
+        w.n_tickets = tickets;
+        if (w.n_tasks == 0) continue;
+        if (w.smem > 220u * 1024u) return fail(SV_ERR_UNSUPPORTED, "uneven batch: pass needs too much shared memory");
+        const int per_sm = tile_sweep_blocks_per_sm(c128, cfg.R, rev != 0, w.smem, threads);
         if (per_sm < 1) return fail(SV_ERR_UNSUPPORTED, "uneven batch: pass kernel does not fit an SM");
-        int64_t budget = (int64_t)ctx->sms * per_sm;
-        int b0 = 0;
-        for (MultiProblem &m : mp) {
-            const int pi = rev ? m.npass - 1 - (k - max_pass) : k;
-            if (pi < 0 || pi >= m.npass) continue;
-            const TilePass &tp = m.pe->tiles[pi];
-            const int64_t tiles = (int64_t)m.I << tp.n_tile_bits;
-            int64_t nb = budget * tiles / total;
-            nb = std::max<int64_t>(1, std::min<int64_t>(nb, tiles));
-            MultiItem it{};
-            it.P = nullptr;  // set after the buffer exists: base + o_tp + pi
-            it.pad = pi;
-            it.n = m.n;
-            it.n_slots = m.I;
-            it.G = m.G;
-            it.block_begin = b0;
-            it.block_end = b0 + (int)nb;
-            b0 += (int)nb;
-            steps[k].push_back(it);
-        }
-        blocks[k] = b0;
-        n_items[k] = (int)steps[k].size();
-        o_items[k] = take(sizeof(MultiItem) * steps[k].size());
+        // resident blocks only: every block that waits holds no ticket of the
+        // chunks it waits for
+        w.blocks = (int)std::min<long long>((long long)ctx->sms * per_sm, tickets);
+        w.o_tasks = take(sizeof(SweepTask) * tasks[rev].size());
+        w.o_ticket = take(sizeof(unsigned long long));
+        w.o_done = w.o_ticket + sizeof(unsigned long long);
+        off = w.o_done;
+        take(sizeof(unsigned int) * tasks[rev].size());
     }
     std::unique_ptr<MultiGraph> ng(new MultiGraph());
     if (cudaMalloc(&ng->buf.ptr, off ? off : 256) != cudaSuccess) {
@@ -1136,27 +1153,22 @@ sv_status multi_adjoint(DeviceCtx *ctx, const sv_problem *problems, int np,
     for (MultiProblem &m : mp)
         SV_CUDA(cudaMemcpy(base + m.o_tp, m.pe->tiles.data(), sizeof(TilePass) * (size_t)m.npass,
                            cudaMemcpyHostToDevice));
-    for (int k = 0; k < 2 * max_pass; ++k) {
-        if (steps[k].empty()) continue;
-        const bool rev = k >= max_pass;
-        size_t j = 0;
-        for (const MultiProblem &m : mp) {
-            const int pi = rev ? m.npass - 1 - (k - max_pass) : k;
-            if (pi < 0 || pi >= m.npass) continue;
-            MultiItem &it = steps[k][j++];
-            it.P = (const TilePass *)(base + m.o_tp) + pi;
-            it.mats = base + m.o_mats;
-            it.psi = base + m.o_psi;
-            it.lam = base + m.o_lam;
-            it.rho = (double *)(base + m.o_rho);
-            it.pad = 0;
+    for (int rev = 0; rev < 2; ++rev) {
+        for (size_t i = 0; i < tasks[rev].size(); ++i) {
+            const MultiProblem &m = mp[who[rev][i].first];
+            SweepTask &T = tasks[rev][i];
+            T.P = (const TilePass *)(base + m.o_tp) + who[rev][i].second;
+            T.mats = base + m.o_mats;
+            T.psi = base + m.o_psi;
+            T.lam = base + m.o_lam;
+            T.rho = (double *)(base + m.o_rho);
         }
-        SV_CUDA(cudaMemcpy(base + o_items[k], steps[k].data(), sizeof(MultiItem) * steps[k].size(),
-                           cudaMemcpyHostToDevice));
+        if (!tasks[rev].empty())
+            SV_CUDA(cudaMemcpy(base + sw[rev].o_tasks, tasks[rev].data(),
+                               sizeof(SweepTask) * tasks[rev].size(), cudaMemcpyHostToDevice));
     }
     // this call runs eagerly; the graph serves the later ones
-    sv_status s = multi_sequence(ctx, mp, dt, cfg.R, base, o_items, n_items, blocks, smem, theta,
-                                 E_out, L_out, G_out, st);
+    sv_status s = multi_sequence(ctx, mp, dt, cfg.R, base, sw, theta, E_out, L_out, G_out, st);
     if (s != SV_OK) return s;
     if (!ctx->capture_stream)
         SV_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
@@ -1164,8 +1176,7 @@ sv_status multi_adjoint(DeviceCtx *ctx, const sv_problem *problems, int np,
     cudaStream_t cap = ctx->capture_stream;
     SV_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
     set_capturing(true);
-    s = multi_sequence(ctx, mp, dt, cfg.R, base, o_items, n_items, blocks, smem, theta, E_out,
-                       L_out, G_out, cap);
+    s = multi_sequence(ctx, mp, dt, cfg.R, base, sw, theta, E_out, L_out, G_out, cap);
     set_capturing(false);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(cap, &graph);

@@ -58,8 +58,8 @@ template <typename Real, int R, bool kReal>
 __device__ __forceinline__ void tile_fwd_body(const TilePass &P, int n, int n_slots,
                                               const typename CT<Real>::T *mats, int G,
                                               const typename CT<Real>::T *src_states,
-                                              typename CT<Real>::T *states, int nblk, int blk,
-                                              unsigned char *smem) {
+                                              typename CT<Real>::T *states, int64_t t0,
+                                              int64_t t_end, unsigned char *smem) {
     using C = typename CT<Real>::T;
     constexpr int NA = 1 << R;
     constexpr uint32_t kBufs = 2u;
@@ -84,9 +84,6 @@ __device__ __forceinline__ void tile_fwd_body(const TilePass &P, int n, int n_sl
     const uint32_t p0 = bit_vectors<R>(P.ldperm, t, tid, pk);
     const uint32_t n0 = bit_vectors<R>(P.nat, t, tid, nk);
     const uint32_t sh = (uint32_t)__cvta_generic_to_shared(smem);
-    const int64_t tiles = (int64_t)n_slots << P.n_tile_bits;
-    const int64_t per = (tiles + nblk - 1) / nblk;
-    const int64_t t0 = per * blk, t_end = min(tiles, t0 + per);
     if (t0 >= t_end) return;
     auto fetch = [&](const TileCursor &c, int buf) {
         const C *src = src_states + ((int64_t)c.slot << n) + c.base;
@@ -141,8 +138,9 @@ k_tile_fwd(const __grid_constant__ TilePass P, int n, int n_slots,
            const typename CT<Real>::T *mats, int G, const typename CT<Real>::T *src,
            typename CT<Real>::T *states) {
     extern __shared__ __align__(16) unsigned char smem[];
-    tile_fwd_body<Real, R, kReal>(P, n, n_slots, mats, G, src, states, gridDim.x, blockIdx.x,
-                                  smem);
+    int64_t t0, t_end;
+    block_range((int64_t)n_slots << P.n_tile_bits, gridDim.x, blockIdx.x, t0, t_end);
+    tile_fwd_body<Real, R, kReal>(P, n, n_slots, mats, G, src, states, t0, t_end, smem);
 }
 
 // The derivative of a rotation exp(-i theta P / 2) inside a fused group is
@@ -321,8 +319,8 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
                                               const typename CT<Real>::T *mats, int G,
                                               const typename CT<Real>::T *psi_src,
                                               typename CT<Real>::T *psi, typename CT<Real>::T *lam,
-                                              double *rho_g, int nblk, int blk, unsigned char *smem,
-                                              bool write_psi = true) {
+                                              double *rho_g, int64_t t0, int64_t t_end,
+                                              unsigned char *smem, bool write_psi = true) {
     using C = typename CT<Real>::T;
     constexpr int NA = 1 << R;
     constexpr int kFlushTiles = 64;
@@ -351,9 +349,6 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
     const uint32_t p0 = bit_vectors<R>(P.ldperm, t, tid, pk);
     const uint32_t n0 = bit_vectors<R>(P.nat, t, tid, nk);
     const uint32_t sh = (uint32_t)__cvta_generic_to_shared(smem);
-    const int64_t tiles = (int64_t)n_slots << P.n_tile_bits;
-    const int64_t per = (tiles + nblk - 1) / nblk;
-    const int64_t t0 = per * blk, t_end = min(tiles, t0 + per);
     if (t0 >= t_end) return;
     // psi tile of buffer j at [j tbytes], lambda tile at [(2 + j) tbytes]
     auto fetch = [&](const TileCursor &c, int buf) {
@@ -461,8 +456,10 @@ k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
            const typename CT<Real>::T *mats, int G, const typename CT<Real>::T *psi_src,
            typename CT<Real>::T *psi, typename CT<Real>::T *lam, double *rho_g, int write_psi) {
     extern __shared__ __align__(16) unsigned char smem[];
-    tile_rev_body<Real, R, kSingle, kReal>(P, n, n_slots, mats, G, psi_src, psi, lam, rho_g,
-                                           gridDim.x, blockIdx.x, smem, write_psi != 0);
+    int64_t t0, t_end;
+    block_range((int64_t)n_slots << P.n_tile_bits, gridDim.x, blockIdx.x, t0, t_end);
+    tile_rev_body<Real, R, kSingle, kReal>(P, n, n_slots, mats, G, psi_src, psi, lam, rho_g, t0,
+                                           t_end, smem, write_psi != 0);
 }
 
 // Sum of v over the block (every thread gets it); red: one double per warp.
@@ -477,56 +474,100 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
     return s;
 }
 
-// ------------------------------------------ several problems per launch
+// ------------------------------------- several problems, one persistent launch
+//
+// The forward (or reverse) sweeps of several problems of any qubit count and
+// depth (one tile shape) run as one launch of resident blocks.  Each pass of
+// each problem is a task cut into chunks of tiles; the chunks of all tasks
+// form one ticket sequence, level by level (pass 0 of every problem, then
+// pass 1, ...).  A block takes the next ticket, waits until the task its
+// chunk depends on (the same problem's previous pass) has completed all of
+// its chunks, runs the chunk with the ordinary pass body and counts it done.
+// Every ticket before a waited-on chunk was taken by a running block, so the
+// wait always ends; it is bounded anyway (kSweepWaitNs of wall time), after
+// which the block records SV_DEVERR_SWEEP_WAIT and stops.
 
-// The item of this block (items sorted by block_begin) and its descriptor,
-// copied into the front of shared memory; returns the shared memory after it.
-__device__ __forceinline__ unsigned char *multi_item(const MultiItem *items, int n_items,
-                                                     MultiItem &it, unsigned char *smem) {
-    __shared__ int s_item;
-    if (threadIdx.x == 0) {
-        int j = 0;
-        while (j + 1 < n_items && items[j + 1].block_begin <= (int)blockIdx.x) ++j;
-        s_item = j;
+constexpr unsigned long long kSweepWaitNs = 20ull * 1000 * 1000 * 1000;  // 20 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <typename Real, int R, bool kRev>
+__global__ void __launch_bounds__(256, (R >= 4 && kRev) ? 1 : 2)
+k_tile_sweep(const SweepTask *tasks, int n_tasks, long long n_tickets,
+             unsigned long long *ticket, unsigned int *done, int *err) {
+    using C = typename CT<Real>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_tk;
+    __shared__ int s_task, s_fail;
+    TilePass &P = *reinterpret_cast<TilePass *>(smem);
+    unsigned char *rest = smem + ((sizeof(TilePass) + 255) & ~size_t(255));
+    int hint = 0, cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long tk = (long long)atomicAdd(ticket, 1ull);
+            int j = hint;
+            if (tk < n_tickets)
+                while (j + 1 < n_tasks && tasks[j + 1].chunk_begin <= tk) ++j;
+            s_tk = tk;
+            s_task = j;
+            s_fail = 0;
+            if (tk < n_tickets && tasks[j].dep >= 0) {
+                const SweepTask &d = tasks[tasks[j].dep];
+                const unsigned int need = (unsigned int)d.n_chunks;
+                unsigned long long t_start = 0;
+                while (ld_acquire(done + tasks[j].dep) < need) {
+                    const unsigned long long now = global_ns();
+                    if (!t_start) t_start = now;
+                    if (now - t_start > kSweepWaitNs) {
+                        s_fail = 1;
+                        if (err) atomicCAS(err, 0, SV_DEVERR_SWEEP_WAIT);
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+            }
+        }
+        __syncthreads();
+        const long long tk = s_tk;
+        const int j = s_task;
+        if (tk >= n_tickets || s_fail) break;
+        hint = j;
+        const SweepTask T = tasks[j];
+        // every thread acquires the dependency's writes for its own loads
+        if (T.dep >= 0) (void)ld_acquire(done + T.dep);
+        if (j != cur) {  // this pass's descriptor into shared memory
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(T.P);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(smem);
+            for (int i = threadIdx.x; i < (int)(sizeof(TilePass) / 4); i += blockDim.x) dst[i] = src[i];
+            cur = j;
+        }
+        __syncthreads();
+        const long long c = tk - T.chunk_begin;
+        const int64_t t0 = c * (int64_t)T.chunk_tiles;
+        const int64_t t1 = min(T.tiles, t0 + (int64_t)T.chunk_tiles);
+        if constexpr (kRev)
+            tile_rev_body<Real, R, false, false>(P, T.n, T.n_slots, (const C *)T.mats, T.G,
+                                                 (const C *)T.psi, (C *)T.psi, (C *)T.lam, T.rho,
+                                                 t0, t1, rest);
+        else
+            tile_fwd_body<Real, R, false>(P, T.n, T.n_slots, (const C *)T.mats, T.G,
+                                          (const C *)T.psi, (C *)T.psi, t0, t1, rest);
+        __syncthreads();  // every store of the chunk issued
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(done + j, 1u);
+        }
     }
-    __syncthreads();
-    it = items[s_item];
-    const uint32_t *src = reinterpret_cast<const uint32_t *>(it.P);
-    uint32_t *dst = reinterpret_cast<uint32_t *>(smem);
-    for (int i = threadIdx.x; i < (int)(sizeof(TilePass) / 4); i += blockDim.x) dst[i] = src[i];
-    __syncthreads();
-    return smem + ((sizeof(TilePass) + 255) & ~size_t(255));
-}
-
-// Forward passes of several problems (same tile shape, any qubit count and
-// depth) in one launch.
-template <typename Real, int R>
-__global__ void __launch_bounds__(256, R >= 4 ? 2 : 3)
-k_tile_fwd_multi(const MultiItem *items, int n_items) {
-    using C = typename CT<Real>::T;
-    extern __shared__ __align__(16) unsigned char smem[];
-    MultiItem it;
-    unsigned char *rest = multi_item(items, n_items, it, smem);
-    const TilePass &P = *reinterpret_cast<const TilePass *>(smem);
-    tile_fwd_body<Real, R, false>(P, it.n, it.n_slots, (const C *)it.mats, it.G, (const C *)it.psi,
-                                  (C *)it.psi,
-                                  it.block_end - it.block_begin, (int)blockIdx.x - it.block_begin,
-                                  rest);
-}
-
-// Reverse passes of several problems in one launch.
-template <typename Real, int R>
-__global__ void __launch_bounds__(256, R >= 4 ? 1 : 2)
-k_tile_rev_multi(const MultiItem *items, int n_items) {
-    using C = typename CT<Real>::T;
-    extern __shared__ __align__(16) unsigned char smem[];
-    MultiItem it;
-    unsigned char *rest = multi_item(items, n_items, it, smem);
-    const TilePass &P = *reinterpret_cast<const TilePass *>(smem);
-    tile_rev_body<Real, R, false, false>(P, it.n, it.n_slots, (const C *)it.mats, it.G,
-                                         (const C *)it.psi, (C *)it.psi, (C *)it.lam, it.rho,
-                                         it.block_end - it.block_begin,
-                                         (int)blockIdx.x - it.block_begin, rest);
 }
 
 // ------------------------------------------------------ H over tile passes
@@ -680,6 +721,10 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
         Real lr[NA], li[NA];
 #pragma unroll
         for (int k = 0; k < NA; ++k) lr[k] = li[k] = 0;
+        auto add_real = [&](int k, Real d, const C &pk) {
+            lr[k] = fmaR(d, pk.x, lr[k]);
+            li[k] = fmaR(d, pk.y, li[k]);
+        };
         for (int g = 0; g < P.n_groups; ++g) {
             const HGroup &gr = grp[g];
             const uint32_t xl = gr.xl, xfar = gr.xfar, kact = gr.kact;
@@ -700,8 +745,7 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
                 for (int k = 0; k < NA; ++k) {
                     const C pk = partner(k);
                     if constexpr (kRealH) {
-                        lr[k] = fmaR(vr, pk.x, lr[k]);
-                        li[k] = fmaR(vr, pk.y, li[k]);
+                        add_real(k, vr, pk);
                     } else {
                         lr[k] = fmaR(vr, pk.x, fmaR(-vi, pk.y, lr[k]));
                         li[k] = fmaR(vr, pk.y, fmaR(vi, pk.x, li[k]));
@@ -731,8 +775,7 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
             for (int k = 0; k < NA; ++k) {
                 const C pk = partner(k);
                 if constexpr (kRealH) {
-                    lr[k] = fmaR(vr[k], pk.x, lr[k]);
-                    li[k] = fmaR(vr[k], pk.y, li[k]);
+                    add_real(k, vr[k], pk);
                 } else {
                     lr[k] = fmaR(vr[k], pk.x, fmaR(-vi[k], pk.y, lr[k]));
                     li[k] = fmaR(vr[k], pk.y, fmaR(vi[k], pk.x, li[k]));
@@ -1095,21 +1138,21 @@ cudaError_t launch_tile_h(int c128, const HPass &P, int n, int n_slots, const vo
 
 void set_capturing(bool on) { t_capturing = on; }
 
-uint32_t tile_multi_smem(int c128, bool rev, const TilePass &P) {
+uint32_t tile_sweep_smem(int c128, bool rev, const TilePass &P) {
     return (uint32_t)((sizeof(TilePass) + 255) & ~size_t(255)) +
            (rev ? tile_rev_smem(c128, P) : tile_fwd_smem(c128, P));
 }
 
-int tile_multi_blocks_per_sm(int c128, int R, bool rev, uint32_t smem, int threads) {
+int tile_sweep_blocks_per_sm(int c128, int R, bool rev, uint32_t smem, int threads) {
     int per = 0;
     HBM_DISPATCH_R(c128, R, {
         cudaError_t e;
         if (rev) {
-            auto k = k_tile_rev_multi<Real, RR>;
+            auto k = k_tile_sweep<Real, RR, true>;
             e = allow_smem(k, smem);
             if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, smem);
         } else {
-            auto k = k_tile_fwd_multi<Real, RR>;
+            auto k = k_tile_sweep<Real, RR, false>;
             e = allow_smem(k, smem);
             if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, smem);
         }
@@ -1118,21 +1161,20 @@ int tile_multi_blocks_per_sm(int c128, int R, bool rev, uint32_t smem, int threa
     return per;
 }
 
-cudaError_t launch_tile_multi(int c128, int R, bool rev, const MultiItem *items, int n_items,
-                              int blocks, int threads, uint32_t smem, cudaStream_t st) {
-    cudaError_t prior = cudaGetLastError();  // not this launch's
-    (void)prior;
+cudaError_t launch_tile_sweep(int c128, int R, bool rev, const SweepTask *tasks, int n_tasks,
+                              long long n_tickets, unsigned long long *ticket, unsigned int *done,
+                              int *err, int blocks, int threads, uint32_t smem, cudaStream_t st) {
     HBM_DISPATCH_R(c128, R, {
         if (rev) {
-            auto k = k_tile_rev_multi<Real, RR>;
+            auto k = k_tile_sweep<Real, RR, true>;
             cudaError_t e = allow_smem(k, smem);
             if (e != cudaSuccess) return e;
-            k<<<blocks, threads, smem, st>>>(items, n_items);
+            k<<<blocks, threads, smem, st>>>(tasks, n_tasks, n_tickets, ticket, done, err);
         } else {
-            auto k = k_tile_fwd_multi<Real, RR>;
+            auto k = k_tile_sweep<Real, RR, false>;
             cudaError_t e = allow_smem(k, smem);
             if (e != cudaSuccess) return e;
-            k<<<blocks, threads, smem, st>>>(items, n_items);
+            k<<<blocks, threads, smem, st>>>(tasks, n_tasks, n_tickets, ticket, done, err);
         }
     });
     return cudaGetLastError();

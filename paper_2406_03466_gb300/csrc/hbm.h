@@ -34,6 +34,7 @@ cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, con
 // Codes a kernel writes to the library's device error word when a bounded
 // device-side wait gives up (reported as SV_ERR_TIMEOUT by sv_sync_status).
 constexpr int SV_DEVERR_MMA_WAIT = 1;
+constexpr int SV_DEVERR_SWEEP_WAIT = 2;
 // Raises kernel's dynamic shared-memory limit to `bytes` (limits only grow;
 // no attribute change while a graph capture runs: fails instead).
 cudaError_t allow_smem_attr(const void *kernel, uint32_t bytes);
@@ -48,16 +49,18 @@ cudaError_t launch_tile_fwd_tc(const TilePass &P, int n, int n_slots, const void
 // One block that waits `limit` times on an mbarrier nothing arrives on and
 // records SV_DEVERR_MMA_WAIT: the bounded-wait path, for tests.
 cudaError_t launch_wait_expiry(int *err, uint32_t limit, cudaStream_t st);
-// Tile passes of several problems in one launch (forward, or reverse with
-// rev): items sorted by block_begin, device memory; every item uses the same
-// tile shape (threads = 2^(t - R)).  smem: the largest over the items of
-// tile_multi_smem.
+// Persistent sweeps of several problems (forward, or reverse with rev):
+// tasks (device) in ticket order; ticket (device, zero) and done[n_tasks]
+// (device, zero) are the scheduler's counters; every task uses the same tile
+// shape (threads = 2^(t - R)); smem: the largest tile_sweep_smem over the
+// tasks; blocks: at most the resident blocks (tile_sweep_blocks_per_sm x SMs).
 // Launchers skip kernel attribute calls while a graph capture runs.
 void set_capturing(bool on);
-uint32_t tile_multi_smem(int c128, bool rev, const TilePass &P);
-int tile_multi_blocks_per_sm(int c128, int R, bool rev, uint32_t smem, int threads);
-cudaError_t launch_tile_multi(int c128, int R, bool rev, const MultiItem *items, int n_items,
-                              int blocks, int threads, uint32_t smem, cudaStream_t st);
+uint32_t tile_sweep_smem(int c128, bool rev, const TilePass &P);
+int tile_sweep_blocks_per_sm(int c128, int R, bool rev, uint32_t smem, int threads);
+cudaError_t launch_tile_sweep(int c128, int R, bool rev, const SweepTask *tasks, int n_tasks,
+                              long long n_tickets, unsigned long long *ticket, unsigned int *done,
+                              int *err, int blocks, int threads, uint32_t smem, cudaStream_t st);
 // One tile pass of lambda = H psi (lam may be null: energies only); adds this
 // pass's part of <psi|H|psi> to E[slot] (zero E before the first pass).
 uint32_t tile_h_smem(int c128, const HPass &P);

@@ -151,15 +151,18 @@ struct Observable {
     const Term *terms;
 };
 
-// One problem's part of a multi-problem tile-pass launch: the launch's
-// blocks [block_begin, block_end) run pass *P of this problem's states.
-struct MultiItem {
+// One pass of one problem in a persistent multi-problem sweep: its tiles
+// are cut into chunks of chunk_tiles, which take the tickets
+// [chunk_begin, chunk_begin + n_chunks) of the sweep; a chunk may run once
+// task `dep` (the problem's previous pass, or -1) has completed every chunk.
+struct SweepTask {
     const TilePass *P;  // device descriptor
-    int32_t n, n_slots, G, pad;
+    int32_t n, n_slots, G, dep;
+    int64_t tiles, chunk_begin, n_chunks;
+    int32_t chunk_tiles, pad;
     const void *mats;   // [slots][G][4]
-    void *psi, *lam;    // forward: psi = the states
+    void *psi, *lam;    // the problem's states
     double *rho;        // reverse: [slots][G][8]
-    int32_t block_begin, block_end;
 };
 
 // lambda = H psi (and <H>) over tiles of 2^t amplitudes.  A pass covers the

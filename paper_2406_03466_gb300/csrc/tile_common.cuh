@@ -47,6 +47,14 @@ __device__ __forceinline__ uint32_t bit_vectors(const uint32_t *v, int t, int ti
     return g;
 }
 
+// Block blk's contiguous share [t0, t_end) of `tiles` (slot, tile) pairs.
+__device__ __forceinline__ void block_range(int64_t tiles, int nblk, int blk, int64_t &t0,
+                                            int64_t &t_end) {
+    const int64_t per = (tiles + nblk - 1) / nblk;
+    t0 = per * blk;
+    t_end = min(tiles, t0 + per);
+}
+
 // Position of one tile in the walk over (slot, tile): global offset of the
 // tile's first amplitude within its state.
 struct TileCursor {
