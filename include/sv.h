@@ -237,7 +237,11 @@ sv_status sv_grad_param_shift(const sv_problem *problem, const double *theta,
 /* sv_grad_param_shift with host buffers, synchronous: copies theta (host
  * [P], any host memory) through library-owned pinned staging to the device,
  * runs the same fused launch, copies loss, gradient and instance energies
- * back in one transfer and waits for `stream` before returning.
+ * back in one transfer and waits for `stream` before returning.  For states
+ * on chip the three steps are recorded once as a CUDA graph (keyed by every
+ * pointer and launch argument they use) and later calls launch that graph;
+ * the first call records it after running the steps, so make it outside any
+ * stream capture of the caller's.
  * energy_host: [n_instances] or NULL; loss_host: [1] or NULL; grad_host: [P].
  * Uses (2P + 1 + I) doubles of pinned host and device staging per stream
  * besides the scratch of sv_grad_param_shift. */

@@ -129,6 +129,17 @@ struct DeviceCtx {
     std::unordered_map<cudaStream_t, std::unique_ptr<struct HostIO>> hostio;
     // Device error word of the kernels with bounded waits (0 = none gave up).
     DeviceBuf err;
+    // Host-buffer parameter-shift calls captured as graphs (theta in, the
+    // energy launch and its dependent assembly, results out), by launch key.
+    std::unordered_map<uint64_t, std::unique_ptr<struct HostGraph>> host_graphs;
+};
+
+struct HostGraph {
+    cudaGraphExec_t exec = nullptr;
+    bool failed = false;  // capture or instantiation refused: run eagerly
+    ~HostGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
 };
 
 struct HostIO {
@@ -1425,9 +1436,21 @@ namespace {
 // Launches the batched energies of every parameter-shift slot into E[B]
 // (and, with `fc`, the gradient assembly in the same launch).
 // Energies of parameter-shift slots [slot_begin, slot_begin + B) into E[B].
+// The arguments of one on-chip energy launch (recorded instead of launched).
+struct EnergyLaunch {
+    OnchipShape sh;
+    Program prog;
+    Observable obs;
+    SlotSource src;
+    BlockConst bc;
+    const void *dtab;
+    double *E;
+    int32_t c128, valid;
+};
+
 sv_status ps_energies_locked(DeviceCtx *ctx, const sv_problem *p, const double *theta, double *E,
                              int B, cudaStream_t st, const FusedCombine *fc = nullptr,
-                             int slot_begin = 0) {
+                             int slot_begin = 0, EnergyLaunch *rec = nullptr) {
     const int I = p->n_instances;
     if (wants_tiles(p->circuit->n_qubits, p->dtype, p->opts)) {
         sv_status s = tiles_energies(ctx, p, theta, SLOTS_PARAM_SHIFT, B, E, st, slot_begin);
@@ -1459,6 +1482,19 @@ sv_status ps_energies_locked(DeviceCtx *ctx, const sv_problem *p, const double *
     src.inputs = p->inputs;
     src.input_stride = p->input_stride;
     src.slot_base = slot_begin;
+    if (rec) {
+        std::memset(rec, 0, sizeof(*rec));
+        rec->sh = sh;
+        rec->prog = plan->dev;
+        rec->obs = obs->dev;
+        rec->src = src;
+        rec->bc = bc;
+        rec->dtab = dtab;
+        rec->E = E;
+        rec->c128 = p->dtype == SV_C128;
+        rec->valid = 1;
+        return SV_OK;
+    }
     cudaError_t e = launch_onchip_energy(p->dtype == SV_C128, sh, plan->dev, obs->dev, src, E, st,
                                          dtab, fc, &bc);
     if (e != cudaSuccess) return cuda_fail(e, "param-shift energy launch");
@@ -1579,10 +1615,6 @@ sv_status sv_grad_param_shift_host(const sv_problem *p, const double *theta_host
     s = get_scratch(ctx, st, sizeof(double) * ((size_t)B + I), &scr);
     if (s != SV_OK) return s;
     double *h = (double *)io->host, *d = (double *)io->dev;
-    if (P > 0) {
-        std::memcpy(h, theta_host, sizeof(double) * P);
-        SV_CUDA(cudaMemcpyAsync(d, h, sizeof(double) * P, cudaMemcpyHostToDevice, st));
-    }
     double *E = (double *)scr;
     FusedCombine fc{};
     fc.I = I;
@@ -1592,9 +1624,64 @@ sv_status sv_grad_param_shift_host(const sv_problem *p, const double *theta_host
     fc.loss_out = d + nP;
     fc.grad_out = d + nP + 1;
     fc.energy_out = d + 2 * nP + 1;
-    s = ps_energies_locked(ctx, p, d, E, B, st, &fc);
-    if (s != SV_OK) return s;
-    SV_CUDA(cudaMemcpyAsync(h + nP, d + nP, sizeof(double) * n_out, cudaMemcpyDeviceToHost, st));
+    if (P > 0) std::memcpy(h, theta_host, sizeof(double) * P);
+    auto copy_in = [&](cudaStream_t q) {
+        return P > 0 ? cudaMemcpyAsync(d, h, sizeof(double) * P, cudaMemcpyHostToDevice, q)
+                     : cudaSuccess;
+    };
+    auto copy_out = [&](cudaStream_t q) {
+        return cudaMemcpyAsync(h + nP, d + nP, sizeof(double) * n_out, cudaMemcpyDeviceToHost, q);
+    };
+    EnergyLaunch L;
+    L.valid = 0;
+    if (!wants_tiles(p->circuit->n_qubits, p->dtype, p->opts)) {
+        s = ps_energies_locked(ctx, p, d, E, B, st, &fc, 0, &L);
+        if (s != SV_OK) return s;
+    }
+    if (!L.valid) {  // states in device memory: the passes launch as they plan
+        SV_CUDA(copy_in(st));
+        s = ps_energies_locked(ctx, p, d, E, B, st, &fc);
+        if (s != SV_OK) return s;
+        SV_CUDA(copy_out(st));
+    } else {
+        // the whole call as one graph, keyed by everything its nodes read
+        uint64_t key = hash_bytes(&L, sizeof(L));
+        key = mix64(key, hash_bytes(&fc, sizeof(fc)));
+        key = mix64(key, mix64((uint64_t)(uintptr_t)h, (uint64_t)(uintptr_t)d));
+        key = mix64(key, mix64((uint64_t)P, (uint64_t)n_out));
+        std::unique_ptr<HostGraph> &g = ctx->host_graphs[key];
+        if (g && g->exec) {
+            SV_CUDA(cudaGraphLaunch(g->exec, st));
+        } else {
+            SV_CUDA(copy_in(st));
+            cudaError_t e = launch_onchip_energy(L.c128, L.sh, L.prog, L.obs, L.src, L.E, st, L.dtab,
+                                                 &fc, &L.bc);
+            if (e != cudaSuccess) return cuda_fail(e, "param-shift energy launch");
+            SV_CUDA(copy_out(st));
+            if (!g) {  // record the same three steps once for later calls
+                g.reset(new HostGraph());
+                if (!ctx->capture_stream)
+                    SV_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+                cudaStream_t cap = ctx->capture_stream;
+                cudaGraph_t graph = nullptr;
+                bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                if (ok) {
+                    ok = copy_in(cap) == cudaSuccess &&
+                         launch_onchip_energy(L.c128, L.sh, L.prog, L.obs, L.src, L.E, cap, L.dtab,
+                                              &fc, &L.bc) == cudaSuccess &&
+                         copy_out(cap) == cudaSuccess;
+                    ok = cudaStreamEndCapture(cap, &graph) == cudaSuccess && ok && graph;
+                }
+                if (ok) ok = cudaGraphInstantiate(&g->exec, graph, 0) == cudaSuccess;
+                if (graph) cudaGraphDestroy(graph);
+                if (!ok) {
+                    g->exec = nullptr;
+                    g->failed = true;
+                    cudaGetLastError();  // a refused capture leaves no pending error behind
+                }
+            }
+        }
+    }
     SV_CUDA(cudaStreamSynchronize(st));
     if (loss_host) *loss_host = h[nP];
     if (P > 0) std::memcpy(grad_host, h + nP + 1, sizeof(double) * P);
