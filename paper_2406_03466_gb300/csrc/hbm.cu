@@ -101,6 +101,9 @@ __device__ __forceinline__ void tile_fwd_body(const TilePass &P, int n, int n_sl
         if (cur.slot != mslot) {  // the previous tile's stages are past their last barrier
             for (int x = tid; x < 4 * P.n_ops; x += T)
                 sm[x] = mats[((size_t)cur.slot * G + P.grp[x >> 2]) * 4 + (x & 3)];
+            __syncthreads();
+            for (int u = tid; u < P.n_ops; u += T)
+                if ((P.real_mask >> u) & 1ull) stage_shears(sm + 4 * u);
             mslot = cur.slot;
         }
         cp_async_wait_all();
@@ -261,8 +264,13 @@ __device__ __forceinline__ void tile_ops_rev(uint32_t ops, uint32_t modes, const
             C m0, m1, m2, m3;
             load_mat(sm, (int)(ob & 63u) - 1, m0, m1, m2, m3);
             if (kReal || (ob & 64u)) {
-                u1r_bit<C, Real, R, I>(a, m0.x, m1.x, m2.x, m3.x);
-                u1r_bit<C, Real, R, I>(al, m0.x, m1.x, m2.x, m3.x);
+                if (m2.y != 0) {
+                    rot3_bit<C, Real, R, I>(a, m0.y, m1.y);
+                    rot3_bit<C, Real, R, I>(al, m0.y, m1.y);
+                } else {
+                    u1r_bit<C, Real, R, I>(a, m0.x, m1.x, m2.x, m3.x);
+                    u1r_bit<C, Real, R, I>(al, m0.x, m1.x, m2.x, m3.x);
+                }
             } else {
                 u1_bit<C, R, I>(a, m0, m1, m2, m3);
                 u1_bit<C, R, I>(al, m0, m1, m2, m3);
@@ -381,6 +389,9 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
                 d.y = -d.y;
                 sm[x] = d;
             }
+            __syncthreads();
+            for (int u = tid; u < P.n_ops; u += T)
+                if ((P.real_mask >> u) & 1ull) stage_shears(sm + 4 * u);
             mslot = cur.slot;
         }
         cp_async_wait_all();

@@ -5,6 +5,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "engine.cuh"
 
 namespace svk {
@@ -142,6 +144,55 @@ __device__ __forceinline__ void load_mat(const double2 *sm, int u, double2 &m0, 
     m3 = sm[4 * u + 3];
 }
 
+// A real rotation [[c, -s], [s, c]] with c > 0 (|angle| < pi/2) as three
+// shears: x += alpha y; y += beta x; x += alpha y, with alpha = -s / (1 + c)
+// = -tan(angle / 2) and beta = s (both in [-1, 1]): three fused
+// multiply-adds per amplitude pair and component instead of four.
+template <typename C, typename Real, int R, int I>
+__device__ __forceinline__ void rot3_bit(C (&a)[1 << R], const Real alpha, const Real beta) {
+    if constexpr (std::is_same<C, float2>::value) {
+        const uint64_t pa = f2pack(alpha, alpha), pb = f2pack(beta, beta);
+#pragma unroll
+        for (int r = 0; r < (1 << R); ++r) {
+            if (r & (1 << I)) continue;
+            uint64_t x = f2of(a[r]), y = f2of(a[r | (1 << I)]);
+            x = f2fma(pa, y, x);
+            y = f2fma(pb, x, y);
+            x = f2fma(pa, y, x);
+            a[r] = f2unpack(x);
+            a[r | (1 << I)] = f2unpack(y);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < (1 << R); ++r) {
+            if (r & (1 << I)) continue;
+            C x = a[r], y = a[r | (1 << I)];
+            x.x = fmaR(alpha, y.x, x.x);
+            x.y = fmaR(alpha, y.y, x.y);
+            y.x = fmaR(beta, x.x, y.x);
+            y.y = fmaR(beta, x.y, y.y);
+            x.x = fmaR(alpha, y.x, x.x);
+            x.y = fmaR(alpha, y.y, x.y);
+            a[r] = x;
+            a[r | (1 << I)] = y;
+        }
+    }
+}
+
+// The imaginary parts of a staged real matrix are unused: for a real
+// rotation with c > 0 they carry the shear form (m0.y = alpha, m1.y = beta,
+// m2.y = 1); otherwise m2.y = 0.  Called once per staged matrix.
+template <typename C>
+__device__ __forceinline__ void stage_shears(C *m) {
+    using Real = decltype(m[0].x);
+    const Real c = m[0].x, s = m[2].x;
+    const bool rot = m[3].x == c && m[1].x == -s && c > (Real)0;
+    m[0].y = rot ? -s / ((Real)1 + c) : (Real)0;
+    m[1].y = rot ? s : (Real)0;
+    m[2].y = rot ? (Real)1 : (Real)0;
+    m[3].y = (Real)0;
+}
+
 // The group ops of one stage (op bytes `ops`), register bits I..R-1 in order.
 // kReal: every op of the pass has a real matrix (no complex path compiled).
 template <typename C, int R, int I, bool kReal>
@@ -151,10 +202,14 @@ __device__ __forceinline__ void tile_ops_fwd(uint32_t ops, const C *sm, C (&a)[1
         if (ob) {
             C m0, m1, m2, m3;
             load_mat(sm, (int)(ob & 63u) - 1, m0, m1, m2, m3);
-            if (kReal || (ob & 64u))
-                u1r_bit<C, decltype(m0.x), R, I>(a, m0.x, m1.x, m2.x, m3.x);
-            else
+            if (kReal || (ob & 64u)) {
+                if (m2.y != 0)
+                    rot3_bit<C, decltype(m0.x), R, I>(a, m0.y, m1.y);
+                else
+                    u1r_bit<C, decltype(m0.x), R, I>(a, m0.x, m1.x, m2.x, m3.x);
+            } else {
                 u1_bit<C, R, I>(a, m0, m1, m2, m3);
+            }
         }
         tile_ops_fwd<C, R, I + 1, kReal>(ops, sm, a);
     }
