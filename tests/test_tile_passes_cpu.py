@@ -691,3 +691,24 @@ def test_relabeled_sweep_with_moved_hamiltonian(name):
     L, E_o, g_o = oracle.grad_param_shift(w)
     np.testing.assert_allclose(E, E_o, atol=1e-12)
     np.testing.assert_allclose(grad, g_o, atol=1e-11)
+
+
+def test_three_shears_equal_the_rotation():
+    """The tile passes apply a real rotation [[c, -s], [s, c]] with c > 0 as
+    x += a y; y += b x; x += a y with a = -s / (1 + c), b = s: the product of
+    the three shears is the rotation, for every angle with |angle| < pi/2,
+    and the staged coefficients stay in [-1, 1]."""
+    rng = np.random.default_rng(3)
+    for phi in np.concatenate([rng.uniform(-np.pi / 2, np.pi / 2, 200), [0.0, 1e-8, -1.5707]]):
+        c, s = np.cos(phi), np.sin(phi)
+        a, b = -s / (1 + c), s
+        assert abs(a) <= 1 and abs(b) <= 1
+        shear_x = np.array([[1.0, a], [0.0, 1.0]])
+        shear_y = np.array([[1.0, 0.0], [b, 1.0]])
+        np.testing.assert_allclose(shear_x @ shear_y @ shear_x, [[c, -s], [s, c]], atol=1e-14)
+        # applied in place to a complex pair, in the kernel's order
+        x, y = rng.normal(size=2) + 1j * rng.normal(size=2)
+        x1 = x + a * y
+        y1 = y + b * x1
+        x1 = x1 + a * y1
+        np.testing.assert_allclose([x1, y1], [c * x - s * y, s * x + c * y], atol=1e-14)
