@@ -1649,6 +1649,12 @@ sv_status sv_grad_param_shift_host(const sv_problem *p, const double *theta_host
         key = mix64(key, hash_bytes(&fc, sizeof(fc)));
         key = mix64(key, mix64((uint64_t)(uintptr_t)h, (uint64_t)(uintptr_t)d));
         key = mix64(key, mix64((uint64_t)P, (uint64_t)n_out));
+        // a bounded cache: a caller cycling through many problems (or staging
+        // buffers) re-records instead of growing it without limit
+        if (ctx->host_graphs.size() >= 64 && !ctx->host_graphs.count(key)) {
+            SV_CUDA(cudaDeviceSynchronize());  // no recorded call still running
+            ctx->host_graphs.clear();
+        }
         std::unique_ptr<HostGraph> &g = ctx->host_graphs[key];
         if (g && g->exec) {
             SV_CUDA(cudaGraphLaunch(g->exec, st));

@@ -336,7 +336,7 @@ k_tile_fwd_tc(const __grid_constant__ TilePass P, int n, int n_slots, const floa
                 bool ok = mbar_wait_bounded(bar_a, phase, kWaitLimit);
                 if (!ok) record_device_error(err, SV_DEVERR_MMA_WAIT);
                 phase ^= 1u;
-                // one verdict for the whole block: tcgen05.ld is warp-collective
+                // one decision for the whole block: tcgen05.ld is warp-collective
                 failed = __syncthreads_or(!ok) != 0;
                 tc_fence_after();
                 if (!failed) {
