@@ -104,6 +104,10 @@ __device__ __forceinline__ void tile_fwd_body(const TilePass &P, int n, int n_sl
             __syncthreads();
             for (int u = tid; u < P.n_ops; u += T)
                 if ((P.real_mask >> u) & 1ull) stage_shears(sm + 4 * u);
+            if constexpr (std::is_same<C, float2>::value) {  // the rotation paths' flags
+                __syncthreads();
+                set_stage_flags(P, rec, sm);
+            }
             mslot = cur.slot;
         }
         cp_async_wait_all();
@@ -117,7 +121,13 @@ __device__ __forceinline__ void tile_fwd_body(const TilePass &P, int n, int n_sl
             C a[NA];
 #pragma unroll
             for (int r = 0; r < NA; ++r) a[r] = *reinterpret_cast<const C *>(tile + (bb.x ^ xsel<R>(r, lq)));
-            tile_ops_fwd<C, R, 0, kReal>(ops, sm, a);
+            // complex64: the branch-free rotation path where the stage allows
+            if constexpr (std::is_same<C, float2>::value) {
+                if (rec[2 * s + 1].w & 1u) tile_ops_fwd_rot<C, R, 0>(ops, sm, a);
+                else tile_ops_fwd<C, R, 0, kReal>(ops, sm, a);
+            } else {
+                tile_ops_fwd<C, R, 0, kReal>(ops, sm, a);
+            }
             __syncthreads();
 #pragma unroll
             for (int r = 0; r < NA; ++r) *reinterpret_cast<C *>(tile + (bb.y ^ xsel<R>(r, sq))) = a[r];
@@ -280,6 +290,23 @@ __device__ __forceinline__ void tile_ops_rev(uint32_t ops, uint32_t modes, const
     }
 }
 
+// tile_ops_rev when every register bit carries a parametrised real
+// rotation in shear form with the single Ry sum (stage flag 2): the same
+// arithmetic without its per-op branches, so the compiler can overlap one
+// op's dependent FMA chains with the next op's.
+template <typename C, typename Real, int R, int I, int NV>
+__device__ __forceinline__ void tile_ops_rev_rot(uint32_t ops, const C *sm, C (&a)[1 << R],
+                                                 C (&al)[1 << R], Real (&k)[NV]) {
+    if constexpr (I >= 0) {
+        k[I] = single_sum<C, Real, R, I>(a, al, 1u);
+        C m0, m1, m2, m3;
+        load_mat(sm, (int)((ops >> (8 * I)) & 63u) - 1, m0, m1, m2, m3);
+        rot3_bit<C, Real, R, I>(a, m0.y, m1.y);
+        rot3_bit<C, Real, R, I>(al, m0.y, m1.y);
+        tile_ops_rev_rot<C, Real, R, I - 1, NV>(ops, sm, a, al, k);
+    }
+}
+
 // Adds the block's sums of slot b (FP64 over warps and lane quads), as i K
 // in reduced-matrix form, to rho_g[b][group][8] and clears them.  Called by
 // every thread.
@@ -392,6 +419,10 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
             __syncthreads();
             for (int u = tid; u < P.n_ops; u += T)
                 if ((P.real_mask >> u) & 1ull) stage_shears(sm + 4 * u);
+            if constexpr (std::is_same<C, float2>::value) {  // the rotation paths' flags
+                __syncthreads();
+                set_stage_flags(P, rec, sm);
+            }
             mslot = cur.slot;
         }
         cp_async_wait_all();
@@ -416,7 +447,12 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
             Real kk[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) kk[v] = 0;
-            tile_ops_rev<C, Real, R, R - 1, NV, kSingle, kReal>(ops, modes, sm, a, al, kk);
+            if constexpr (kSingle && std::is_same<C, float2>::value) {  // complex64 only
+                if (rec[2 * s + 1].w & 2u) tile_ops_rev_rot<C, Real, R, R - 1, NV>(ops, sm, a, al, kk);
+                else tile_ops_rev<C, Real, R, R - 1, NV, kSingle, kReal>(ops, modes, sm, a, al, kk);
+            } else {
+                tile_ops_rev<C, Real, R, R - 1, NV, kSingle, kReal>(ops, modes, sm, a, al, kk);
+            }
             warp_reduce_quad<Real, NV>(kk, lane);
             if constexpr (kSingle) {  // lane: the sum of register bit lane & 3
                 const int m = lane & 3;

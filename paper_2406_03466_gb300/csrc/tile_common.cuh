@@ -215,6 +215,43 @@ __device__ __forceinline__ void tile_ops_fwd(uint32_t ops, const C *sm, C (&a)[1
     }
 }
 
+// The forward stage ops when every register bit carries a real rotation in
+// shear form (stage flag 1): the same arithmetic as tile_ops_fwd without
+// its per-op branches, so the compiler can overlap one op's dependent FMA
+// chains with the next op's.
+template <typename C, int R, int I>
+__device__ __forceinline__ void tile_ops_fwd_rot(uint32_t ops, const C *sm, C (&a)[1 << R]) {
+    if constexpr (I < R) {
+        C m0, m1, m2, m3;
+        load_mat(sm, (int)((ops >> (8 * I)) & 63u) - 1, m0, m1, m2, m3);
+        rot3_bit<C, decltype(m0.x), R, I>(a, m0.y, m1.y);
+        tile_ops_fwd_rot<C, R, I + 1>(ops, sm, a);
+    }
+}
+
+// Stage flags, the w word of a stage's second record, set for the staged
+// matrices of the current slot: bit 0: every register bit carries an op
+// with a real matrix in shear form (a rotation with c > 0); bit 1: also
+// every op is parametrised with the single Ry sum (fmode 1).  Called by
+// every thread once the slot's shear forms are in shared memory; visible
+// after the next barrier.
+template <typename C>
+__device__ __forceinline__ void set_stage_flags(const TilePass &P, uint4 *rec, const C *sm) {
+    for (int s = threadIdx.x; s < P.n_stages; s += blockDim.x) {
+        const uint32_t ops = rec[2 * s].x, modes = rec[2 * s + 1].y;
+        bool rot = true, single = true;
+        for (int i = 0; i < P.R; ++i) {
+            const uint32_t ob = (ops >> (8 * i)) & 0xffu;
+            if (!ob || !(ob & 64u) || sm[4 * ((int)(ob & 63u) - 1) + 2].y == 0) {
+                rot = false;
+                break;
+            }
+            single = single && (ob & 128u) && ((modes >> (8 * i)) & 3u) == 1u;
+        }
+        rec[2 * s + 1].w = (rot ? 1u : 0u) | (rot && single ? 2u : 0u);
+    }
+}
+
 // Every op of pass P has a real matrix.
 __host__ __device__ inline bool pass_all_real(const TilePass &P) {
     const uint64_t all = P.n_ops >= 64 ? ~0ull : ((1ull << P.n_ops) - 1ull);
