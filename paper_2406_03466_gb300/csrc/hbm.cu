@@ -54,6 +54,23 @@ __global__ void k_set_ref(C *states, int n, SlotSource src) {
 }
 
 // One forward pass over every tile of every slot.  mats: [slots][G][4].
+// One forward stage: the branch-free path when register bits 0..M-1 carry
+// real rotations in shear form (M from the stage flags), tile_ops_fwd
+// otherwise.
+template <typename C, int R, bool kReal>
+__device__ __forceinline__ void stage_ops_fwd(uint32_t ops, uint32_t m, const C *sm,
+                                              C (&a)[1 << R]) {
+    if constexpr (R >= 4) {
+        if (m == 4) return tile_ops_fwd_rot<C, R, 0, 4>(ops, sm, a);
+    }
+    if constexpr (R >= 3) {
+        if (m == 3) return tile_ops_fwd_rot<C, R, 0, 3>(ops, sm, a);
+    }
+    if (m == 2) return tile_ops_fwd_rot<C, R, 0, 2>(ops, sm, a);
+    if (m == 1) return tile_ops_fwd_rot<C, R, 0, 1>(ops, sm, a);
+    tile_ops_fwd<C, R, 0, kReal>(ops, sm, a);
+}
+
 template <typename Real, int R, bool kReal>
 __device__ __forceinline__ void tile_fwd_body(const TilePass &P, int n, int n_slots,
                                               const typename CT<Real>::T *mats, int G,
@@ -123,8 +140,7 @@ __device__ __forceinline__ void tile_fwd_body(const TilePass &P, int n, int n_sl
             for (int r = 0; r < NA; ++r) a[r] = *reinterpret_cast<const C *>(tile + (bb.x ^ xsel<R>(r, lq)));
             // complex64: the branch-free rotation path where the stage allows
             if constexpr (std::is_same<C, float2>::value) {
-                if (rec[2 * s + 1].w & 1u) tile_ops_fwd_rot<C, R, 0>(ops, sm, a);
-                else tile_ops_fwd<C, R, 0, kReal>(ops, sm, a);
+                stage_ops_fwd<C, R, kReal>(ops, rec[2 * s + 1].w & 15u, sm, a);
             } else {
                 tile_ops_fwd<C, R, 0, kReal>(ops, sm, a);
             }
@@ -307,6 +323,24 @@ __device__ __forceinline__ void tile_ops_rev_rot(uint32_t ops, const C *sm, C (&
     }
 }
 
+// One reverse stage of single-sum ops: the branch-free path when register
+// bits 0..M-1 carry parametrised real rotations (M from the stage flags),
+// tile_ops_rev otherwise.
+template <typename C, typename Real, int R, int NV, bool kReal>
+__device__ __forceinline__ void stage_ops_rev(uint32_t ops, uint32_t modes, uint32_t m,
+                                              const C *sm, C (&a)[1 << R], C (&al)[1 << R],
+                                              Real (&k)[NV]) {
+    if constexpr (R >= 4) {
+        if (m == 4) return tile_ops_rev_rot<C, Real, R, 3, NV>(ops, sm, a, al, k);
+    }
+    if constexpr (R >= 3) {
+        if (m == 3) return tile_ops_rev_rot<C, Real, R, 2, NV>(ops, sm, a, al, k);
+    }
+    if (m == 2) return tile_ops_rev_rot<C, Real, R, 1, NV>(ops, sm, a, al, k);
+    if (m == 1) return tile_ops_rev_rot<C, Real, R, 0, NV>(ops, sm, a, al, k);
+    tile_ops_rev<C, Real, R, R - 1, NV, true, kReal>(ops, modes, sm, a, al, k);
+}
+
 // Adds the block's sums of slot b (FP64 over warps and lane quads), as i K
 // in reduced-matrix form, to rho_g[b][group][8] and clears them.  Called by
 // every thread.
@@ -448,8 +482,8 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
 #pragma unroll
             for (int v = 0; v < NV; ++v) kk[v] = 0;
             if constexpr (kSingle && std::is_same<C, float2>::value) {  // complex64 only
-                if (rec[2 * s + 1].w & 2u) tile_ops_rev_rot<C, Real, R, R - 1, NV>(ops, sm, a, al, kk);
-                else tile_ops_rev<C, Real, R, R - 1, NV, kSingle, kReal>(ops, modes, sm, a, al, kk);
+                stage_ops_rev<C, Real, R, NV, kReal>(ops, modes, (rec[2 * s + 1].w >> 4) & 15u, sm, a,
+                                                     al, kk);
             } else {
                 tile_ops_rev<C, Real, R, R - 1, NV, kSingle, kReal>(ops, modes, sm, a, al, kk);
             }

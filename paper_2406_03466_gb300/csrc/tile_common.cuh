@@ -215,40 +215,43 @@ __device__ __forceinline__ void tile_ops_fwd(uint32_t ops, const C *sm, C (&a)[1
     }
 }
 
-// The forward stage ops when every register bit carries a real rotation in
-// shear form (stage flag 1): the same arithmetic as tile_ops_fwd without
-// its per-op branches, so the compiler can overlap one op's dependent FMA
-// chains with the next op's.
-template <typename C, int R, int I>
+// The forward stage ops when register bits 0..M-1 carry real rotations in
+// shear form and the others carry no op (stage flags): the arithmetic of
+// tile_ops_fwd without its per-op branches, so the compiler can overlap one
+// op's dependent FMA chains with the next op's.
+template <typename C, int R, int I, int M>
 __device__ __forceinline__ void tile_ops_fwd_rot(uint32_t ops, const C *sm, C (&a)[1 << R]) {
-    if constexpr (I < R) {
+    if constexpr (I < M) {
         C m0, m1, m2, m3;
         load_mat(sm, (int)((ops >> (8 * I)) & 63u) - 1, m0, m1, m2, m3);
         rot3_bit<C, decltype(m0.x), R, I>(a, m0.y, m1.y);
-        tile_ops_fwd_rot<C, R, I + 1>(ops, sm, a);
+        tile_ops_fwd_rot<C, R, I + 1, M>(ops, sm, a);
     }
 }
 
 // Stage flags, the w word of a stage's second record, set for the staged
-// matrices of the current slot: bit 0: every register bit carries an op
-// with a real matrix in shear form (a rotation with c > 0); bit 1: also
-// every op is parametrised with the single Ry sum (fmode 1).  Called by
-// every thread once the slot's shear forms are in shared memory; visible
-// after the next barrier.
+// matrices of the current slot.  Bits 0-3: M > 0 when register bits
+// 0..M-1 carry ops with real matrices in shear form (rotations with c > 0)
+// and the other bits none (the forward's branch-free path); bits 4-7: the
+// same M when those ops are moreover parametrised with the single Ry sum
+// (fmode 1; the reverse's); 0 otherwise.  Called by every thread once the
+// slot's shear forms are in shared memory; visible after the next barrier.
 template <typename C>
 __device__ __forceinline__ void set_stage_flags(const TilePass &P, uint4 *rec, const C *sm) {
     for (int s = threadIdx.x; s < P.n_stages; s += blockDim.x) {
         const uint32_t ops = rec[2 * s].x, modes = rec[2 * s + 1].y;
-        bool rot = true, single = true;
+        int m = 0;
+        bool single = true;
         for (int i = 0; i < P.R; ++i) {
             const uint32_t ob = (ops >> (8 * i)) & 0xffu;
-            if (!ob || !(ob & 64u) || sm[4 * ((int)(ob & 63u) - 1) + 2].y == 0) {
-                rot = false;
-                break;
-            }
+            if (!ob) break;
+            if (!(ob & 64u) || sm[4 * ((int)(ob & 63u) - 1) + 2].y == 0) break;
             single = single && (ob & 128u) && ((modes >> (8 * i)) & 3u) == 1u;
+            m = i + 1;
         }
-        rec[2 * s + 1].w = (rot ? 1u : 0u) | (rot && single ? 2u : 0u);
+        // the bits above M must carry no op
+        if (m > 0 && m < 4 && (ops >> (8 * m)) != 0u) m = 0;
+        rec[2 * s + 1].w = (uint32_t)m | (single ? (uint32_t)m << 4 : 0u);
     }
 }
 
