@@ -720,7 +720,8 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
     constexpr int NA = 1 << R;
     static_assert(R <= kHRegBitsMax, "H kernel register bits");
     extern __shared__ __align__(16) unsigned char smem[];
-    const int tid = threadIdx.x, T = blockDim.x, t = P.t;
+    // 256 threads whenever R >= 3 (tiles of 2^11 and 2^12 amplitudes)
+    const int tid = threadIdx.x, T = R >= 3 ? 256 : (int)blockDim.x, t = P.t;
     const uint32_t tbytes = (uint32_t)sizeof(C) << t;
     // psi tiles at [0, 2 tbytes), the lambda tile being added to at [2 tbytes, 3 tbytes)
     HGroup *grp = reinterpret_cast<HGroup *>(smem + 3 * tbytes);
@@ -799,19 +800,26 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
         else cp_async_commit();  // keeps "all but the newest group" meaning the lambda tile
         const C *tile = reinterpret_cast<const C *>(smem + (uint32_t)buf * tbytes);
         const C *Sg = psi + ((int64_t)cur.slot << n);
-        Real lr[NA], li[NA];
+        // lambda_k = acc[k] (real part .x, imaginary part .y)
+        C acc[NA];
 #pragma unroll
-        for (int k = 0; k < NA; ++k) lr[k] = li[k] = 0;
+        for (int k = 0; k < NA; ++k) acc[k].x = acc[k].y = 0;
         auto add_real = [&](int k, Real d, const C &pk) {
-            lr[k] = fmaR(d, pk.x, lr[k]);
-            li[k] = fmaR(d, pk.y, li[k]);
+            acc[k].x = fmaR(d, pk.x, acc[k].x);
+            acc[k].y = fmaR(d, pk.y, acc[k].y);
         };
+        // byte offset in shared memory of partner j ^ x (j = tid + k T) is
+        // gb ^ (k T sizeof(C)): thread and register bits are disjoint, and
+        // the buffer offset is above every in-tile offset
+        const uint32_t bufb = (uint32_t)buf * tbytes;
         for (int g = 0; g < P.n_groups; ++g) {
             const HGroup &gr = grp[g];
             const uint32_t xl = gr.xl, xfar = gr.xfar, kact = gr.kact;
+            const uint32_t gb = ((uint32_t)(tid ^ (int)xl) * (uint32_t)sizeof(C)) ^ bufb;
             auto partner = [&](int k) -> C {
                 return xfar ? Sg[(cur.base ^ g0 ^ xsel<R>(k, gk)) ^ xfar]
-                            : tile[(uint32_t)(tid + k * T) ^ xl];
+                            : *reinterpret_cast<const C *>(
+                                  smem + (gb ^ ((uint32_t)(k * T) * (uint32_t)sizeof(C))));
             };
             if (kact == 0) {
                 // no class has a Z on a register bit: one value per thread
@@ -822,14 +830,21 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
                     vr += nt ? -h.re : h.re;
                     if constexpr (!kRealH) vi += nt ? -h.im : h.im;
                 }
+                if constexpr (kRealH && std::is_same<C, float2>::value) {
+                    // one packed FP32-pair FMA per amplitude
+                    const uint64_t d2 = f2pack(vr, vr);
 #pragma unroll
-                for (int k = 0; k < NA; ++k) {
-                    const C pk = partner(k);
-                    if constexpr (kRealH) {
-                        add_real(k, vr, pk);
-                    } else {
-                        lr[k] = fmaR(vr, pk.x, fmaR(-vi, pk.y, lr[k]));
-                        li[k] = fmaR(vr, pk.y, fmaR(vi, pk.x, li[k]));
+                    for (int k = 0; k < NA; ++k) acc[k] = f2unpack(f2fma(d2, f2of(partner(k)), f2of(acc[k])));
+                } else {
+#pragma unroll
+                    for (int k = 0; k < NA; ++k) {
+                        const C pk = partner(k);
+                        if constexpr (kRealH) {
+                            add_real(k, vr, pk);
+                        } else {
+                            acc[k].x = fmaR(vr, pk.x, fmaR(-vi, pk.y, acc[k].x));
+                            acc[k].y = fmaR(vr, pk.y, fmaR(vi, pk.x, acc[k].y));
+                        }
                     }
                 }
                 continue;
@@ -858,8 +873,8 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
                 if constexpr (kRealH) {
                     add_real(k, vr[k], pk);
                 } else {
-                    lr[k] = fmaR(vr[k], pk.x, fmaR(-vi[k], pk.y, lr[k]));
-                    li[k] = fmaR(vr[k], pk.y, fmaR(vi[k], pk.x, li[k]));
+                    acc[k].x = fmaR(vr[k], pk.x, fmaR(-vi[k], pk.y, acc[k].x));
+                    acc[k].y = fmaR(vr[k], pk.y, fmaR(vi[k], pk.x, acc[k].y));
                 }
             }
         }
@@ -868,12 +883,10 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
 #pragma unroll
         for (int k = 0; k < NA; ++k) {
             const C pj = tile[tid + k * T];
-            part = fmaR(pj.x, lr[k], fmaR(pj.y, li[k], part));
+            part = fmaR(pj.x, acc[k].x, fmaR(pj.y, acc[k].y, part));
             if constexpr (kLam) {
                 const uint32_t go = g0 ^ xsel<R>(k, gk);
-                C out;
-                out.x = lr[k];
-                out.y = li[k];
+                C out = acc[k];
                 if (add) {  // each thread reads back only its own copies
                     const C old = lt[tid + k * T];
                     out.x += old.x;
