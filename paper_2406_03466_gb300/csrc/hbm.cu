@@ -121,8 +121,8 @@ __device__ __forceinline__ void tile_fwd_body(const TilePass &P, int n, int n_sl
             __syncthreads();
             for (int u = tid; u < P.n_ops; u += T)
                 if ((P.real_mask >> u) & 1ull) stage_shears(sm + 4 * u);
-            if constexpr (std::is_same<C, float2>::value) {  // the rotation paths' flags
-                __syncthreads();
+            if constexpr (kReal && std::is_same<C, float2>::value) {
+                __syncthreads();  // the rotation path's stage flags
                 set_stage_flags(P, rec, sm);
             }
             mslot = cur.slot;
@@ -138,8 +138,9 @@ __device__ __forceinline__ void tile_fwd_body(const TilePass &P, int n, int n_sl
             C a[NA];
 #pragma unroll
             for (int r = 0; r < NA; ++r) a[r] = *reinterpret_cast<const C *>(tile + (bb.x ^ xsel<R>(r, lq)));
-            // complex64: the branch-free rotation path where the stage allows
-            if constexpr (std::is_same<C, float2>::value) {
+            // complex64 passes of real matrices: the branch-free rotation path
+            // where the stage allows
+            if constexpr (kReal && std::is_same<C, float2>::value) {
                 stage_ops_fwd<C, R, kReal>(ops, rec[2 * s + 1].w & 15u, sm, a);
             } else {
                 tile_ops_fwd<C, R, 0, kReal>(ops, sm, a);
@@ -453,8 +454,8 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
             __syncthreads();
             for (int u = tid; u < P.n_ops; u += T)
                 if ((P.real_mask >> u) & 1ull) stage_shears(sm + 4 * u);
-            if constexpr (std::is_same<C, float2>::value) {  // the rotation paths' flags
-                __syncthreads();
+            if constexpr (kSingle && kReal && std::is_same<C, float2>::value) {
+                __syncthreads();  // the rotation path's stage flags
                 set_stage_flags(P, rec, sm);
             }
             mslot = cur.slot;
@@ -481,7 +482,7 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
             Real kk[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) kk[v] = 0;
-            if constexpr (kSingle && std::is_same<C, float2>::value) {  // complex64 only
+            if constexpr (kSingle && kReal && std::is_same<C, float2>::value) {
                 stage_ops_rev<C, Real, R, NV, kReal>(ops, modes, (rec[2 * s + 1].w >> 4) & 15u, sm, a,
                                                      al, kk);
             } else {
