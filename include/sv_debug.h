@@ -41,12 +41,12 @@ sv_status sv_debug_tile_passes(const sv_circuit *circuit, int32_t tile_bits, int
                                int32_t fuse, int32_t dtype, int32_t relabel, int32_t *counts,
                                void *groups, void *members, void *tile_passes, int32_t *layout);
 
-/* The tile passes of lambda = H psi: counts[0..3] = passes, groups, classes,
- * terms.  In the exported pass records the three array pointers hold the
- * pass's first index into `groups`, `classes` and `terms`. */
+/* The tile passes of lambda = H psi: counts[0..4] = passes, groups, classes,
+ * terms, rows.  In the exported pass records the four array pointers hold
+ * the pass's first index into `groups`, `classes`, `terms` and `rows`. */
 sv_status sv_debug_h_passes(const sv_pauli_sum *h, int32_t tile_bits, int32_t coalesce_bits,
                             int32_t *counts, void *passes, void *groups, void *classes,
-                            void *terms);
+                            void *terms, void *rows);
 
 /* The bounded-wait path end to end: launches one block on `stream` that
  * waits `limit` times on an mbarrier nothing arrives on and then records the

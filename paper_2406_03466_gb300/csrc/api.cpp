@@ -603,6 +603,7 @@ sv_status get_hplan(ObsEntry *obs, int n, sv_dtype dt, HPlanEntry **out,
         const size_t og = pk.add(h.groups.data(), h.groups.size() * sizeof(HGroup));
         const size_t oc = pk.add(h.classes.data(), h.classes.size() * sizeof(HClass));
         const size_t ot = pk.add(h.terms.data(), h.terms.size() * sizeof(HTerm));
+        const size_t orw = pk.add(h.rows.data(), h.rows.size() * sizeof(HRow));
         e->buf.bytes = pk.bytes.size() ? pk.bytes.size() : 256;
         SV_CUDA(cudaMalloc(&e->buf.ptr, e->buf.bytes));
         if (!pk.bytes.empty())
@@ -613,6 +614,7 @@ sv_status get_hplan(ObsEntry *obs, int n, sv_dtype dt, HPlanEntry **out,
             P.groups = (const HGroup *)(base + og) + h.g_begin[i];
             P.classes = (const HClass *)(base + oc) + h.c_begin[i];
             P.terms = (const HTerm *)(base + ot) + h.t_begin[i];
+            P.rows = (const HRow *)(base + orw) + h.r_begin[i];
             e->passes.push_back(P);
         }
         slot = std::move(e);

@@ -84,7 +84,7 @@ sv_status sv_debug_tile_passes(const sv_circuit *c, int32_t tile_bits, int32_t r
 
 sv_status sv_debug_h_passes(const sv_pauli_sum *h, int32_t tile_bits, int32_t coalesce_bits,
                             int32_t *counts, void *passes, void *groups, void *classes,
-                            void *terms) {
+                            void *terms, void *rows) {
     if (!h || !counts) return SV_ERR_ARG;
     HostObservable ho;
     std::string err = plan_observable(*h, h->n_qubits, 4, &ho);
@@ -95,18 +95,21 @@ sv_status sv_debug_h_passes(const sv_pauli_sum *h, int32_t tile_bits, int32_t co
     counts[1] = (int32_t)hp.groups.size();
     counts[2] = (int32_t)hp.classes.size();
     counts[3] = (int32_t)hp.terms.size();
+    counts[4] = (int32_t)hp.rows.size();
     if (passes) {
         std::vector<HPass> ps = hp.passes;
         for (size_t i = 0; i < ps.size(); ++i) {  // offsets into the arrays, as pointers
             ps[i].groups = (const HGroup *)(uintptr_t)hp.g_begin[i];
             ps[i].classes = (const HClass *)(uintptr_t)hp.c_begin[i];
             ps[i].terms = (const HTerm *)(uintptr_t)hp.t_begin[i];
+            ps[i].rows = (const HRow *)(uintptr_t)hp.r_begin[i];
         }
         std::memcpy(passes, ps.data(), ps.size() * sizeof(HPass));
     }
     if (groups) std::memcpy(groups, hp.groups.data(), hp.groups.size() * sizeof(HGroup));
     if (classes) std::memcpy(classes, hp.classes.data(), hp.classes.size() * sizeof(HClass));
     if (terms) std::memcpy(terms, hp.terms.data(), hp.terms.size() * sizeof(HTerm));
+    if (rows) std::memcpy(rows, hp.rows.data(), hp.rows.size() * sizeof(HRow));
     return SV_OK;
 }
 

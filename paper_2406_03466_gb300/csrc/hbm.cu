@@ -685,34 +685,19 @@ template <typename Real> struct HCoef {
     Real re, im;
 };
 
-// Walsh-Hadamard transform over the NA = 2^R entries of v (in place):
-// v[k] <- sum_p v[p] (-1)^|k & p|.
-template <typename Real, int NA>
-__device__ __forceinline__ void wht(Real (&v)[NA]) {
-#pragma unroll
-    for (int b = 1; b < NA; b <<= 1)
-#pragma unroll
-        for (int p = 0; p < NA; ++p)
-            if (!(p & b)) {
-                const Real x = v[p], y = v[p | b];
-                v[p] = x + y;
-                v[p | b] = x - y;
-            }
-}
-
 // One H pass: for the pass's X-mask groups g,
 //   lambda_j (+)= sum_g D_g(j ^ x_g) psi_(j ^ x_g),
 //   D_g(k) = sum_(t in g) c_t i^phase_t (-1)^|k & z_t|,
 // and E[slot] += sum_j Re(conj(psi_j) lambda_j) over this pass's part of
 // lambda.  psi tiles arrive by cp.async (double-buffered) in natural order;
-// the thread's amplitudes are j = tid + k 2^(t-R).  Per group, every
-// thread adds its signed class coefficients (the sign of the class's Z mask
-// on the thread bits) into one bucket per register-bit Z mask (the planner
-// sorted the classes that way) and a Walsh-Hadamard transform over the
-// register bits turns the buckets into D_g at the thread's 2^R amplitudes:
-// the work per class is per thread, not per amplitude.  Products in the
-// state's precision, sums over the block's amplitudes in FP64.  kLam =
-// false: energies only.
+// the thread's amplitudes are j = tid + k 2^(t-R).  A group whose classes
+// put no Z on a register bit takes one value per thread (its signed class
+// coefficients summed).  The others read D_g at the thread's 2^R amplitudes
+// from a per-tile table: one row of 2^R values per distinct Z mask on the
+// thread bits (the row's class coefficients times their register-bit signs,
+// built once per tile by the whole block), each row added with the sign of
+// its thread-bit mask.  Products in the state's precision, sums over the
+// block's amplitudes in FP64.  kLam = false: energies only.
 template <typename Real, int R, bool kLam, bool kRealH>
 __global__ void __launch_bounds__(256)
 k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<Real>::T *psi,
@@ -724,15 +709,21 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
     // 256 threads whenever R >= 3 (tiles of 2^11 and 2^12 amplitudes)
     const int tid = threadIdx.x, T = R >= 3 ? 256 : (int)blockDim.x, t = P.t;
     const uint32_t tbytes = (uint32_t)sizeof(C) << t;
-    // psi tiles at [0, 2 tbytes), the lambda tile being added to at [2 tbytes, 3 tbytes)
-    HGroup *grp = reinterpret_cast<HGroup *>(smem + 3 * tbytes);
+    // psi tiles at [0, 2 tbytes), the lambda tile being added to at [2 tbytes,
+    // 3 tbytes), then this tile's row table (NA values per row, real parts,
+    // then imaginary parts unless kRealH)
+    constexpr int kRowVals = kRealH ? NA : 2 * NA;
+    Real *etab = reinterpret_cast<Real *>(smem + 3 * tbytes);
+    HGroup *grp = reinterpret_cast<HGroup *>(etab + P.n_rows * kRowVals);
     HCoef<Real> *coef = reinterpret_cast<HCoef<Real> *>(grp + P.n_groups);
     HTerm *trm = reinterpret_cast<HTerm *>(coef + P.n_classes);
     HClass *cls = reinterpret_cast<HClass *>(trm + P.n_terms);
-    double *red = reinterpret_cast<double *>(cls + P.n_classes);
+    HRow *rows = reinterpret_cast<HRow *>(cls + P.n_classes);
+    double *red = reinterpret_cast<double *>(rows + P.n_rows);
     for (int i = tid; i < P.n_terms; i += T) trm[i] = P.terms[i];
     for (int i = tid; i < P.n_groups; i += T) grp[i] = P.groups[i];
     for (int i = tid; i < P.n_classes; i += T) cls[i] = P.classes[i];
+    for (int i = tid; i < P.n_rows; i += T) rows[i] = P.rows[i];
     __syncthreads();
     const bool add = kLam && !P.first;
     uint32_t gk[R];
@@ -785,6 +776,22 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
             h.re = re;
             h.im = im;
             coef[c] = h;
+        }
+        if (P.n_rows) {  // the row table: E[k] = sum_c coef_c (-1)^|k & kz_c|
+            __syncthreads();
+            for (int x = tid; x < P.n_rows * NA; x += T) {
+                const HRow rw = rows[x / NA];
+                const int k = x & (NA - 1);
+                Real er = 0, ei = 0;
+                for (int c = rw.c_begin; c < rw.c_end; ++c) {
+                    const bool neg = __popc((uint32_t)k & (cls[c].zl >> (t - R))) & 1u;
+                    er += neg ? -coef[c].re : coef[c].re;
+                    if constexpr (!kRealH) ei += neg ? -coef[c].im : coef[c].im;
+                }
+                Real *e = etab + (x / NA) * kRowVals;
+                e[k] = er;
+                if constexpr (!kRealH) e[NA + k] = ei;
+            }
         }
         cp_async_wait_all();
         __syncthreads();
@@ -850,24 +857,19 @@ k_tile_h(const __grid_constant__ HPass P, int n, int n_slots, const typename CT<
                 }
                 continue;
             }
-            // buckets: classes with register-bit Z mask p (a subset of kact)
+            // D(tid, k) = sum over the group's rows of (-1)^|tid & zt| E_row[k]
             Real vr[NA], vi[NA];
 #pragma unroll
-            for (int p = 0; p < NA; ++p) vr[p] = vi[p] = 0;
-            int c = gr.c_begin;
+            for (int k = 0; k < NA; ++k) vr[k] = vi[k] = 0;
+            for (int r = gr.r_begin; r < gr.r_end; ++r) {
+                const Real sg = (__popc((uint32_t)tid & rows[r].zt) & 1u) ? (Real)-1 : (Real)1;
+                const Real *e = etab + r * kRowVals;
 #pragma unroll
-            for (int p = 0; p < NA; ++p) {
-                if (p & ~kact) continue;
-                const int c_end = c + (int)gr.nk[p];
-                for (; c < c_end; ++c) {
-                    const HCoef<Real> h = coef[c];
-                    const bool nt = __popc((uint32_t)tid & h.zt) & 1u;
-                    vr[p] += nt ? -h.re : h.re;
-                    if constexpr (!kRealH) vi[p] += nt ? -h.im : h.im;
+                for (int k = 0; k < NA; ++k) {
+                    vr[k] = fmaR(sg, e[k], vr[k]);
+                    if constexpr (!kRealH) vi[k] = fmaR(sg, e[NA + k], vi[k]);
                 }
             }
-            wht<Real, NA>(vr);
-            if constexpr (!kRealH) wht<Real, NA>(vi);
 #pragma unroll
             for (int k = 0; k < NA; ++k) {
                 const C pk = partner(k);
@@ -1193,7 +1195,9 @@ cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, con
 
 uint32_t tile_h_smem(int c128, const HPass &P) {
     const uint32_t csz = c128 ? 16u : 8u;
-    return 3u * (csz << P.t) + (uint32_t)P.n_groups * (uint32_t)sizeof(HGroup) +
+    const uint32_t row_vals = (1u << h_reg_bits(P.t)) * (P.real ? 1u : 2u);
+    return 3u * (csz << P.t) + (uint32_t)P.n_rows * (row_vals * (csz / 2u) + (uint32_t)sizeof(HRow)) +
+           (uint32_t)P.n_groups * (uint32_t)sizeof(HGroup) +
            (uint32_t)P.n_classes * (csz + 8u + (uint32_t)sizeof(HClass)) +
            (uint32_t)P.n_terms * (uint32_t)sizeof(HTerm) + 32u * 8u + 16u;
 }

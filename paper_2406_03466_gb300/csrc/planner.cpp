@@ -660,8 +660,10 @@ std::string plan_h_passes(const HostObservable &h, int tile_bits, int coalesce_b
         out->g_begin.push_back((int)out->groups.size());
         out->c_begin.push_back((int)out->classes.size());
         out->t_begin.push_back((int)out->terms.size());
+        out->r_begin.push_back((int)out->rows.size());
         const int g0 = (int)out->groups.size(), c0 = (int)out->classes.size(),
-                  t0 = (int)out->terms.size();
+                  t0 = (int)out->terms.size(), r0 = (int)out->rows.size();
+        const uint32_t tmask = (1u << (t - P.R)) - 1u;
         for (int gi : taken) {
             const TermGroup &tg = h.tgroups[gi];
             HGroup G{};
@@ -671,8 +673,11 @@ std::string plan_h_passes(const HostObservable &h, int tile_bits, int coalesce_b
             G.c_begin = (int)out->classes.size() - c0;
             std::vector<int> order;
             for (int ti = tg.t_begin; ti < tg.t_end; ++ti) order.push_back(ti);
+            // by the Z mask's thread bits, then its register bits
             std::stable_sort(order.begin(), order.end(), [&](int a, int bb) {
-                return local(h.terms[a].z) < local(h.terms[bb].z);
+                const uint32_t za = local(h.terms[a].z), zb = local(h.terms[bb].z);
+                if ((za & tmask) != (zb & tmask)) return (za & tmask) < (zb & tmask);
+                return za < zb;
             });
             for (size_t i = 0; i < order.size(); ++i) {
                 const Term &tm = h.terms[order[i]];
@@ -694,13 +699,22 @@ std::string plan_h_passes(const HostObservable &h, int tile_bits, int coalesce_b
                 out->classes.back().t_end = (int)out->terms.size() - t0;
             }
             G.c_end = (int)out->classes.size() - c0;
-            // classes are in increasing zl order, hence grouped by their
-            // register-bit Z mask kz = zl >> (t - R)
-            for (int c = G.c_begin; c < G.c_end; ++c) {
-                const uint32_t kz = out->classes[(size_t)(c0 + c)].zl >> (t - P.R);
-                G.nk[kz] += 1;
-                G.kact |= kz;
-            }
+            for (int c = G.c_begin; c < G.c_end; ++c)
+                G.kact |= out->classes[(size_t)(c0 + c)].zl >> (t - P.R);
+            // rows: the runs of classes with the same Z mask on the thread bits
+            G.r_begin = G.r_end = (int)out->rows.size() - r0;
+            if (G.kact)
+                for (int c = G.c_begin; c < G.c_end; ++c) {
+                    const uint32_t zt = out->classes[(size_t)(c0 + c)].zl & tmask;
+                    if (c == G.c_begin || zt != out->rows.back().zt) {
+                        HRow rw{};
+                        rw.zt = zt;
+                        rw.c_begin = c;
+                        out->rows.push_back(rw);
+                    }
+                    out->rows.back().c_end = c + 1;
+                }
+            G.r_end = (int)out->rows.size() - r0;
             out->groups.push_back(G);
         }
         P.real = 1;
@@ -708,12 +722,14 @@ std::string plan_h_passes(const HostObservable &h, int tile_bits, int coalesce_b
         P.n_groups = (int)out->groups.size() - g0;
         P.n_classes = (int)out->classes.size() - c0;
         P.n_terms = (int)out->terms.size() - t0;
+        P.n_rows = (int)out->rows.size() - r0;
         out->passes.push_back(P);
         pending.swap(rest);
     }
     out->g_begin.push_back((int)out->groups.size());
     out->c_begin.push_back((int)out->classes.size());
     out->t_begin.push_back((int)out->terms.size());
+    out->r_begin.push_back((int)out->rows.size());
     return "";
 }
 

@@ -69,10 +69,11 @@ struct HostObservable {
 // etc.  Device pointers of HPass are left null (set after upload).
 struct HostHPlan {
     std::vector<HPass> passes;
-    std::vector<int> g_begin, c_begin, t_begin;  // per pass, plus an end entry
+    std::vector<int> g_begin, c_begin, t_begin, r_begin;  // per pass, plus an end entry
     std::vector<HGroup> groups;
     std::vector<HClass> classes;
     std::vector<HTerm> terms;
+    std::vector<HRow> rows;
 };
 std::string plan_h_passes(const HostObservable &h, int tile_bits, int coalesce_bits,
                           HostHPlan *out);

@@ -171,20 +171,29 @@ struct SweepTask {
 // coefficient is summed once per tile (the Z mask's tile-number bits only
 // give each term a sign per tile).
 // The H kernel's threads hold 2^R amplitudes j = tid + k 2^(t - R) (k over
-// the R register bits, the top R tile-local bits).  A group's classes are
-// sorted by their Z mask on the register bits, kz = zl >> (t - R): the
-// kernel sums each thread's signed class coefficients into one bucket per
-// kz and expands the 2^R buckets to the thread's 2^R diagonal values by a
-// Walsh-Hadamard transform over the register bits.
+// the R register bits, the top R tile-local bits).  A class's Z mask splits
+// into its thread bits zt = zl & (2^(t-R) - 1) and its register bits
+// kz = zl >> (t - R), so the group's diagonal factor at thread tid and
+// register index k is D(tid, k) = sum over its rows of (-1)^|tid & zt| E[k],
+// one row per distinct zt, E[k] = sum of the row's class coefficients times
+// (-1)^|k & kz| (per tile, shared by all threads).  Groups whose classes put
+// no Z on a register bit (kact = 0) take one value per thread instead.
 constexpr int kHRegBitsMax = 4;
 struct HGroup {
     uint32_t xl;              // flip mask on tile-local bits
-    int32_t c_begin, c_end;   // its classes
+    int32_t c_begin, c_end;   // its classes, sorted by (zt, kz)
     uint32_t xfar;            // whole flip mask when it leaves the tile (partner read from
                               // global memory), else 0
     uint32_t kact;            // register bits in some class's Z mask (0: one value per thread)
-    uint32_t pad[3];
-    uint16_t nk[1 << kHRegBitsMax];  // classes with register Z mask kz, in kz order
+    int32_t r_begin, r_end;   // its rows (kact != 0), else empty
+    uint32_t pad;
+};
+
+// A run of a group's classes with the same Z mask on the thread bits.
+struct HRow {
+    uint32_t zt;              // Z mask on the thread bits
+    int32_t c_begin, c_end;   // its classes (pass-relative)
+    int32_t pad;
 };
 
 struct HClass {
@@ -207,9 +216,11 @@ struct HPass {
     int32_t R;                  // register bits of the kernel's threads (h_reg_bits(t))
     uint32_t gl[kTileBitsMax];  // tile-local bit b -> global offset bit
     uint32_t gpre[kNMax];       // gt[0] ^ ... ^ gt[k] for tile-number bit k
+    int32_t n_rows, pad;
     const HGroup *groups;       // device arrays of this pass
     const HClass *classes;
     const HTerm *terms;
+    const HRow *rows;
 };
 
 // Register bits of the H-pass kernel for tiles of 2^t amplitudes: 256

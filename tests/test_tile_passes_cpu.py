@@ -445,14 +445,18 @@ def test_rejects_tiles_narrower_than_a_warp():
 class HPassRec(ctypes.Structure):
     _fields_ = [("t", I32), ("n_tile_bits", I32), ("n_groups", I32), ("n_classes", I32),
                 ("n_terms", I32), ("first", I32), ("real", I32), ("R", I32), ("gl", U32 * KT),
-                ("gpre", U32 * 30),
+                ("gpre", U32 * 30), ("n_rows", I32), ("pad", I32),
                 ("groups", ctypes.c_void_p), ("classes", ctypes.c_void_p),
-                ("terms", ctypes.c_void_p)]
+                ("terms", ctypes.c_void_p), ("rows", ctypes.c_void_p)]
 
 
 class HGroup(ctypes.Structure):
     _fields_ = [("xl", U32), ("c_begin", I32), ("c_end", I32), ("xfar", U32), ("kact", U32),
-                ("pad", U32 * 3), ("nk", ctypes.c_uint16 * 16)]
+                ("r_begin", I32), ("r_end", I32), ("pad", U32)]
+
+
+class HRow(ctypes.Structure):
+    _fields_ = [("zt", U32), ("c_begin", I32), ("c_end", I32), ("pad", I32)]
 
 
 class HClass(ctypes.Structure):
@@ -465,48 +469,44 @@ class HTerm(ctypes.Structure):
 
 
 def export_h(obs, t, c):
+    """(passes, groups, classes, terms, rows) of the H tile plan."""
     L = sv.library()
-    L.sv_debug_h_passes.argtypes = [ctypes.c_void_p, I32, I32, ctypes.POINTER(I32)] + [ctypes.c_void_p] * 4
+    L.sv_debug_h_passes.argtypes = [ctypes.c_void_p, I32, I32, ctypes.POINTER(I32)] + [ctypes.c_void_p] * 5
     L.sv_debug_h_passes.restype = I32
-    counts = (I32 * 4)()
-    assert L.sv_debug_h_passes(ctypes.byref(obs.struct), t, c, counts, None, None, None, None) == 0
+    counts = (I32 * 5)()
+    assert L.sv_debug_h_passes(ctypes.byref(obs.struct), t, c, counts, None, None, None, None,
+                               None) == 0
     arrs = [(HPassRec * counts[0])(), (HGroup * max(1, counts[1]))(),
-            (HClass * max(1, counts[2]))(), (HTerm * max(1, counts[3]))()]
+            (HClass * max(1, counts[2]))(), (HTerm * max(1, counts[3]))(),
+            (HRow * max(1, counts[4]))()]
     assert L.sv_debug_h_passes(ctypes.byref(obs.struct), t, c, counts, *arrs) == 0
     return [a[:k] for a, k in zip(arrs, counts)]
 
 
-def _wht(v):
-    """v[k] <- sum_p v[p] (-1)^|k & p| over the last axis (length 2^R)."""
-    v = v.copy()
-    b = 1
-    while b < v.shape[-1]:
-        for p in range(v.shape[-1]):
-            if not p & b:
-                x, y = v[..., p].copy(), v[..., p | b].copy()
-                v[..., p], v[..., p | b] = x + y, x - y
-        b <<= 1
-    return v
-
-
 def run_h(plan, psi, n):
     """The tile H kernel, tile by tile: returns lambda = H psi and <psi|H|psi>.
-    Like the kernel, thread tid holds amplitudes j = tid + k 2^(t - R); per
-    group it sums its signed class coefficients into one bucket per
-    register-bit Z mask (the classes' planned order and the group's bucket
-    counts) and expands the buckets by a Walsh-Hadamard transform."""
-    passes, groups, classes, terms = plan
+    Like the kernel, thread tid holds amplitudes j = tid + k 2^(t - R).  A
+    group without a Z on a register bit takes one value per thread (its
+    signed class coefficients); the others take, per row (a run of classes
+    with one Z mask zt on the thread bits), the per-tile row values
+    E[k] = sum_c coef_c (-1)^|k & kz_c| times the thread's sign (-1)^|tid & zt|."""
+    passes, groups, classes, terms, rows = plan
     lam = np.zeros_like(psi)
     E = 0.0
     for P in passes:
         t, ntb = P.t, P.n_tile_bits
-        g0, c0, t0 = P.groups or 0, P.classes or 0, P.terms or 0
+        g0, c0, t0, r0 = P.groups or 0, P.classes or 0, P.terms or 0, P.rows or 0
         loc = np.zeros(1 << t, np.int64)
         for i in range(1 << t):
             for b in range(t):
                 if i >> b & 1:
                     loc[i] ^= P.gl[b]
         j = np.arange(1 << t)
+        R = P.R
+        T = 1 << (t - R)
+        tid = np.arange(T)
+        kk = np.arange(1 << R)
+        par = lambda a: np.array([bin(int(v)).count("1") & 1 for v in a])
         for slot, base in tile_walk(P, 1, 3):
             tile = psi[base + loc]
             coef = []
@@ -515,30 +515,39 @@ def run_h(plan, psi, n):
                 for tm in terms[t0 + cl.t_begin:t0 + cl.t_end]:
                     sgn = -1.0 if bin((base ^ cl.xnl) & tm.z).count("1") & 1 else 1.0
                     v += sgn * tm.coeff * 1j ** tm.phase
-                coef.append(v)
+                # the class's sign on the flip bits: D(j ^ xl) = D(j) x that
+                sx = -1.0 if bin(cl.xl & cl.zl).count("1") & 1 else 1.0
+                coef.append(sx * v)
+            # the kernel's row table of this tile
+            etab = []
+            for rw in rows[r0:r0 + P.n_rows]:
+                e = np.zeros(1 << R, complex)
+                for c in range(rw.c_begin, rw.c_end):
+                    zl = classes[c0 + c].zl
+                    assert zl & (T - 1) == rw.zt
+                    e += np.where(par(kk & (zl >> (t - R))) == 1, -coef[c], coef[c])
+                etab.append(e)
             part = np.zeros(1 << t, complex)
-            R = P.R
-            T = 1 << (t - R)
-            tid = np.arange(T)
             for gr in groups[g0:g0 + P.n_groups]:
                 jx = j ^ gr.xl
-                # the kernel's buckets: classes in planned order, nk[p] per
-                # register-bit Z mask p; per thread the signed coefficients
-                V = np.zeros((T, 1 << R), complex)
-                c = gr.c_begin
-                for p in range(1 << R):
-                    for _ in range(gr.nk[p]):
-                        zl = classes[c0 + c].zl
-                        assert zl >> (t - R) == p
-                        # the class's sign on the flip bits: D(j ^ xl) = D(j) x that
-                        sx = -1.0 if bin(gr.xl & zl).count("1") & 1 else 1.0
-                        par = np.array([bin(v).count("1") & 1 for v in (tid & zl)])
-                        V[:, p] += sx * np.where(par == 1, -coef[c], coef[c])
-                        c += 1
-                assert c == gr.c_end
-                assert gr.kact == np.bitwise_or.reduce(
-                    [classes[c0 + x].zl >> (t - R) for x in range(gr.c_begin, gr.c_end)] + [0])
-                Dk = _wht(V) if gr.kact else np.repeat(V[:, :1], 1 << R, axis=1)
+                kact = 0
+                for c in range(gr.c_begin, gr.c_end):
+                    kact |= classes[c0 + c].zl >> (t - R)
+                assert gr.kact == kact
+                Dk = np.zeros((T, 1 << R), complex)
+                if kact == 0:
+                    assert gr.r_begin == gr.r_end
+                    for c in range(gr.c_begin, gr.c_end):
+                        zt = classes[c0 + c].zl & (T - 1)
+                        Dk += np.where(par(tid & zt) == 1, -coef[c], coef[c])[:, None]
+                else:
+                    # the rows cover the group's classes, in order
+                    covered = [c for r in range(gr.r_begin, gr.r_end)
+                               for c in range(rows[r0 + r].c_begin, rows[r0 + r].c_end)]
+                    assert covered == list(range(gr.c_begin, gr.c_end))
+                    for r in range(gr.r_begin, gr.r_end):
+                        sg = np.where(par(tid & rows[r0 + r].zt) == 1, -1.0, 1.0)
+                        Dk += sg[:, None] * etab[r][None, :]
                 # amplitude j = tid + k T holds D(j ^ xl) at [tid, k]
                 D = Dk.T.reshape(-1)
                 part += D * (psi[(base + loc) ^ gr.xfar] if gr.xfar else tile[jx])
