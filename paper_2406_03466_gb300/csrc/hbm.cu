@@ -384,7 +384,7 @@ __device__ void flush_acc(const TilePass &P, Real *acc, int wps, double *rho_g, 
 // reduced matrices of its parametrised groups (as i K) into
 // rho_g[slot][group][8].  The sums run in the state's precision over one
 // warp and at most 64 tiles, then in FP64.
-template <typename Real, int R, bool kSingle, bool kReal>
+template <typename Real, int R, bool kSingle, bool kReal, int NB = 2>
 __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_slots,
                                               const typename CT<Real>::T *mats, int G,
                                               const typename CT<Real>::T *psi_src,
@@ -397,8 +397,10 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
     const int tid = threadIdx.x, T = blockDim.x, t = P.t, S = P.n_stages;
     const int lane = tid & 31, wps = T >> 5;
     const uint32_t tbytes = (uint32_t)sizeof(C) << t;
-    uint2 *tb = reinterpret_cast<uint2 *>(smem + 4 * tbytes);
-    uint4 *rec = reinterpret_cast<uint4 *>(smem + 4 * tbytes + (uint32_t)S * T * 8u);
+    // NB tile buffers (2: the next tile's copy overlaps this one's stages;
+    // 1: more blocks per SM, the copy after the tile is written back)
+    uint2 *tb = reinterpret_cast<uint2 *>(smem + 2 * NB * tbytes);
+    uint4 *rec = reinterpret_cast<uint4 *>(smem + 2 * NB * tbytes + (uint32_t)S * T * 8u);
     C *sm = reinterpret_cast<C *>(rec + 2 * S);
     Real *acc = reinterpret_cast<Real *>(sm + 4 * P.n_ops);
     build_stage_recs(P, rec);
@@ -420,11 +422,11 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
     const uint32_t n0 = bit_vectors<R>(P.nat, t, tid, nk);
     const uint32_t sh = (uint32_t)__cvta_generic_to_shared(smem);
     if (t0 >= t_end) return;
-    // psi tile of buffer j at [j tbytes], lambda tile at [(2 + j) tbytes]
+    // psi tile of buffer j at [j tbytes], lambda tile at [(NB + j) tbytes]
     auto fetch = [&](const TileCursor &c, int buf) {
         const int64_t off = ((int64_t)c.slot << n) + c.base;
         const C *sp = psi_src + off, *sl = lam + off;
-        const uint32_t dp = sh + (uint32_t)buf * tbytes, dl = dp + 2 * tbytes;
+        const uint32_t dp = sh + (uint32_t)buf * tbytes, dl = dp + NB * tbytes;
 #pragma unroll
         for (int k = 0; k < NA; ++k) {
             const uint32_t so = n0 ^ xsel<R>(k, nk), go = g0 ^ xsel<R>(k, gk);
@@ -438,7 +440,7 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
     TileCursor nxt = tile_next(P, cur);
     int mslot = -1, since = 0;
     for (int64_t tix = t0, i = 0; tix < t_end; ++tix, ++i) {
-        const int buf = (int)(i & 1);
+        const int buf = NB == 2 ? (int)(i & 1) : 0;
         if (cur.slot != mslot || since == kFlushTiles) {
             if (mslot >= 0) flush_acc<Real, kSingle>(P, acc, wps, rho_g, mslot, G);
             since = 0;
@@ -462,8 +464,8 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
         }
         cp_async_wait_all();
         __syncthreads();
-        if (tix + 1 < t_end) fetch(nxt, buf ^ 1);
-        unsigned char *tp = smem + (uint32_t)buf * tbytes, *tl = tp + 2 * tbytes;
+        if (NB == 2 && tix + 1 < t_end) fetch(nxt, buf ^ 1);
+        unsigned char *tp = smem + (uint32_t)buf * tbytes, *tl = tp + NB * tbytes;
         for (int s = S - 1; s >= 0; --s) {
             const uint2 bb = tb[s * T + tid];
             uint32_t lq[R], sq[R];
@@ -526,22 +528,27 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
             }
         }
         ++since;
+        if (NB == 1 && tix + 1 < t_end) {
+            __syncthreads();  // every thread has read its part of the tile
+            fetch(nxt, 0);
+        }
         cur = nxt;
         nxt = tile_next(P, nxt);
     }
     flush_acc<Real, kSingle>(P, acc, wps, rho_g, mslot, G);
 }
 
-template <typename Real, int R, bool kSingle, bool kReal>
-__global__ void __launch_bounds__(256, R >= 4 ? 1 : 2)
+// NB = 1: launched with 64 threads only (five blocks per SM).
+template <typename Real, int R, bool kSingle, bool kReal, int NB = 2>
+__global__ void __launch_bounds__(NB == 1 ? 64 : 256, NB == 1 ? 5 : (R >= 4 ? 1 : 2))
 k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
            const typename CT<Real>::T *mats, int G, const typename CT<Real>::T *psi_src,
            typename CT<Real>::T *psi, typename CT<Real>::T *lam, double *rho_g, int write_psi) {
     extern __shared__ __align__(16) unsigned char smem[];
     int64_t t0, t_end;
     block_range((int64_t)n_slots << P.n_tile_bits, gridDim.x, blockIdx.x, t0, t_end);
-    tile_rev_body<Real, R, kSingle, kReal>(P, n, n_slots, mats, G, psi_src, psi, lam, rho_g, t0,
-                                           t_end, smem, write_psi != 0);
+    tile_rev_body<Real, R, kSingle, kReal, NB>(P, n, n_slots, mats, G, psi_src, psi, lam, rho_g,
+                                               t0, t_end, smem, write_psi != 0);
 }
 
 // Sum of v over the block (every thread gets it); red: one double per warp.
@@ -1148,9 +1155,12 @@ uint32_t tile_fwd_smem(int c128, const TilePass &P) {
     return 2u * (csz << P.t) + (uint32_t)P.n_stages * (T * 8u + 32u) + (uint32_t)P.n_ops * 4u * csz;
 }
 
-uint32_t tile_rev_smem(int c128, const TilePass &P) {
+// Reverse passes with at least this many register stages run single-buffered.
+constexpr int kOneBufStages = 6;
+
+uint32_t tile_rev_smem(int c128, const TilePass &P, int bufs) {
     const uint32_t csz = c128 ? 16u : 8u, rsz = c128 ? 8u : 4u, T = 1u << (P.t - P.R);
-    return 4u * (csz << P.t) + (uint32_t)P.n_stages * (T * 8u + 32u) + (uint32_t)P.n_ops * 4u * csz +
+    return 2u * (uint32_t)bufs * (csz << P.t) + (uint32_t)P.n_stages * (T * 8u + 32u) + (uint32_t)P.n_ops * 4u * csz +
            (uint32_t)P.n_ops * T * rsz;
 }
 
@@ -1175,7 +1185,12 @@ cudaError_t launch_tile_fwd(int c128, const TilePass &P, int n, int n_slots, con
 cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, const void *mats,
                             int G, void *psi, void *lam, double *rho_g, int64_t max_blocks,
                             cudaStream_t st, const void *psi_src, bool write_psi) {
-    const uint32_t smem = tile_rev_smem(c128, P);
+    // passes of many stages are arithmetic-bound: one tile buffer, more
+    // blocks per SM (complex64 real single-sum passes, tiles of 2^10 at 16
+    // amplitudes per thread: 64 threads)
+    const bool one_buf = !c128 && P.R == 4 && P.t == 10 && P.all_single && pass_all_real(P) &&
+                         P.n_stages >= kOneBufStages;
+    const uint32_t smem = tile_rev_smem(c128, P, one_buf ? 1 : 2);
     const int threads = 1 << (P.t - P.R);
     HBM_DISPATCH_R(c128, P.R, {
         using C = typename CT<Real>::T;
@@ -1183,6 +1198,9 @@ cudaError_t launch_tile_rev(int c128, const TilePass &P, int n, int n_slots, con
                                                   : k_tile_rev<Real, RR, true, false>)
                               : (pass_all_real(P) ? k_tile_rev<Real, RR, false, true>
                                                   : k_tile_rev<Real, RR, false, false>);
+        if constexpr (std::is_same<Real, float>::value && RR == 4) {
+            if (one_buf) k = k_tile_rev<Real, RR, true, true, 1>;
+        }
         cudaError_t e = allow_smem(k, smem);
         if (e != cudaSuccess) return e;
         const int blocks = fill_blocks(k, threads, smem, max_blocks);

@@ -16,7 +16,7 @@ cudaError_t launch_init_states(int c128, void *states, int n, const SlotSource &
                                cudaStream_t st);
 // Shared memory of one block of the forward / reverse kernels of pass P.
 uint32_t tile_fwd_smem(int c128, const TilePass &P);
-uint32_t tile_rev_smem(int c128, const TilePass &P);
+uint32_t tile_rev_smem(int c128, const TilePass &P, int bufs = 2);
 // Forward pass P over n_slots states of n qubits (mats: [slots][G][4]).
 // src (null: states) holds the pass's input; the output goes to states.
 cudaError_t launch_tile_fwd(int c128, const TilePass &P, int n, int n_slots, const void *mats,
