@@ -54,12 +54,13 @@ __global__ void k_set_ref(C *states, int n, SlotSource src) {
 }
 
 // One forward pass over every tile of every slot.  mats: [slots][G][4].
-// One forward stage: the branch-free path when register bits 0..M-1 carry
-// real rotations in shear form (M from the stage flags), tile_ops_fwd
-// otherwise.
+// One forward stage: a branch-free path when register bits 0..M-1 carry
+// real rotations in shear form or complex matrices (M from the stage
+// flags), tile_ops_fwd otherwise.
 template <typename C, int R, bool kReal>
-__device__ __forceinline__ void stage_ops_fwd(uint32_t ops, uint32_t m, const C *sm,
+__device__ __forceinline__ void stage_ops_fwd(uint32_t ops, uint32_t flags, const C *sm,
                                               C (&a)[1 << R]) {
+    const uint32_t m = flags & 15u;
     if constexpr (R >= 4) {
         if (m == 4) return tile_ops_fwd_rot<C, R, 0, 4>(ops, sm, a);
     }
@@ -68,6 +69,17 @@ __device__ __forceinline__ void stage_ops_fwd(uint32_t ops, uint32_t m, const C 
     }
     if (m == 2) return tile_ops_fwd_rot<C, R, 0, 2>(ops, sm, a);
     if (m == 1) return tile_ops_fwd_rot<C, R, 0, 1>(ops, sm, a);
+    if constexpr (!kReal) {
+        const uint32_t mc = (flags >> 8) & 15u;
+        if constexpr (R >= 4) {
+            if (mc == 4) return tile_ops_fwd_cplx<C, R, 0, 4>(ops, sm, a);
+        }
+        if constexpr (R >= 3) {
+            if (mc == 3) return tile_ops_fwd_cplx<C, R, 0, 3>(ops, sm, a);
+        }
+        if (mc == 2) return tile_ops_fwd_cplx<C, R, 0, 2>(ops, sm, a);
+        if (mc == 1) return tile_ops_fwd_cplx<C, R, 0, 1>(ops, sm, a);
+    }
     tile_ops_fwd<C, R, 0, kReal>(ops, sm, a);
 }
 
@@ -121,8 +133,8 @@ __device__ __forceinline__ void tile_fwd_body(const TilePass &P, int n, int n_sl
             __syncthreads();
             for (int u = tid; u < P.n_ops; u += T)
                 if ((P.real_mask >> u) & 1ull) stage_shears(sm + 4 * u);
-            if constexpr (kReal && std::is_same<C, float2>::value) {
-                __syncthreads();  // the rotation path's stage flags
+            if constexpr (std::is_same<C, float2>::value) {
+                __syncthreads();  // the branch-free paths' stage flags
                 set_stage_flags(P, rec, sm);
             }
             mslot = cur.slot;
@@ -138,10 +150,9 @@ __device__ __forceinline__ void tile_fwd_body(const TilePass &P, int n, int n_sl
             C a[NA];
 #pragma unroll
             for (int r = 0; r < NA; ++r) a[r] = *reinterpret_cast<const C *>(tile + (bb.x ^ xsel<R>(r, lq)));
-            // complex64 passes of real matrices: the branch-free rotation path
-            // where the stage allows
-            if constexpr (kReal && std::is_same<C, float2>::value) {
-                stage_ops_fwd<C, R, kReal>(ops, rec[2 * s + 1].w & 15u, sm, a);
+            // complex64: the branch-free paths where the stage allows
+            if constexpr (std::is_same<C, float2>::value) {
+                stage_ops_fwd<C, R, kReal>(ops, rec[2 * s + 1].w, sm, a);
             } else {
                 tile_ops_fwd<C, R, 0, kReal>(ops, sm, a);
             }

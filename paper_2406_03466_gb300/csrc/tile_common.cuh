@@ -229,29 +229,49 @@ __device__ __forceinline__ void tile_ops_fwd_rot(uint32_t ops, const C *sm, C (&
     }
 }
 
+// The forward stage ops when register bits 0..M-1 carry complex matrices
+// and the others carry no op (stage flags, bits 8-11): tile_ops_fwd's
+// complex arithmetic without its per-op branches.
+template <typename C, int R, int I, int M>
+__device__ __forceinline__ void tile_ops_fwd_cplx(uint32_t ops, const C *sm, C (&a)[1 << R]) {
+    if constexpr (I < M) {
+        C m0, m1, m2, m3;
+        load_mat(sm, (int)((ops >> (8 * I)) & 63u) - 1, m0, m1, m2, m3);
+        u1_bit<C, R, I>(a, m0, m1, m2, m3);
+        tile_ops_fwd_cplx<C, R, I + 1, M>(ops, sm, a);
+    }
+}
+
 // Stage flags, the w word of a stage's second record, set for the staged
 // matrices of the current slot.  Bits 0-3: M > 0 when register bits
 // 0..M-1 carry ops with real matrices in shear form (rotations with c > 0)
 // and the other bits none (the forward's branch-free path); bits 4-7: the
 // same M when those ops are moreover parametrised with the single Ry sum
-// (fmode 1; the reverse's); 0 otherwise.  Called by every thread once the
-// slot's shear forms are in shared memory; visible after the next barrier.
+// (fmode 1; the reverse's); bits 8-11: M when register bits 0..M-1 carry
+// ops with complex matrices and the other bits none; 0 otherwise.  Called
+// by every thread once the slot's shear forms are in shared memory;
+// visible after the next barrier.
 template <typename C>
 __device__ __forceinline__ void set_stage_flags(const TilePass &P, uint4 *rec, const C *sm) {
     for (int s = threadIdx.x; s < P.n_stages; s += blockDim.x) {
         const uint32_t ops = rec[2 * s].x, modes = rec[2 * s + 1].y;
-        int m = 0;
-        bool single = true;
+        int m = 0, mc = 0;
+        bool single = true, rot = true, cplx = true;
         for (int i = 0; i < P.R; ++i) {
             const uint32_t ob = (ops >> (8 * i)) & 0xffu;
             if (!ob) break;
-            if (!(ob & 64u) || sm[4 * ((int)(ob & 63u) - 1) + 2].y == 0) break;
-            single = single && (ob & 128u) && ((modes >> (8 * i)) & 3u) == 1u;
-            m = i + 1;
+            rot = rot && (ob & 64u) && sm[4 * ((int)(ob & 63u) - 1) + 2].y != 0;
+            cplx = cplx && !(ob & 64u);
+            if (rot) {
+                single = single && (ob & 128u) && ((modes >> (8 * i)) & 3u) == 1u;
+                m = i + 1;
+            }
+            if (cplx) mc = i + 1;
         }
         // the bits above M must carry no op
         if (m > 0 && m < 4 && (ops >> (8 * m)) != 0u) m = 0;
-        rec[2 * s + 1].w = (uint32_t)m | (single ? (uint32_t)m << 4 : 0u);
+        if (mc > 0 && mc < 4 && (ops >> (8 * mc)) != 0u) mc = 0;
+        rec[2 * s + 1].w = (uint32_t)m | (single ? (uint32_t)m << 4 : 0u) | ((uint32_t)mc << 8);
     }
 }
 
