@@ -324,3 +324,27 @@ def test_mcvqe22_full_depth_against_oracle(sv):
     close(e_.cpu().numpy(), E, TOL["c64"]["E"])
     close(l_.cpu().numpy()[0], L, TOL["c64"]["E"])
     close(g_.cpu().numpy()[ks], g, TOL["c64"]["G"])
+
+
+@pytest.mark.parametrize("tile_bits", [9, 10])
+def test_stage_paths_with_mixed_rotation_forms(sv, tile_bits):
+    """Tile passes take a branch-free path for stages whose register bits
+    0..M-1 all carry real rotations in shear form (cos(angle/2) > 0) and the
+    generic path otherwise.  Angles beyond pi (cos < 0), exactly 0 and
+    exactly pi put both kinds of stages, and stages with fewer ops, into the
+    same passes; the adjoint at every checkpoint interval and the energies
+    must still match the oracle."""
+    w = wl.mcvqe(12, 4, "nn+nnn", n_refs=3)
+    theta = np.array(w.theta)
+    rng = np.random.default_rng(5)
+    theta[rng.choice(w.n_params, 12, replace=False)] += 2 * np.pi  # cos(angle / 2) < 0
+    theta[rng.choice(w.n_params, 4, replace=False)] = 0.0
+    theta[rng.choice(w.n_params, 3, replace=False)] = np.pi
+    w.theta = theta
+    L, E, g = oracle.grad_param_shift(w)
+    prob = sv.Problem.from_spec(w, "c64", opts=sv.plan_opts(reg_bits=4, tile_bits=tile_bits))
+    for every in (1, 2, 0):
+        l_, e_, g_ = sv.sv_grad_adjoint(prob, theta_of(w), checkpoint_every=every)
+        close(e_.cpu().numpy(), E, TOL["c64"]["E"])
+        close(l_.cpu().numpy()[0], L, TOL["c64"]["E"])
+        close(g_.cpu().numpy()[: w.n_params], g, TOL["c64"]["G"])
