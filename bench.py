@@ -45,6 +45,37 @@ sys.path.insert(0, ROOT)
 import workloads as wl  # noqa: E402
 
 METRIC = "gradients/sec & shifted circuits/sec, batched/adjoint vs plain; % HBM roofline"
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# 28-qubit gradient's reverse sweep, the 16 k_tile_rev launches of one
+# adjoint at tile shape (10, 4) with stored states every second pass, summed
+# from one ncu capture of `bench.py --tile-shape 10,4 --steps 1 --warmup 1
+# --no-extras`.  It is reported only while the library sources hash to the
+# digest they had when it was taken (a changed kernel gives null).
+REVERSE_TRAFFIC = {"workload": "mcvqe28", "tile_bits": 10, "reg_bits": 4, "checkpoint_every": 2,
+                   "csrc_sha256": None, "bytes": None}
+
+
+def csrc_digest() -> str:
+    """SHA-256 over the library's C++/CUDA sources, in name order."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2406_03466_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".cpp", ".h")):
+            h.update(name.encode())
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
+def reverse_traffic(w, tile_bits, reg_bits, every):
+    """The captured reverse-sweep traffic when it applies to this run, else None."""
+    t = REVERSE_TRAFFIC
+    if t["bytes"] is None or w.name != t["workload"] or (tile_bits, reg_bits) != (
+            t["tile_bits"], t["reg_bits"]) or every != t["checkpoint_every"]:
+        return None
+    return t["bytes"] if csrc_digest() == t["csrc_sha256"] else None
 WORKLOAD_MCVQE8 = ("mcvqe8: multi-contracted VQE gradient, 8 qubits, 4 layers Ry + CNOT ladder "
             "(32 params), 128-term Eq. 2 Hamiltonian, 9 references, 585 shifted circuits")
 L2_FLUSH_BYTES = 256 << 20   # larger than the 126.5 MiB L2
@@ -254,11 +285,13 @@ def forward_passes_roofline(sv, w, dev, flush, stream, reps=5, opts=None):
             "forward_ms": t * 1e3, "bytes_per_forward": nbytes, "peak_source": src}
 
 
-def adjoint_phases(sv, w, prob, theta, out, info, flush, stream, reps, step=None):
+def adjoint_phases(sv, w, prob, theta, out, info, flush, stream, reps, step=None, reg_bits=None):
     """Per-phase CUDA-event times of the device-memory adjoint (the library's
     phase timer records events on the call's stream), each step after an L2
     flush; the reverse tile passes are the dominant kernel: per pass they
-    read and write psi and lambda of every state."""
+    read psi (or its stored state) and lambda of every state and write
+    lambda, and psi unless the next pass restarts from a stored state (the
+    library reports the bytes of the passes it launched)."""
     import torch
     sv.sv_phase_timing(True)
     ph = {"forward_ms": 0.0, "h_ms": 0.0, "reverse_ms": 0.0}
@@ -275,19 +308,23 @@ def adjoint_phases(sv, w, prob, theta, out, info, flush, stream, reps, step=None
     torch.cuda.synchronize()
     n, I = w.n_qubits, w.n_instances
     state = I * (8 << n)
-    nbytes = 4 * info["n_passes"] * state
+    last = sv.sv_last_adjoint_info()
+    nbytes = last["reverse_bytes"]
     peak, src = measured_hbm_gbs()
     achieved = nbytes / (ph["reverse_ms"] * 1e-3) / 1e9
     # the gradient's own forward passes (the same relabeling plan), 16 B per
     # amplitude per pass; the phase also holds |ref>, the group matrices and
     # the stored checkpoint copies
     fwd_bytes = 2 * info["n_passes"] * state
+    traffic = reverse_traffic(w, info["tile_bits"], reg_bits, last["checkpoint_every"])
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic,
             "kernel": f"k_tile_rev x {info['n_passes']} reverse tile passes of "
                       f"2^{info['tile_bits']} amplitudes ({w.name}: {I} states of {n} qubits; "
-                      "psi and lambda read and written per pass)",
-            "reverse_ms": ph["reverse_ms"], "bytes_per_reverse": nbytes, "peak_source": src,
+                      "psi and lambda read and lambda written per pass, psi written "
+                      "unless the next pass restarts from a stored state)",
+            "reverse_ms": ph["reverse_ms"], "bytes_per_reverse": nbytes,
+            "checkpoint_every": last["checkpoint_every"], "peak_source": src,
             "phases_ms": ph,
             "forward_phase_frac": fwd_bytes / (ph["forward_ms"] * 1e-3) / 1e9 / peak}
 
@@ -398,7 +435,7 @@ def run_device_memory(args, sv, dev, stream, dist, world, rank):
               "clocks": clk, "wall_s_timed_region": t_wall}
     if rank == 0:
         result["roofline"] = adjoint_phases(sv, w, prob, theta, out, info, flush, stream,
-                                            reps=2 if w.n_qubits > 24 else 5)
+                                            reps=2 if w.n_qubits > 24 else 5, reg_bits=R)
         result["roofline_forward"] = forward_passes_roofline(sv, w, dev, flush, stream,
                                                              reps=3 if w.n_qubits > 24 else 5,
                                                              opts=opts)

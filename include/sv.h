@@ -418,6 +418,17 @@ sv_status sv_h_plan_info(const sv_pauli_sum *observable, sv_dtype dtype, int32_t
 sv_status sv_phase_timing(int32_t on);
 sv_status sv_last_phase_ms(float *forward_ms, float *h_ms, float *reverse_ms);
 
+/* What the last adjoint gradient of states in device memory (sv_grad_adjoint,
+ * sv_grad_adjoint_host or sv_grad_ddcl on the tile path of the current
+ * device) did: the checkpoint interval it used (1, 2 or 4) and the
+ * algorithmic bytes of its reverse tile passes (per pass psi, or its stored
+ * state, and lambda read, lambda written, and psi written unless the next
+ * reverse pass restarts from a stored state; summed over the call's chunks
+ * of instances).  Both are 0 after an adjoint that ran on chip.  Host-only:
+ * reads values the host recorded when it launched the passes.  Any
+ * out-pointer may be NULL. */
+sv_status sv_last_adjoint_info(int32_t *checkpoint_every, int64_t *reverse_bytes);
+
 /* ------------------------------------------------------------- autotune */
 
 /* Times the launch shapes (register bits 1..4, 32..512 threads per block) of

@@ -85,7 +85,7 @@ EXPORTED = ("sv_alloc", "sv_free", "sv_state_info", "sv_apply_circuit_batch",
             "sv_grad_adjoint_multi", "sv_grad_ddcl", "sv_grad_ddcl_param_shift",
             "sv_grad_param_shift_host", "sv_grad_adjoint_host", "sv_param_shift_energies_range", "sv_sample",
             "sv_param_shift_combine",
-            "sv_last_phase_ms", "sv_status_string",
+            "sv_last_phase_ms", "sv_last_adjoint_info", "sv_status_string",
             "sv_last_error",
             "sv_sync_status", "sv_shutdown", "sv_version")
 
@@ -125,6 +125,7 @@ def _load():
     lib.sv_h_plan_info.argtypes = [P(sv_pauli_sum), I32, P(I32), P(I32)]
     lib.sv_phase_timing.argtypes = [I32]
     lib.sv_last_phase_ms.argtypes = [P(ctypes.c_float)] * 3
+    lib.sv_last_adjoint_info.argtypes = [P(ctypes.c_int32), P(ctypes.c_int64)]
     lib.sv_status_string.argtypes = [I32]
     lib.sv_status_string.restype = ctypes.c_char_p
     lib.sv_last_error.restype = ctypes.c_char_p
@@ -581,6 +582,16 @@ def sv_last_phase_ms() -> dict:
     vals = [ctypes.c_float() for _ in range(3)]
     _check(_lib.sv_last_phase_ms(*[ctypes.byref(v) for v in vals]), "sv_last_phase_ms")
     return {"forward_ms": vals[0].value, "h_ms": vals[1].value, "reverse_ms": vals[2].value}
+
+
+def sv_last_adjoint_info() -> dict:
+    """The checkpoint interval and the algorithmic bytes of the reverse tile
+    passes of the last device-memory adjoint on the current device (both 0
+    after an on-chip adjoint)."""
+    every, nbytes = ctypes.c_int32(), ctypes.c_int64()
+    _check(_lib.sv_last_adjoint_info(ctypes.byref(every), ctypes.byref(nbytes)),
+           "sv_last_adjoint_info")
+    return {"checkpoint_every": every.value, "reverse_bytes": nbytes.value}
 
 
 def sv_status_string(status: int) -> str:

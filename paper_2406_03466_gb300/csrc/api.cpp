@@ -119,6 +119,10 @@ struct DeviceCtx {
     bool timing = false;
     std::vector<cudaEvent_t> phase_ev;
     int phase_used = 0;
+    // The last adjoint of states in device memory: its checkpoint interval and
+    // the algorithmic bytes of its reverse tile passes.
+    int last_every = 0;
+    int64_t last_rev_bytes = 0;
     // Uneven batches: one instantiated graph per configuration, and the
     // stream the captures run on.
     std::unordered_map<uint64_t, std::unique_ptr<struct MultiGraph>> graphs;
@@ -816,6 +820,8 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
                         double *grad_out, int every, cudaStream_t st,
                         const double *ddcl_target = nullptr, const TileCfg *forced = nullptr) {
     ctx->phase_used = 0;
+    ctx->last_every = 0;
+    ctx->last_rev_bytes = 0;
     const sv_dtype dt = p->dtype;
     const int c128 = dt == SV_C128, n = p->circuit->n_qubits, I = p->n_instances;
     const int P = p->circuit->n_params, Pp = P > 0 ? P : 1;
@@ -880,6 +886,7 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
             }
     }
     const int ncp = npass > 1 ? (npass - 1) / every : 0;
+    ctx->last_every = every;
     const size_t per = per_instance(every);
     int64_t chunk = (int64_t)(budget / (per + 2048));
     if (chunk < 1) return fail(SV_ERR_OOM, "psi, lambda and the stored states do not fit");
@@ -945,6 +952,8 @@ sv_status tiles_adjoint(DeviceCtx *ctx, const sv_problem *p, const double *theta
             e = launch_tile_rev(c128, tp, n, src.n_slots, mats, G, psi, lam, rho,
                                 tile_blocks(ctx, tiles), st, psi_in, write_psi);
             if (e != cudaSuccess) return cuda_fail(e, "reverse tile pass");
+            // psi (or its stored state) and lambda read, lambda (and psi) written
+            ctx->last_rev_bytes += (int64_t)cb * (write_psi ? 4 : 3);
         }
         phase_mark(ctx, st);
         e = launch_group_grads(c128, pe->dev, src, rho, cs, Es + c0, Gs + (size_t)c0 * Pp, st);
@@ -1764,6 +1773,8 @@ sv_status adjoint_locked(DeviceCtx *ctx, const sv_problem *p, const double *thet
                          double *grad_out, int checkpoint_every, cudaStream_t st) {
     sv_status s = SV_OK;
     const int P = p->circuit->n_params, I = p->n_instances;
+    ctx->last_every = 0;  // on chip unless the tile path records its own
+    ctx->last_rev_bytes = 0;
     if (wants_tiles(p->circuit->n_qubits, p->dtype, p->opts))
         return tiles_adjoint(ctx, p, theta, weights, energy_out, loss_out, grad_out,
                              checkpoint_every, st);
@@ -2351,6 +2362,15 @@ sv_status sv_last_phase_ms(float *forward_ms, float *h_ms, float *reverse_ms) {
     if (forward_ms) *forward_ms = ph[0];
     if (h_ms) *h_ms = ph[1];
     if (reverse_ms) *reverse_ms = ph[2];
+    return SV_OK;
+}
+
+sv_status sv_last_adjoint_info(int32_t *checkpoint_every, int64_t *reverse_bytes) {
+    DeviceCtx *ctx = context();
+    if (!ctx) return fail(SV_ERR_CUDA, "no CUDA device");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (checkpoint_every) *checkpoint_every = ctx->last_every;
+    if (reverse_bytes) *reverse_bytes = ctx->last_rev_bytes;
     return SV_OK;
 }
 

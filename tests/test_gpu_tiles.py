@@ -348,3 +348,28 @@ def test_stage_paths_with_mixed_rotation_forms(sv, tile_bits):
         close(e_.cpu().numpy(), E, TOL["c64"]["E"])
         close(l_.cpu().numpy()[0], L, TOL["c64"]["E"])
         close(g_.cpu().numpy()[: w.n_params], g, TOL["c64"]["G"])
+
+
+def test_last_adjoint_info_counts_reverse_bytes(sv):
+    """sv_last_adjoint_info reports the checkpoint interval the tile adjoint
+    used and the algorithmic bytes of its reverse passes: per pass psi (or
+    its stored state) and lambda read and lambda written, psi written unless
+    the next pass restarts from a stored state; zeros after an on-chip
+    adjoint."""
+    w = wl.mcvqe(12, 8, "nn+nnn", n_refs=3)
+    opts = sv.plan_opts(reg_bits=4, tile_bits=9)
+    prob = sv.Problem.from_spec(w, "c64", opts=opts)
+    d = 0 if w.inputs is None else 1
+    npass = sv.sv_plan_info(sv.Circuit(w.n_qubits, w.gates, w.n_params, d), "c64",
+                            opts)["n_passes"]
+    assert npass >= 5
+    state = w.n_instances * (8 << w.n_qubits)
+    for every in (1, 2, 4):
+        sv.sv_grad_adjoint(prob, theta_of(w), checkpoint_every=every)
+        got = sv.sv_last_adjoint_info()
+        writes = sum(1 for i in range(npass) if i > 0 and not (i % every == 0 and i < npass))
+        assert got["checkpoint_every"] == every
+        assert got["reverse_bytes"] == state * (3 * npass + writes)
+    small = sv.Problem.from_spec(wl.vqe_random_pauli(4, 2, 10), "c64")
+    sv.sv_grad_adjoint(small, theta_of(wl.vqe_random_pauli(4, 2, 10)))
+    assert sv.sv_last_adjoint_info() == {"checkpoint_every": 0, "reverse_bytes": 0}
