@@ -353,6 +353,40 @@ __device__ __forceinline__ void stage_ops_rev(uint32_t ops, uint32_t modes, uint
     tile_ops_rev<C, Real, R, R - 1, NV, true, kReal>(ops, modes, sm, a, al, k);
 }
 
+// tile_ops_rev's four-sum complex path when register bits 0..M-1 all carry
+// parametrised complex matrices (stage flags, bits 12-15), without its
+// per-op branches.
+template <typename C, typename Real, int R, int I, int NV>
+__device__ __forceinline__ void tile_ops_rev_cplx(uint32_t ops, const C *sm, C (&a)[1 << R],
+                                                  C (&al)[1 << R], Real (&k)[NV]) {
+    if constexpr (I >= 0) {
+        kmat_bit<C, Real, R, I>(a, al, &k[4 * I]);
+        C m0, m1, m2, m3;
+        load_mat(sm, (int)((ops >> (8 * I)) & 63u) - 1, m0, m1, m2, m3);
+        u1_bit<C, R, I>(a, m0, m1, m2, m3);
+        u1_bit<C, R, I>(al, m0, m1, m2, m3);
+        tile_ops_rev_cplx<C, Real, R, I - 1, NV>(ops, sm, a, al, k);
+    }
+}
+
+// One reverse stage of four-sum ops: the branch-free complex path when
+// register bits 0..M-1 carry parametrised complex matrices, tile_ops_rev
+// otherwise.
+template <typename C, typename Real, int R, int NV, bool kReal>
+__device__ __forceinline__ void stage_ops_rev4(uint32_t ops, uint32_t modes, uint32_t m,
+                                               const C *sm, C (&a)[1 << R], C (&al)[1 << R],
+                                               Real (&k)[NV]) {
+    if constexpr (R >= 4) {
+        if (m == 4) return tile_ops_rev_cplx<C, Real, R, 3, NV>(ops, sm, a, al, k);
+    }
+    if constexpr (R >= 3) {
+        if (m == 3) return tile_ops_rev_cplx<C, Real, R, 2, NV>(ops, sm, a, al, k);
+    }
+    if (m == 2) return tile_ops_rev_cplx<C, Real, R, 1, NV>(ops, sm, a, al, k);
+    if (m == 1) return tile_ops_rev_cplx<C, Real, R, 0, NV>(ops, sm, a, al, k);
+    tile_ops_rev<C, Real, R, R - 1, NV, false, kReal>(ops, modes, sm, a, al, k);
+}
+
 // Adds the block's sums of slot b (FP64 over warps and lane quads), as i K
 // in reduced-matrix form, to rho_g[b][group][8] and clears them.  Called by
 // every thread.
@@ -467,8 +501,8 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
             __syncthreads();
             for (int u = tid; u < P.n_ops; u += T)
                 if ((P.real_mask >> u) & 1ull) stage_shears(sm + 4 * u);
-            if constexpr (kSingle && kReal && std::is_same<C, float2>::value) {
-                __syncthreads();  // the rotation path's stage flags
+            if constexpr (std::is_same<C, float2>::value && kSingle == kReal) {
+                __syncthreads();  // the branch-free paths' stage flags
                 set_stage_flags(P, rec, sm);
             }
             mslot = cur.slot;
@@ -498,6 +532,9 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
             if constexpr (kSingle && kReal && std::is_same<C, float2>::value) {
                 stage_ops_rev<C, Real, R, NV, kReal>(ops, modes, (rec[2 * s + 1].w >> 4) & 15u, sm, a,
                                                      al, kk);
+            } else if constexpr (!kSingle && !kReal && std::is_same<C, float2>::value) {
+                stage_ops_rev4<C, Real, R, NV, kReal>(ops, modes, (rec[2 * s + 1].w >> 12) & 15u, sm,
+                                                      a, al, kk);
             } else {
                 tile_ops_rev<C, Real, R, R - 1, NV, kSingle, kReal>(ops, modes, sm, a, al, kk);
             }

@@ -248,15 +248,16 @@ __device__ __forceinline__ void tile_ops_fwd_cplx(uint32_t ops, const C *sm, C (
 // and the other bits none (the forward's branch-free path); bits 4-7: the
 // same M when those ops are moreover parametrised with the single Ry sum
 // (fmode 1; the reverse's); bits 8-11: M when register bits 0..M-1 carry
-// ops with complex matrices and the other bits none; 0 otherwise.  Called
-// by every thread once the slot's shear forms are in shared memory;
-// visible after the next barrier.
+// ops with complex matrices and the other bits none; bits 12-15: that M
+// when those complex ops are moreover all parametrised (the reverse's
+// four-sum path); 0 otherwise.  Called by every thread once the slot's
+// shear forms are in shared memory; visible after the next barrier.
 template <typename C>
 __device__ __forceinline__ void set_stage_flags(const TilePass &P, uint4 *rec, const C *sm) {
     for (int s = threadIdx.x; s < P.n_stages; s += blockDim.x) {
         const uint32_t ops = rec[2 * s].x, modes = rec[2 * s + 1].y;
         int m = 0, mc = 0;
-        bool single = true, rot = true, cplx = true;
+        bool single = true, rot = true, cplx = true, cpar = true;
         for (int i = 0; i < P.R; ++i) {
             const uint32_t ob = (ops >> (8 * i)) & 0xffu;
             if (!ob) break;
@@ -266,12 +267,16 @@ __device__ __forceinline__ void set_stage_flags(const TilePass &P, uint4 *rec, c
                 single = single && (ob & 128u) && ((modes >> (8 * i)) & 3u) == 1u;
                 m = i + 1;
             }
-            if (cplx) mc = i + 1;
+            if (cplx) {
+                cpar = cpar && (ob & 128u);
+                mc = i + 1;
+            }
         }
         // the bits above M must carry no op
         if (m > 0 && m < 4 && (ops >> (8 * m)) != 0u) m = 0;
         if (mc > 0 && mc < 4 && (ops >> (8 * mc)) != 0u) mc = 0;
-        rec[2 * s + 1].w = (uint32_t)m | (single ? (uint32_t)m << 4 : 0u) | ((uint32_t)mc << 8);
+        rec[2 * s + 1].w = (uint32_t)m | (single ? (uint32_t)m << 4 : 0u) | ((uint32_t)mc << 8) |
+                           (cpar ? (uint32_t)mc << 12 : 0u);
     }
 }
 
