@@ -318,10 +318,10 @@ __device__ __forceinline__ void tile_ops_rev(uint32_t ops, uint32_t modes, const
     }
 }
 
-// tile_ops_rev when every register bit carries a parametrised real
-// rotation in shear form with the single Ry sum (stage flag 2): the same
-// arithmetic without its per-op branches, so the compiler can overlap one
-// op's dependent FMA chains with the next op's.
+// tile_ops_rev for register bits I..0 that all carry parametrised real
+// rotations in shear form with the single Ry sum (stage flags, bits 4-7):
+// the same arithmetic without its per-op branches, so the compiler can
+// overlap one op's dependent FMA chains with the next op's.
 template <typename C, typename Real, int R, int I, int NV>
 __device__ __forceinline__ void tile_ops_rev_rot(uint32_t ops, const C *sm, C (&a)[1 << R],
                                                  C (&al)[1 << R], Real (&k)[NV]) {
@@ -586,7 +586,7 @@ __device__ __forceinline__ void tile_rev_body(const TilePass &P, int n, int n_sl
     flush_acc<Real, kSingle>(P, acc, wps, rho_g, mslot, G);
 }
 
-// NB = 1: launched with 64 threads only (five blocks per SM).
+// NB = 1: launched with 64 threads only (at least five blocks per SM).
 template <typename Real, int R, bool kSingle, bool kReal, int NB = 2>
 __global__ void __launch_bounds__(NB == 1 ? 64 : 256, NB == 1 ? 5 : (R >= 4 ? 1 : 2))
 k_tile_rev(const __grid_constant__ TilePass P, int n, int n_slots,
