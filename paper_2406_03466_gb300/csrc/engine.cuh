@@ -364,9 +364,26 @@ __device__ __forceinline__ void bit_ops_fwd(const Program &p, const Stage *sg, c
     }
 }
 
+// bit_ops_fwd for a stage whose register bits each carry exactly one real
+// group (sorted = 2): no loops or branches between the ops, so one op's FMA
+// chains can overlap the next op's.
+template <typename C, int R, int I>
+__device__ __forceinline__ void bit_ops_fwd_one_real(const Program &p, const Stage *sg,
+                                                     const C *mats, C (&a)[1 << R]) {
+    if constexpr (I < R) {
+        const C *m = mats + 4 * p.ops[sg->op_begin + sg->bit_begin[I]].group;
+        u1r_bit<C, decltype(m[0].x), R, I>(a, m[0].x, m[1].x, m[2].x, m[3].x);
+        bit_ops_fwd_one_real<C, R, I + 1>(p, sg, mats, a);
+    }
+}
+
 template <typename C, int R>
 __device__ __forceinline__ void apply_stage_ops(const Program &p, const Stage *sg, const C *mats,
                                                 C (&a)[1 << R], uint32_t lg, const int (&qq)[R]) {
+    if (sg->sorted == 2) {
+        bit_ops_fwd_one_real<C, R, 0>(p, sg, mats, a);
+        return;
+    }
     if (sg->sorted) {
         bit_ops_fwd<C, R, 0>(p, sg, mats, a);
         return;

@@ -142,6 +142,13 @@ void stage_lops(const std::vector<LOp> &lops, const std::vector<int> &pos, int t
                 st.bit_begin[i] = k;
             }
             st.bit_begin[kRMax] = (int)sops.size();
+            // every register bit carries exactly one group, all real: the
+            // kernels' straight-line path
+            bool one_real = true;
+            for (int i = 0; i < R && one_real; ++i)
+                one_real = st.bit_begin[i + 1] - st.bit_begin[i] == 1 &&
+                           P->groups[(size_t)sops[(size_t)st.bit_begin[i]].group].real;
+            if (one_real) st.sorted = 2;
         }
         st.op_begin = (int)P->ops.size();
         for (const Op &o : sops) P->ops.push_back(o);

@@ -61,7 +61,8 @@ struct Stage {
     uint32_t stt[kNMax];
     // sorted = 1: the stage's ops are all fused groups, ordered by register
     // bit (ops on different bits commute), and bit i owns the ops
-    // [op_begin + bit_begin[i], op_begin + bit_begin[i + 1]).
+    // [op_begin + bit_begin[i], op_begin + bit_begin[i + 1]); sorted = 2:
+    // moreover every register bit owns exactly one group, and all are real.
     int32_t sorted;
     int32_t bit_begin[kRMax + 1];
 };
