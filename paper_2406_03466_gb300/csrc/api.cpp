@@ -314,6 +314,8 @@ sv_status get_obs(DeviceCtx *ctx, const sv_pauli_sum &h, int n, sv_dtype dt, Obs
     unsigned char *base = (unsigned char *)e->buf.ptr;
     e->dev.n_tgroups = (int)e->host.tgroups.size();
     e->dev.n_terms = (int)e->host.terms.size();
+    e->dev.real = 1;
+    for (const Term &tm : e->host.terms) e->dev.real &= (tm.phase & 1) == 0;
     e->dev.tgroups = (const TermGroup *)(base + o_g);
     e->dev.terms = (const Term *)(base + o_t);
     const int64_t entries = (int64_t(1) << n) * e->dev.n_tgroups;

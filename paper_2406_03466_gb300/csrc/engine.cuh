@@ -518,7 +518,9 @@ __device__ double expect_partial(const Observable &o, const typename CT<Real>::T
 // D_g(j) = sum_{t in g} c_t i^{phase_t} (-1)^{|j & z_t|} (table `dtab`,
 // [groups][2^n] complex in natural index order), E = sum_g sum_j
 // Re(conj(psi_{j^x}) psi_j D_g(j)).
-template <typename Real, int R>
+// kRealD: every D_g is real (a real observable): the imaginary parts are
+// skipped.
+template <typename Real, int R, bool kRealD = false>
 __device__ double expect_table(const Observable &o, const typename CT<Real>::T *dtab,
                                const typename CT<Real>::T *st, int tid, int sh, int w, int dim) {
     using C = typename CT<Real>::T;
@@ -555,8 +557,12 @@ __device__ double expect_table(const Observable &o, const typename CT<Real>::T *
             const C px = st[s0 ^ xsel<R>(k, v) ^ sx];
             const C d = D[(size_t)k << sh];  // shared memory when staged, else global
             const Real wr = fmaR(px.x, pj[k].x, px.y * pj[k].y);
-            const Real wi = fmaR(px.x, pj[k].y, -px.y * pj[k].x);
-            run[k] = fmaR(wr, d.x, fmaR(-wi, d.y, run[k]));
+            if constexpr (kRealD) {
+                run[k] = fmaR(wr, d.x, run[k]);
+            } else {
+                const Real wi = fmaR(px.x, pj[k].y, -px.y * pj[k].x);
+                run[k] = fmaR(wr, d.x, fmaR(-wi, d.y, run[k]));
+            }
         }
         if ((g + 1) % kRun == 0) fold();
     }

@@ -169,6 +169,8 @@ extern "C" sv_status sv_grad_param_shift_noalloc(const sv_problem *p, const doub
     Observable obs{};
     obs.n_tgroups = (int)ho.tgroups.size();
     obs.n_terms = (int)ho.terms.size();
+    obs.real = 1;
+    for (const Term &tm : ho.terms) obs.real &= (tm.phase & 1) == 0;
     obs.tgroups = (const TermGroup *)(base + o_tg);
     obs.terms = (const Term *)(base + o_tm);
     double *E = (double *)(base + o_E);

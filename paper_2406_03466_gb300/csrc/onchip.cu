@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(512) k_energy(Program p, Observable o, SlotSou
     double e;
     if (kMode > 0 && bc.n16[6]) {  // diagonal tables staged in shared memory
         const C *tab = reinterpret_cast<const C *>(smem + bc.base + bc.off[6]);
-        e = expect_table<Real, R>(o, tab, st, tid, shb, p.swz_bits, 1 << n);
+        e = o.real ? expect_table<Real, R, true>(o, tab, st, tid, shb, p.swz_bits, 1 << n)
+                   : expect_table<Real, R>(o, tab, st, tid, shb, p.swz_bits, 1 << n);
     } else if (dtab) {
         e = expect_table<Real, R>(o, dtab, st, tid, shb, p.swz_bits, 1 << n);
     } else {

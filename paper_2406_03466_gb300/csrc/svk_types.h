@@ -148,6 +148,7 @@ struct Program {
 
 struct Observable {
     int32_t n_tgroups, n_terms;
+    int32_t real, pad;  // real: every c_t i^phase_t is real (no Y-parity imaginary parts)
     const TermGroup *tgroups;
     const Term *terms;
 };
