@@ -1813,7 +1813,7 @@ sv_status adjoint_locked(DeviceCtx *ctx, const sv_problem *p, const double *thet
     src.input_stride = p->input_stride;
     const CostSource cs = cost_of(p, weights);
     cudaError_t e = launch_onchip_adjoint(p->dtype == SV_C128, sh, plan->dev, obs->dev, src, cs,
-                                          G, E, st, &bc);
+                                          G, E, st, &bc, obs->dtab.ptr);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
     e = launch_adjoint_combine(G, E, I, P, cs, energy_out, loss_out, grad_out, st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint combine launch");
@@ -2264,7 +2264,7 @@ sv_status sv_autotune(const sv_problem *p, const double *theta, int32_t kinds,
                                ? launch_onchip_energy(p->dtype == SV_C128, sh, plan->dev, obs->dev,
                                                       src, E, st, dt, nullptr, &bc)
                                : launch_onchip_adjoint(p->dtype == SV_C128, sh, plan->dev, obs->dev,
-                                                       src, cs, G, E2, st, &bc);
+                                                       src, cs, G, E2, st, &bc, obs->dtab.ptr);
                 };
                 if (run() != cudaSuccess) {
                     cudaGetLastError();

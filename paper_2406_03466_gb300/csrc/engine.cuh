@@ -612,6 +612,48 @@ __device__ double apply_h(const Observable &o, const typename CT<Real>::T *psi,
     return e;
 }
 
+// apply_h from the observable's diagonal tables `dtab` ([groups][2^n]
+// complex, natural index order; device memory, read through the cache):
+// lambda_j = sum_g D_g(j ^ x_g) psi_(j ^ x_g).  kRealD: every D_g is real.
+template <typename Real, int R, bool kRealD>
+__device__ double apply_h_table(const Observable &o, const typename CT<Real>::T *dtab,
+                                const typename CT<Real>::T *psi, typename CT<Real>::T *lam,
+                                int tid, int sh, int w, int dim) {
+    using C = typename CT<Real>::T;
+    constexpr int NA = 1 << R;
+    uint32_t v[R];
+    const uint32_t s0 = natural_vectors<R>(tid, sh, w, v);
+    C acc[NA];
+#pragma unroll
+    for (int k = 0; k < NA; ++k) acc[k] = cmk<C>(0, 0);
+    for (int g = 0; g < o.n_tgroups; ++g) {
+        const TermGroup tg = o.tgroups[g];
+        const C *D = dtab + (size_t)g * dim;
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+            const uint32_t jx = ((uint32_t)tid | ((uint32_t)k << sh)) ^ tg.x;
+            const C d = __ldg(D + jx);
+            const C px = psi[s0 ^ xsel<R>(k, v) ^ tg.sx];
+            if constexpr (kRealD) {
+                acc[k].x = fmaR(d.x, px.x, acc[k].x);
+                acc[k].y = fmaR(d.x, px.y, acc[k].y);
+            } else {
+                acc[k].x = fmaR(d.x, px.x, fmaR(-d.y, px.y, acc[k].x));
+                acc[k].y = fmaR(d.x, px.y, fmaR(d.y, px.x, acc[k].y));
+            }
+        }
+    }
+    double e = 0.0;
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+        const uint32_t sj = s0 ^ xsel<R>(k, v);
+        const C pj = psi[sj];
+        lam[sj] = acc[k];
+        e += (double)fmaR(pj.x, acc[k].x, pj.y * acc[k].y);
+    }
+    return e;
+}
+
 // Parameter-shift combination by one block: dL/dtheta_k = sum_i L'_i
 // (E_{k+,i} - E_{k-,i}) / 2, the energies and the cost.  `red`: 32 doubles.
 __device__ void ps_combine_block(const double *E, int I, int P, const CostSource &c, double *lp,

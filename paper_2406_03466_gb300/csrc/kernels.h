@@ -95,10 +95,12 @@ cudaError_t launch_onchip_store(int c128, const OnchipShape &sh, const Program &
 cudaError_t launch_onchip_expect(int c128, const OnchipShape &sh, int n, int swz_bits,
                                  const Observable &o, const void *states, int n_rows,
                                  double *out, cudaStream_t st);
+// dtab: the observable's diagonal tables (launch_build_dtable) in device
+// memory, or null (lambda = H psi then sums each group's terms per amplitude).
 cudaError_t launch_onchip_adjoint(int c128, const OnchipShape &sh, const Program &p,
                                   const Observable &o, const SlotSource &s, const CostSource &c,
                                   double *slot_grads, double *slot_energies, cudaStream_t st,
-                                  const BlockConst *bc = nullptr);
+                                  const BlockConst *bc = nullptr, const void *dtab = nullptr);
 
 cudaError_t launch_ps_combine(const double *E, int I, int P, const CostSource &c,
                               double *lprime_scratch, double *energy_out, double *loss_out,

@@ -114,7 +114,8 @@ template <typename Real, int R, int kMode>
 __global__ void __launch_bounds__(512) k_adjoint(Program p, Observable o, SlotSource src,
                                                  CostSource cs, OnchipShape sh,
                                                  double *slot_grads, double *slot_E,
-                                                 BlockConst bc) {
+                                                 BlockConst bc,
+                                                 const typename CT<Real>::T *dtab) {
     using C = typename CT<Real>::T;
     constexpr int NA = 1 << R;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -139,7 +140,10 @@ __global__ void __launch_bounds__(512) k_adjoint(Program p, Observable o, SlotSo
     for (int q = tid; q < P; q += Ts) grad[q] = 0.0;
     __syncthreads();
     forward_stages<Real, R, kMode>(p, psi, mats, tid, si.ref);
-    double e = apply_h<Real, R>(o, psi, lam, tid, shb, p.swz_bits);
+    double e = !dtab ? apply_h<Real, R>(o, psi, lam, tid, shb, p.swz_bits)
+                     : (o.real ? apply_h_table<Real, R, true>(o, dtab, psi, lam, tid, shb, p.swz_bits, 1 << n)
+                               : apply_h_table<Real, R, false>(o, dtab, psi, lam, tid, shb, p.swz_bits,
+                                                               1 << n));
     e = slot_sum(e, Ts, red);
     __syncthreads();
 
@@ -475,25 +479,28 @@ cudaError_t launch_onchip_expect(int c128, const OnchipShape &sh, int n, int swz
 template <typename Real, int R>
 static cudaError_t run_adjoint(const OnchipShape &sh, const Program &p, const Observable &o,
                                const SlotSource &s, const CostSource &c, double *G, double *E,
-                               const BlockConst &b, cudaStream_t st) {
+                               const BlockConst &b, cudaStream_t st, const void *dtab) {
     auto k = !b.bytes ? k_adjoint<Real, R, 0> : (b.n16[7] ? k_adjoint<Real, R, 2>
                                                          : k_adjoint<Real, R, 1>);
     cudaError_t e = prep(k, sh.smem);
     if (e != cudaSuccess) return e;
-    k<<<sh.blocks, sh.S * sh.Ts, sh.smem, st>>>(p, o, s, c, sh, G, E, b);
+    k<<<sh.blocks, sh.S * sh.Ts, sh.smem, st>>>(
+        p, o, s, c, sh, G, E, b, reinterpret_cast<const typename CT<Real>::T *>(dtab));
     return cudaGetLastError();
 }
 
 cudaError_t launch_onchip_adjoint(int c128, const OnchipShape &sh, const Program &p,
                                   const Observable &o, const SlotSource &s, const CostSource &c,
-                                  double *G, double *E, cudaStream_t st, const BlockConst *bc) {
+                                  double *G, double *E, cudaStream_t st, const BlockConst *bc,
+                                  const void *dtab) {
     if (sh.blocks == 0) return cudaSuccess;
     BlockConst b = fit_const(sh, bc);
     b.n16[6] = 0;
     if (c128) {
-        SVK_DISPATCH_R_C128(sh.R, return (run_adjoint<double, RR>(sh, p, o, s, c, G, E, b, st)));
+        SVK_DISPATCH_R_C128(sh.R,
+                            return (run_adjoint<double, RR>(sh, p, o, s, c, G, E, b, st, dtab)));
     }
-    SVK_DISPATCH_R(sh.R, return (run_adjoint<float, RR>(sh, p, o, s, c, G, E, b, st)));
+    SVK_DISPATCH_R(sh.R, return (run_adjoint<float, RR>(sh, p, o, s, c, G, E, b, st, dtab)));
     return cudaSuccess;
 }
 
