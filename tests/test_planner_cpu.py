@@ -303,3 +303,28 @@ def test_pass_counts_at_scale():
     stages, ops, groups, members, passes = export_passes(circ, 12, 4, 4, True, 4)
     assert 10 <= len(passes) <= 40
     assert sum(p.n_u1 for p in passes) == len(groups)
+
+
+@pytest.mark.parametrize("name,R", [("mcvqe8", 3), ("mcvqe8", 2), ("qcl8", 3), ("rand8", 2)])
+def test_straight_line_stage_flag(name, R):
+    """The planner marks a stage sorted = 2 (the kernels' straight-line path)
+    exactly when every register bit carries one fused group and all of them
+    are real; other sorted stages stay 1."""
+    w = {"mcvqe8": lambda: wl.mcvqe(8, 4, "all"), "qcl8": lambda: wl.qcl(8, 3, 2),
+         "rand8": lambda: wl.random_workload(8, 60, 4, 2, seed=3, with_encoding=True)}[name]()
+    d = 0 if w.inputs is None else 1
+    circ = sv.Circuit(w.n_qubits, w.gates, w.n_params, d)
+    stages, ops, groups, members = export_plan(circ, R, True, 4)
+    flagged = 0
+    for st in stages:
+        if not st.sorted:
+            continue
+        counts = [st.bit_begin[i + 1] - st.bit_begin[i] for i in range(R)]
+        one_real = all(c == 1 for c in counts) and all(
+            groups[ops[st.op_begin + st.bit_begin[i]].group].real for i in range(R))
+        assert st.sorted == (2 if one_real else 1)
+        flagged += st.sorted == 2
+    if name == "mcvqe8":
+        assert flagged > 0  # single Ry groups on every register bit
+    if name == "qcl8":
+        assert flagged == 0  # Rx Rz Rx groups are complex
