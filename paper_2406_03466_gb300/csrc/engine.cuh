@@ -804,6 +804,39 @@ __device__ void group_gradients(const Program &p, int g, const double *rho8, con
     }
 }
 
+// Stores the sums of the 8 values x over the slot's `width` lanes (a power
+// of two) to dst[0..8).  From 8 lanes up: a reduce-scatter over lane bits
+// 0-2 (the kept half follows the lane bit; afterwards x[0] holds value
+// lane & 7), then butterfly adds over the remaining lane bits, and lanes
+// 0..7 store one value each: 8 + log2(width / 8) shuffles instead of
+// 8 log2(width).  Below 8 lanes, plain butterflies and lane 0 stores.
+template <typename Real>
+__device__ __forceinline__ void store_rho8(Real (&x)[8], int tid, int width, Real *dst) {
+    constexpr unsigned full = 0xffffffffu;
+    const int lane = tid & 31;
+    if (width >= 8) {
+#pragma unroll
+        for (int j = 0, M = 8; j < 3; ++j, M >>= 1) {
+            const bool b = (lane >> j) & 1;
+#pragma unroll
+            for (int m = 0; m < M / 2; ++m) {
+                const Real keep = b ? x[2 * m + 1] : x[2 * m], give = b ? x[2 * m] : x[2 * m + 1];
+                x[m] = keep + __shfl_xor_sync(full, give, 1 << j);
+            }
+        }
+        for (int off = 8; off < width; off <<= 1) x[0] += __shfl_xor_sync(full, x[0], off);
+        if ((lane & (width - 1)) < 8) dst[lane & 7] = x[0];
+    } else {
+#pragma unroll
+        for (int v = 0; v < 8; ++v)
+            for (int off = width >> 1; off > 0; off >>= 1) x[v] += __shfl_xor_sync(full, x[v], off);
+        if ((lane & (width - 1)) == 0) {
+#pragma unroll
+            for (int v = 0; v < 8; ++v) dst[v] = x[v];
+        }
+    }
+}
+
 // Reverse of bit_ops_fwd for bits I, I-1, ..., 0: per op, the partial reduced
 // matrix of bit I (reduced over the warp, written to rw[group][warp]) then
 // the inverse gate on psi and lambda.
@@ -819,15 +852,7 @@ __device__ __forceinline__ void bit_ops_rev(const Program &p, const Stage *sg, c
             if (grp.has_param) {
                 Real rh[8] = {0, 0, 0, 0, 0, 0, 0, 0};
                 rho_bit<C, Real, R, I>(a, al, rh);
-#pragma unroll
-                for (int v = 0; v < 8; ++v)
-                    for (int off = width >> 1; off > 0; off >>= 1)
-                        rh[v] += __shfl_xor_sync(0xffffffffu, rh[v], off);
-                if ((tid & 31) == 0) {
-                    Real *dst = rw + (op.group * wps + (tid >> 5)) * 8;
-#pragma unroll
-                    for (int v = 0; v < 8; ++v) dst[v] = rh[v];
-                }
+                store_rho8<Real>(rh, tid, width, rw + (op.group * wps + (tid >> 5)) * 8);
             }
             const C *m = mats + 4 * op.group;
             if (grp.real) {
@@ -886,15 +911,7 @@ __device__ void reverse_stages(const Program &p, typename CT<Real>::T *psi,
                 if (p.groups[op.group].has_param) {
                     Real rh[8] = {0, 0, 0, 0, 0, 0, 0, 0};
                     rho_reg<C, Real, R>(a, al, op.a, rh);
-#pragma unroll
-                    for (int v = 0; v < 8; ++v)
-                        for (int off = width >> 1; off > 0; off >>= 1)
-                            rh[v] += __shfl_xor_sync(0xffffffffu, rh[v], off);
-                    if ((tid & 31) == 0) {
-                        Real *dst = rw + (op.group * wps + (tid >> 5)) * 8;
-#pragma unroll
-                        for (int v = 0; v < 8; ++v) dst[v] = rh[v];
-                    }
+                    store_rho8<Real>(rh, tid, width, rw + (op.group * wps + (tid >> 5)) * 8);
                 }
                 const C *m = mats + 4 * op.group;
                 const C d0 = cconj(m[0]), d1 = cconj(m[2]), d2 = cconj(m[1]), d3 = cconj(m[3]);
